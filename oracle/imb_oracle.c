@@ -1,0 +1,705 @@
+/*
+ * imb_oracle.c -- plain, slow FP64 CPU oracle of one coupled LBM-DEM step with
+ * the Noble-Torczynski immersed moving boundary, after Yang, Jing, Kwok &
+ * Sobral, "A comprehensive study of coupled LBM-DEM with immersed moving
+ * boundary" (arXiv 1809.07008).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline and reference legs may load it.  It shares no code with the
+ * CUDA library.  Compile with -ffp-contract=off: the two places where floating
+ * point decides an integer (cell coverage, contact detection) must round every
+ * operation separately, as the CUDA kernels do.
+ *
+ * One step, in the order of the paper's coupling cycle (Sec. 2.4, Fig. 4):
+ *   1. DEM: N_sub sub-cycles with dt = 1/N_sub (Eq. 17), the hydrodynamic
+ *      force and torque of the previous collision held fixed (Sec. 2.4);
+ *      contacts by Eqs. 7-9 (linear spring-dashpot), motion by Eqs. 10-11
+ *      integrated with the leapfrog form of Verlet's method.
+ *   2. Map particles onto the lattice: per cell the covering particles and
+ *      their solid ratios (Sec. 2.3, Fig. 3).
+ *   3. Collide every node: BGK (Eq. 1 RHS, Eq. 2) with a Smagorinsky effective
+ *      relaxation time (Sec. 3.3), blended with the solid operator of Eq. 12
+ *      by the weight of Eq. 14 (Eq. 13); hydrodynamic force and torque by
+ *      Eqs. 15-16 (force on the particle = minus the fluid's momentum gain).
+ *   4. Stream (Eq. 1 LHS) with periodic, halfway bounce-back and
+ *      inlet/outlet boundaries.
+ *
+ * Readings of points the paper leaves open are listed in the design doc; the ones
+ * that change arithmetic are repeated at the code that applies them.
+ */
+#include "imb_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* D2Q9 velocities, opposites and weights (Qian et al. 1992, cited in Sec. 2). */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+struct orc_sim {
+    orc_params p;
+    double *f;    /* f(x,t): post-stream, pre-collision  [9][ny][nx] */
+    double *fs;   /* post-collision scratch                [9][ny][nx] */
+    int np;
+    double *px, *py, *vx, *vy, *w, *r, *m, *I;
+    double *Ffx, *Ffy, *Tf;        /* hydrodynamic force/torque (Eqs. 15-16) */
+    double *xi;                    /* tangential spring per pair, [np][np], a < b */
+    double *xiw;                   /* tangential spring per particle-wall, [np][4] */
+    int *cnt, *ids;                /* per cell: covering particles (ascending id) */
+    double *eps;                   /* per cell and slot: solid ratio of that particle */
+    double zeta;                   /* damping ratio from the restitution coefficient */
+    double gx_eff, gy_eff;         /* buoyancy-reduced gravity */
+};
+
+#define IDX(s, q, k, i) (((size_t)(q) * (s)->p.ny + (size_t)(k)) * (s)->p.nx + (size_t)(i))
+
+/* ---------------------------------------------------------------- Eq. 2 */
+void orc_feq(double rho, double ux, double uy, double *feq)
+{
+    double usq = ux * ux + uy * uy;
+    for (int q = 0; q < 9; ++q) {
+        double cu = CX[q] * ux + CY[q] * uy;
+        /* c.u/cs^2 + (c.u)^2/(2 cs^4) - u^2/(2 cs^2) with cs^2 = 1/3 */
+        feq[q] = W[q] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    }
+}
+
+/* ---------------------------------------------------------------- Eq. 14 */
+double orc_B(double eps, double tau)
+{
+    double t = tau - 0.5;
+    return eps * t / ((1.0 - eps) + t);
+}
+
+/* Moments (Eqs. 3-4, the garbled "u_i" of Eq. 4 read as c_i) with the
+ * half-force velocity shift of Guo forcing. */
+static void moments(const double *f9, double Fx, double Fy, double *rho, double *ux, double *uy)
+{
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    for (int q = 0; q < 9; ++q) {
+        r += f9[q];
+        jx += CX[q] * f9[q];
+        jy += CY[q] * f9[q];
+    }
+    *rho = r;
+    *ux = (jx + 0.5 * Fx) / r;
+    *uy = (jy + 0.5 * Fy) / r;
+}
+
+/* Smagorinsky effective relaxation time (Sec. 3.3; the paper names the model
+ * but not its formula -- this is the closure of Hou et al. 1996 it cites):
+ * Pi = sum_i c_i c_i (f_i - f_i^eq), Q = Pi:Pi,
+ * tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 sqrt(Q) / rho)) / 2. */
+double orc_tau_eff(const double *f9, double Fx, double Fy, double tau, double C_smag)
+{
+    if (C_smag <= 0.0)
+        return tau;
+    double rho, ux, uy, fe[9];
+    moments(f9, Fx, Fy, &rho, &ux, &uy);
+    orc_feq(rho, ux, uy, fe);
+    double pxx = 0.0, pyy = 0.0, pxy = 0.0;
+    for (int q = 0; q < 9; ++q) {
+        double ne = f9[q] - fe[q];
+        pxx += CX[q] * CX[q] * ne;
+        pyy += CY[q] * CY[q] * ne;
+        pxy += CX[q] * CY[q] * ne;
+    }
+    double Q = pxx * pxx + pyy * pyy + 2.0 * pxy * pxy;
+    return 0.5 * (tau + sqrt(tau * tau + 18.0 * sqrt(2.0) * C_smag * C_smag * sqrt(Q) / rho));
+}
+
+/* ------------------------------------------------ solid ratio (Sec. 2.3) */
+/* int_0^x sqrt(r^2 - t^2) dt for |x| <= r. */
+static double half_chord_prim(double x, double r)
+{
+    double h = sqrt(fmax(0.0, r * r - x * x));
+    double s = x / r;
+    if (s > 1.0) s = 1.0;
+    if (s < -1.0) s = -1.0;
+    return 0.5 * (x * h + r * r * asin(s));
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Exact area of the disk X^2 + Y^2 <= r^2 inside the rectangle [a0,a1]x[b0,b1]
+ * (coordinates relative to the disk centre): the integral over X of the length
+ * of [b0,b1] cut by the chord [-h(X), h(X)], h = sqrt(r^2 - X^2), taken piece by
+ * piece between the points where h meets |b0| or |b1|. */
+double orc_cell_area(double a0, double a1, double b0, double b1, double r)
+{
+    double A = fmax(a0, -r), B = fmin(a1, r);
+    if (!(A < B))
+        return 0.0;
+    double bp[6];
+    int nb = 0;
+    bp[nb++] = A;
+    bp[nb++] = B;
+    const double lev[2] = {b0, b1};
+    for (int k = 0; k < 2; ++k) {
+        double c = fabs(lev[k]);
+        if (c < r) {
+            double s = sqrt(r * r - c * c);
+            if (s > A && s < B) bp[nb++] = s;
+            if (-s > A && -s < B) bp[nb++] = -s;
+        }
+    }
+    qsort(bp, (size_t)nb, sizeof(double), cmp_double);
+    double area = 0.0;
+    for (int k = 0; k + 1 < nb; ++k) {
+        double p = bp[k], q = bp[k + 1];
+        if (!(q > p))
+            continue;
+        double xm = 0.5 * (p + q);
+        double hm = sqrt(fmax(0.0, r * r - xm * xm));
+        int upper_is_arc = hm < b1;     /* top of the chord inside the strip */
+        int lower_is_arc = -hm > b0;    /* bottom of the chord inside the strip */
+        double top = upper_is_arc ? hm : b1;
+        double bot = lower_is_arc ? -hm : b0;
+        if (!(top > bot))
+            continue;
+        double hint = half_chord_prim(q, r) - half_chord_prim(p, r);
+        double up = upper_is_arc ? hint : b1 * (q - p);
+        double lo = lower_is_arc ? -hint : b0 * (q - p);
+        area += up - lo;
+    }
+    return area;
+}
+
+/* Cell decomposition of Sec. 2.3 (Fig. 3b) in 2D: n x n sub-cells, a sub-cell
+ * counts as solid when its centre lies in the disk (a tie counts as inside).
+ * Decided in single precision, operation for operation as the kernel does. */
+double orc_eps_subcell(float lox, float loy, float r, int n)
+{
+    float r2 = r * r;
+    int inside = 0;
+    for (int ky = 0; ky < n; ++ky) {
+        float ty = ((float)ky + 0.5f) / (float)n;
+        float py = loy + ty;
+        for (int kx = 0; kx < n; ++kx) {
+            float tx = ((float)kx + 0.5f) / (float)n;
+            float px = lox + tx;
+            float d2 = px * px + py * py;
+            if (d2 <= r2)
+                inside++;
+        }
+    }
+    return (double)inside / (double)(n * n);
+}
+
+/* Does the disk of radius r reach into the open unit cell whose lower-left
+ * corner is (lox, loy) relative to the disk centre?  Nearest point of the cell
+ * to the centre, strictly inside the circle.  Single precision, every
+ * operation rounded separately. */
+int orc_covers(float lox, float loy, float r)
+{
+    float hix = lox + 1.0f, hiy = loy + 1.0f;
+    float dx = lox > 0.0f ? lox : (hix < 0.0f ? hix : 0.0f);
+    float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
+    float d2 = dx * dx + dy * dy;
+    return d2 < r * r;
+}
+
+/* Solid collision operator, Eq. 12:
+ * Omega^s_i = f_{-i} - f^eq_{-i}(rho, u_f) + f^eq_i(rho, u_s) - f_i. */
+void orc_omega_s(const double *f9, double rho, double ux, double uy, double usx, double usy,
+                 double *om)
+{
+    double fe[9], fes[9];
+    orc_feq(rho, ux, uy, fe);
+    orc_feq(rho, usx, usy, fes);
+    for (int q = 0; q < 9; ++q)
+        om[q] = f9[OPP[q]] - fe[OPP[q]] + fes[q] - f9[q];
+}
+
+/* --------------------------------------------------------- simulation */
+static void stream(orc_sim *s)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < nx; ++i)
+            for (int q = 0; q < 9; ++q) {
+                double v = s->fs[IDX(s, q, k, i)];
+                int xn = i + CX[q], yn = k + CY[q];
+                if (yn < 0 || yn >= ny) {
+                    if (s->p.bc_y == ORC_PERIODIC) {
+                        yn = (yn + ny) % ny;
+                    } else { /* halfway bounce-back at y = 0 and y = ny */
+                        s->f[IDX(s, OPP[q], k, i)] = v;
+                        continue;
+                    }
+                }
+                if (xn < 0 || xn >= nx) {
+                    if (s->p.bc_x == ORC_PERIODIC) {
+                        xn = (xn + nx) % nx;
+                    } else if (s->p.bc_x == ORC_WALL) {
+                        s->f[IDX(s, OPP[q], k, i)] = v;
+                        continue;
+                    } else {
+                        continue; /* leaves through inlet/outlet; columns rebuilt below */
+                    }
+                }
+                s->f[IDX(s, q, yn, xn)] = v;
+            }
+    if (s->p.bc_x == ORC_INLET_OUTLET) {
+        /* inlet column x = 0: equilibrium at the prescribed velocity with the
+         * density of the first interior column; outlet column x = nx-1: copy of
+         * column nx-2 (zero gradient) */
+        for (int k = 0; k < ny; ++k) {
+            double rho1 = 0.0, fe[9];
+            for (int q = 0; q < 9; ++q)
+                rho1 += s->f[IDX(s, q, k, 1)];
+            orc_feq(rho1, s->p.u_in_x, s->p.u_in_y, fe);
+            for (int q = 0; q < 9; ++q) {
+                s->f[IDX(s, q, k, 0)] = fe[q];
+                s->f[IDX(s, q, k, nx - 1)] = s->f[IDX(s, q, k, nx - 2)];
+            }
+        }
+    }
+}
+
+orc_sim *orc_new(const orc_params *p)
+{
+    if (p->nx < 3 || p->ny < 3 || !(p->tau > 0.5) || p->C_smag < 0.0)
+        return NULL;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    s->p = *p;
+    size_t n = (size_t)9 * p->nx * p->ny;
+    s->f = (double *)calloc(n, sizeof(double));
+    s->fs = (double *)calloc(n, sizeof(double));
+    s->cnt = (int *)calloc((size_t)p->nx * p->ny, sizeof(int));
+    s->ids = (int *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS, sizeof(int));
+    s->eps = (double *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS, sizeof(double));
+    double le = log(p->e_rest > 0.0 ? p->e_rest : 1.0);
+    s->zeta = -le / sqrt(M_PI * M_PI + le * le);
+    s->gx_eff = (1.0 - 1.0 / p->rho_s) * p->gx;
+    s->gy_eff = (1.0 - 1.0 / p->rho_s) * p->gy;
+    /* initial condition: the post-collision field is f^eq(rho0, u0); streaming
+     * it once (with the boundary rules) gives f(x, 0) */
+    double fe[9];
+    orc_feq(p->rho0, p->ux0, p->uy0, fe);
+    for (int q = 0; q < 9; ++q)
+        for (size_t c = 0; c < (size_t)p->nx * p->ny; ++c)
+            s->fs[(size_t)q * p->nx * p->ny + c] = fe[q];
+    stream(s);
+    return s;
+}
+
+static void free_particles(orc_sim *s)
+{
+    free(s->px); free(s->py); free(s->vx); free(s->vy); free(s->w); free(s->r);
+    free(s->m); free(s->I); free(s->Ffx); free(s->Ffy); free(s->Tf); free(s->xi); free(s->xiw);
+    s->px = s->py = s->vx = s->vy = s->w = s->r = s->m = s->I = NULL;
+    s->Ffx = s->Ffy = s->Tf = s->xi = s->xiw = NULL;
+    s->np = 0;
+}
+
+void orc_free(orc_sim *s)
+{
+    if (!s) return;
+    free_particles(s);
+    free(s->f); free(s->fs); free(s->cnt); free(s->ids); free(s->eps);
+    free(s);
+}
+
+int orc_set_particles(orc_sim *s, int n, const double *x, const double *v, const double *w,
+                      const double *r)
+{
+    free_particles(s);
+    s->np = n;
+    if (n == 0) return 0;
+    s->px = malloc(n * sizeof(double)); s->py = malloc(n * sizeof(double));
+    s->vx = malloc(n * sizeof(double)); s->vy = malloc(n * sizeof(double));
+    s->w = malloc(n * sizeof(double)); s->r = malloc(n * sizeof(double));
+    s->m = malloc(n * sizeof(double)); s->I = malloc(n * sizeof(double));
+    s->Ffx = calloc(n, sizeof(double)); s->Ffy = calloc(n, sizeof(double));
+    s->Tf = calloc(n, sizeof(double));
+    s->xi = calloc((size_t)n * n, sizeof(double));
+    s->xiw = calloc((size_t)n * 4, sizeof(double));
+    for (int p = 0; p < n; ++p) {
+        if (!(r[p] > 0.0)) return -1;
+        s->px[p] = x[2 * p]; s->py[p] = x[2 * p + 1];
+        s->vx[p] = v[2 * p]; s->vy[p] = v[2 * p + 1];
+        s->w[p] = w[p]; s->r[p] = r[p];
+        /* disk of unit depth: m = rho_s pi r^2, I = m r^2 / 2 */
+        s->m[p] = s->p.rho_s * M_PI * r[p] * r[p];
+        s->I[p] = 0.5 * s->m[p] * r[p] * r[p];
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- DEM */
+/* Linear spring-dashpot contact between particle a and a partner seen from a
+ * (Eqs. 7-9).  n points from a to the partner, t = z x n.  dvx,dvy is the
+ * partner's translational velocity minus a's; rot = w_a r_a + w_b r_b.
+ * Returns the force on a (fx, fy) and the tangential force magnitude Ft (the
+ * torque on each side is its own radius times Ft). */
+static void contact_law(const orc_sim *s, double nxv, double nyv, double delta, double dvx,
+                        double dvy, double rot, double mstar, double dt, double *xi, double *fx,
+                        double *fy, double *Ft_out)
+{
+    double tx = -nyv, ty = nxv;
+    double vn = dvx * nxv + dvy * nyv;
+    double vt = (dvx * tx + dvy * ty) - rot;
+    double cn = 2.0 * s->zeta * sqrt(mstar * s->p.kn);
+    double ct = s->p.ct_ratio * cn;
+    *xi = *xi + vt * dt;                      /* incremental spring of Eq. 9 */
+    double Fn = s->p.kn * delta - cn * vn;    /* Eq. 8, repulsive when positive */
+    double Ft = s->p.kt * *xi + ct * vt;      /* Eq. 9 */
+    double lim = s->p.mu * fabs(Fn);          /* Coulomb cap */
+    if (fabs(Ft) > lim) {
+        Ft = copysign(lim, Ft);
+        *xi = copysign(lim / s->p.kt, *xi);
+    }
+    *fx = -Fn * nxv + Ft * tx;
+    *fy = -Fn * nyv + Ft * ty;
+    *Ft_out = Ft;
+}
+
+static double min_image(double d, int periodic, int L)
+{
+    if (periodic) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+static void dem_substep(orc_sim *s, double dt, double *Fcx, double *Fcy, double *Tc)
+{
+    const int n = s->np;
+    const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
+    for (int p = 0; p < n; ++p) Fcx[p] = Fcy[p] = Tc[p] = 0.0;
+    /* particle-particle, brute force over all pairs a < b */
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b) {
+            double dx = min_image(s->px[b] - s->px[a], perx, s->p.nx);
+            double dy = min_image(s->py[b] - s->py[a], pery, s->p.ny);
+            double d2 = dx * dx + dy * dy;
+            double R = s->r[a] + s->r[b];
+            double *xi = &s->xi[(size_t)a * n + b];
+            if (!(d2 < R * R)) { /* Eq. 7: no overlap, the spring is released */
+                *xi = 0.0;
+                continue;
+            }
+            double d = sqrt(d2);
+            double nxv = dx / d, nyv = dy / d;
+            double delta = R - d;
+            double mstar = s->m[a] * s->m[b] / (s->m[a] + s->m[b]);
+            double rot = s->w[a] * s->r[a] + s->w[b] * s->r[b];
+            double fx, fy, Ft;
+            contact_law(s, nxv, nyv, delta, s->vx[b] - s->vx[a], s->vy[b] - s->vy[a], rot, mstar,
+                        dt, xi, &fx, &fy, &Ft);
+            Fcx[a] += fx; Fcy[a] += fy; Tc[a] += s->r[a] * Ft;
+            Fcx[b] -= fx; Fcy[b] -= fy; Tc[b] += s->r[b] * Ft;
+        }
+    /* particle-wall: walls on the domain edges, an immovable partner of
+     * infinite mass (m* = m) */
+    for (int p = 0; p < n; ++p)
+        for (int wl = 0; wl < 4; ++wl) {
+            int active = (wl < 2) ? s->p.bc_x == ORC_WALL : s->p.bc_y == ORC_WALL;
+            if (!active) continue;
+            double dist, nxv, nyv;
+            switch (wl) {
+            case 0: dist = s->px[p]; nxv = -1.0; nyv = 0.0; break;
+            case 1: dist = (double)s->p.nx - s->px[p]; nxv = 1.0; nyv = 0.0; break;
+            case 2: dist = s->py[p]; nxv = 0.0; nyv = -1.0; break;
+            default: dist = (double)s->p.ny - s->py[p]; nxv = 0.0; nyv = 1.0; break;
+            }
+            double *xi = &s->xiw[(size_t)p * 4 + wl];
+            if (!(dist < s->r[p])) {
+                *xi = 0.0;
+                continue;
+            }
+            double delta = s->r[p] - dist;
+            double fx, fy, Ft;
+            contact_law(s, nxv, nyv, delta, -s->vx[p], -s->vy[p], s->w[p] * s->r[p], s->m[p], dt,
+                        xi, &fx, &fy, &Ft);
+            Fcx[p] += fx; Fcy[p] += fy; Tc[p] += s->r[p] * Ft;
+        }
+    /* Eqs. 10-11, leapfrog: kick with a(x^n), then drift with v^{n+1/2} */
+    for (int p = 0; p < n; ++p) {
+        double ax = (Fcx[p] + s->Ffx[p]) / s->m[p] + s->gx_eff;
+        double ay = (Fcy[p] + s->Ffy[p]) / s->m[p] + s->gy_eff;
+        double al = (Tc[p] + s->Tf[p]) / s->I[p];
+        s->vx[p] = s->vx[p] + ax * dt;
+        s->vy[p] = s->vy[p] + ay * dt;
+        s->w[p] = s->w[p] + al * dt;
+        s->px[p] = s->px[p] + s->vx[p] * dt;
+        s->py[p] = s->py[p] + s->vy[p] * dt;
+        if (perx) {
+            if (s->px[p] >= s->p.nx) s->px[p] -= s->p.nx;
+            else if (s->px[p] < 0.0) s->px[p] += s->p.nx;
+        }
+        if (pery) {
+            if (s->py[p] >= s->p.ny) s->py[p] -= s->p.ny;
+            else if (s->py[p] < 0.0) s->py[p] += s->p.ny;
+        }
+    }
+}
+
+int orc_dem_substeps(orc_sim *s, int nsub)
+{
+    if (s->np == 0 || nsub <= 0) return 0;
+    double dt = 1.0 / (double)s->p.N_sub;
+    double *Fcx = malloc(s->np * sizeof(double));
+    double *Fcy = malloc(s->np * sizeof(double));
+    double *Tc = malloc(s->np * sizeof(double));
+    for (int k = 0; k < nsub; ++k)
+        dem_substep(s, dt, Fcx, Fcy, Tc);
+    free(Fcx); free(Fcy); free(Tc);
+    return 0;
+}
+
+/* ------------------------------------------------ map particles (Sec. 2.4) */
+/* Particle p seen from cell (i,k): lower-left corner of the cell relative to
+ * the centre in single precision, decided from the integer cell of the centre
+ * and the fractional offset, with the minimum image in periodic directions. */
+static int rel_index(int i, int ci, int periodic, int L)
+{
+    int d = i - ci;
+    if (periodic) {
+        while (d >= L / 2) d -= L;
+        while (d < -(L / 2)) d += L;
+    }
+    return d;
+}
+
+static int map_particles(orc_sim *s)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
+    memset(s->cnt, 0, sizeof(int) * (size_t)nx * ny);
+    int overflow = 0;
+    for (int p = 0; p < s->np; ++p) {
+        double cx = s->px[p], cy = s->py[p], r = s->r[p];
+        int ci = (int)floor(cx), cj = (int)floor(cy);
+        float fx = (float)(cx - ci), fy = (float)(cy - cj);
+        float rf = (float)r;
+        int span = (int)ceil(r) + 2;
+        for (int dk = -span; dk <= span; ++dk)
+            for (int di = -span; di <= span; ++di) {
+                int i = ci + di, k = cj + dk;
+                if (perx) i = ((i % nx) + nx) % nx;
+                else if (i < 0 || i >= nx) continue;
+                if (pery) k = ((k % ny) + ny) % ny;
+                else if (k < 0 || k >= ny) continue;
+                int ri = rel_index(i, ci, perx, nx), rk = rel_index(k, cj, pery, ny);
+                float lox = (float)ri - fx, loy = (float)rk - fy;
+                if (!orc_covers(lox, loy, rf))
+                    continue;
+                double e;
+                if (s->p.eps_mode == ORC_EPS_SUBCELL) {
+                    e = orc_eps_subcell(lox, loy, rf, s->p.n_sub);
+                } else {
+                    double a0 = (double)ri - (cx - ci), b0 = (double)rk - (cy - cj);
+                    e = orc_cell_area(a0, a0 + 1.0, b0, b0 + 1.0, r);
+                }
+                size_t c = (size_t)k * nx + i;
+                int slot = s->cnt[c];
+                /* a cell can be listed for the same particle once only; the
+                 * periodic wrap of a small lattice could revisit it */
+                int dup = 0;
+                for (int t = 0; t < slot; ++t)
+                    if (s->ids[c * ORC_MAX_SLOTS + t] == p) dup = 1;
+                if (dup) continue;
+                if (slot >= ORC_MAX_SLOTS) {
+                    overflow = 1;
+                    continue;
+                }
+                s->ids[c * ORC_MAX_SLOTS + slot] = p;
+                s->eps[c * ORC_MAX_SLOTS + slot] = e;
+                s->cnt[c] = slot + 1;
+            }
+    }
+    return overflow ? -2 : 0;
+}
+
+/* ------------------------------------------------------------ collide */
+static void collide(orc_sim *s)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
+    const double Fx = s->p.Fx, Fy = s->p.Fy;
+    for (int p = 0; p < s->np; ++p) s->Ffx[p] = s->Ffy[p] = s->Tf[p] = 0.0;
+    for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < nx; ++i) {
+            double f[9], fe[9], fo[9];
+            for (int q = 0; q < 9; ++q) f[q] = s->f[IDX(s, q, k, i)];
+            double rho, ux, uy;
+            moments(f, Fx, Fy, &rho, &ux, &uy);
+            orc_feq(rho, ux, uy, fe);
+            double te = orc_tau_eff(f, Fx, Fy, s->p.tau, s->p.C_smag);
+            size_t c = (size_t)k * nx + i;
+            int nc = s->cnt[c];
+            double esum = 0.0;
+            for (int t = 0; t < nc; ++t) esum += s->eps[c * ORC_MAX_SLOTS + t];
+            double B = 0.0;
+            if (nc > 0 && esum > 0.0)
+                B = orc_B(esum < 1.0 ? esum : 1.0, te);   /* Eq. 14 with tau_eff */
+            for (int q = 0; q < 9; ++q) {
+                double omf = -(f[q] - fe[q]) / te;          /* Eq. 1 RHS */
+                double cmu_x = CX[q] - ux, cmu_y = CY[q] - uy;
+                double cu = CX[q] * ux + CY[q] * uy;
+                /* Guo forcing term, switched off inside solids with (1 - B) */
+                double S = (1.0 - 0.5 / te) * W[q] *
+                           (3.0 * (cmu_x * Fx + cmu_y * Fy) + 9.0 * cu * (CX[q] * Fx + CY[q] * Fy));
+                fo[q] = f[q] + (1.0 - B) * (omf + S);       /* Eq. 13, fluid part */
+            }
+            for (int t = 0; t < nc && B > 0.0; ++t) {
+                int p = s->ids[c * ORC_MAX_SLOTS + t];
+                double Bp = B * s->eps[c * ORC_MAX_SLOTS + t] / esum;
+                /* lever arm from the particle centre to the node (Eq. 16) */
+                double dx = min_image((i + 0.5) - s->px[p], perx, nx);
+                double dy = min_image((k + 0.5) - s->py[p], pery, ny);
+                double usx = s->vx[p] - s->w[p] * dy;    /* u_s = v + w z x (x_j - x_s) */
+                double usy = s->vy[p] + s->w[p] * dx;
+                double om[9];
+                orc_omega_s(f, rho, ux, uy, usx, usy, om);
+                double mx = 0.0, my = 0.0;
+                for (int q = 0; q < 9; ++q) {
+                    fo[q] += Bp * om[q];                    /* Eq. 13, solid part */
+                    mx += om[q] * CX[q];
+                    my += om[q] * CY[q];
+                }
+                /* Eq. 15: B sum_i Omega^s_i c_i is the momentum the fluid gains
+                 * in this cell; the particle receives the opposite */
+                double fpx = -Bp * mx, fpy = -Bp * my;
+                s->Ffx[p] += fpx;
+                s->Ffy[p] += fpy;
+                s->Tf[p] += dx * fpy - dy * fpx;            /* Eq. 16 */
+            }
+            for (int q = 0; q < 9; ++q) s->fs[IDX(s, q, k, i)] = fo[q];
+        }
+}
+
+int orc_step(orc_sim *s, int nsteps)
+{
+    for (int t = 0; t < nsteps; ++t) {
+        if (s->p.dem_on && s->np > 0)
+            orc_dem_substeps(s, s->p.N_sub);
+        int rc = map_particles(s);
+        if (rc) return rc;
+        collide(s);
+        stream(s);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------- readback */
+void orc_get_f(const orc_sim *s, double *f)
+{
+    memcpy(f, s->f, sizeof(double) * 9 * (size_t)s->p.nx * s->p.ny);
+}
+
+void orc_set_f(orc_sim *s, const double *f)
+{
+    memcpy(s->f, f, sizeof(double) * 9 * (size_t)s->p.nx * s->p.ny);
+}
+
+void orc_get_macro(const orc_sim *s, double *rho, double *ux, double *uy)
+{
+    for (int k = 0; k < s->p.ny; ++k)
+        for (int i = 0; i < s->p.nx; ++i) {
+            double f[9], r, u, v;
+            for (int q = 0; q < 9; ++q) f[q] = s->f[IDX(s, q, k, i)];
+            moments(f, s->p.Fx, s->p.Fy, &r, &u, &v);
+            size_t c = (size_t)k * s->p.nx + i;
+            rho[c] = r; ux[c] = u; uy[c] = v;
+        }
+}
+
+void orc_get_forces(const orc_sim *s, double *F, double *T)
+{
+    for (int p = 0; p < s->np; ++p) {
+        F[2 * p] = s->Ffx[p]; F[2 * p + 1] = s->Ffy[p]; T[p] = s->Tf[p];
+    }
+}
+
+void orc_set_forces(orc_sim *s, const double *F, const double *T)
+{
+    for (int p = 0; p < s->np; ++p) {
+        s->Ffx[p] = F[2 * p]; s->Ffy[p] = F[2 * p + 1]; s->Tf[p] = T[p];
+    }
+}
+
+void orc_get_particles(const orc_sim *s, double *x, double *v, double *w)
+{
+    for (int p = 0; p < s->np; ++p) {
+        x[2 * p] = s->px[p]; x[2 * p + 1] = s->py[p];
+        v[2 * p] = s->vx[p]; v[2 * p + 1] = s->vy[p];
+        w[p] = s->w[p];
+    }
+}
+
+int orc_cell_map(orc_sim *s, int *count, int *ids, double *eps)
+{
+    int rc = map_particles(s);
+    size_t n = (size_t)s->p.nx * s->p.ny;
+    memcpy(count, s->cnt, n * sizeof(int));
+    for (size_t c = 0; c < n; ++c)
+        for (int t = 0; t < ORC_MAX_SLOTS; ++t) {
+            int valid = t < s->cnt[c];
+            ids[c * ORC_MAX_SLOTS + t] = valid ? s->ids[c * ORC_MAX_SLOTS + t] : -1;
+            eps[c * ORC_MAX_SLOTS + t] = valid ? s->eps[c * ORC_MAX_SLOTS + t] : 0.0;
+        }
+    return rc;
+}
+
+int orc_contacts(const orc_sim *s, int max_pairs, int *pairs)
+{
+    const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
+    int k = 0;
+    for (int a = 0; a < s->np; ++a)
+        for (int b = a + 1; b < s->np; ++b) {
+            double dx = min_image(s->px[b] - s->px[a], perx, s->p.nx);
+            double dy = min_image(s->py[b] - s->py[a], pery, s->p.ny);
+            double d2 = dx * dx + dy * dy;
+            double R = s->r[a] + s->r[b];
+            if (d2 < R * R) {
+                if (k < max_pairs) { pairs[2 * k] = a; pairs[2 * k + 1] = b; }
+                k++;
+            }
+        }
+    return k;
+}
+
+/* Uniform bins of edge `bin` cells over [0,nx) x [0,ny): bin of a particle =
+ * (floor(x/bin), floor(y/bin)); ids listed per bin in ascending order. */
+int orc_bins(const orc_sim *s, int bin, int *bin_start, int *bin_ids)
+{
+    int nbx = (s->p.nx + bin - 1) / bin, nby = (s->p.ny + bin - 1) / bin;
+    int nb = nbx * nby;
+    for (int b = 0; b <= nb; ++b) bin_start[b] = 0;
+    int *which = malloc(sizeof(int) * (s->np > 0 ? s->np : 1));
+    for (int p = 0; p < s->np; ++p) {
+        int bx = (int)floor(s->px[p] / bin), by = (int)floor(s->py[p] / bin);
+        if (bx < 0) bx = 0;
+        if (bx >= nbx) bx = nbx - 1;
+        if (by < 0) by = 0;
+        if (by >= nby) by = nby - 1;
+        which[p] = by * nbx + bx;
+        bin_start[which[p] + 1]++;
+    }
+    for (int b = 0; b < nb; ++b) bin_start[b + 1] += bin_start[b];
+    int *fill = calloc((size_t)nb, sizeof(int));
+    for (int p = 0; p < s->np; ++p) {
+        int b = which[p];
+        bin_ids[bin_start[b] + fill[b]++] = p;
+    }
+    free(fill);
+    free(which);
+    return nb;
+}
+
+double orc_wall_contact_xi(const orc_sim *s, int p, int wall)
+{
+    return s->xiw[(size_t)p * 4 + wall];
+}

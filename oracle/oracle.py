@@ -1,0 +1,256 @@
+"""ctypes wrapper and build step for the FP64 CPU oracle (``imb_oracle.c``).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  It never imports the CUDA package and the CUDA package never imports
+it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "liborc.so")
+SRC = os.path.join(HERE, "imb_oracle.c")
+HDR = os.path.join(HERE, "imb_oracle.h")
+
+PERIODIC, WALL, INLET_OUTLET = 0, 1, 2
+EPS_EXACT, EPS_SUBCELL = 0, 1
+MAX_SLOTS = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library (plain gcc, no GPU code)."""
+    os.makedirs(BUILD, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(HDR))):
+        return LIB
+    tmp = LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int),
+                ("tau", C.c_double), ("C_smag", C.c_double),
+                ("bc_x", C.c_int), ("bc_y", C.c_int),
+                ("u_in_x", C.c_double), ("u_in_y", C.c_double),
+                ("Fx", C.c_double), ("Fy", C.c_double),
+                ("rho0", C.c_double), ("ux0", C.c_double), ("uy0", C.c_double),
+                ("eps_mode", C.c_int), ("n_sub", C.c_int),
+                ("dem_on", C.c_int), ("N_sub", C.c_int),
+                ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
+                ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+        L.orc_B.argtypes = [C.c_double, C.c_double]
+        L.orc_B.restype = C.c_double
+        L.orc_tau_eff.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_tau_eff.restype = C.c_double
+        L.orc_cell_area.argtypes = [C.c_double] * 5
+        L.orc_cell_area.restype = C.c_double
+        L.orc_eps_subcell.argtypes = [C.c_float, C.c_float, C.c_float, C.c_int]
+        L.orc_eps_subcell.restype = C.c_double
+        L.orc_covers.argtypes = [C.c_float, C.c_float, C.c_float]
+        L.orc_covers.restype = C.c_int
+        L.orc_omega_s.argtypes = [_dp] + [C.c_double] * 5 + [_dp]
+        L.orc_new.argtypes = [C.POINTER(Params)]
+        L.orc_new.restype = C.c_void_p
+        L.orc_free.argtypes = [C.c_void_p]
+        L.orc_set_particles.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_get_f.argtypes = [C.c_void_p, _dp]
+        L.orc_set_f.argtypes = [C.c_void_p, _dp]
+        L.orc_get_macro.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.orc_get_forces.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_set_forces.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_get_particles.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.orc_cell_map.argtypes = [C.c_void_p, _ip, _ip, _dp]
+        L.orc_contacts.argtypes = [C.c_void_p, C.c_int, _ip]
+        L.orc_bins.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
+        L.orc_dem_substeps.argtypes = [C.c_void_p, C.c_int]
+        L.orc_wall_contact_xi.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_wall_contact_xi.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def feq(rho, ux, uy):
+    out = np.zeros(9)
+    lib().orc_feq(rho, ux, uy, _d(out))
+    return out
+
+
+def B(eps, tau):
+    return lib().orc_B(eps, tau)
+
+
+def tau_eff(f9, tau, C_smag, force=(0.0, 0.0)):
+    f9 = np.ascontiguousarray(f9, dtype=np.float64)
+    return lib().orc_tau_eff(_d(f9), force[0], force[1], tau, C_smag)
+
+
+def cell_area(a0, a1, b0, b1, r):
+    return lib().orc_cell_area(a0, a1, b0, b1, r)
+
+
+def eps_subcell(lox, loy, r, n):
+    return lib().orc_eps_subcell(lox, loy, r, n)
+
+
+def covers(lox, loy, r):
+    return bool(lib().orc_covers(lox, loy, r))
+
+
+def omega_s(f9, rho, ux, uy, usx, usy):
+    f9 = np.ascontiguousarray(f9, dtype=np.float64)
+    out = np.zeros(9)
+    lib().orc_omega_s(_d(f9), rho, ux, uy, usx, usy, _d(out))
+    return out
+
+
+def params_from_workload(w) -> Params:
+    p = Params()
+    p.nx, p.ny = w.nx, w.ny
+    p.tau, p.C_smag = w.tau, w.C_smag
+    p.bc_x, p.bc_y = w.bc_x, w.bc_y
+    p.u_in_x, p.u_in_y = w.u_in
+    p.Fx, p.Fy = w.force
+    p.rho0 = w.rho0
+    p.ux0, p.uy0 = w.u0
+    p.eps_mode, p.n_sub = w.eps_mode, w.n_sub
+    p.dem_on, p.N_sub = w.dem_on, w.N_sub
+    p.kn, p.kt, p.e_rest, p.ct_ratio = w.kn, w.kt, w.e_rest, w.ct_ratio
+    p.mu, p.rho_s = w.mu, w.rho_s
+    p.gx, p.gy = w.gravity
+    return p
+
+
+class Sim:
+    """One oracle simulation; mirrors the calls of the C-ABI library."""
+
+    def __init__(self, w, particles: bool = True):
+        self.w = w
+        self.p = params_from_workload(w)
+        self.h = lib().orc_new(C.byref(self.p))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+        self.np = 0
+        if particles and w.n_particles:
+            self.set_particles(w.x, w.v, w.omega, w.r)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_free(self.h)
+            self.h = None
+
+    def set_particles(self, x, v, omega, r):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        omega = np.ascontiguousarray(omega, dtype=np.float64).reshape(-1)
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+        rc = lib().orc_set_particles(self.h, r.shape[0], _d(x), _d(v), _d(omega), _d(r))
+        if rc:
+            raise ValueError("oracle rejected the particles")
+        self.np = r.shape[0]
+
+    def step(self, n=1):
+        rc = lib().orc_step(self.h, n)
+        if rc:
+            raise RuntimeError(f"oracle step failed with code {rc}")
+
+    def dem_substeps(self, n):
+        lib().orc_dem_substeps(self.h, n)
+
+    @property
+    def shape(self):
+        return (self.w.ny, self.w.nx)
+
+    def f(self):
+        out = np.zeros((9, self.w.ny, self.w.nx))
+        lib().orc_get_f(self.h, _d(out))
+        return out
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        lib().orc_set_f(self.h, _d(f))
+
+    def macro(self):
+        rho = np.zeros(self.shape)
+        ux = np.zeros(self.shape)
+        uy = np.zeros(self.shape)
+        lib().orc_get_macro(self.h, _d(rho), _d(ux), _d(uy))
+        return rho, ux, uy
+
+    def forces(self):
+        F = np.zeros((self.np, 2))
+        T = np.zeros(self.np)
+        if self.np:
+            lib().orc_get_forces(self.h, _d(F), _d(T))
+        return F, T
+
+    def set_forces(self, F, T):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        lib().orc_set_forces(self.h, _d(F), _d(T))
+
+    def particles(self):
+        x = np.zeros((self.np, 2))
+        v = np.zeros((self.np, 2))
+        w = np.zeros(self.np)
+        if self.np:
+            lib().orc_get_particles(self.h, _d(x), _d(v), _d(w))
+        return x, v, w
+
+    def cell_map(self):
+        count = np.zeros(self.shape, dtype=np.int32)
+        ids = np.zeros(self.shape + (MAX_SLOTS,), dtype=np.int32)
+        eps = np.zeros(self.shape + (MAX_SLOTS,))
+        rc = lib().orc_cell_map(self.h, _i(count), _i(ids), _d(eps))
+        if rc:
+            raise RuntimeError("more than four particles cover one cell")
+        return count, ids, eps
+
+    def contacts(self):
+        n = lib().orc_contacts(self.h, 0, None)
+        pairs = np.zeros((max(n, 1), 2), dtype=np.int32)
+        lib().orc_contacts(self.h, n, _i(pairs))
+        return pairs[:n]
+
+    def bins(self, edge=32):
+        nbx = (self.w.nx + edge - 1) // edge
+        nby = (self.w.ny + edge - 1) // edge
+        start = np.zeros(nbx * nby + 1, dtype=np.int32)
+        ids = np.zeros(max(self.np, 1), dtype=np.int32)
+        lib().orc_bins(self.h, edge, _i(start), _i(ids))
+        return start, ids[:self.np]
+
+    def wall_xi(self, p, wall):
+        return lib().orc_wall_contact_xi(self.h, p, wall)

@@ -1,0 +1,247 @@
+"""Seeded synthetic inputs for the IMB-LBM-DEM workloads.
+
+This module is the only thing the FP64 oracle (``oracle/``) and the CUDA path
+(``paper_1809_07008_gb300``) have in common: it draws particle layouts and
+parameter sets from a counter-free splitmix64 stream and holds none of the
+method's arithmetic (no equilibrium, collision, overlap area or contact law).
+
+Geometry convention shared by both sides (stated here because both receive
+these numbers): lattice cell (i, k) is the unit square [i, i+1) x [k, k+1) and
+its node sits at (i + 1/2, k + 1/2); the domain is [0, nx) x [0, ny); wall
+boundaries lie on the domain edges, half a cell outside the first and last node
+rows (halfway bounce-back).  Particle centres are given in the same frame.
+
+Workloads (lattice units, dx = dt = 1, rho0 = 1):
+  * ``c1``  200 x 100 channel, one fixed disk d = 20 at the centre, velocity
+            inlet u = 0.01, zero-gradient outlet, no-slip walls, tau = 0.6.
+  * ``c2``  2048 x 1024 closed box, 1000 disks d ~ U[16, 24] on a jittered grid
+            in a 640-wide left column (granular collapse), tau = 0.52,
+            Smagorinsky C = 0.1, linear spring-dashpot DEM with gravity.
+  * ``c3``  8192 x 4096, periodic in x, walls in y, 20000 disks d = 20 placed by
+            random sequential addition with a one-cell gap, random velocities of
+            magnitude 0.005, tau = 0.51, Smagorinsky C = 0.1, DEM on, no gravity.
+  * ``c3sub`` the 512 x 512 subdomain of ``c3`` at the same number density.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+# boundary codes (same integers in include/imblbm.h and oracle/imb_oracle.h)
+BC_PERIODIC = 0
+BC_WALL = 1
+BC_INLET_OUTLET = 2
+
+EPS_EXACT = 0
+EPS_SUBCELL = 1
+
+STORE_FP32 = 0
+STORE_FP16 = 1
+STORE_BF16 = 2
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea & Flood 2014): 64-bit state, golden-ratio increment."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        """Uniform double in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def uniform_range(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * self.uniform()
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    tau: float
+    C_smag: float = 0.0
+    bc_x: int = BC_PERIODIC
+    bc_y: int = BC_WALL
+    u_in: tuple = (0.0, 0.0)
+    force: tuple = (0.0, 0.0)          # body force density on the fluid
+    u0: tuple = (0.0, 0.0)             # initial uniform fluid velocity
+    rho0: float = 1.0
+    eps_mode: int = EPS_EXACT
+    n_sub: int = 5
+    dem_on: int = 0
+    N_sub: int = 100
+    kn: float = 1.0e5
+    kt: float = 0.5e5
+    e_rest: float = 0.5
+    ct_ratio: float = 0.5
+    mu: float = 0.5
+    rho_s: float = 2.65
+    gravity: tuple = (0.0, 0.0)
+    steps: int = 1000
+    x: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
+    v: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
+    omega: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    r: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def n_particles(self) -> int:
+        return int(self.r.shape[0])
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+    def solid_fraction(self) -> float:
+        return float(np.sum(math.pi * self.r ** 2) / self.cells)
+
+
+def _particles(x, v, omega, r):
+    return (np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 2)),
+            np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, 2)),
+            np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1)),
+            np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1)))
+
+
+def random_sequential_addition(nx, ny, n, radius_fn, seed, gap=1.0, periodic_x=True,
+                               wall_gap=1.0, region=None, max_attempts=None):
+    """Place ``n`` non-overlapping disks by random sequential addition.
+
+    Each attempt draws a centre uniformly in ``region`` (default: the domain, kept
+    ``r + wall_gap`` away from non-periodic edges) and keeps it when every placed
+    disk is at least ``r_a + r_b + gap`` away (minimum image in periodic x).
+    Radii are drawn per disk by ``radius_fn(rng)`` before its first attempt.
+    """
+    rng = SplitMix64(seed)
+    x0, y0, x1, y1 = region if region is not None else (0.0, 0.0, float(nx), float(ny))
+    cell = 32.0
+    ncx = max(1, int(math.ceil(nx / cell)))
+    ncy = max(1, int(math.ceil(ny / cell)))
+    grid = {}
+    xs, ys, rs = [], [], []
+    attempts = 0
+    limit = max_attempts if max_attempts is not None else 200 * n + 10000
+    while len(rs) < n:
+        r = radius_fn(rng)
+        placed = False
+        while not placed:
+            attempts += 1
+            if attempts > limit:
+                raise RuntimeError(f"random sequential addition stalled at {len(rs)}/{n} disks")
+            if periodic_x and region is None:
+                cx = rng.uniform_range(0.0, float(nx))
+            else:
+                cx = rng.uniform_range(x0 + r + wall_gap, x1 - r - wall_gap)
+            cy = rng.uniform_range(y0 + r + wall_gap, y1 - r - wall_gap)
+            gx, gy = int(cx // cell), int(cy // cell)
+            ok = True
+            for dy in (-1, 0, 1):
+                if not ok:
+                    break
+                for dx in (-1, 0, 1):
+                    kx, ky = gx + dx, gy + dy
+                    if periodic_x:
+                        kx %= ncx
+                    if ky < 0 or ky >= ncy or kx < 0 or kx >= ncx:
+                        continue
+                    for j in grid.get((kx, ky), ()):
+                        ddx = xs[j] - cx
+                        if periodic_x:
+                            if ddx > nx / 2:
+                                ddx -= nx
+                            elif ddx < -nx / 2:
+                                ddx += nx
+                        ddy = ys[j] - cy
+                        if ddx * ddx + ddy * ddy < (rs[j] + r + gap) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+            if ok:
+                grid.setdefault((gx % ncx if periodic_x else gx, gy), []).append(len(rs))
+                xs.append(cx)
+                ys.append(cy)
+                rs.append(r)
+                placed = True
+    return np.stack([np.array(xs), np.array(ys)], axis=1), np.array(rs)
+
+
+def random_directions(n, speed, seed):
+    rng = SplitMix64(seed)
+    v = np.zeros((n, 2))
+    for k in range(n):
+        a = 2.0 * math.pi * rng.uniform()
+        v[k] = (speed * math.cos(a), speed * math.sin(a))
+    return v
+
+
+def c1(steps=2000, d=20.0, nx=200, ny=100, u_in=0.01, tau=0.6) -> Workload:
+    """Fixed disk of diameter ``d`` at the centre of an ``nx`` x ``ny`` channel."""
+    x, v, om, r = _particles([[nx / 2.0, ny / 2.0]], [[0.0, 0.0]], [0.0], [d / 2.0])
+    return Workload(name=f"c1_channel_{nx}x{ny}_disk_d{d:g}", nx=nx, ny=ny, tau=tau,
+                    bc_x=BC_INLET_OUTLET, bc_y=BC_WALL, u_in=(u_in, 0.0), dem_on=0,
+                    steps=steps, x=x, v=v, omega=om, r=r)
+
+
+def c2(steps=20000, n=1000, nx=2048, ny=1024, column=640, seed=1809) -> Workload:
+    """Granular column collapse: ``n`` disks d ~ U[16, 24] on a jittered grid."""
+    rng = SplitMix64(seed)
+    ncol = max(1, int(round(math.sqrt(n * column / ny))))
+    nrow = int(math.ceil(n / ncol))
+    sx, sy = column / ncol, ny / nrow
+    xs, rs = [], []
+    for k in range(n):
+        i, j = k % ncol, k // ncol
+        d = rng.uniform_range(16.0, 24.0)
+        d = min(d, min(sx, sy) - 1.0)
+        ax = max(0.0, (sx - d - 1.0) / 2.0)
+        ay = max(0.0, (sy - d - 1.0) / 2.0)
+        cx = (i + 0.5) * sx + rng.uniform_range(-ax, ax)
+        cy = (j + 0.5) * sy + rng.uniform_range(-ay, ay)
+        xs.append((cx, cy))
+        rs.append(d / 2.0)
+    x, v, om, r = _particles(xs, np.zeros((n, 2)), np.zeros(n), rs)
+    return Workload(name=f"c2_collapse_{nx}x{ny}_{n}disks", nx=nx, ny=ny, tau=0.52, C_smag=0.1,
+                    bc_x=BC_WALL, bc_y=BC_WALL, dem_on=1, gravity=(0.0, -1.0e-5),
+                    steps=steps, x=x, v=v, omega=om, r=r)
+
+
+def c3(steps=20000, n=20000, nx=8192, ny=4096, seed=7008, d=20.0, speed=0.005) -> Workload:
+    """Periodic-x suspension of ``n`` disks of diameter ``d`` with random velocities."""
+    x, r = random_sequential_addition(nx, ny, n, lambda g: d / 2.0, seed, gap=1.0,
+                                      periodic_x=True, wall_gap=1.0)
+    v = random_directions(n, speed, seed ^ 0x5DEECE66D)
+    x, v, om, r = _particles(x, v, np.zeros(n), r)
+    return Workload(name=f"c3_suspension_{nx}x{ny}_{n}disks", nx=nx, ny=ny, tau=0.51, C_smag=0.1,
+                    bc_x=BC_PERIODIC, bc_y=BC_WALL, dem_on=1, gravity=(0.0, 0.0),
+                    steps=steps, x=x, v=v, omega=om, r=r)
+
+
+def c3sub(steps=1000, nx=512, ny=512, seed=7008) -> Workload:
+    """``c3`` at the same disk number density on a smaller lattice."""
+    n = int(round(20000 * nx * ny / (8192 * 4096)))
+    w = c3(steps=steps, n=n, nx=nx, ny=ny, seed=seed)
+    return w.with_(name=f"c3sub_suspension_{nx}x{ny}_{n}disks")
+
+
+def poiseuille(H=32, nx=4, tau=0.6, g=1.0e-6, steps=20000) -> Workload:
+    """Body-force driven channel, periodic in x, walls at y = 0 and y = H, no particles."""
+    return Workload(name=f"poiseuille_H{H}", nx=nx, ny=H, tau=tau, bc_x=BC_PERIODIC, bc_y=BC_WALL,
+                    force=(g, 0.0), steps=steps)
+
+
+WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c3sub": c3sub}
