@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 IMB-LBM-DEM step.
+
+A step is one coupling cycle of the hot path (DEM sub-cycles, particle map,
+fused stream-collide with the immersed boundary and the force/torque
+reduction) over the 8192 x 4096 periodic-x suspension of 20000 disks (d = 20,
+tau = 0.51, Smagorinsky C = 0.1, DEM on) -- the mixed-precision scale-up
+workload on which the metric (MLUPS and HBM roofline fraction against the
+plain FP32 path) is quoted.  Its populations (2 x 1.2 GB in FP32) exceed the
+129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line.  ``value`` = lattice updates per second of whole steps
+(all ranks), device-timed with CUDA events on the library's stream;
+``e2e`` = the same through the C ABI with host buffers (particle kinematics
+uploaded and forces/torques read back every step); ``roofline`` = the
+stream-collide kernel's algorithmic bytes per launch over its event-timed
+duration against the measured HBM copy bandwidth; ``cpu_baseline`` = the FP64
+oracle on a bounded sample, timed on this host.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload c3|c2|c1]
+                  [--storage fp32|fp16|bf16] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "IMB-LBM MLUPS & HBM roofline fraction vs plain FP32 path at stated error"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def make_workload(name):
+    if name == "c1":
+        return W.c1()
+    if name == "c2":
+        return W.c2()
+    return W.c3()
+
+
+# --------------------------------------------------------------- distributed
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _cuda_ok():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.index is not None:
+            cmd += ["-i", str(self.index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        parsed = []
+        for ts, line in self.rows:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                parsed.append((ts, float(f[1]), float(f[2]), f[4:]))
+            except ValueError:
+                continue
+        window = "timed"
+        sel = [p for p in parsed if t0 <= p[0] <= t1 + 0.25]
+        if len(sel) < 2:
+            sel, window = parsed[-8:], "around-timed"
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, _, flags in sel:
+            for name, val in zip(names[1:], flags[1:5]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[1] for s in sel), "sm_max_mhz": max(s[2] for s in sel),
+                "reasons": sorted(reasons), "samples": len(sel), "window": window}
+
+
+def gpu_index_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        items = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(items) and items[local_rank].strip().isdigit():
+            return int(items[local_rank])
+    return local_rank
+
+
+# ----------------------------------------------------------------- baselines
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "of fallback"
+
+
+def committed_traffic(kernel_src_hash, workload, storage):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    entry = t.get(f"{workload}:{storage}")
+    if not entry or entry.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("imb_lbm.cu", "imb_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1809_07008_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def oracle_sample_workload():
+    # bounded sample: the 512 x 512 subdomain of the suspension at the same disk density
+    return W.c3sub(steps=0)
+
+
+def time_oracle(target_s=12.0, max_steps=2000):
+    """FP64 oracle (as it stands, one host thread) on the bounded sample; MLUPS."""
+    from oracle import oracle as O
+    O.build()
+    w = oracle_sample_workload()
+    sim = O.Sim(w)
+    sim.step(2)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s and steps < max_steps:
+        sim.step(5)
+        steps += 5
+    dt = time.perf_counter() - t0
+    mlups = w.cells * steps / dt / 1e6
+    return mlups, {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{w.name}, {steps} steps in {dt:.1f} s, FP64, single host thread"}
+
+
+# ------------------------------------------------------------------- runs
+def run_reference(args):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    mlups, cpu = time_oracle(target_s=max(5.0, min(60.0, 0.05 * (args.steps + args.warmup))))
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "sample": oracle_sample_workload().name},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_1809_07008_gb300 as imb
+    imb.load()
+    w = make_workload(args.workload)
+    lat = imb.Lattice.from_workload(w, storage=args.storage)
+    ts = torch.cuda.Stream()
+    lat.set_stream(ts.cuda_stream)
+    cells = w.cells
+
+    sampler = ClockSampler(gpu_index_for_smi(local))
+    sampler.start()
+    time.sleep(0.3)
+    lat.step(max(args.warmup, 3))
+    lat.enable_kernel_timing(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = lat.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(ts)
+    lat.step_async(args.steps)
+    ev1.record(ts)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    lat.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches = lat.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = lat.kernel_time()
+    lat.enable_kernel_timing(False)
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+    ms_max = max_over_ranks(ms, world)
+    total_cells = sum_over_ranks(float(cells) * args.steps, world)
+    mlups = total_cells / (ms_max * 1e-3) / 1e6
+
+    # roofline of the fused stream-collide kernel (the dominant kernel)
+    bpc = lat.bytes_per_cell()
+    k_avg_s = k_ms / max(k_n, 1) * 1e-3
+    achieved = bpc * cells / k_avg_s / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    traffic = committed_traffic(kernel_source_hash(), w.name, args.storage)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_stream_collide", "bytes_per_cell": bpc,
+                "kernel_ms_avg": round(k_avg_s * 1e3, 4),
+                "kernel_share_of_step": round(k_ms / ms, 4) if ms > 0 else None}
+
+    # end to end through the C ABI with host buffers (kinematics in, forces out, every step)
+    e2e_steps = args.e2e_steps or max(10, min(args.steps, 100))
+    n = lat.np
+    x, v, om = lat.particles()
+    hx = torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    hv = torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+    hw = torch.from_numpy(np.ascontiguousarray(om)).pin_memory().numpy()
+    F = torch.zeros((n, 2), dtype=torch.float64).pin_memory().numpy()
+    T = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        if n:
+            lat.set_kinematics(hx, hv, hw)
+        lat.step(1)
+        if n:
+            lat.forces(F, T)
+            hx[:], hv[:], hw[:] = lat.particles()
+    t1 = time.perf_counter()
+    e2e_s = max_over_ranks(t1 - t0, world)
+    e2e_mlups = sum_over_ranks(float(cells) * e2e_steps, world) / e2e_s / 1e6
+    e2e = {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 40 * n,
+           "d2h_bytes_per_step": 24 * n + 40 * n, "steps": e2e_steps}
+
+    variants = {}
+    if not args.no_variants and args.storage == "fp32" and rank == 0:
+        lat.close()
+        del lat
+        torch.cuda.synchronize()
+        for st in ("fp16", "bf16"):
+            lv = imb.Lattice.from_workload(w, storage=st)
+            lv.set_stream(ts.cuda_stream)
+            lv.step(max(args.warmup, 3))
+            lv.enable_kernel_timing(True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ts)
+            lv.step_async(args.steps)
+            e1.record(ts)
+            torch.cuda.synchronize()
+            lv.sync()
+            vms = e0.elapsed_time(e1)
+            km, kn = lv.kernel_time()
+            kavg = km / max(kn, 1) * 1e-3
+            variants[st] = {"mlups": round(cells * args.steps / (vms * 1e-3) / 1e6, 1),
+                            "kernel_ms_avg": round(kavg * 1e3, 4),
+                            "kernel_gbs": round(lv.bytes_per_cell() * cells / kavg / 1e9, 1),
+                            "bytes_per_cell": lv.bytes_per_cell()}
+            lv.close()
+            del lv
+            torch.cuda.synchronize()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, cpu = time_oracle()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "particles": w.n_particles,
+                           "storage": args.storage, "tau": w.tau, "C_smag": w.C_smag,
+                           "N_sub": w.N_sub if w.dem_on else 0, "dem": bool(w.dem_on),
+                           "l2": "populations larger than L2 (no flush needed)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks}
+        if variants:
+            line["storage_variants"] = variants
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

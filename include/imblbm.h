@@ -1,0 +1,178 @@
+/*
+ * imblbm.h -- C ABI of the GB300 (sm_103a) coupled LBM-DEM step with the
+ * immersed moving boundary of Yang, Jing, Kwok & Sobral, "A comprehensive study
+ * of coupled LBM-DEM with immersed moving boundary" (arXiv 1809.07008).
+ *
+ * One time step, imb_step(ctx, 1), follows the coupling cycle of Sec. 2.4
+ * (Fig. 4):
+ *   1. DEM: N_sub sub-cycles of dt = 1/N_sub (Eq. 17) with the hydrodynamic
+ *      force and torque of the previous step held fixed; linear spring-dashpot
+ *      contacts (Eqs. 7-9), Newton-Euler motion (Eqs. 10-11), leapfrog Verlet;
+ *   2. map the particles on the lattice (Sec. 2.4) -- per-cell solid ratio
+ *      (Sec. 2.3, Fig. 3) from the exact disk/cell overlap or from n_sub x n_sub
+ *      sub-cells;
+ *   3. one fused D2Q9 pull-stream + collide kernel: streaming (Eq. 1 LHS),
+ *      moments (Eqs. 3-4), BGK with a Smagorinsky effective relaxation time
+ *      (Eq. 1 RHS, Eq. 2, Sec. 3.3), the solid operator (Eq. 12) blended by
+ *      B(eps, tau) (Eqs. 13-14), and the per-particle force and torque
+ *      (Eqs. 15-16) reduced in the same pass.
+ *
+ * Lattice units: dx = dt = 1.  Cell (i, k) is [i, i+1) x [k, k+1) with its node
+ * at the centre; the domain is [0, nx) x [0, ny); walls lie on the domain edges
+ * (halfway bounce-back).  D2Q9 direction order: 0:(0,0) 1:(1,0) 2:(0,1)
+ * 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *
+ * Sign convention of Eq. 15: the returned force is the force ON the particle,
+ * minus the momentum the fluid gains through the solid operator.
+ *
+ * Ownership: the library allocates and owns all device memory of a context.
+ * Every array argument below is a HOST pointer owned by the caller, read or
+ * written synchronously before the call returns, unless stated otherwise.
+ * All calls return IMB_OK (0) or a negative IMB_E_* code; imb_last_error()
+ * then holds a message.  No call aborts the process.
+ */
+#ifndef IMBLBM_H
+#define IMBLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IMB_OK 0
+#define IMB_E_INVALID_ARG (-1) /* bad size, tau <= 1/2, C_smag < 0, radius, ... */
+#define IMB_E_CUDA (-2)        /* a CUDA runtime call failed                    */
+#define IMB_E_NOMEM (-3)       /* device allocation failed                      */
+#define IMB_E_UNSTABLE (-4)    /* NaN or |u| >= 0.3 (Mach guard, Sec. 2.1)      */
+#define IMB_E_OVERFLOW (-5)    /* > 4 particles in a cell, tile or list full    */
+#define IMB_E_TIMEOUT (-6)     /* a bounded wait (host or device) ran out       */
+#define IMB_E_SKIN (-7)        /* a particle moved > skin/2 in one coupling cycle */
+#define IMB_E_STATE (-8)       /* call out of order (e.g. no particles set)     */
+
+enum { IMB_BC_PERIODIC = 0, IMB_BC_WALL = 1, IMB_BC_INLET_OUTLET = 2 };
+enum { IMB_STORE_FP32 = 0, IMB_STORE_FP16 = 1, IMB_STORE_BF16 = 2 };
+enum { IMB_EPS_EXACT = 0, IMB_EPS_SUBCELL = 1 };
+
+/* Parameters of a lattice.  imb_default_params() fills every field. */
+typedef struct imb_params {
+    int bc_x;            /* PERIODIC, WALL, or INLET_OUTLET (inlet x = 0, outlet x = nx-1) */
+    int bc_y;            /* PERIODIC or WALL                                                  */
+    double u_in_x, u_in_y; /* inlet velocity for INLET_OUTLET                                  */
+    double Fx, Fy;       /* body force density on the fluid (Guo forcing); 0 = none            */
+    double rho0, ux0, uy0; /* initial field: the post-collision state is f^eq(rho0, u0)        */
+    int storage;         /* IMB_STORE_*: populations stored as f_i - w_i in FP32, FP16 or BF16 */
+    int eps_mode;        /* IMB_EPS_EXACT (disk/cell overlap) or IMB_EPS_SUBCELL (Fig. 3b)    */
+    int n_sub;           /* sub-cells per axis for IMB_EPS_SUBCELL (paper: 5)                 */
+    int dem_on;          /* 1: particles move by DEM; 0: particles are fixed with the given
+                            (v, omega) as the solid velocity of Eq. 12                         */
+    int N_sub;           /* DEM sub-cycles per LBM step (Eq. 17; paper: 100)                  */
+    double kn, kt;       /* normal / tangential spring stiffness (Eqs. 8-9)                    */
+    double e_rest;       /* restitution coefficient, sets c_n = 2 zeta sqrt(m* kn)            */
+    double ct_ratio;     /* c_t = ct_ratio * c_n                                               */
+    double mu;           /* Coulomb friction coefficient (Eq. 9 cap)                           */
+    double rho_s;        /* particle density (fluid density is 1)                              */
+    double gx, gy;       /* gravity; particles feel (1 - 1/rho_s) g (buoyancy-reduced)         */
+    double skin;         /* DEM neighbour-list skin in cells (default 1)                       */
+    int timeout_ms;      /* bound on every host wait (default 60000)                           */
+} imb_params;
+
+typedef struct imb_ctx imb_ctx;
+
+/* Defaults: bc_x = PERIODIC, bc_y = WALL, rho0 = 1, u = 0, FP32 storage, exact eps,
+ * n_sub = 5, dem_on = 0, N_sub = 100, kn = 1e5, kt = kn/2, e = 0.5, ct_ratio = 0.5,
+ * mu = 0.5, rho_s = 2.65, g = 0, skin = 1, timeout 60 s. */
+void imb_default_params(imb_params *p);
+
+/* Create a lattice (Sec. 2.1).  nx, ny >= 3; tau > 1/2 (Eq. 5: nu = (tau - 1/2)/3);
+ * C_smag >= 0 is the Smagorinsky constant (0 = plain BGK).  p may be NULL (defaults).
+ * Allocates two population buffers of 9 planes [q][ny][pitch] on the current device
+ * and initialises them.  *out is set on success. */
+int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, double C_smag,
+                     const imb_params *p);
+
+/* Set the particles (disks of unit depth), copying n centres x[2n], velocities
+ * v[2n], angular velocities omega[n] and radii r[n] (FP64).  Mass rho_s pi r^2,
+ * inertia m r^2 / 2.  Resets contact history and hydrodynamic forces.
+ * IMB_E_INVALID_ARG if r <= 0, r > 31, a centre lies outside a non-periodic
+ * domain, or (dem_on) 2 r_max + skin > 32.  n = 0 removes all particles. */
+int imb_set_particles(imb_ctx *ctx, int n, const double *x, const double *v,
+                      const double *omega, const double *r);
+
+/* Overwrite positions, velocities and angular velocities of the current particles
+ * (same n, radii kept) without touching contact history or forces. */
+int imb_set_kinematics(imb_ctx *ctx, const double *x, const double *v, const double *omega);
+
+/* Advance n coupling cycles (Sec. 2.4).  Kernels are queued on the context stream;
+ * the call waits (bounded by timeout_ms) for them and checks the device error flags. */
+int imb_step(imb_ctx *ctx, int n);
+
+/* Queue n coupling cycles without waiting and without reading the error flags
+ * (imb_sync() does both).  Used for timing. */
+int imb_step_async(imb_ctx *ctx, int n);
+
+/* Run only the DEM part of n coupling cycles (n * N_sub sub-cycles) with the
+ * current hydrodynamic force and torque held fixed. */
+int imb_dem_step(imb_ctx *ctx, int n);
+
+/* Wait (bounded) for queued work and translate the device error flags. */
+int imb_sync(imb_ctx *ctx);
+
+/* Populations f_i(x, t) of Eq. 1 -- after streaming, before the collision of the
+ * next step -- as 9 * nx * ny doubles, layout [q][y][x] (x fastest, no pitch). */
+int imb_get_populations(imb_ctx *ctx, double *f);
+
+/* Macroscopic fields (Eqs. 3-4, 6) from f(x, t): density and velocity (with the
+ * half-force shift of Guo forcing), each nx * ny doubles [y][x]. */
+int imb_get_macro(imb_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* Hydrodynamic force F[2n] and torque T[n] on each particle (Eqs. 15-16) from the
+ * last collision. */
+int imb_get_forces(imb_ctx *ctx, double *F, double *T);
+
+/* Overwrite the hydrodynamic force and torque used by the next DEM sub-cycles. */
+int imb_set_forces(imb_ctx *ctx, const double *F, const double *T);
+
+/* Particle state x[2n], v[2n], omega[n]. */
+int imb_get_particles(imb_ctx *ctx, double *x, double *v, double *omega);
+
+/* Particle-to-lattice map (Sec. 2.4) for the current positions: per cell the
+ * number of covering particles count[ny*nx], their ids ids[ny*nx*4] in ascending
+ * order (-1 in unused slots) and each one's solid ratio eps[ny*nx*4]. */
+int imb_get_cell_map(imb_ctx *ctx, int *count, int *ids, float *eps);
+
+/* Pairs (a < b) of particles in contact (Eq. 7: overlap > 0) at the current
+ * positions, ascending; writes min(max_pairs, total) pairs and *n_pairs = total. */
+int imb_get_contacts(imb_ctx *ctx, int max_pairs, int *pairs, int *n_pairs);
+
+/* Uniform bins of 32 x 32 cells: bin_start[nbins + 1] and bin_ids[n] (ascending
+ * within each bin), nbins = ceil(nx/32) * ceil(ny/32), bin = by * nbx + bx. */
+int imb_get_bins(imb_ctx *ctx, int *bin_start, int *bin_ids);
+
+/* Use an external cudaStream_t (e.g. PyTorch's current stream); NULL restores the
+ * context's own stream.  The caller keeps ownership of the stream. */
+int imb_set_stream(imb_ctx *ctx, void *stream);
+void *imb_get_stream(imb_ctx *ctx);
+
+/* Timing of the fused stream-collide kernel: when enabled, every launch is
+ * bracketed by CUDA events on the context stream; imb_kernel_time returns the
+ * summed milliseconds and launch count since the last reset (waits first). */
+int imb_enable_kernel_timing(imb_ctx *ctx, int on);
+int imb_kernel_time(imb_ctx *ctx, double *ms, long long *launches);
+
+/* Number of kernels this context has launched (all kinds). */
+long long imb_launch_count(imb_ctx *ctx);
+
+/* Algorithmic bytes of one stream-collide cell update for this lattice's storage
+ * (9 loads + 9 stores of one population). */
+double imb_bytes_per_cell(imb_ctx *ctx);
+
+/* Last error message of ctx (or of the last failed imb_init_lattice when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char *imb_last_error(imb_ctx *ctx);
+
+/* Free the context and its device memory.  NULL is accepted. */
+void imb_destroy(imb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMBLBM_H */

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of ``libimblbm.so`` (the C ABI of ``include/imblbm.h``).
+
+Argument marshalling only: every step of the IMB-LBM-DEM path runs in the CUDA
+library.  There is no fallback -- if the library cannot be loaded, or no CUDA
+device is present, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IMB_OK = 0
+ERRORS = {
+    -1: "IMB_E_INVALID_ARG", -2: "IMB_E_CUDA", -3: "IMB_E_NOMEM", -4: "IMB_E_UNSTABLE",
+    -5: "IMB_E_OVERFLOW", -6: "IMB_E_TIMEOUT", -7: "IMB_E_SKIN", -8: "IMB_E_STATE",
+}
+BC_PERIODIC, BC_WALL, BC_INLET_OUTLET = 0, 1, 2
+STORE_FP32, STORE_FP16, STORE_BF16 = 0, 1, 2
+STORAGE_NAMES = {"fp32": STORE_FP32, "fp16": STORE_FP16, "bf16": STORE_BF16}
+EPS_EXACT, EPS_SUBCELL = 0, 1
+MAX_SLOTS = 4
+
+# every symbol include/imblbm.h declares
+EXPORTS = (
+    "imb_default_params", "imb_init_lattice", "imb_set_particles", "imb_set_kinematics",
+    "imb_step", "imb_step_async", "imb_dem_step", "imb_sync", "imb_get_populations",
+    "imb_get_macro", "imb_get_forces", "imb_set_forces", "imb_get_particles",
+    "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
+    "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
+    "imb_last_error", "imb_destroy",
+)
+
+
+class ImbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("bc_x", C.c_int), ("bc_y", C.c_int),
+                ("u_in_x", C.c_double), ("u_in_y", C.c_double),
+                ("Fx", C.c_double), ("Fy", C.c_double),
+                ("rho0", C.c_double), ("ux0", C.c_double), ("uy0", C.c_double),
+                ("storage", C.c_int), ("eps_mode", C.c_int), ("n_sub", C.c_int),
+                ("dem_on", C.c_int), ("N_sub", C.c_int),
+                ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
+                ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double), ("skin", C.c_double),
+                ("timeout_ms", C.c_int)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libimblbm.so not found at {path}; run paper_1809_07008_gb300/build.py")
+    L = C.CDLL(path)
+    L.imb_default_params.argtypes = [C.POINTER(Params)]
+    L.imb_default_params.restype = None
+    L.imb_init_lattice.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_double, C.c_double,
+                                   C.POINTER(Params)]
+    L.imb_set_particles.argtypes = [_vp, C.c_int, _dp, _dp, _dp, _dp]
+    L.imb_set_kinematics.argtypes = [_vp, _dp, _dp, _dp]
+    for name in ("imb_step", "imb_step_async", "imb_dem_step"):
+        getattr(L, name).argtypes = [_vp, C.c_int]
+    L.imb_sync.argtypes = [_vp]
+    L.imb_get_populations.argtypes = [_vp, _dp]
+    L.imb_get_macro.argtypes = [_vp, _dp, _dp, _dp]
+    L.imb_get_forces.argtypes = [_vp, _dp, _dp]
+    L.imb_set_forces.argtypes = [_vp, _dp, _dp]
+    L.imb_get_particles.argtypes = [_vp, _dp, _dp, _dp]
+    L.imb_get_cell_map.argtypes = [_vp, _ip, _ip, _fp]
+    L.imb_get_contacts.argtypes = [_vp, C.c_int, _ip, _ip]
+    L.imb_get_bins.argtypes = [_vp, _ip, _ip]
+    L.imb_set_stream.argtypes = [_vp, _vp]
+    L.imb_get_stream.argtypes = [_vp]
+    L.imb_get_stream.restype = _vp
+    L.imb_enable_kernel_timing.argtypes = [_vp, C.c_int]
+    L.imb_kernel_time.argtypes = [_vp, _dp, C.POINTER(C.c_longlong)]
+    L.imb_launch_count.argtypes = [_vp]
+    L.imb_launch_count.restype = C.c_longlong
+    L.imb_bytes_per_cell.argtypes = [_vp]
+    L.imb_bytes_per_cell.restype = C.c_double
+    L.imb_last_error.argtypes = [_vp]
+    L.imb_last_error.restype = C.c_char_p
+    L.imb_destroy.argtypes = [_vp]
+    L.imb_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.shape[0] != n:
+        raise ValueError(f"expected {n} values, got {a.shape[0]}")
+    return a
+
+
+def default_params() -> Params:
+    p = Params()
+    load().imb_default_params(C.byref(p))
+    return p
+
+
+class Lattice:
+    """One lattice context of the CUDA library (see include/imblbm.h for the semantics)."""
+
+    def __init__(self, nx, ny, tau, C_smag=0.0, params: Params | None = None, **kw):
+        L = load()
+        p = params if params is not None else default_params()
+        for k, v in kw.items():
+            if k == "storage" and isinstance(v, str):
+                v = STORAGE_NAMES[v]
+            setattr(p, k, v)
+        self.params = p
+        self.nx, self.ny = int(nx), int(ny)
+        h = _vp()
+        rc = L.imb_init_lattice(C.byref(h), self.nx, self.ny, float(tau), float(C_smag), C.byref(p))
+        if rc != IMB_OK:
+            raise ImbError(rc, L.imb_last_error(None).decode())
+        self.h = h
+        self.np = 0
+        self._L = L
+
+    @classmethod
+    def from_workload(cls, w, storage="fp32", particles=True, **kw):
+        p = default_params()
+        p.bc_x, p.bc_y = w.bc_x, w.bc_y
+        p.u_in_x, p.u_in_y = w.u_in
+        p.Fx, p.Fy = w.force
+        p.rho0 = w.rho0
+        p.ux0, p.uy0 = w.u0
+        p.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else storage
+        p.eps_mode, p.n_sub = w.eps_mode, w.n_sub
+        p.dem_on, p.N_sub = w.dem_on, w.N_sub
+        p.kn, p.kt, p.e_rest, p.ct_ratio = w.kn, w.kt, w.e_rest, w.ct_ratio
+        p.mu, p.rho_s = w.mu, w.rho_s
+        p.gx, p.gy = w.gravity
+        for k, v in kw.items():
+            setattr(p, k, v)
+        lat = cls(w.nx, w.ny, w.tau, w.C_smag, params=p)
+        if particles and w.n_particles:
+            lat.set_particles(w.x, w.v, w.omega, w.r)
+        return lat
+
+    def _check(self, rc):
+        if rc != IMB_OK:
+            raise ImbError(rc, self._L.imb_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.imb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- state
+    def set_particles(self, x, v, omega, r):
+        r = _f64(r, np.size(r))
+        n = r.shape[0]
+        x, v, omega = _f64(x, 2 * n), _f64(v, 2 * n), _f64(omega, n)
+        self._check(self._L.imb_set_particles(self.h, n, _d(x), _d(v), _d(omega), _d(r)))
+        self.np = n
+
+    def set_kinematics(self, x, v, omega):
+        n = self.np
+        x, v, omega = _f64(x, 2 * n), _f64(v, 2 * n), _f64(omega, n)
+        self._check(self._L.imb_set_kinematics(self.h, _d(x), _d(v), _d(omega)))
+
+    def step(self, n=1):
+        self._check(self._L.imb_step(self.h, int(n)))
+
+    def step_async(self, n=1):
+        self._check(self._L.imb_step_async(self.h, int(n)))
+
+    def sync(self):
+        self._check(self._L.imb_sync(self.h))
+
+    def dem_step(self, n=1):
+        self._check(self._L.imb_dem_step(self.h, int(n)))
+
+    # ------------------------------------------------------------- readback
+    def populations(self):
+        out = np.zeros((9, self.ny, self.nx))
+        self._check(self._L.imb_get_populations(self.h, _d(out)))
+        return out
+
+    def macro(self):
+        rho, ux, uy = (np.zeros((self.ny, self.nx)) for _ in range(3))
+        self._check(self._L.imb_get_macro(self.h, _d(rho), _d(ux), _d(uy)))
+        return rho, ux, uy
+
+    def forces(self, F=None, T=None):
+        F = np.zeros((self.np, 2)) if F is None else F
+        T = np.zeros(self.np) if T is None else T
+        self._check(self._L.imb_get_forces(self.h, _d(F), _d(T)))
+        return F, T
+
+    def set_forces(self, F, T):
+        F, T = _f64(F, 2 * self.np), _f64(T, self.np)
+        self._check(self._L.imb_set_forces(self.h, _d(F), _d(T)))
+
+    def particles(self):
+        x, v, w = np.zeros((self.np, 2)), np.zeros((self.np, 2)), np.zeros(self.np)
+        self._check(self._L.imb_get_particles(self.h, _d(x), _d(v), _d(w)))
+        return x, v, w
+
+    def cell_map(self):
+        count = np.zeros((self.ny, self.nx), dtype=np.int32)
+        ids = np.zeros((self.ny, self.nx, MAX_SLOTS), dtype=np.int32)
+        eps = np.zeros((self.ny, self.nx, MAX_SLOTS), dtype=np.float32)
+        self._check(self._L.imb_get_cell_map(self.h, count.ctypes.data_as(_ip),
+                                             ids.ctypes.data_as(_ip), eps.ctypes.data_as(_fp)))
+        return count, ids, eps
+
+    def contacts(self):
+        n = C.c_int(0)
+        self._check(self._L.imb_get_contacts(self.h, 0, None, C.byref(n)))
+        pairs = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        self._check(self._L.imb_get_contacts(self.h, n.value, pairs.ctypes.data_as(_ip), C.byref(n)))
+        return pairs[:n.value]
+
+    def bins(self):
+        nb = ((self.nx + 31) // 32) * ((self.ny + 31) // 32)
+        start = np.zeros(nb + 1, dtype=np.int32)
+        ids = np.zeros(max(self.np, 1), dtype=np.int32)
+        self._check(self._L.imb_get_bins(self.h, start.ctypes.data_as(_ip), ids.ctypes.data_as(_ip)))
+        return start, ids[:self.np]
+
+    # ----------------------------------------------------------------- misc
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self._L.imb_set_stream(self.h, stream_ptr or None))
+
+    @property
+    def stream(self) -> int:
+        return self._L.imb_get_stream(self.h) or 0
+
+    def enable_kernel_timing(self, on=True):
+        self._check(self._L.imb_enable_kernel_timing(self.h, int(on)))
+
+    def kernel_time(self):
+        ms = C.c_double(0.0)
+        n = C.c_longlong(0)
+        self._check(self._L.imb_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self._L.imb_launch_count(self.h))
+
+    def bytes_per_cell(self) -> float:
+        return float(self._L.imb_bytes_per_cell(self.h))

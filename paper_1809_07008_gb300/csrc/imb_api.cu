@@ -1,0 +1,655 @@
+// imb_api.cu -- host runtime of the GB300 IMB-LBM-DEM library: the C ABI declared
+// in include/imblbm.h.  Owns device memory, the stream, the per-step launch
+// sequence of the coupling cycle (Sec. 2.4, Fig. 4), bounded waits and the
+// translation of device error bits.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/imblbm.h"
+#include "imb_device.cuh"
+#include "imb_kernels.h"
+
+using namespace imb;
+
+struct imb_ctx {
+    int nx = 0, ny = 0, pitch = 0;
+    double tau = 0.0, C_smag = 0.0;
+    imb_params p{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    void *fbuf[2] = {nullptr, nullptr};
+    int cur = 0;               // buffer holding the latest post-collision populations
+    size_t plane = 0, elem = 4;
+    // particles
+    int np = 0, cap = 0;
+    double r_max = 0.0;
+    double *x = nullptr, *v = nullptr, *w = nullptr, *r = nullptr, *m = nullptr, *I = nullptr;
+    double *F = nullptr, *T = nullptr, *x1 = nullptr, *v1 = nullptr, *w1 = nullptr, *xs = nullptr;
+    int *nbr_cnt[2] = {nullptr, nullptr}, *nbr_id[2] = {nullptr, nullptr};
+    double *nbr_xi[2] = {nullptr, nullptr};
+    int nbr_cur = 0;
+    double *wall_xi = nullptr;
+    int *free_ids = nullptr, *coupled_ids = nullptr, *counters = nullptr;
+    int *pbin = nullptr;
+    PRec *prec = nullptr;
+    // bins
+    int nbx = 0, nby = 0, nbins = 0;
+    int *bin_count = nullptr, *bin_fill = nullptr, *bin_start = nullptr, *bin_ids = nullptr;
+    GridBarrier *barrier = nullptr;
+    unsigned *err = nullptr;
+    // parameters derived on the host
+    double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
+    // timing / accounting
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    long long launches = 0;
+    std::string msg;
+};
+
+static std::string g_init_error;
+
+static int fail(imb_ctx *c, int code, const std::string &m) {
+    if (c) c->msg = m;
+    else g_init_error = m;
+    return code;
+}
+
+static int cuda_fail(imb_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? IMB_E_NOMEM : IMB_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+static void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+extern "C" void imb_default_params(imb_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->bc_x = IMB_BC_PERIODIC;
+    p->bc_y = IMB_BC_WALL;
+    p->rho0 = 1.0;
+    p->storage = IMB_STORE_FP32;
+    p->eps_mode = IMB_EPS_EXACT;
+    p->n_sub = 5;
+    p->dem_on = 0;
+    p->N_sub = 100;
+    p->kn = 1.0e5;
+    p->kt = 0.5e5;
+    p->e_rest = 0.5;
+    p->ct_ratio = 0.5;
+    p->mu = 0.5;
+    p->rho_s = 2.65;
+    p->skin = 1.0;
+    p->timeout_ms = 60000;
+}
+
+static LatticeArgs lattice_args(const imb_ctx *c) {
+    LatticeArgs a;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.pitch = c->pitch;
+    a.bc_x = c->p.bc_x;
+    a.bc_y = c->p.bc_y;
+    a.plane = c->plane;
+    a.tau = (float)c->tau;
+    a.smag_coef = (float)(18.0 * std::sqrt(2.0) * c->C_smag * c->C_smag);
+    a.Fx = (float)c->p.Fx;
+    a.Fy = (float)c->p.Fy;
+    a.u_in_x = (float)c->p.u_in_x;
+    a.u_in_y = (float)c->p.u_in_y;
+    a.eps_mode = c->p.eps_mode;
+    a.n_sub = c->p.n_sub;
+    a.nbx = c->nbx;
+    a.nby = c->nby;
+    a.np = c->np;
+    a.bin_start = c->bin_start;
+    a.bin_ids = c->bin_ids;
+    a.prec = c->prec;
+    a.F = c->F;
+    a.T = c->T;
+    a.err = c->err;
+    return a;
+}
+
+static DemArgs dem_args(imb_ctx *c) {
+    DemArgs d;
+    d.np = c->np;
+    d.nx = c->nx;
+    d.ny = c->ny;
+    d.bc_x = c->p.bc_x;
+    d.bc_y = c->p.bc_y;
+    d.N_sub = c->p.N_sub;
+    d.dt = 1.0 / (double)c->p.N_sub;
+    d.kn = c->p.kn;
+    d.kt = c->p.kt;
+    d.zeta = c->zeta;
+    d.ct_ratio = c->p.ct_ratio;
+    d.mu = c->p.mu;
+    d.gx_eff = c->gx_eff;
+    d.gy_eff = c->gy_eff;
+    d.skin = c->p.skin;
+    d.x = c->x;
+    d.v = c->v;
+    d.w = c->w;
+    d.x1 = c->x1;
+    d.v1 = c->v1;
+    d.w1 = c->w1;
+    d.x_start = c->xs;
+    d.r = c->r;
+    d.m = c->m;
+    d.I = c->I;
+    d.F = c->F;
+    d.T = c->T;
+    d.nbr_cnt_old = c->nbr_cnt[c->nbr_cur ^ 1];
+    d.nbr_cnt = c->nbr_cnt[c->nbr_cur];
+    d.nbr_id_old = c->nbr_id[c->nbr_cur ^ 1];
+    d.nbr_id = c->nbr_id[c->nbr_cur];
+    d.nbr_xi_old = c->nbr_xi[c->nbr_cur ^ 1];
+    d.nbr_xi = c->nbr_xi[c->nbr_cur];
+    d.wall_xi = c->wall_xi;
+    d.free_ids = c->free_ids;
+    d.coupled_ids = c->coupled_ids;
+    d.counters = c->counters;
+    d.bin_start = c->bin_start;
+    d.bin_ids = c->bin_ids;
+    d.pbin = c->pbin;
+    d.nbx = c->nbx;
+    d.nby = c->nby;
+    d.barrier = c->barrier;
+    d.err = c->err;
+    return d;
+}
+
+static void free_particles(imb_ctx *c) {
+    double **dp[] = {&c->x, &c->v, &c->w, &c->r, &c->m, &c->I, &c->F, &c->T,
+                     &c->x1, &c->v1, &c->w1, &c->xs, &c->nbr_xi[0], &c->nbr_xi[1], &c->wall_xi};
+    for (double **q : dp) { dfree(*q); *q = nullptr; }
+    int **ip[] = {&c->nbr_cnt[0], &c->nbr_cnt[1], &c->nbr_id[0], &c->nbr_id[1], &c->free_ids,
+                  &c->coupled_ids, &c->pbin, &c->bin_ids};
+    for (int **q : ip) { dfree(*q); *q = nullptr; }
+    dfree(c->prec);
+    c->prec = nullptr;
+    c->np = c->cap = 0;
+}
+
+extern "C" void imb_destroy(imb_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_particles(c);
+    dfree(c->fbuf[0]);
+    dfree(c->fbuf[1]);
+    dfree(c->bin_count);
+    dfree(c->bin_fill);
+    dfree(c->bin_start);
+    dfree(c->counters);
+    dfree(c->barrier);
+    dfree(c->err);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, double C_smag,
+                                const imb_params *pin) {
+    if (!out) return fail(nullptr, IMB_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    imb_params p;
+    if (pin) p = *pin;
+    else imb_default_params(&p);
+    if (nx < 3 || ny < 3) return fail(nullptr, IMB_E_INVALID_ARG, "nx and ny must be >= 3");
+    if (!(tau > 0.5)) return fail(nullptr, IMB_E_INVALID_ARG, "tau must be > 1/2 (Eq. 5)");
+    if (!(C_smag >= 0.0)) return fail(nullptr, IMB_E_INVALID_ARG, "C_smag must be >= 0");
+    if (p.bc_x < 0 || p.bc_x > 2 || p.bc_y < 0 || p.bc_y > 1)
+        return fail(nullptr, IMB_E_INVALID_ARG, "bad boundary code");
+    if (p.storage < 0 || p.storage > 2) return fail(nullptr, IMB_E_INVALID_ARG, "bad storage");
+    if (p.eps_mode < 0 || p.eps_mode > 1 || p.n_sub < 1 || p.n_sub > 64)
+        return fail(nullptr, IMB_E_INVALID_ARG, "bad solid-ratio mode");
+    if (p.N_sub < 1 || !(p.kn > 0.0) || !(p.kt > 0.0) || !(p.e_rest > 0.0) || !(p.e_rest <= 1.0) ||
+        !(p.rho_s > 0.0) || !(p.mu >= 0.0) || !(p.skin > 0.0))
+        return fail(nullptr, IMB_E_INVALID_ARG, "bad DEM parameters");
+    if (p.timeout_ms <= 0) p.timeout_ms = 60000;
+    if ((long long)nx * ny > (1ll << 31) / 16) return fail(nullptr, IMB_E_INVALID_ARG, "lattice too large");
+
+    imb_ctx *c = new imb_ctx();
+    c->nx = nx;
+    c->ny = ny;
+    c->tau = tau;
+    c->C_smag = C_smag;
+    c->p = p;
+    cudaGetDevice(&c->device);
+    c->pitch = (nx + 31) / 32 * 32;
+    c->plane = (size_t)c->pitch * ny;
+    c->elem = p.storage == IMB_STORE_FP32 ? 4 : 2;
+    c->nbx = (nx + TILE - 1) / TILE;
+    c->nby = (ny + TILE - 1) / TILE;
+    c->nbins = c->nbx * c->nby;
+    const double le = std::log(p.e_rest);
+    c->zeta = -le / std::sqrt(M_PI * M_PI + le * le);
+    c->gx_eff = (1.0 - 1.0 / p.rho_s) * p.gx;
+    c->gy_eff = (1.0 - 1.0 / p.rho_s) * p.gy;
+    auto bail = [&](cudaError_t e, const char *what) {
+        g_init_error = std::string(what) + ": " + cudaGetErrorString(e);
+        imb_destroy(c);
+        return e == cudaErrorMemoryAllocation ? IMB_E_NOMEM : IMB_E_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
+    c->stream = c->own_stream;
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess)
+            return bail(e, "population buffers");
+    if ((e = dalloc(&c->bin_count, c->nbins)) != cudaSuccess || (e = dalloc(&c->bin_fill, c->nbins)) != cudaSuccess ||
+        (e = dalloc(&c->bin_start, c->nbins + 1)) != cudaSuccess || (e = dalloc(&c->counters, 2)) != cudaSuccess ||
+        (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess)
+        return bail(e, "bookkeeping buffers");
+    cudaMemsetAsync(c->bin_count, 0, sizeof(int) * c->nbins, c->stream);
+    cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * c->nbins, c->stream);
+    cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (c->nbins + 1), c->stream);
+    cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream);
+    cudaMemsetAsync(c->barrier, 0, sizeof(GridBarrier), c->stream);
+    cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
+    LatticeArgs a = lattice_args(c);
+    for (int b = 0; b < 2; ++b) {
+        if ((e = launch_init_populations(c->fbuf[b], p.storage, a, (float)p.rho0, (float)p.ux0,
+                                         (float)p.uy0, c->stream)) != cudaSuccess)
+            return bail(e, "init kernel");
+        c->launches++;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e, "init sync");
+    *out = c;
+    return IMB_OK;
+}
+
+// rebuild bins and the lattice particle records for the current positions
+static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
+    if (c->np == 0) return IMB_OK;
+    CK(launch_particle_table(c->x, c->r, x_start, c->np, c->nx, c->ny, c->p.bc_x, c->p.bc_y,
+                             0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
+                             c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
+       "particle table");
+    CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->counters, c->stream),
+       "bin scan");
+    CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
+    c->launches += 3;
+    return IMB_OK;
+}
+
+extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const double *v,
+                                 const double *omega, const double *r) {
+    if (!c) return IMB_E_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!x || !v || !omega || !r)))
+        return fail(c, IMB_E_INVALID_ARG, "bad particle arrays");
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(r[i] > 0.0) || !(r[i] <= 31.0))
+            return fail(c, IMB_E_INVALID_ARG, "radius must be in (0, 31]");
+        if (!(x[2 * i] >= 0.0 && x[2 * i] < c->nx && x[2 * i + 1] >= 0.0 && x[2 * i + 1] < c->ny))
+            return fail(c, IMB_E_INVALID_ARG, "particle centre outside [0,nx) x [0,ny)");
+        rmax = std::max(rmax, r[i]);
+    }
+    if (c->p.dem_on && 2.0 * rmax + c->p.skin > (double)TILE)
+        return fail(c, IMB_E_INVALID_ARG, "DEM needs 2 r_max + skin <= 32 cells");
+    if ((c->p.bc_x == IMB_BC_PERIODIC && c->nx < 2.0 * rmax + 4.0) ||
+        (c->p.bc_y == IMB_BC_PERIODIC && c->ny < 2.0 * rmax + 4.0))
+        return fail(c, IMB_E_INVALID_ARG, "periodic extent must exceed 2 r_max + 4");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (n > c->cap) {
+        free_particles(c);
+        cudaError_t e = cudaSuccess;
+        size_t N = (size_t)n;
+        double **d2[] = {&c->x, &c->v, &c->F, &c->x1, &c->v1, &c->xs};
+        for (double **q : d2) if (e == cudaSuccess) e = dalloc(q, 2 * N);
+        double **d1[] = {&c->w, &c->r, &c->m, &c->I, &c->T, &c->w1};
+        for (double **q : d1) if (e == cudaSuccess) e = dalloc(q, N);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = dalloc(&c->nbr_cnt[b], N);
+            if (e == cudaSuccess) e = dalloc(&c->nbr_id[b], N * MAX_NBR);
+            if (e == cudaSuccess) e = dalloc(&c->nbr_xi[b], N * MAX_NBR);
+        }
+        if (e == cudaSuccess) e = dalloc(&c->wall_xi, 4 * N);
+        if (e == cudaSuccess) e = dalloc(&c->free_ids, N);
+        if (e == cudaSuccess) e = dalloc(&c->coupled_ids, N);
+        if (e == cudaSuccess) e = dalloc(&c->pbin, N);
+        if (e == cudaSuccess) e = dalloc(&c->bin_ids, N);
+        if (e == cudaSuccess) e = dalloc(&c->prec, N);
+        if (e != cudaSuccess) {
+            free_particles(c);
+            return cuda_fail(c, e, "particle buffers");
+        }
+        c->cap = n;
+    }
+    c->np = n;
+    c->r_max = rmax;
+    if (n > 0) {
+        std::vector<double> m(n), I(n);
+        for (int i = 0; i < n; ++i) {
+            m[i] = c->p.rho_s * M_PI * r[i] * r[i];   // disk of unit depth
+            I[i] = 0.5 * m[i] * r[i] * r[i];
+        }
+        CK(cudaMemcpy(c->x, x, 16 * (size_t)n, cudaMemcpyHostToDevice), "copy x");
+        CK(cudaMemcpy(c->v, v, 16 * (size_t)n, cudaMemcpyHostToDevice), "copy v");
+        CK(cudaMemcpy(c->w, omega, 8 * (size_t)n, cudaMemcpyHostToDevice), "copy omega");
+        CK(cudaMemcpy(c->r, r, 8 * (size_t)n, cudaMemcpyHostToDevice), "copy r");
+        CK(cudaMemcpy(c->m, m.data(), 8 * (size_t)n, cudaMemcpyHostToDevice), "copy m");
+        CK(cudaMemcpy(c->I, I.data(), 8 * (size_t)n, cudaMemcpyHostToDevice), "copy I");
+        for (int b = 0; b < 2; ++b) CK(cudaMemset(c->nbr_cnt[b], 0, 4 * (size_t)n), "reset history");
+        CK(cudaMemset(c->wall_xi, 0, 32 * (size_t)n), "reset wall history");
+        CK(cudaMemset(c->F, 0, 16 * (size_t)n), "reset forces");
+        CK(cudaMemset(c->T, 0, 8 * (size_t)n), "reset torques");
+    }
+    CK(cudaMemset(c->counters, 0, 8), "reset counters");
+    int rc = rebuild_table(c, nullptr, false);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return IMB_OK;
+}
+
+extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, const double *omega) {
+    if (!c) return IMB_E_INVALID_ARG;
+    if (c->np == 0) return IMB_OK;
+    if (!x || !v || !omega) return fail(c, IMB_E_INVALID_ARG, "bad kinematics arrays");
+    for (int i = 0; i < c->np; ++i)
+        if (!(x[2 * i] >= 0.0 && x[2 * i] < c->nx && x[2 * i + 1] >= 0.0 && x[2 * i + 1] < c->ny))
+            return fail(c, IMB_E_INVALID_ARG, "particle centre outside [0,nx) x [0,ny)");
+    CK(cudaMemcpyAsync(c->x, x, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy x");
+    CK(cudaMemcpyAsync(c->v, v, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy v");
+    CK(cudaMemcpyAsync(c->w, omega, 8 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy omega");
+    return rebuild_table(c, nullptr, false);
+}
+
+// ------------------------------------------------------------- stepping
+static int dem_cycle(imb_ctx *c, bool zero_forces) {
+    DemArgs d = dem_args(c);
+    CK(launch_dem_neighbours(d, c->stream), "dem neighbours");
+    CK(launch_dem_free(d, c->stream), "dem free");
+    CK(launch_dem_coupled(d, dem_coupled_blocks(), c->stream), "dem coupled");
+    c->launches += 3;
+    c->nbr_cur ^= 1;
+    return rebuild_table(c, c->xs, zero_forces);
+}
+
+static int lattice_step(imb_ctx *c) {
+    if (c->np > 0 && !c->p.dem_on) {
+        CK(cudaMemsetAsync(c->F, 0, 16 * (size_t)c->np, c->stream), "zero forces");
+        CK(cudaMemsetAsync(c->T, 0, 8 * (size_t)c->np, c->stream), "zero torques");
+    }
+    LatticeArgs a = lattice_args(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        while (c->events.size() < c->ev_used + 2) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e), "cudaEventCreate");
+            c->events.push_back(e);
+        }
+        e0 = c->events[c->ev_used];
+        e1 = c->events[c->ev_used + 1];
+        c->ev_used += 2;
+        CK(cudaEventRecord(e0, c->stream), "event record");
+    }
+    CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, c->stream),
+       "stream-collide");
+    c->launches++;
+    if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");
+    c->cur ^= 1;
+    return IMB_OK;
+}
+
+static int queue_steps(imb_ctx *c, int n) {
+    if (!c) return IMB_E_INVALID_ARG;
+    if (n < 0) return fail(c, IMB_E_INVALID_ARG, "n must be >= 0");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    for (int t = 0; t < n; ++t) {
+        if (c->p.dem_on && c->np > 0) {
+            int rc = dem_cycle(c, true);
+            if (rc) return rc;
+        }
+        int rc = lattice_step(c);
+        if (rc) return rc;
+    }
+    return IMB_OK;
+}
+
+static int bounded_wait(imb_ctx *c) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return IMB_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "stream");
+        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                      std::chrono::steady_clock::now() - t0).count();
+        if (ms > c->p.timeout_ms) return fail(c, IMB_E_TIMEOUT, "timed out waiting for the GPU");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+extern "C" int imb_sync(imb_ctx *c) {
+    if (!c) return IMB_E_INVALID_ARG;
+    int rc = bounded_wait(c);
+    if (rc) return rc;
+    unsigned bits = 0;
+    CK(cudaMemcpy(&bits, c->err, sizeof(bits), cudaMemcpyDeviceToHost), "read error flags");
+    if (!bits) return IMB_OK;
+    CK(cudaMemset(c->err, 0, sizeof(unsigned)), "clear error flags");
+    if (bits & ERR_UNSTABLE) return fail(c, IMB_E_UNSTABLE, "NaN or |u| >= 0.3 (Mach guard)");
+    if (bits & ERR_CELL_SLOTS) return fail(c, IMB_E_OVERFLOW, "more than 4 particles cover one cell");
+    if (bits & ERR_TILE_LIST) return fail(c, IMB_E_OVERFLOW, "more than 32 particles touch one tile");
+    if (bits & ERR_NEIGHBOURS) return fail(c, IMB_E_OVERFLOW, "DEM neighbour list full (16)");
+    if (bits & ERR_BARRIER) return fail(c, IMB_E_TIMEOUT, "DEM grid barrier timed out");
+    if (bits & ERR_SKIN) return fail(c, IMB_E_SKIN, "a particle moved more than skin/2 in one step");
+    return fail(c, IMB_E_CUDA, "unknown device error flag");
+}
+
+extern "C" int imb_step_async(imb_ctx *c, int n) { return queue_steps(c, n); }
+
+extern "C" int imb_step(imb_ctx *c, int n) {
+    int rc = queue_steps(c, n);
+    if (rc) return rc;
+    return imb_sync(c);
+}
+
+extern "C" int imb_dem_step(imb_ctx *c, int n) {
+    if (!c) return IMB_E_INVALID_ARG;
+    if (n < 0) return fail(c, IMB_E_INVALID_ARG, "n must be >= 0");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    for (int t = 0; t < n && c->np > 0; ++t) {
+        int rc = dem_cycle(c, false);
+        if (rc) return rc;
+    }
+    return imb_sync(c);
+}
+
+// ------------------------------------------------------------- readback
+template <typename T>
+struct DevTmp {
+    T *p = nullptr;
+    ~DevTmp() { if (p) cudaFree(p); }
+};
+
+extern "C" int imb_get_populations(imb_ctx *c, double *f) {
+    if (!c || !f) return IMB_E_INVALID_ARG;
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    size_t n = (size_t)9 * c->nx * c->ny;
+    DevTmp<double> t;
+    CK(dalloc(&t.p, n), "readback buffer");
+    LatticeArgs a = lattice_args(c);
+    CK(launch_gather(c->fbuf[c->cur], c->p.storage, a, t.p, nullptr, nullptr, nullptr, c->stream), "gather");
+    c->launches++;
+    CK(cudaMemcpyAsync(f, t.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
+    return imb_sync(c);
+}
+
+extern "C" int imb_get_macro(imb_ctx *c, double *rho, double *ux, double *uy) {
+    if (!c || !rho || !ux || !uy) return IMB_E_INVALID_ARG;
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    size_t n = (size_t)c->nx * c->ny;
+    DevTmp<double> t;
+    CK(dalloc(&t.p, 3 * n), "readback buffer");
+    LatticeArgs a = lattice_args(c);
+    CK(launch_gather(c->fbuf[c->cur], c->p.storage, a, nullptr, t.p, t.p + n, t.p + 2 * n, c->stream), "gather");
+    c->launches++;
+    CK(cudaMemcpyAsync(rho, t.p, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho");
+    CK(cudaMemcpyAsync(ux, t.p + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy ux");
+    CK(cudaMemcpyAsync(uy, t.p + 2 * n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy uy");
+    return imb_sync(c);
+}
+
+extern "C" int imb_get_forces(imb_ctx *c, double *F, double *T) {
+    if (!c || (c->np && (!F || !T))) return IMB_E_INVALID_ARG;
+    if (c->np == 0) return IMB_OK;
+    CK(cudaMemcpyAsync(F, c->F, 16 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy F");
+    CK(cudaMemcpyAsync(T, c->T, 8 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy T");
+    return imb_sync(c);
+}
+
+extern "C" int imb_set_forces(imb_ctx *c, const double *F, const double *T) {
+    if (!c || (c->np && (!F || !T))) return IMB_E_INVALID_ARG;
+    if (c->np == 0) return IMB_OK;
+    CK(cudaMemcpyAsync(c->F, F, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy F");
+    CK(cudaMemcpyAsync(c->T, T, 8 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy T");
+    return imb_sync(c);
+}
+
+extern "C" int imb_get_particles(imb_ctx *c, double *x, double *v, double *omega) {
+    if (!c || (c->np && (!x || !v || !omega))) return IMB_E_INVALID_ARG;
+    if (c->np == 0) return IMB_OK;
+    CK(cudaMemcpyAsync(x, c->x, 16 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy x");
+    CK(cudaMemcpyAsync(v, c->v, 16 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy v");
+    CK(cudaMemcpyAsync(omega, c->w, 8 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy w");
+    return imb_sync(c);
+}
+
+extern "C" int imb_get_cell_map(imb_ctx *c, int *count, int *ids, float *eps) {
+    if (!c || !count || !ids || !eps) return IMB_E_INVALID_ARG;
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    size_t n = (size_t)c->nx * c->ny;
+    DevTmp<int> tc, ti;
+    DevTmp<float> te;
+    CK(dalloc(&tc.p, n), "readback buffer");
+    CK(dalloc(&ti.p, n * MAX_SLOTS), "readback buffer");
+    CK(dalloc(&te.p, n * MAX_SLOTS), "readback buffer");
+    if (c->np == 0) {
+        std::fill(count, count + n, 0);
+        std::fill(ids, ids + n * MAX_SLOTS, -1);
+        std::fill(eps, eps + n * MAX_SLOTS, 0.0f);
+        return IMB_OK;
+    }
+    LatticeArgs a = lattice_args(c);
+    CK(launch_cell_map(a, tc.p, ti.p, te.p, c->stream), "cell map");
+    c->launches++;
+    CK(cudaMemcpyAsync(count, tc.p, n * 4, cudaMemcpyDeviceToHost, c->stream), "copy count");
+    CK(cudaMemcpyAsync(ids, ti.p, n * 4 * MAX_SLOTS, cudaMemcpyDeviceToHost, c->stream), "copy ids");
+    CK(cudaMemcpyAsync(eps, te.p, n * 4 * MAX_SLOTS, cudaMemcpyDeviceToHost, c->stream), "copy eps");
+    return imb_sync(c);
+}
+
+extern "C" int imb_get_contacts(imb_ctx *c, int max_pairs, int *pairs, int *n_pairs) {
+    if (!c || !n_pairs || max_pairs < 0 || (max_pairs > 0 && !pairs)) return IMB_E_INVALID_ARG;
+    *n_pairs = 0;
+    if (c->np == 0) return IMB_OK;
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    const int max_per = 32;
+    const int reach = (int)std::ceil(2.0 * c->r_max / TILE);
+    DevTmp<int> tc, tp;
+    CK(dalloc(&tc.p, c->np), "contacts buffer");
+    CK(dalloc(&tp.p, (size_t)c->np * max_per), "contacts buffer");
+    CK(launch_contacts(c->x, c->r, c->np, c->nx, c->ny, c->p.bc_x, c->p.bc_y, c->bin_start, c->bin_ids,
+                       c->pbin, c->nbx, c->nby, reach, tc.p, tp.p, max_per, c->stream),
+       "contacts");
+    c->launches++;
+    std::vector<int> cnt(c->np), lst((size_t)c->np * max_per);
+    CK(cudaMemcpyAsync(cnt.data(), tc.p, 4 * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaMemcpyAsync(lst.data(), tp.p, 4 * lst.size(), cudaMemcpyDeviceToHost, c->stream), "copy");
+    rc = imb_sync(c);
+    if (rc) return rc;
+    std::vector<std::pair<int, int>> all;
+    for (int a = 0; a < c->np; ++a) {
+        if (cnt[a] > max_per) return fail(c, IMB_E_OVERFLOW, "more than 32 contacts of one particle");
+        for (int k = 0; k < cnt[a]; ++k) all.emplace_back(a, lst[(size_t)a * max_per + k]);
+    }
+    std::sort(all.begin(), all.end());
+    *n_pairs = (int)all.size();
+    for (int k = 0; k < (int)all.size() && k < max_pairs; ++k) {
+        pairs[2 * k] = all[k].first;
+        pairs[2 * k + 1] = all[k].second;
+    }
+    return IMB_OK;
+}
+
+extern "C" int imb_get_bins(imb_ctx *c, int *bin_start, int *bin_ids) {
+    if (!c || !bin_start || (c->np && !bin_ids)) return IMB_E_INVALID_ARG;
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    CK(cudaMemcpy(bin_start, c->bin_start, 4 * (size_t)(c->nbins + 1), cudaMemcpyDeviceToHost), "copy");
+    if (c->np == 0) return IMB_OK;
+    CK(cudaMemcpy(bin_ids, c->bin_ids, 4 * (size_t)c->np, cudaMemcpyDeviceToHost), "copy");
+    for (int b = 0; b < c->nbins; ++b) std::sort(bin_ids + bin_start[b], bin_ids + bin_start[b + 1]);
+    return IMB_OK;
+}
+
+// ---------------------------------------------------------------- misc
+extern "C" int imb_set_stream(imb_ctx *c, void *stream) {
+    if (!c) return IMB_E_INVALID_ARG;
+    c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+    return IMB_OK;
+}
+
+extern "C" void *imb_get_stream(imb_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+extern "C" int imb_enable_kernel_timing(imb_ctx *c, int on) {
+    if (!c) return IMB_E_INVALID_ARG;
+    c->timing = on != 0;
+    c->ev_used = 0;
+    return IMB_OK;
+}
+
+extern "C" int imb_kernel_time(imb_ctx *c, double *ms, long long *launches) {
+    if (!c || !ms || !launches) return IMB_E_INVALID_ARG;
+    int rc = bounded_wait(c);
+    if (rc) return rc;
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, c->events[k], c->events[k + 1]), "event elapsed");
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (long long)(c->ev_used / 2);
+    c->ev_used = 0;
+    return IMB_OK;
+}
+
+extern "C" long long imb_launch_count(imb_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" double imb_bytes_per_cell(imb_ctx *c) { return c ? 18.0 * (double)c->elem : 0.0; }
+
+extern "C" const char *imb_last_error(imb_ctx *c) {
+    return c ? c->msg.c_str() : g_init_error.c_str();
+}

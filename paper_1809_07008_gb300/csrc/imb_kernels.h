@@ -1,0 +1,81 @@
+// imb_kernels.h -- host-side launch wrappers of the CUDA kernels (internal to the
+// library; the public interface is include/imblbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace imb {
+
+struct PRec;
+struct GridBarrier;
+
+// Everything the lattice kernels read about the lattice and the particles.
+struct LatticeArgs {
+    int nx, ny, pitch, bc_x, bc_y;
+    size_t plane;
+    float tau, smag_coef;      // smag_coef = 18 sqrt(2) C^2 (0 switches the model off)
+    float Fx, Fy;              // body force density (0, 0 = no forcing)
+    float u_in_x, u_in_y;
+    int eps_mode, n_sub;
+    int nbx, nby;              // bins of 32 x 32 cells
+    int np;
+    const int *bin_start;      // [nbx*nby + 1]
+    const int *bin_ids;        // [np]
+    const PRec *prec;          // [np]
+    double *F;                 // [2 np] hydrodynamic force accumulators
+    double *T;                 // [np]   hydrodynamic torque accumulators
+    unsigned *err;
+};
+
+// DEM state and parameters (FP64).
+struct DemArgs {
+    int np, nx, ny, bc_x, bc_y, N_sub;
+    double dt, kn, kt, zeta, ct_ratio, mu, gx_eff, gy_eff, skin;
+    double *x, *v, *w;          // primary state [2np], [2np], [np]
+    double *x1, *v1, *w1;       // second buffer of the coupled sub-cycle loop
+    double *x_start;            // positions at the start of the coupling cycle
+    const double *r, *m, *I;
+    const double *F, *T;        // hydrodynamic force/torque (frozen during the sub-cycles)
+    int *nbr_cnt_old, *nbr_cnt;       // [np]
+    int *nbr_id_old, *nbr_id;         // [np * MAX_NBR]
+    double *nbr_xi_old, *nbr_xi;      // [np * MAX_NBR]
+    double *wall_xi;                  // [np * 4]
+    int *free_ids, *coupled_ids;      // [np]
+    int *counters;                    // [0] free, [1] coupled
+    const int *bin_start, *bin_ids;   // bins of the positions at cycle start
+    int *pbin;                        // [np]
+    int nbx, nby;
+    GridBarrier *barrier;
+    unsigned *err;
+};
+
+// lattice kernels (imb_lbm.cu)
+cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, float rho0, float ux0,
+                                    float uy0, cudaStream_t s);
+cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
+                                  cudaStream_t s);
+cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
+                          double *rho, double *ux, double *uy, cudaStream_t s);
+cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);
+
+// particle kernels (imb_particles.cu)
+cudaError_t launch_particle_table(const double *x, const double *r, const double *x_start, int np,
+                                  int nx, int ny, int bc_x, int bc_y, double skin_half, int nbx,
+                                  int nby, int *bin_count, int *pbin, PRec *prec, const double *v,
+                                  const double *w, double *F, double *T, unsigned *err,
+                                  cudaStream_t s);
+cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins,
+                            int *dem_counters, cudaStream_t s);
+cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *bin_start,
+                            int *bin_ids, cudaStream_t s);
+cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s);
+cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s);
+cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s);
+cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
+                            int bc_y, const int *bin_start, const int *bin_ids, const int *pbin,
+                            int nbx, int nby, int reach, int *pair_cnt, int *pairs, int max_per,
+                            cudaStream_t s);
+int dem_coupled_blocks();
+
+}  // namespace imb

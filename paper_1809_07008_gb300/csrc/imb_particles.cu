@@ -1,0 +1,441 @@
+// imb_particles.cu -- particle kernels of the GB300 IMB-LBM-DEM library.
+//
+//   k_particle_table  after every DEM update: bin of each particle (32 x 32 cells),
+//                     the FP32 record read by the lattice kernels, the skin check,
+//                     and zeroing of the hydrodynamic force accumulators;
+//   k_bin_scan        exclusive scan of the bin counts (one block);
+//   k_bin_fill        scatter of particle ids into their bins;
+//   k_dem_neighbours  sorted neighbour candidates within r_a + r_b + skin, carrying
+//                     the tangential spring of each pair over, and the split of the
+//                     particles into free (no candidate) and coupled ones;
+//   k_dem_free        the N_sub sub-cycles (Eq. 17) of a free particle in registers;
+//   k_dem_coupled     the N_sub sub-cycles of the coupled particles, one bounded grid
+//                     barrier per sub-cycle (cooperative launch);
+//   k_contacts        pairs in contact (Eq. 7) for readback.
+//
+// DEM arithmetic is FP64.  This file is compiled with --fmad=false so that every
+// multiply and add is rounded separately; with the contact partners summed in
+// ascending id order, particle trajectories then reproduce a plain sequential
+// FP64 evaluation of Eqs. 7-11 exactly.
+#include "imb_device.cuh"
+#include "imb_kernels.h"
+
+namespace imb {
+
+// ------------------------------------------------------------- binning
+__device__ __forceinline__ double min_image(double d, bool periodic, int L) {
+    if (periodic) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ int bin_of(double px, double py, int nbx, int nby) {
+    int bx = (int)floor(px / (double)TILE), by = (int)floor(py / (double)TILE);
+    bx = bx < 0 ? 0 : (bx >= nbx ? nbx - 1 : bx);
+    by = by < 0 ? 0 : (by >= nby ? nby - 1 : by);
+    return by * nbx + bx;
+}
+
+__global__ void k_particle_table(const double *__restrict__ x, const double *__restrict__ r,
+                                 const double *__restrict__ x_start, int np, int nx, int ny, int bc_x,
+                                 int bc_y, double skin_half, int nbx, int nby, int *bin_count, int *pbin,
+                                 PRec *prec, const double *__restrict__ v, const double *__restrict__ w,
+                                 double *F, double *T, unsigned *err) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double px = x[2 * p], py = x[2 * p + 1];
+    const int b = bin_of(px, py, nbx, nby);
+    pbin[p] = b;
+    atomicAdd(&bin_count[b], 1);
+    PRec P;
+    P.ci = (int)floor(px);
+    P.cj = (int)floor(py);
+    P.fx = __double2float_rn(px - (double)P.ci);
+    P.fy = __double2float_rn(py - (double)P.cj);
+    P.r = __double2float_rn(r[p]);
+    P.vx = __double2float_rn(v[2 * p]);
+    P.vy = __double2float_rn(v[2 * p + 1]);
+    P.w = __double2float_rn(w[p]);
+    prec[p] = P;
+    if (x_start) {
+        const double dx = min_image(px - x_start[2 * p], bc_x == BC_PERIODIC, nx);
+        const double dy = min_image(py - x_start[2 * p + 1], bc_y == BC_PERIODIC, ny);
+        if (dx * dx + dy * dy > skin_half * skin_half) set_err(err, ERR_SKIN);
+    }
+    if (F) {
+        F[2 * p] = 0.0;
+        F[2 * p + 1] = 0.0;
+        T[p] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *start, int nbins,
+                                                   int *dem_counters) {
+    __shared__ int s[1024];
+    const int t = threadIdx.x;
+    const int chunk = (nbins + 1023) / 1024;
+    const int b0 = min(t * chunk, nbins), b1 = min(b0 + chunk, nbins);
+    int sum = 0;
+    for (int b = b0; b < b1; ++b) sum += count[b];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int add = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += add;
+        __syncthreads();
+    }
+    int run = s[t] - sum;
+    for (int b = b0; b < b1; ++b) {
+        start[b] = run;
+        run += count[b];
+        count[b] = 0;
+        fill[b] = 0;
+    }
+    if (t == 1023) start[nbins] = s[1023];
+    if (t == 0 && dem_counters) {
+        dem_counters[0] = 0;
+        dem_counters[1] = 0;
+    }
+}
+
+__global__ void k_bin_fill(const int *__restrict__ pbin, int np, int *fill, const int *__restrict__ start,
+                           int *ids) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int b = pbin[p];
+    ids[start[b] + atomicAdd(&fill[b], 1)] = p;
+}
+
+// ----------------------------------------------------------------- DEM
+// Linear spring-dashpot contact seen from particle a (Eqs. 7-9): n from a to the
+// partner, t = z x n, (dvx, dvy) partner minus a, rot = w_a r_a + w_b r_b.
+// Returns the force on a and the tangential force magnitude.
+__device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double nyv, double delta,
+                                            double dvx, double dvy, double rot, double mstar,
+                                            double &xi, double &fx, double &fy, double &Ft) {
+    const double tx = -nyv, ty = nxv;
+    const double vn = dvx * nxv + dvy * nyv;
+    const double vt = (dvx * tx + dvy * ty) - rot;
+    const double cn = 2.0 * d.zeta * sqrt(mstar * d.kn);
+    const double ct = d.ct_ratio * cn;
+    xi = xi + vt * d.dt;                     // incremental tangential spring (Eq. 9)
+    const double Fn = d.kn * delta - cn * vn; // Eq. 8, repulsive when positive
+    double F_t = d.kt * xi + ct * vt;        // Eq. 9
+    const double lim = d.mu * fabs(Fn);      // Coulomb cap
+    if (fabs(F_t) > lim) {
+        F_t = copysign(lim, F_t);
+        xi = copysign(lim / d.kt, xi);
+    }
+    fx = -Fn * nxv + F_t * tx;
+    fy = -Fn * nyv + F_t * ty;
+    Ft = F_t;
+}
+
+// Walls on the domain edges of non-periodic axes, an immovable partner (m* = m).
+__device__ __forceinline__ void wall_contacts(const DemArgs &d, int p, double px, double py, double vx,
+                                              double vy, double w, double rp, double mp, double *xiw,
+                                              double &Fcx, double &Fcy, double &Tc) {
+#pragma unroll
+    for (int wl = 0; wl < 4; ++wl) {
+        const bool active = wl < 2 ? d.bc_x == BC_WALL : d.bc_y == BC_WALL;
+        if (!active) continue;
+        double dist, nxv, nyv;
+        if (wl == 0) { dist = px; nxv = -1.0; nyv = 0.0; }
+        else if (wl == 1) { dist = (double)d.nx - px; nxv = 1.0; nyv = 0.0; }
+        else if (wl == 2) { dist = py; nxv = 0.0; nyv = -1.0; }
+        else { dist = (double)d.ny - py; nxv = 0.0; nyv = 1.0; }
+        if (!(dist < rp)) {
+            xiw[wl] = 0.0;
+            continue;
+        }
+        double fx, fy, Ft;
+        contact_law(d, nxv, nyv, rp - dist, -vx, -vy, w * rp, mp, xiw[wl], fx, fy, Ft);
+        Fcx += fx;
+        Fcy += fy;
+        Tc += rp * Ft;
+    }
+}
+
+// Eqs. 10-11, leapfrog kick-drift.
+__device__ __forceinline__ void integrate(const DemArgs &d, int p, double Fcx, double Fcy, double Tc,
+                                          double &px, double &py, double &vx, double &vy, double &w) {
+    const double ax = (Fcx + d.F[2 * p]) / d.m[p] + d.gx_eff;
+    const double ay = (Fcy + d.F[2 * p + 1]) / d.m[p] + d.gy_eff;
+    const double al = (Tc + d.T[p]) / d.I[p];
+    vx = vx + ax * d.dt;
+    vy = vy + ay * d.dt;
+    w = w + al * d.dt;
+    px = px + vx * d.dt;
+    py = py + vy * d.dt;
+    if (d.bc_x == BC_PERIODIC) {
+        if (px >= d.nx) px -= d.nx;
+        else if (px < 0.0) px += d.nx;
+    }
+    if (d.bc_y == BC_PERIODIC) {
+        if (py >= d.ny) py -= d.ny;
+        else if (py < 0.0) py += d.ny;
+    }
+}
+
+__global__ void k_dem_neighbours(const DemArgs d) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d.np) return;
+    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
+    const double px = d.x[2 * p], py = d.x[2 * p + 1], rp = d.r[p];
+    d.x_start[2 * p] = px;
+    d.x_start[2 * p + 1] = py;
+    const int b = d.pbin[p];
+    const int bx = b % d.nbx, by = b / d.nbx;
+    int ids[MAX_NBR];
+    int n = 0;
+    int seen[9];
+    int nseen = 0;
+    for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+            int ix = bx + ox, iy = by + oy;
+            if (ix < 0 || ix >= d.nbx) {
+                if (!perx) continue;
+                ix = (ix + d.nbx) % d.nbx;
+            }
+            if (iy < 0 || iy >= d.nby) {
+                if (!pery) continue;
+                iy = (iy + d.nby) % d.nby;
+            }
+            const int bb = iy * d.nbx + ix;
+            bool dup = false;
+            for (int k = 0; k < nseen; ++k) dup |= seen[k] == bb;
+            if (dup) continue;
+            seen[nseen++] = bb;
+            for (int k = d.bin_start[bb]; k < d.bin_start[bb + 1]; ++k) {
+                const int q = d.bin_ids[k];
+                if (q == p) continue;
+                const double dx = min_image(d.x[2 * q] - px, perx, d.nx);
+                const double dy = min_image(d.x[2 * q + 1] - py, pery, d.ny);
+                const double R = rp + d.r[q] + d.skin;
+                if (!(dx * dx + dy * dy < R * R)) continue;
+                if (n == MAX_NBR) {
+                    set_err(d.err, ERR_NEIGHBOURS);
+                    continue;
+                }
+                int j = n++;  // insertion keeps the list in ascending id order
+                while (j > 0 && ids[j - 1] > q) {
+                    ids[j] = ids[j - 1];
+                    --j;
+                }
+                ids[j] = q;
+            }
+        }
+    const int nold = d.nbr_cnt_old[p];
+    for (int j = 0; j < n; ++j) {
+        double xi = 0.0;
+        for (int k = 0; k < nold; ++k)
+            if (d.nbr_id_old[p * MAX_NBR + k] == ids[j]) xi = d.nbr_xi_old[p * MAX_NBR + k];
+        d.nbr_id[p * MAX_NBR + j] = ids[j];
+        d.nbr_xi[p * MAX_NBR + j] = xi;
+    }
+    d.nbr_cnt[p] = n;
+    if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
+    else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
+}
+
+__global__ void k_dem_free(const DemArgs d) {
+    const int nfree = d.counters[0];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nfree; c += gridDim.x * blockDim.x) {
+        const int p = d.free_ids[c];
+        double px = d.x[2 * p], py = d.x[2 * p + 1], vx = d.v[2 * p], vy = d.v[2 * p + 1], w = d.w[p];
+        const double rp = d.r[p], mp = d.m[p];
+        double xiw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xiw[k] = d.wall_xi[4 * p + k];
+        for (int s = 0; s < d.N_sub; ++s) {
+            double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+            wall_contacts(d, p, px, py, vx, vy, w, rp, mp, xiw, Fcx, Fcy, Tc);
+            integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+        }
+        d.x[2 * p] = px;
+        d.x[2 * p + 1] = py;
+        d.v[2 * p] = vx;
+        d.v[2 * p + 1] = vy;
+        d.w[p] = w;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d.wall_xi[4 * p + k] = xiw[k];
+    }
+}
+
+__global__ void k_dem_coupled(const DemArgs d) {
+    const int ncpl = d.counters[1];
+    const int nb_active = min((int)gridDim.x, (ncpl + (int)blockDim.x - 1) / (int)blockDim.x);
+    if (ncpl == 0 || (int)blockIdx.x >= nb_active) return;
+    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
+    const int stride = nb_active * blockDim.x;
+    for (int s = 0; s < d.N_sub; ++s) {
+        const double *xc = (s & 1) ? d.x1 : d.x;
+        const double *vc = (s & 1) ? d.v1 : d.v;
+        const double *wc = (s & 1) ? d.w1 : d.w;
+        double *xn = (s & 1) ? d.x : d.x1;
+        double *vn = (s & 1) ? d.v : d.v1;
+        double *wn = (s & 1) ? d.w : d.w1;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += stride) {
+            const int p = d.coupled_ids[c];
+            double px = __ldcg(&xc[2 * p]), py = __ldcg(&xc[2 * p + 1]);
+            double vx = __ldcg(&vc[2 * p]), vy = __ldcg(&vc[2 * p + 1]), w = __ldcg(&wc[p]);
+            const double rp = d.r[p], mp = d.m[p];
+            double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+            const int n = d.nbr_cnt[p];
+            for (int j = 0; j < n; ++j) {
+                const int q = d.nbr_id[p * MAX_NBR + j];
+                double &xi = d.nbr_xi[p * MAX_NBR + j];
+                const double qx = __ldcg(&xc[2 * q]), qy = __ldcg(&xc[2 * q + 1]);
+                const double dx = min_image(qx - px, perx, d.nx);
+                const double dy = min_image(qy - py, pery, d.ny);
+                const double d2 = dx * dx + dy * dy;
+                const double R = rp + d.r[q];
+                if (!(d2 < R * R)) {  // Eq. 7: no overlap, the spring is released
+                    xi = 0.0;
+                    continue;
+                }
+                const double dist = sqrt(d2);
+                const double nxv = dx / dist, nyv = dy / dist;
+                const double mq = d.m[q];
+                const double mstar = mp * mq / (mp + mq);
+                const double rot = w * rp + __ldcg(&wc[q]) * d.r[q];
+                double fx, fy, Ft;
+                contact_law(d, nxv, nyv, R - dist, __ldcg(&vc[2 * q]) - vx, __ldcg(&vc[2 * q + 1]) - vy,
+                            rot, mstar, xi, fx, fy, Ft);
+                Fcx += fx;
+                Fcy += fy;
+                Tc += rp * Ft;
+            }
+            wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
+            integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+            __stcg(&xn[2 * p], px);
+            __stcg(&xn[2 * p + 1], py);
+            __stcg(&vn[2 * p], vx);
+            __stcg(&vn[2 * p + 1], vy);
+            __stcg(&wn[p], w);
+        }
+        if (nb_active > 1) {
+            if (!grid_barrier(d.barrier, (unsigned)nb_active, d.err)) return;
+        } else {
+            __syncthreads();
+        }
+    }
+    if (d.N_sub & 1) {  // the last sub-cycle wrote the second buffer
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += stride) {
+            const int p = d.coupled_ids[c];
+            d.x[2 * p] = __ldcg(&d.x1[2 * p]);
+            d.x[2 * p + 1] = __ldcg(&d.x1[2 * p + 1]);
+            d.v[2 * p] = __ldcg(&d.v1[2 * p]);
+            d.v[2 * p + 1] = __ldcg(&d.v1[2 * p + 1]);
+            d.w[p] = __ldcg(&d.w1[p]);
+        }
+    }
+}
+
+__global__ void k_contacts(const double *__restrict__ x, const double *__restrict__ r, int np, int nx,
+                           int ny, int bc_x, int bc_y, const int *__restrict__ bin_start,
+                           const int *__restrict__ bin_ids, const int *__restrict__ pbin, int nbx,
+                           int nby, int reach, int *pair_cnt, int *pairs, int max_per) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= np) return;
+    const bool perx = bc_x == BC_PERIODIC, pery = bc_y == BC_PERIODIC;
+    const int b = pbin[a];
+    const int bx = b % nbx, by = b / nbx;
+    int n = 0;
+    const int wx = min(2 * reach + 1, nbx), wy = min(2 * reach + 1, nby);
+    for (int oy = 0; oy < wy; ++oy)
+        for (int ox = 0; ox < wx; ++ox) {
+            int ix = bx - reach + ox, iy = by - reach + oy;
+            if (perx) ix = ((ix % nbx) + nbx) % nbx;
+            else if (ix < 0 || ix >= nbx) continue;
+            if (pery) iy = ((iy % nby) + nby) % nby;
+            else if (iy < 0 || iy >= nby) continue;
+            const int bb = iy * nbx + ix;
+            for (int k = bin_start[bb]; k < bin_start[bb + 1]; ++k) {
+                const int q = bin_ids[k];
+                if (q <= a) continue;
+                const double dx = min_image(x[2 * q] - x[2 * a], perx, nx);
+                const double dy = min_image(x[2 * q + 1] - x[2 * a + 1], pery, ny);
+                const double R = r[a] + r[q];
+                if (dx * dx + dy * dy < R * R) {
+                    if (n < max_per) pairs[a * max_per + n] = q;
+                    ++n;
+                }
+            }
+        }
+    pair_cnt[a] = n;
+}
+
+// ------------------------------------------------------------ launchers
+static inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+cudaError_t launch_particle_table(const double *x, const double *r, const double *x_start, int np,
+                                  int nx, int ny, int bc_x, int bc_y, double skin_half, int nbx,
+                                  int nby, int *bin_count, int *pbin, PRec *prec, const double *v,
+                                  const double *w, double *F, double *T, unsigned *err,
+                                  cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    k_particle_table<<<blocks_for(np, 128), 128, 0, s>>>(x, r, x_start, np, nx, ny, bc_x, bc_y,
+                                                         skin_half, nbx, nby, bin_count, pbin, prec,
+                                                         v, w, F, T, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins,
+                            int *dem_counters, cudaStream_t s) {
+    k_bin_scan<<<1, 1024, 0, s>>>(bin_count, bin_fill, bin_start, nbins, dem_counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *bin_start,
+                            int *bin_ids, cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    k_bin_fill<<<blocks_for(np, 128), 128, 0, s>>>(pbin, np, bin_fill, bin_start, bin_ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s) {
+    if (d.np == 0) return cudaSuccess;
+    k_dem_neighbours<<<blocks_for(d.np, 64), 64, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s) {
+    if (d.np == 0) return cudaSuccess;
+    k_dem_free<<<blocks_for(d.np, 64), 64, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+static int g_coupled_blocks = 0;
+
+int dem_coupled_blocks() {
+    if (g_coupled_blocks == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_coupled_blocks = sms > 0 ? sms : 1;
+    }
+    return g_coupled_blocks;
+}
+
+cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s) {
+    if (d.np == 0) return cudaSuccess;
+    DemArgs copy = d;
+    void *args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void *)k_dem_coupled, dim3(nblocks), dim3(32), args, 0, s);
+}
+
+cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
+                            int bc_y, const int *bin_start, const int *bin_ids, const int *pbin,
+                            int nbx, int nby, int reach, int *pair_cnt, int *pairs, int max_per,
+                            cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    k_contacts<<<blocks_for(np, 128), 128, 0, s>>>(x, r, np, nx, ny, bc_x, bc_y, bin_start, bin_ids,
+                                                   pbin, nbx, nby, reach, pair_cnt, pairs, max_per);
+    return cudaGetLastError();
+}
+
+}  // namespace imb

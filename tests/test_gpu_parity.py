@@ -1,0 +1,265 @@
+"""GPU (sm_103a) path against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 populations, compared after the stated number of steps):
+  * velocity field: relative L2 <= 1e-5 over the fluid cells (denominator ||u_oracle||);
+  * populations: max |f_gpu - f_oracle| <= 1e-6 (FP32 storage of f - w: ~1e-8 per step);
+  * per-particle force: |F_gpu - F_oracle| <= 1e-4 * max(|F_oracle|, mean_p |F_oracle|),
+    torque likewise with the scale r * that force;
+  * integer bookkeeping (bins, cells covered per particle, contact pairs) bit-exact;
+  * solid ratio per cell within 2e-6 of the FP64 overlap area (FP32 geometry).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imb():
+    import paper_1809_07008_gb300 as imb
+    imb.load()
+    return imb
+
+
+def _fluid_mask(orc_sim):
+    count, _, _ = orc_sim.cell_map() if orc_sim.np else (np.zeros(orc_sim.shape, int), None, None)
+    return count == 0
+
+
+def _u_rel_l2(g, o, mask):
+    gu = np.stack(g[1:])[:, mask]
+    ou = np.stack(o[1:])[:, mask]
+    return np.linalg.norm(gu - ou) / np.linalg.norm(ou)
+
+
+def _force_ok(Fg, Tg, Fo, To, r, tol=1e-4):
+    scale = max(np.abs(Fo).max(), np.linalg.norm(Fo, axis=1).mean(), 1e-30)
+    errF = np.abs(Fg - Fo).max() / scale
+    errT = np.abs(Tg - To).max() / (scale * max(r.max(), 1.0))
+    return errF, errT
+
+
+def _run_pair(orc, imb, w, steps, storage="fp32"):
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w, storage=storage)
+    o.step(steps)
+    g.step(steps)
+    return o, g
+
+
+@pytest.mark.parametrize("bc", ["channel", "periodic_forced_smag", "closed_box"])
+def test_fluid_only_parity(orc, imb, bc):
+    if bc == "channel":
+        w = W.Workload(name="ch", nx=70, ny=45, tau=0.6, bc_x=W.BC_INLET_OUTLET, bc_y=W.BC_WALL,
+                       u_in=(0.02, 0.0))
+    elif bc == "periodic_forced_smag":
+        w = W.Workload(name="pf", nx=67, ny=40, tau=0.52, C_smag=0.15, bc_x=W.BC_PERIODIC,
+                       bc_y=W.BC_WALL, force=(2e-5, 1e-6), u0=(0.01, 0.0))
+    else:
+        w = W.Workload(name="box", nx=64, ny=33, tau=0.8, bc_x=W.BC_WALL, bc_y=W.BC_WALL,
+                       u0=(0.03, -0.02))
+    o, g = _run_pair(orc, imb, w, 300)
+    fo, fg = o.f(), g.populations()
+    assert np.abs(fg - fo).max() < 1e-6
+    mask = np.ones(o.shape, bool)
+    assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
+
+
+def test_initial_state_and_readback(orc, imb):
+    w = W.Workload(name="init", nx=40, ny=35, tau=0.7, bc_x=W.BC_INLET_OUTLET, bc_y=W.BC_WALL,
+                   u_in=(0.02, 0.0), u0=(0.01, 0.005), rho0=1.01)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    assert np.abs(g.populations() - o.f()).max() < 2e-7
+
+
+def test_channel_disk_c1_parity(orc, imb):
+    # 200 x 100 channel, fixed disk d = 20 at the centre, u_in = 0.01, tau = 0.6 (2000 steps)
+    w = W.c1(steps=2000)
+    o, g = _run_pair(orc, imb, w, w.steps)
+    mask = _fluid_mask(o)
+    assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    errF, errT = _force_ok(Fg, Tg, Fo, To, w.r)
+    assert Fo[0, 0] > 0 and errF < 1e-4 and errT < 1e-4
+
+
+def test_cell_map_bit_exact_and_eps(orc, imb):
+    w = W.c3sub(steps=0, nx=256, ny=192)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    co, io, eo = o.cell_map()
+    cg, ig, eg = g.cell_map()
+    assert np.array_equal(co, cg)
+    assert np.array_equal(io, ig)
+    assert np.abs(eg - eo).max() < 2e-6
+    # sum of the solid ratios of each disk equals its area
+    for p in range(w.n_particles):
+        tot = eg[ig == p].sum(dtype=np.float64)
+        assert abs(tot - math.pi * w.r[p] ** 2) < 1e-5 * math.pi * w.r[p] ** 2
+
+
+def test_cell_map_subcell_bit_exact(orc, imb):
+    w = W.c3sub(steps=0, nx=128, ny=128).with_(eps_mode=W.EPS_SUBCELL, n_sub=5)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    co, io, eo = o.cell_map()
+    cg, ig, eg = g.cell_map()
+    assert np.array_equal(co, cg) and np.array_equal(io, ig)
+    assert np.abs(eg - eo).max() < 1e-7
+
+
+def test_bins_bit_exact(orc, imb):
+    w = W.c3sub(steps=0, nx=512, ny=512)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    so, ido = o.bins(32)
+    sg, idg = g.bins()
+    assert np.array_equal(so, sg) and np.array_equal(ido, idg)
+
+
+def _pile(rows=6, cols=10, R=8.0, overlap=3e-4, seed=5, gy=-2e-3, e=0.5, mu=0.5, N_sub=50,
+          speed=1e-3):
+    """Disks on a triangular lattice in a box just wide enough to hold them: neighbours
+    overlap by ~``overlap`` (radii jittered by +-1e-4), the bottom row rests on the wall
+    y = 0, small random velocities, gravity down."""
+    rng = W.SplitMix64(seed)
+    s = 2 * R - overlap
+    xs, rs = [], []
+    for j in range(rows):
+        for i in range(cols):
+            xs.append((R + 0.3 + i * s + (j % 2) * s / 2, R - 1e-4 + j * s * math.sqrt(3) / 2))
+            rs.append(R + rng.uniform_range(-1e-4, 1e-4))
+    n = len(rs)
+    v = W.random_directions(n, speed, seed + 1)
+    nx = int(math.ceil(2 * R + 0.6 + (cols - 0.5) * s))
+    ny = int(rows * s + 3 * R)
+    return W.Workload(name="pile", nx=nx, ny=ny, tau=0.6, bc_x=W.BC_WALL, bc_y=W.BC_WALL, dem_on=1,
+                      N_sub=N_sub, gravity=(0.0, gy), e_rest=e, mu=mu, x=np.array(xs), v=v,
+                      omega=np.zeros(n), r=np.array(rs))
+
+
+def test_contacts_bit_exact(orc, imb):
+    w = _pile()
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    po, pg = o.contacts(), g.contacts()
+    assert len(po) > 10
+    assert np.array_equal(po, pg)
+
+
+def test_dem_only_trajectories_bit_exact(orc, imb):
+    # DEM alone (fluid force held at zero): the GPU sub-cycles reproduce the sequential
+    # FP64 evaluation of Eqs. 7-11 bit for bit, contacts and walls included
+    w = _pile()
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    cycles = 40
+    o.dem_substeps(cycles * w.N_sub)
+    g.dem_step(cycles)
+    xo, vo, wo = o.particles()
+    xg, vg, wg = g.particles()
+    assert np.array_equal(xo, xg) and np.array_equal(vo, vg) and np.array_equal(wo, wg)
+    assert np.array_equal(o.contacts(), g.contacts())
+    assert len(o.contacts()) > 10
+
+
+def test_dem_only_with_frozen_fluid_force_bit_exact(orc, imb):
+    w = _pile(rows=4, cols=10, seed=9)
+    rng = np.random.default_rng(9)
+    F = 1e-2 * rng.standard_normal((w.n_particles, 2))
+    T = 1e-2 * rng.standard_normal(w.n_particles)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    o.set_forces(F, T)
+    g.set_forces(F, T)
+    o.dem_substeps(10 * w.N_sub)
+    g.dem_step(10)
+    for a, b in zip(o.particles(), g.particles()):
+        assert np.array_equal(a, b)
+
+
+def test_moving_particles_coupled_parity(orc, imb):
+    # c3 at the same density on 256 x 192: DEM + IMB + Smagorinsky, tau = 0.51
+    w = W.c3sub(steps=0, nx=256, ny=192)
+    o, g = _run_pair(orc, imb, w, 300)
+    mask = _fluid_mask(o)
+    assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    errF, errT = _force_ok(Fg, Tg, Fo, To, w.r)
+    assert errF < 1e-4 and errT < 1e-4
+    xo, _, _ = o.particles()
+    xg, _, _ = g.particles()
+    assert np.abs(xo - xg).max() < 1e-9
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-2), ("bf16", 1e-2)])
+def test_shifted_low_precision_drag(orc, imb, storage, tol):
+    w = W.c1(steps=2000)
+    o, g = _run_pair(orc, imb, w, w.steps, storage=storage)
+    Fo, _ = o.forces()
+    Fg, _ = g.forces()
+    assert abs(Fg[0, 0] - Fo[0, 0]) / abs(Fo[0, 0]) < tol
+
+
+def test_mass_conserved_on_gpu(imb):
+    w = W.c3sub(steps=0, nx=128, ny=96).with_(bc_y=W.BC_PERIODIC, tau=0.53)
+    g = imb.Lattice.from_workload(w)
+    m0 = g.macro()[0].sum()
+    g.step(1000)
+    assert abs(g.macro()[0].sum() - m0) / m0 < 1e-6   # FP32 storage of f - w
+
+
+# ----------------------------------------------------------------- error paths
+def test_invalid_arguments(imb):
+    with pytest.raises(imb.ImbError) as e:
+        imb.Lattice(2, 10, 0.6)
+    assert e.value.code == -1
+    with pytest.raises(imb.ImbError):
+        imb.Lattice(10, 10, 0.5)
+    lat = imb.Lattice(64, 64, 0.6)
+    with pytest.raises(imb.ImbError):
+        lat.set_particles([[10.0, 10.0]], [[0, 0]], [0.0], [-1.0])
+    with pytest.raises(imb.ImbError):
+        lat.set_particles([[70.0, 10.0]], [[0, 0]], [0.0], [5.0])
+
+
+def test_mach_guard_reports_unstable(imb):
+    lat = imb.Lattice(64, 32, 0.6, bc_x=imb.BC_INLET_OUTLET, u_in_x=0.45)
+    with pytest.raises(imb.ImbError) as e:
+        lat.step(5)
+    assert e.value.code == -4
+
+
+def test_skin_violation_reported(imb):
+    # a lone particle crossing two cells in one coupling cycle breaks the neighbour-list skin
+    w = _pile(rows=1, cols=3, seed=3)
+    w = w.with_(nx=200, ny=100, x=np.array([[30.0, 60.0], [120.0, 8.0], [150.0, 8.0]]),
+                v=np.array([[2.0, 0.0], [0.0, 0.0], [0.0, 0.0]]), gravity=(0.0, 0.0))
+    lat = imb.Lattice.from_workload(w)
+    with pytest.raises(imb.ImbError) as e:
+        lat.dem_step(1)
+    assert e.value.code == -7
+
+
+def test_host_wait_is_bounded(imb):
+    # a 1 ms bound on a queued 4096^2 step returns IMB_E_TIMEOUT; the context stays usable
+    lat = imb.Lattice(4096, 4096, 0.6, timeout_ms=1)
+    lat.step_async(50)
+    with pytest.raises(imb.ImbError) as e:
+        lat.sync()
+    assert e.value.code == -6
+    import time
+    for _ in range(600):
+        try:
+            lat.sync()
+            break
+        except imb.ImbError:
+            time.sleep(0.05)
+    lat.sync()
