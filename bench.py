@@ -56,14 +56,19 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--nx", type=int, default=None, help="smaller lattice at the same disk density")
+    ap.add_argument("--ny", type=int, default=None)
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, nx=None, ny=None):
     if name == "c1":
         return W.c1()
     if name == "c2":
         return W.c2()
+    if nx or ny:
+        nx, ny = nx or 8192, ny or 4096
+        return W.c3(n=int(round(20000 * nx * ny / (8192 * 4096))), nx=nx, ny=ny)
     return W.c3()
 
 
@@ -243,7 +248,7 @@ def run_reference(args):
     rank, world, _ = dist_init(args.gpus)
     if rank != 0:
         return
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.nx, args.ny)
     mlups, cpu = time_oracle(target_s=max(5.0, min(60.0, 0.05 * (args.steps + args.warmup))))
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -262,7 +267,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     import paper_1809_07008_gb300 as imb
     imb.load()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.nx, args.ny)
     lat = imb.Lattice.from_workload(w, storage=args.storage)
     ts = torch.cuda.Stream()
     lat.set_stream(ts.cuda_stream)

@@ -194,9 +194,11 @@ def test_moving_particles_coupled_parity(orc, imb):
     Fg, Tg = g.forces()
     errF, errT = _force_ok(Fg, Tg, Fo, To, w.r)
     assert errF < 1e-4 and errT < 1e-4
+    # trajectories: the 1e-4 force tolerance integrated over 300 steps allows ~1e-6 cells
     xo, _, _ = o.particles()
     xg, _, _ = g.particles()
-    assert np.abs(xo - xg).max() < 1e-9
+    assert np.abs(xo - w.x).max() > 0.5
+    assert np.abs(xo - xg).max() < 1e-5
 
 
 @pytest.mark.parametrize("storage,tol", [("fp16", 1e-2), ("bf16", 1e-2)])
