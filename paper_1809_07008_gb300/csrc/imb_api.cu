@@ -11,6 +11,9 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/imblbm.h"
 #include "imb_device.cuh"
 #include "imb_kernels.h"
@@ -43,6 +46,11 @@ struct imb_ctx {
     int *bin_count = nullptr, *bin_fill = nullptr, *bin_start = nullptr, *bin_ids = nullptr;
     GridBarrier *barrier = nullptr;
     unsigned *err = nullptr;
+    TileCand *tiles = nullptr;      // per 32 x 32 tile: particles that can reach it
+    float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
+    size_t eps_tab_cap = 0;
+    int tab_w = 0, tab_h = 0;
+    CUtensorMap tmap[2];            // TMA descriptors of the two population buffers
     // parameters derived on the host
     double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
     // timing / accounting
@@ -113,6 +121,7 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.bc_y = c->p.bc_y;
     a.plane = c->plane;
     a.tau = (float)c->tau;
+    a.omega0 = (float)(1.0 / c->tau);
     a.smag_coef = (float)(18.0 * std::sqrt(2.0) * c->C_smag * c->C_smag);
     a.Fx = (float)c->p.Fx;
     a.Fy = (float)c->p.Fy;
@@ -126,6 +135,10 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.bin_start = c->bin_start;
     a.bin_ids = c->bin_ids;
     a.prec = c->prec;
+    a.eps_tab = c->eps_tab;
+    a.tab_w = c->tab_w;
+    a.tab_h = c->tab_h;
+    a.tab_stride = c->tab_w * c->tab_w;
     a.F = c->F;
     a.T = c->T;
     a.err = c->err;
@@ -206,9 +219,37 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->counters);
     dfree(c->barrier);
     dfree(c->err);
+    dfree(c->tiles);
+    dfree(c->eps_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
+}
+
+// TMA descriptor of one population buffer: a 3D tensor (x over the padded row,
+// y, plane) read in boxes of (32 + 2 halo) x 32 x 1 elements.
+static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const CUtensorMapDataType dt = c->p.storage == IMB_STORE_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->p.storage == IMB_STORE_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, 9};
+    cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->elem, (cuuint64_t)c->plane * c->elem};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage), (cuuint32_t)TILE, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(map, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, double C_smag,
@@ -263,8 +304,12 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
             return bail(e, "population buffers");
     if ((e = dalloc(&c->bin_count, c->nbins)) != cudaSuccess || (e = dalloc(&c->bin_fill, c->nbins)) != cudaSuccess ||
         (e = dalloc(&c->bin_start, c->nbins + 1)) != cudaSuccess || (e = dalloc(&c->counters, 2)) != cudaSuccess ||
-        (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess)
+        (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
+        (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
+    cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
+    for (int b = 0; b < 2; ++b)
+        if ((e = make_tensor_map(c, c->fbuf[b], &c->tmap[b])) != cudaSuccess) return bail(e, "TMA descriptor");
     cudaMemsetAsync(c->bin_count, 0, sizeof(int) * c->nbins, c->stream);
     cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * c->nbins, c->stream);
     cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (c->nbins + 1), c->stream);
@@ -285,7 +330,10 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
 
 // rebuild bins and the lattice particle records for the current positions
 static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
-    if (c->np == 0) return IMB_OK;
+    if (c->np == 0) {
+        CK(cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream), "clear tile lists");
+        return IMB_OK;
+    }
     CK(launch_particle_table(c->x, c->r, x_start, c->np, c->nx, c->ny, c->p.bc_x, c->p.bc_y,
                              0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
                              c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
@@ -293,7 +341,8 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
     CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->counters, c->stream),
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
-    c->launches += 3;
+    CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
+    c->launches += 4;
     return IMB_OK;
 }
 
@@ -312,9 +361,10 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
     }
     if (c->p.dem_on && 2.0 * rmax + c->p.skin > (double)TILE)
         return fail(c, IMB_E_INVALID_ARG, "DEM needs 2 r_max + skin <= 32 cells");
-    if ((c->p.bc_x == IMB_BC_PERIODIC && c->nx < 2.0 * rmax + 4.0) ||
-        (c->p.bc_y == IMB_BC_PERIODIC && c->ny < 2.0 * rmax + 4.0))
-        return fail(c, IMB_E_INVALID_ARG, "periodic extent must exceed 2 r_max + 4");
+    // a periodic axis must be long enough that a tile sees a single image of a disk
+    if (n > 0 && ((c->p.bc_x == IMB_BC_PERIODIC && c->nx < 2.0 * (TILE + rmax + 2.0)) ||
+                  (c->p.bc_y == IMB_BC_PERIODIC && c->ny < 2.0 * (TILE + rmax + 2.0))))
+        return fail(c, IMB_E_INVALID_ARG, "periodic extent must be at least 2 (32 + r_max + 2) cells");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(c->stream), "sync");
     if (n > c->cap) {
@@ -344,6 +394,20 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
     }
     c->np = n;
     c->r_max = rmax;
+    {
+        const int th = (int)std::ceil(rmax) + 1, tw = 2 * th + 1;
+        const size_t need = (size_t)std::max(n, 1) * tw * tw;
+        if (need > c->eps_tab_cap) {
+            dfree(c->eps_tab);
+            c->eps_tab = nullptr;
+            c->eps_tab_cap = 0;
+            cudaError_t e = dalloc(&c->eps_tab, need);
+            if (e != cudaSuccess) return cuda_fail(c, e, "solid-ratio table");
+            c->eps_tab_cap = need;
+        }
+        c->tab_h = th;
+        c->tab_w = tw;
+    }
     if (n > 0) {
         std::vector<double> m(n), I(n);
         for (int i = 0; i < n; ++i) {
@@ -410,7 +474,8 @@ static int lattice_step(imb_ctx *c) {
         c->ev_used += 2;
         CK(cudaEventRecord(e0, c->stream), "event record");
     }
-    CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, c->stream),
+    CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur],
+                             c->tiles, c->stream),
        "stream-collide");
     c->launches++;
     if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");

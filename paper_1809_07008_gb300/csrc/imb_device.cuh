@@ -37,6 +37,7 @@ enum : unsigned {
     ERR_NEIGHBOURS = 8u,     // DEM neighbour list full
     ERR_SKIN = 16u,          // a particle moved more than skin/2 in one coupling cycle
     ERR_BARRIER = 32u,       // a bounded grid barrier gave up
+    ERR_TMA = 64u,           // a bounded wait on a TMA / bulk copy gave up
 };
 
 constexpr int TILE = 32;        // stream-collide tile edge == bin edge (cells)
@@ -53,11 +54,15 @@ struct __align__(16) PRec {
     float r, vx, vy, w;
 };
 
-struct LatticeGeom {
-    int nx, ny, pitch;       // pitch = row stride in elements (multiple of 32)
-    int bc_x, bc_y;
-    size_t plane;            // elements per population plane = pitch * ny
+// Particles that can reach one 32 x 32 tile, ascending id (built by k_tile_lists,
+// bulk-copied into shared memory by the stream-collide kernel).
+struct __align__(16) TileCand {
+    int n;
+    int pad[3];
+    int id[TILE_CAND];
+    PRec p[TILE_CAND];
 };
+static_assert(sizeof(TileCand) % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ int wrap_rel(int d, int L, bool periodic) {
@@ -84,6 +89,20 @@ __device__ __forceinline__ bool covers(float lox, float loy, float r) {
     float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
     float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     return d2 < __fmul_rn(r, r);
+}
+
+// Is the whole cell inside the disk?  Farthest corner within the circle, every
+// operation rounded separately (the same decision wherever it is taken).
+__device__ __forceinline__ bool fully_covered(float lox, float loy, float r) {
+    const float fx = fmaxf(fabsf(lox), fabsf(__fadd_rn(lox, 1.0f)));
+    const float fy = fmaxf(fabsf(loy), fabsf(__fadd_rn(loy, 1.0f)));
+    return __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)) <= __fmul_rn(r, r);
+}
+
+// 0: the disk does not reach into the cell, 1: it covers part of it, 2: all of it.
+__device__ __forceinline__ int cover_state(float lox, float loy, float r) {
+    if (!covers(lox, loy, r)) return 0;
+    return fully_covered(lox, loy, r) ? 2 : 1;
 }
 
 // asin(s) - s sqrt(1 - s^2): twice the area of the circular segment of a unit circle
@@ -155,8 +174,7 @@ __device__ __forceinline__ float cell_disk_area(float lox, float loy, float r) {
     if (fabsf(x0 + 0.5f) > fabsf(y0 + 0.5f)) { float t = x0; x0 = y0; y0 = t; }
     if (y0 + 0.5f < 0.0f) y0 = -y0 - 1.0f;
     float x1 = x0 + 1.0f, y1 = y0 + 1.0f;
-    float fxm = fmaxf(fabsf(x0), fabsf(x1)), fym = fmaxf(fabsf(y0), fabsf(y1));
-    if (fxm * fxm + fym * fym <= r * r) return 1.0f;
+    if (fully_covered(lox, loy, r)) return 1.0f;
     float a0 = fmaxf(x0, -r), a1 = fminf(x1, r);
     if (!(a1 > a0)) return 0.0f;
     float A = strip_under_arc(a0, a1, y0, y1, r);
@@ -185,16 +203,19 @@ __device__ __forceinline__ float cell_subcell_ratio(float lox, float loy, float 
 template <typename S> struct Store;
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
         return __bfloat162float(__ldg(p));
     }
+    static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
@@ -236,6 +257,59 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *b, unsigned nblocks, u
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// --------------------------------------------- mbarrier / TMA primitives
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// 3D tiled TMA load of one box into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+// untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 }  // namespace imb

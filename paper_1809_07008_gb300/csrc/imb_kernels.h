@@ -2,19 +2,22 @@
 // library; the public interface is include/imblbm.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 namespace imb {
 
 struct PRec;
+struct TileCand;
 struct GridBarrier;
 
 // Everything the lattice kernels read about the lattice and the particles.
 struct LatticeArgs {
     int nx, ny, pitch, bc_x, bc_y;
     size_t plane;
-    float tau, smag_coef;      // smag_coef = 18 sqrt(2) C^2 (0 switches the model off)
+    float tau, omega0;         // relaxation time and 1 / tau
+    float smag_coef;           // 18 sqrt(2) C^2 (0 switches the Smagorinsky model off)
     float Fx, Fy;              // body force density (0, 0 = no forcing)
     float u_in_x, u_in_y;
     int eps_mode, n_sub;
@@ -23,6 +26,8 @@ struct LatticeArgs {
     const int *bin_start;      // [nbx*nby + 1]
     const int *bin_ids;        // [np]
     const PRec *prec;          // [np]
+    float *eps_tab;            // [np * tab_stride] solid ratios of partially covered cells
+    int tab_w, tab_h, tab_stride; // table row width 2 th + 1, half width th, floats per particle
     double *F;                 // [2 np] hydrodynamic force accumulators
     double *T;                 // [np]   hydrodynamic torque accumulators
     unsigned *err;
@@ -54,7 +59,9 @@ struct DemArgs {
 cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, float rho0, float ux0,
                                     float uy0, cudaStream_t s);
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
-                                  cudaStream_t s);
+                                  const CUtensorMap *tmap_in, const TileCand *tiles, cudaStream_t s);
+cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
+int tma_box_width(int storage);
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s);
 cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);

@@ -13,6 +13,7 @@
 //
 // A block owns one 32 x 32 tile, which is also one bin of the particle grid, so
 // the particles that can reach the tile sit in the 3 x 3 surrounding bins.
+#include <algorithm>
 #include <type_traits>
 
 #include "imb_device.cuh"
@@ -114,12 +115,12 @@ __device__ __forceinline__ float tile_gap(int dc, float frac, int L, bool period
     return g;
 }
 
-// Collect (ascending id) the particles whose disk can reach into tile (bx, by), and
-// per tile row a bit mask of the candidates whose y-extent meets that row.
-__device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared &sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Collect (ascending id, into sh.id / sh.p) the particles whose disk can reach into
+// tile (bx, by).  Executed by one full warp; returns the count (warp-uniform).
+__device__ int gather_tile_candidates(const LatticeArgs &a, int bx, int by, TileShared &sh) {
+    const int lane = threadIdx.x & 31;
     const bool perx = a.bc_x == BC_PERIODIC, pery = a.bc_y == BC_PERIODIC;
-    if (warp == 0) {
+    {
         int bidx = -1;
         if (lane < 9) {
             int ix = bx + (lane % 3) - 1, iy = by + (lane / 3) - 1;
@@ -198,7 +199,19 @@ __device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared
             sh.id[rank] = myid;
             sh.p[rank] = myp;
         }
-        if (lane == 0) sh.nc = nc;
+        __syncwarp();
+        return nc;
+    }
+}
+
+// gather_tile_candidates by warp 0, then per tile row a bit mask of the candidates
+// whose y-extent meets that row (whole block).
+__device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared &sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool pery = a.bc_y == BC_PERIODIC;
+    if (warp == 0) {
+        const int n = gather_tile_candidates(a, bx, by, sh);
+        if (lane == 0) sh.nc = n;
     }
     __syncthreads();
     const int nc = sh.nc;
@@ -227,175 +240,112 @@ __device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared
 }
 
 // ------------------------------------------------- fused stream-collide
-template <typename S>
-__global__ void __launch_bounds__(BLOCK)
-k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a) {
-    __shared__ TileShared sh;
-    __shared__ float s_part[WARPS][TILE_CAND][3];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx = blockIdx.x, by = blockIdx.y;
-    const int x0 = bx * TILE, y0 = by * TILE;
-    int nc = 0;
-    if (a.np > 0) {
-        tile_candidates(a, bx, by, sh);
-        nc = sh.nc;
-        for (int i = threadIdx.x; i < WARPS * TILE_CAND * 3; i += BLOCK) (&s_part[0][0][0])[i] = 0.0f;
-        __syncthreads();
-    }
-    const bool perx = a.bc_x == BC_PERIODIC, pery = a.bc_y == BC_PERIODIC;
-    const bool interior = x0 >= 1 && x0 + TILE <= a.nx - 1 && y0 >= 1 && y0 + TILE <= a.ny - 1;
-    const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
-    const bool smag = a.smag_coef > 0.0f;
-    const int x = x0 + lane;
-    const bool xin = x < a.nx;
-    bool unstable = false;
+// Solid ratio of the cell at offset (di, dk) from the centre cell of tile candidate
+// P: 0 when the disk does not reach in, 1 when the cell is fully covered (exact-area
+// mode), else the value that k_particle_eps stored for this particle and offset.
+__device__ __forceinline__ float cand_eps(const PRec &P, int di, int dk, const float *__restrict__ tab,
+                                          int tw, int th, bool exact, bool &covered) {
+    const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
+    const int st = cover_state(lox, loy, P.r);
+    covered = st != 0;
+    if (st == 0) return 0.0f;
+    if (st == 2 && exact) return 1.0f;
+    return __ldg(tab + (dk + th) * tw + (di + th));
+}
 
-    for (int rr = 0; rr < TILE / WARPS; ++rr) {
-        const int y = y0 + warp + WARPS * rr;
-        if (y >= a.ny) break;
-        float d[9];
-        if (xin) {
-            if (interior) pull_interior(fin, a, x, y, d);
-            else pull_cell(fin, a, x, y, d);
-        } else {
+// Per-row body shared by every tile kind: d[] holds the post-stream populations of
+// node (x, y) (f_i - w_i); the row's candidate particles are cand[] (mask bits), with
+// centres relative to the tile (cand[s].ci, .cj) and table rows ctab[s].
+// Collides, stores, and adds the per-particle force/torque of this warp row into
+// part[s][0..2] (lane 0, warp-private).
+template <typename S>
+__device__ __forceinline__ void collide_store_row(float (&d)[9], const int lane, const int yy, const int x,
+                                                  const int y, const bool xin, const unsigned mask,
+                                                  const PRec *__restrict__ cand, const int *__restrict__ cid,
+                                                  float (*part)[3], S *__restrict__ fout,
+                                                  const LatticeArgs &a, const bool forced, const bool smag,
+                                                  bool &unstable) {
+    // ---- moments (Eqs. 3-4, Guo half-force shift)
+    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const float rho = 1.0f + drho;
+    float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    if (forced) {
+        jx = fmaf(0.5f, a.Fx, jx);
+        jy = fmaf(0.5f, a.Fy, jy);
+    }
+    const float inv = __fdividef(1.0f, rho);
+    const float ux = jx * inv, uy = jy * inv;
+    const float usq = ux * ux + uy * uy;
+    if (xin && !(usq < 0.09f)) unstable = true;       // Mach guard, also catches NaN
+    // ---- non-equilibrium parts (Eq. 2)
+    float n[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) d[q] = 0.0f;
-        }
-        // ---- moments (Eqs. 3-4, Guo half-force shift)
-        float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-        const float rho = 1.0f + drho;
-        float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-        float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-        if (forced) {
-            jx = fmaf(0.5f, a.Fx, jx);
-            jy = fmaf(0.5f, a.Fy, jy);
-        }
-        const float inv = 1.0f / rho;
-        const float ux = jx * inv, uy = jy * inv;
-        const float usq = ux * ux + uy * uy;
-        if (xin && !(usq < 0.09f)) unstable = true;       // Mach guard, also catches NaN
-        // ---- non-equilibrium parts (Eq. 2)
-        float n[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
-            n[q] = d[q] - w_of(q) * (drho + rho * (cu * (3.0f + 4.5f * cu) - 1.5f * usq));
-        }
-        // ---- Smagorinsky effective relaxation time (Hou et al. 1996 closure)
-        float te = a.tau;
-        if (smag) {
-            const float pxx = (n[1] + n[3]) + (n[5] + n[6]) + (n[7] + n[8]);
-            const float pyy = (n[2] + n[4]) + (n[5] + n[6]) + (n[7] + n[8]);
-            const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
-            const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
-            te = 0.5f * (a.tau + sqrtf(a.tau * a.tau + a.smag_coef * sqrtf(Q) * inv));
-        }
-        const float omega = 1.0f / te;
-        // ---- immersed moving boundary: solid ratio, B, solid velocity moments
-        float B = 0.0f;
-        float m1x = 0.0f, m1y = 0.0f, m2xx = 0.0f, m2xy = 0.0f, m2yy = 0.0f;
-        int c0 = -1, c1 = -1, c2 = -1, c3 = -1;
-        float fx0 = 0.f, fy0 = 0.f, t0 = 0.f, fx1 = 0.f, fy1 = 0.f, t1 = 0.f;
-        float fx2 = 0.f, fy2 = 0.f, t2 = 0.f, fx3 = 0.f, fy3 = 0.f, t3 = 0.f;
-        const unsigned mask = nc ? sh.rowmask[y - y0] : 0u;
-        if (mask) {
-            int ns = 0;
-            float esum = 0.0f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-            unsigned m = mask;
-            while (m) {
-                const int s = __ffs(m) - 1;
-                m &= m - 1u;
-                if (!xin) continue;
-                const PRec P = sh.p[s];
-                const int di = wrap_rel(x - P.ci, a.nx, perx), dk = wrap_rel(y - P.cj, a.ny, pery);
-                const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
-                if (!covers(lox, loy, P.r)) continue;
-                const float e = a.eps_mode == EPS_EXACT ? cell_disk_area(lox, loy, P.r)
-                                                        : cell_subcell_ratio(lox, loy, P.r, a.n_sub);
-                if (ns == 0) { c0 = s; e0 = e; }
-                else if (ns == 1) { c1 = s; e1 = e; }
-                else if (ns == 2) { c2 = s; e2 = e; }
-                else if (ns == 3) { c3 = s; e3 = e; }
-                else { set_err(a.err, ERR_CELL_SLOTS); continue; }
-                ++ns;
+    for (int q = 0; q < 9; ++q) {
+        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        n[q] = d[q] - w_of(q) * (drho + rho * (cu * (3.0f + 4.5f * cu) - 1.5f * usq));
+    }
+    // ---- Smagorinsky effective relaxation time (Hou et al. 1996 closure)
+    float omega = a.omega0;
+    float te = a.tau;
+    if (smag) {
+        const float pxx = (n[1] + n[3]) + (n[5] + n[6]) + (n[7] + n[8]);
+        const float pyy = (n[2] + n[4]) + (n[5] + n[6]) + (n[7] + n[8]);
+        const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
+        const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
+        const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;          // sqrt(Q)
+        const float disc = fmaf(a.smag_coef * sq, inv, a.tau * a.tau);
+        te = 0.5f * (a.tau + disc * rsqrtf(disc));                  // (tau + sqrt(disc)) / 2
+        omega = __fdividef(1.0f, te);
+    }
+    // ---- immersed moving boundary (Sec. 2.3): total solid ratio of the node, then
+    // per-particle weights B_p = B eps_p / sum eps, solid-velocity moments, force
+    float B = 0.0f;
+    float m1x = 0.0f, m1y = 0.0f, m2xx = 0.0f, m2xy = 0.0f, m2yy = 0.0f;
+    if (mask) {
+        const bool exact = a.eps_mode == EPS_EXACT;
+        float esum = 0.0f;
+        int ns = 0;
+        for (unsigned m = mask; m; m &= m - 1u) {
+            const int s = __ffs(m) - 1;
+            const PRec &P = cand[s];
+            bool cov;
+            const float e = cand_eps(P, lane - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride,
+                                     a.tab_w, a.tab_h, exact, cov);
+            if (xin && cov) {
                 esum += e;
-            }
-            if (ns > 0 && esum > 0.0f) {
-                const float eps = fminf(esum, 1.0f);
-                const float tm = te - 0.5f;
-                B = eps * tm / ((1.0f - eps) + tm);                 // Eq. 14
-                const float Bs = B / esum;
-#pragma unroll
-                for (int k = 0; k < MAX_SLOTS; ++k) {
-                    const int ck = k == 0 ? c0 : (k == 1 ? c1 : (k == 2 ? c2 : c3));
-                    const float ek = k == 0 ? e0 : (k == 1 ? e1 : (k == 2 ? e2 : e3));
-                    if (ck < 0) continue;
-                    const PRec P = sh.p[ck];
-                    const int di = wrap_rel(x - P.ci, a.nx, perx), dk = wrap_rel(y - P.cj, a.ny, pery);
-                    const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
-                    const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
-                    const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
-                    const float Bp = Bs * ek;
-                    m1x += Bp * usx;
-                    m1y += Bp * usy;
-                    m2xx += Bp * usx * usx;
-                    m2xy += Bp * usx * usy;
-                    m2yy += Bp * usy * usy;
-                    // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F)
-                    const float fxk = Bp * (jx - rho * usx - a.Fx);
-                    const float fyk = Bp * (jy - rho * usy - a.Fy);
-                    const float tk = rx * fyk - ry * fxk;              // Eq. 16 (z)
-                    if (k == 0) { fx0 = fxk; fy0 = fyk; t0 = tk; }
-                    else if (k == 1) { fx1 = fxk; fy1 = fyk; t1 = tk; }
-                    else if (k == 2) { fx2 = fxk; fy2 = fyk; t2 = tk; }
-                    else { fx3 = fxk; fy3 = fyk; t3 = tk; }
-                }
+                ++ns;
             }
         }
-        // ---- collision and store (Eq. 13): fluid part weighted 1 - B, solid part by B
-        if (xin) {
-            const float fl = 1.0f - B;
-            const float sf = 1.0f - 0.5f * omega;
-            S *outp = fout + (size_t)y * a.pitch + x;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-                float upd = -omega * n[q];
-                if (forced) {  // Guo forcing term
-                    const float cu = cxq * ux + cyq * uy;
-                    const float S_q = w_of(q) * (3.0f * ((cxq - ux) * a.Fx + (cyq - uy) * a.Fy) +
-                                                 9.0f * cu * (cxq * a.Fx + cyq * a.Fy));
-                    upd = fmaf(sf, S_q, upd);
-                }
-                upd *= fl;
-                if (B > 0.0f) {
-                    // Eq. 12 summed over the covering particles:
-                    // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u))
-                    const float cu = cxq * ux + cyq * uy;
-                    const float cm1 = cxq * m1x + cyq * m1y;
-                    const float cm2c = cxq * cxq * m2xx + 2.0f * cxq * cyq * m2xy + cyq * cyq * m2yy;
-                    const float dfeq = rho * w_of(q) *
-                                       (3.0f * (cm1 - B * cu) + 4.5f * (cm2c - B * cu * cu) -
-                                        1.5f * ((m2xx + m2yy) - B * usq));
-                    upd += B * (n[opp_of(q)] - n[q]) + dfeq;
-                }
-                Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);
-            }
+        if (ns > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
+        if (esum > 0.0f) {
+            const float eps = fminf(esum, 1.0f);
+            const float tm = te - 0.5f;
+            B = eps * tm / ((1.0f - eps) + tm);                 // Eq. 14
         }
-        // ---- per-particle force / torque: warp reduction per candidate of this row
-        if (mask) {
-            unsigned m = mask;
-            while (m) {
+        if (__any_sync(FULL, B > 0.0f)) {
+            const float Bs = B > 0.0f ? B / esum : 0.0f;
+            for (unsigned m = mask; m; m &= m - 1u) {
                 const int s = __ffs(m) - 1;
-                m &= m - 1u;
-                const bool mine = c0 == s || c1 == s || c2 == s || c3 == s;
-                if (!__any_sync(FULL, mine && B > 0.0f)) continue;
-                float vx = (c0 == s ? fx0 : 0.f) + (c1 == s ? fx1 : 0.f) + (c2 == s ? fx2 : 0.f) +
-                           (c3 == s ? fx3 : 0.f);
-                float vy = (c0 == s ? fy0 : 0.f) + (c1 == s ? fy1 : 0.f) + (c2 == s ? fy2 : 0.f) +
-                           (c3 == s ? fy3 : 0.f);
-                float vt = (c0 == s ? t0 : 0.f) + (c1 == s ? t1 : 0.f) + (c2 == s ? t2 : 0.f) +
-                           (c3 == s ? t3 : 0.f);
+                const PRec &P = cand[s];
+                const int di = lane - P.ci, dk = yy - P.cj;
+                bool cov;
+                const float e = cand_eps(P, di, dk, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w,
+                                         a.tab_h, exact, cov);
+                const float Bp = (xin && cov) ? Bs * e : 0.0f;
+                const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
+                const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
+                const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
+                m1x += Bp * usx;
+                m1y += Bp * usy;
+                m2xx += Bp * usx * usx;
+                m2xy += Bp * usx * usy;
+                m2yy += Bp * usy * usy;
+                if (!__any_sync(FULL, Bp > 0.0f)) continue;
+                // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
+                float vx = Bp * (jx - rho * usx - a.Fx);
+                float vy = Bp * (jy - rho * usy - a.Fy);
+                float vt = rx * vy - ry * vx;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     vx += __shfl_xor_sync(FULL, vx, o);
@@ -403,27 +353,251 @@ k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const LatticeA
                     vt += __shfl_xor_sync(FULL, vt, o);
                 }
                 if (lane == 0) {
-                    s_part[warp][s][0] += vx;
-                    s_part[warp][s][1] += vy;
-                    s_part[warp][s][2] += vt;
+                    part[s][0] += vx;
+                    part[s][1] += vy;
+                    part[s][2] += vt;
                 }
             }
         }
     }
-    if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
-    if (nc) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < nc * 3; t += BLOCK) {
-            const int s = t / 3, c = t - 3 * s;
+    // ---- collision and store (Eq. 13): fluid part weighted 1 - B, solid part by B
+    if (xin) {
+        const float fl = 1.0f - B;
+        const float sf = 1.0f - 0.5f * omega;
+        // Eq. 12 summed over the covering particles:
+        // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u)), with
+        // sum_p B_p f^eq_q(u_s,p) - B f^eq_q(u) = rho w_q (3 c.A1 + 4.5 c.A2.c - 1.5 tr A2)
+        const float a1x = m1x - B * ux, a1y = m1y - B * uy;
+        const float a2xx = m2xx - B * ux * ux, a2yy = m2yy - B * uy * uy, a2xy = m2xy - B * ux * uy;
+        const float tra2 = a2xx + a2yy;
+        S *outp = fout + (size_t)y * a.pitch + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
+            float upd = -omega * n[q];
+            if (forced) {  // Guo forcing term
+                const float cu = cxq * ux + cyq * uy;
+                const float S_q = w_of(q) * (3.0f * ((cxq - ux) * a.Fx + (cyq - uy) * a.Fy) +
+                                             9.0f * cu * (cxq * a.Fx + cyq * a.Fy));
+                upd = fmaf(sf, S_q, upd);
+            }
+            upd *= fl;
+            if (B > 0.0f) {
+                const float ca1 = cxq * a1x + cyq * a1y;
+                const float ca2c = cxq * cxq * a2xx + 2.0f * cxq * cyq * a2xy + cyq * cyq * a2yy;
+                upd += B * (n[opp_of(q)] - n[q]) + rho * w_of(q) * (3.0f * ca1 + 4.5f * ca2c - 1.5f * tra2);
+            }
+            Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);
+        }
+    }
+}
+
+// Row mask: bit s set when candidate s can cover a cell of tile row yy (dy_near^2 <
+// r^2, the same rounding as covers(), hence a necessary condition).  Lane-parallel.
+__device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int nc, int yy, bool row_ok) {
+    const int lane = threadIdx.x & 31;
+    bool rel = false;
+    if (lane < nc && row_ok) {
+        const PRec &P = cand[lane];
+        const float loy = __fsub_rn((float)(yy - P.cj), P.fy);
+        const float hiy = __fadd_rn(loy, 1.0f);
+        const float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
+        rel = __fmul_rn(dy, dy) < __fmul_rn(P.r, P.r);
+    }
+    return __ballot_sync(FULL, rel);
+}
+
+// TMA box geometry per storage type: the box starts HALO cells left of the tile so
+// that its x coordinate is 16-byte aligned, and spans the tile plus both halos.
+template <typename S> struct Box {
+    static constexpr int HALO = 16 / (int)sizeof(S);
+    static constexpr int W = TILE + 2 * HALO;
+    static constexpr int BYTES = W * TILE * (int)sizeof(S);
+    static constexpr int POP_BYTES = 9 * BYTES;
+    static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
+    static constexpr int PART_FLOATS = 2 * WARPS * TILE_CAND * 3;
+    static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + PART_FLOATS * 4 + 16;
+};
+static_assert(Box<float>::BYTES % 128 == 0 && Box<__half>::BYTES % 128 == 0, "TMA boxes stay 128-B aligned");
+
+__device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
+    // every neighbour read of the tile lies inside the lattice: no boundary rule applies
+    return bx >= 1 && by >= 1 && (bx + 1) * TILE <= nx - 1 && (by + 1) * TILE <= ny - 1;
+}
+
+// Persistent fused stream-collide.  Each block walks tiles t = blockIdx.x + k * gridDim.x.
+// Thread 0 keeps two tiles in flight: for interior tiles nine TMA boxes (one per
+// population plane, shifted by -c_i) plus the tile's candidate block; boundary tiles
+// take the candidate block only and pull their populations with the boundary rules.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 2)
+k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__ fin, S *__restrict__ fout,
+                 const LatticeArgs a, const TileCand *__restrict__ tiles, const int ntiles) {
+    using G = Box<S>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4);
+    float *part_base = reinterpret_cast<float *>(smem + 2 * G::STAGE_BYTES);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nbx = a.nbx;
+    const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
+    const bool smag = a.smag_coef > 0.0f;
+
+    for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part_base[i] = 0.0f;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto stage_pop = [&](int st) { return reinterpret_cast<S *>(smem + st * G::STAGE_BYTES); };
+    auto stage_cand = [&](int st) {
+        return reinterpret_cast<TileCand *>(smem + st * G::STAGE_BYTES + G::POP_BYTES);
+    };
+    auto issue = [&](int k, int st) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) return;
+        const int bx = t % nbx, by = t / nbx;
+        const bool in = tma_tile(bx, by, a.nx, a.ny);
+        mbar_arrive_expect_tx(&mbar[st], (uint32_t)sizeof(TileCand) + (in ? (uint32_t)G::POP_BYTES : 0u));
+        bulk_load(stage_cand(st), &tiles[t], (uint32_t)sizeof(TileCand), &mbar[st]);
+        if (in) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                tma_load_3d(stage_pop(st) + q * (G::W * TILE), &tmap, bx * TILE - G::HALO,
+                            by * TILE - cy_of(q), q, &mbar[st]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        issue(0, 0);
+        issue(1, 1);
+    }
+    bool unstable = false;
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int st = k & 1;
+        const bool ok = mbar_wait(&mbar[st], (uint32_t)((k >> 1) & 1));
+        const int bx = t % nbx, by = t / nbx;
+        const int x0 = bx * TILE, y0 = by * TILE;
+        const bool in = tma_tile(bx, by, a.nx, a.ny);
+        const TileCand *tc = stage_cand(st);
+        const int nc = ok ? min(tc->n, TILE_CAND) : 0;
+        const S *pop = stage_pop(st);
+        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + (st * WARPS + warp) * TILE_CAND * 3);
+        const int x = x0 + lane;
+        const bool xin = x < a.nx;
+#pragma unroll 1
+        for (int rr = 0; rr < TILE / WARPS; ++rr) {
+            const int yy = warp + WARPS * rr;
+            const int y = y0 + yy;
+            if (y >= a.ny) break;
+            float d[9];
+            if (in) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    d[q] = Store<S>::lds(pop + q * (G::W * TILE) + yy * G::W + lane + G::HALO - cx_of(q));
+            } else if (xin) {
+                pull_cell(fin, a, x, y, d);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) d[q] = 0.0f;
+            }
+            const unsigned mask = nc ? row_mask(tc->p, nc, yy, true) : 0u;
+            collide_store_row(d, lane, yy, x, y, xin, mask, tc->p, tc->id, part, fout, a, forced, smag,
+                              unstable);
+        }
+        // the threads that flush this tile's forces take their particle id before the
+        // stage is handed back to the copy engine
+        const int fid = threadIdx.x < nc * 3 ? tc->id[threadIdx.x / 3] : -1;
+        const int bad = __syncthreads_or(!ok);
+        if (threadIdx.x == 0 && !bad) {
+            fence_proxy_async_smem();
+            issue(k + 2, st);
+        }
+        if (fid >= 0) {
+            const int s = threadIdx.x / 3, c = threadIdx.x - 3 * s;
+            float *pb = part_base + st * WARPS * TILE_CAND * 3 + s * 3 + c;
             double acc = 0.0;
 #pragma unroll
-            for (int w = 0; w < WARPS; ++w) acc += (double)s_part[w][s][c];
+            for (int w = 0; w < WARPS; ++w) {
+                acc += (double)pb[w * TILE_CAND * 3];
+                pb[w * TILE_CAND * 3] = 0.0f;
+            }
             if (acc != 0.0) {
-                const int id = sh.id[s];
-                if (c < 2) atomicAdd(&a.F[2 * id + c], acc);
-                else atomicAdd(&a.T[id], acc);
+                if (c < 2) atomicAdd(&a.F[2 * fid + c], acc);
+                else atomicAdd(&a.T[fid], acc);
             }
         }
+        if (bad) {
+            if (threadIdx.x == 0) set_err(a.err, ERR_TMA);
+            break;
+        }
+    }
+    if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
+}
+
+// Per-tile candidate lists: one warp per tile gathers the particles of the 3 x 3
+// surrounding bins whose disk can reach the tile, in ascending id order.
+__global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCand *tiles, int ntiles) {
+    __shared__ TileShared sh[WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * WARPS + warp;
+    if (t >= ntiles) return;
+    const int bx = t % a.nbx, by = t / a.nbx;
+    const int nc = gather_tile_candidates(a, bx, by, sh[warp]);
+    TileCand *out = &tiles[t];
+    if (lane == 0) out->n = nc;
+    if (lane < nc) {
+        // centre cell relative to the tile origin, taking the periodic image nearest to
+        // the tile centre: cell offsets inside the tile are then lane - ci and row - cj
+        PRec P = sh[warp].p[lane];
+        const int xc = bx * TILE + TILE / 2, yc = by * TILE + TILE / 2;
+        P.ci = TILE / 2 - wrap_rel(xc - P.ci, a.nx, a.bc_x == BC_PERIODIC);
+        P.cj = TILE / 2 - wrap_rel(yc - P.cj, a.ny, a.bc_y == BC_PERIODIC);
+        out->id[lane] = sh[warp].id[lane];
+        out->p[lane] = P;
+    }
+}
+
+// The map step of the coupling cycle (Sec. 2.4) for the partially covered cells: one
+// block per particle lists the cells of its bounding box that the disk covers only in
+// part, then computes their solid ratios lane-compacted into the particle's table
+// (row dk + th, column di + th for the cell at offset (di, dk) from the centre cell).
+// In cell-decomposition mode fully covered cells are tabulated too.
+__global__ void __launch_bounds__(128) k_particle_eps(const PRec *__restrict__ prec, int np, int eps_mode,
+                                                      int n_sub, float *tab, int tw, int th, int stride) {
+    __shared__ short s_off[2][1024];
+    __shared__ int s_n;
+    const int p = blockIdx.x;
+    if (p >= np) return;
+    const PRec P = prec[p];
+    const bool exact = eps_mode == EPS_EXACT;
+    const int span = (int)ceilf(P.r) + 1;
+    const int side = 2 * span + 1;
+    float *out = tab + (size_t)p * stride;
+    for (int base = 0; base < side * side; base += 1024) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const int end = min(base + 1024, side * side);
+        for (int k = base + threadIdx.x; k < end; k += blockDim.x) {
+            const int di = k % side - span, dk = k / side - span;
+            const int st = cover_state(__fsub_rn((float)di, P.fx), __fsub_rn((float)dk, P.fy), P.r);
+            if (st == 1 || (st == 2 && !exact)) {
+                const int slot = atomicAdd(&s_n, 1);
+                s_off[0][slot] = (short)di;
+                s_off[1][slot] = (short)dk;
+            }
+        }
+        __syncthreads();
+        const int n = s_n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int di = s_off[0][k], dk = s_off[1][k];
+            const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
+            out[(dk + th) * tw + (di + th)] = exact ? cell_disk_area(lox, loy, P.r)
+                                                    : cell_subcell_ratio(lox, loy, P.r, n_sub);
+        }
+        __syncthreads();
     }
 }
 
@@ -527,14 +701,45 @@ cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, 
     });
 }
 
+template <typename S>
+static int stream_collide_grid(int ntiles) {
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(k_stream_collide<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Box<S>::SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<S>, BLOCK, Box<S>::SMEM_BYTES);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return std::min(ntiles, per_sm * sms);
+}
+
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
-                                  cudaStream_t s) {
+                                  const CUtensorMap *tmap_in, const TileCand *tiles, cudaStream_t s) {
+    const int ntiles = a.nbx * a.nby;
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        dim3 grid((a.nx + TILE - 1) / TILE, (a.ny + TILE - 1) / TILE);
-        k_stream_collide<S><<<grid, BLOCK, 0, s>>>((const S *)fin, (S *)fout, a);
+        const int grid = stream_collide_grid<S>(ntiles);
+        k_stream_collide<S><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(*tmap_in, (const S *)fin, (S *)fout, a,
+                                                                   tiles, ntiles);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s) {
+    const int ntiles = a.nbx * a.nby;
+    k_tile_lists<<<(ntiles + WARPS - 1) / WARPS, BLOCK, 0, s>>>(a, tiles, ntiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.np == 0) return e;
+    k_particle_eps<<<a.np, 128, 0, s>>>(a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h,
+                                       a.tab_stride);
+    return cudaGetLastError();
+}
+
+int tma_box_width(int storage) {
+    return storage == 0 ? Box<float>::W : Box<__half>::W;
 }
 
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,

@@ -71,31 +71,84 @@ __global__ void k_particle_table(const double *__restrict__ x, const double *__r
     }
 }
 
+// Exclusive scan of the bin counts by one block: warps reduce coalesced 32-bin
+// segments, the block scans the segment sums, warps write the prefixes back.
+// Also resets the counts and fill cursors (and the DEM list counters) for reuse.
 __global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *start, int nbins,
                                                    int *dem_counters) {
-    __shared__ int s[1024];
-    const int t = threadIdx.x;
-    const int chunk = (nbins + 1023) / 1024;
-    const int b0 = min(t * chunk, nbins), b1 = min(b0 + chunk, nbins);
-    int sum = 0;
-    for (int b = b0; b < b1; ++b) sum += count[b];
-    s[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int add = t >= o ? s[t - o] : 0;
+    __shared__ int seg[4096];
+    __shared__ int wsum[32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    const int nseg = (nbins + 31) / 32;
+    for (int base = 0; base < nseg; base += 4096) {
+        const int nchunk = min(4096, nseg - base);
+        for (int sg = warp; sg < nchunk; sg += 32) {
+            const int b = (base + sg) * 32 + lane;
+            int v = b < nbins ? count[b] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) seg[sg] = v;
+        }
         __syncthreads();
-        s[t] += add;
+        // block scan of the segment sums: each thread owns 4 consecutive segments
+        const int per = 4;
+        int loc[per], tot = 0;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int sg = threadIdx.x * per + k;
+            loc[k] = sg < nchunk ? seg[sg] : 0;
+            tot += loc[k];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        int run = carry + (warp ? wsum[warp - 1] : 0) + incl - tot;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int sg = threadIdx.x * per + k;
+            if (sg < nchunk) seg[sg] = run;
+            run += loc[k];
+        }
+        __syncthreads();
+        for (int sg = warp; sg < nchunk; sg += 32) {
+            const int b = (base + sg) * 32 + lane;
+            const int v = b < nbins ? count[b] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            if (b < nbins) {
+                start[b] = seg[sg] + x - v;
+                count[b] = 0;
+                fill[b] = 0;
+            }
+            if (b == nbins - 1) start[nbins] = seg[sg] + x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + wsum[31];
         __syncthreads();
     }
-    int run = s[t] - sum;
-    for (int b = b0; b < b1; ++b) {
-        start[b] = run;
-        run += count[b];
-        count[b] = 0;
-        fill[b] = 0;
-    }
-    if (t == 1023) start[nbins] = s[1023];
-    if (t == 0 && dem_counters) {
+    if (threadIdx.x == 0 && dem_counters) {
         dem_counters[0] = 0;
         dem_counters[1] = 0;
     }
@@ -250,10 +303,41 @@ __global__ void k_dem_free(const DemArgs d) {
         double xiw[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) xiw[k] = d.wall_xi[4 * p + k];
+        // without a wall contact the accelerations are the same every sub-cycle:
+        // evaluate them once, with exactly the operations integrate() would use
+        const double ax0 = (0.0 + d.F[2 * p]) / mp + d.gx_eff;
+        const double ay0 = (0.0 + d.F[2 * p + 1]) / mp + d.gy_eff;
+        const double al0 = (0.0 + d.T[p]) / d.I[p];
+        const bool walls = d.bc_x == BC_WALL || d.bc_y == BC_WALL;
         for (int s = 0; s < d.N_sub; ++s) {
-            double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
-            wall_contacts(d, p, px, py, vx, vy, w, rp, mp, xiw, Fcx, Fcy, Tc);
-            integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+            bool touching = false;
+            if (walls) {
+                const double m_ = rp;
+                touching = (d.bc_x == BC_WALL && (px < m_ || (double)d.nx - px < m_)) ||
+                           (d.bc_y == BC_WALL && (py < m_ || (double)d.ny - py < m_));
+            }
+            if (touching) {
+                double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+                wall_contacts(d, p, px, py, vx, vy, w, rp, mp, xiw, Fcx, Fcy, Tc);
+                integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+            } else {
+                // a released wall spring (wall_contacts would zero it)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
+                vx = vx + ax0 * d.dt;
+                vy = vy + ay0 * d.dt;
+                w = w + al0 * d.dt;
+                px = px + vx * d.dt;
+                py = py + vy * d.dt;
+                if (d.bc_x == BC_PERIODIC) {
+                    if (px >= d.nx) px -= d.nx;
+                    else if (px < 0.0) px += d.nx;
+                }
+                if (d.bc_y == BC_PERIODIC) {
+                    if (py >= d.ny) py -= d.ny;
+                    else if (py < 0.0) py += d.ny;
+                }
+            }
         }
         d.x[2 * p] = px;
         d.x[2 * p + 1] = py;
