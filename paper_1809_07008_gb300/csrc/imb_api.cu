@@ -302,17 +302,19 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     for (int b = 0; b < 2; ++b)
         if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess)
             return bail(e, "population buffers");
-    if ((e = dalloc(&c->bin_count, c->nbins)) != cudaSuccess || (e = dalloc(&c->bin_fill, c->nbins)) != cudaSuccess ||
-        (e = dalloc(&c->bin_start, c->nbins + 1)) != cudaSuccess || (e = dalloc(&c->counters, 2)) != cudaSuccess ||
+    // bin arrays padded to a multiple of 32 entries (the scan moves 16-byte vectors)
+    const int nbins_pad = (c->nbins + 31) / 32 * 32;
+    if ((e = dalloc(&c->bin_count, nbins_pad)) != cudaSuccess || (e = dalloc(&c->bin_fill, nbins_pad)) != cudaSuccess ||
+        (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 2)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
     cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
     for (int b = 0; b < 2; ++b)
         if ((e = make_tensor_map(c, c->fbuf[b], &c->tmap[b])) != cudaSuccess) return bail(e, "TMA descriptor");
-    cudaMemsetAsync(c->bin_count, 0, sizeof(int) * c->nbins, c->stream);
-    cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * c->nbins, c->stream);
-    cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (c->nbins + 1), c->stream);
+    cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins_pad, c->stream);
+    cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * nbins_pad, c->stream);
+    cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (nbins_pad + 32), c->stream);
     cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream);
     cudaMemsetAsync(c->barrier, 0, sizeof(GridBarrier), c->stream);
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);

@@ -253,141 +253,157 @@ __device__ __forceinline__ float cand_eps(const PRec &P, int di, int dk, const f
     return __ldg(tab + (dk + th) * tw + (di + th));
 }
 
-// Per-row body shared by every tile kind: d[] holds the post-stream populations of
-// node (x, y) (f_i - w_i); the row's candidate particles are cand[] (mask bits), with
-// centres relative to the tile (cand[s].ci, .cj) and table rows ctab[s].
-// Collides, stores, and adds the per-particle force/torque of this warp row into
-// part[s][0..2] (lane 0, warp-private).
-template <typename S>
-__device__ __forceinline__ void collide_store_row(float (&d)[9], const int lane, const int yy, const int x,
-                                                  const int y, const bool xin, const unsigned mask,
-                                                  const PRec *__restrict__ cand, const int *__restrict__ cid,
-                                                  float (*part)[3], S *__restrict__ fout,
-                                                  const LatticeArgs &a, const bool forced, const bool smag,
-                                                  bool &unstable) {
+// Macroscopic state of one node (Eqs. 2-4) and its relaxation rate.
+struct NodeState {
+    float drho, rho, jx, jy, ux, uy, usq, te, omega;
+    float n[9];   // non-equilibrium parts f_i - f_i^eq
+};
+
+__device__ __forceinline__ void node_state(const float (&d)[9], const LatticeArgs &a, const bool forced,
+                                           const bool smag, NodeState &c) {
     // ---- moments (Eqs. 3-4, Guo half-force shift)
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const float rho = 1.0f + drho;
-    float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    c.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    c.rho = 1.0f + c.drho;
+    c.jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    c.jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
     if (forced) {
-        jx = fmaf(0.5f, a.Fx, jx);
-        jy = fmaf(0.5f, a.Fy, jy);
+        c.jx = fmaf(0.5f, a.Fx, c.jx);
+        c.jy = fmaf(0.5f, a.Fy, c.jy);
     }
-    const float inv = __fdividef(1.0f, rho);
-    const float ux = jx * inv, uy = jy * inv;
-    const float usq = ux * ux + uy * uy;
-    if (xin && !(usq < 0.09f)) unstable = true;       // Mach guard, also catches NaN
+    const float inv = __fdividef(1.0f, c.rho);
+    c.ux = c.jx * inv;
+    c.uy = c.jy * inv;
+    c.usq = c.ux * c.ux + c.uy * c.uy;
     // ---- non-equilibrium parts (Eq. 2)
-    float n[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
-        n[q] = d[q] - w_of(q) * (drho + rho * (cu * (3.0f + 4.5f * cu) - 1.5f * usq));
+        const float cu = (float)cx_of(q) * c.ux + (float)cy_of(q) * c.uy;
+        c.n[q] = d[q] - w_of(q) * (c.drho + c.rho * (cu * (3.0f + 4.5f * cu) - 1.5f * c.usq));
     }
     // ---- Smagorinsky effective relaxation time (Hou et al. 1996 closure)
-    float omega = a.omega0;
-    float te = a.tau;
+    c.omega = a.omega0;
+    c.te = a.tau;
     if (smag) {
-        const float pxx = (n[1] + n[3]) + (n[5] + n[6]) + (n[7] + n[8]);
-        const float pyy = (n[2] + n[4]) + (n[5] + n[6]) + (n[7] + n[8]);
-        const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
+        const float pxx = (c.n[1] + c.n[3]) + (c.n[5] + c.n[6]) + (c.n[7] + c.n[8]);
+        const float pyy = (c.n[2] + c.n[4]) + (c.n[5] + c.n[6]) + (c.n[7] + c.n[8]);
+        const float pxy = (c.n[5] - c.n[6]) + (c.n[7] - c.n[8]);
         const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
         const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;          // sqrt(Q)
         const float disc = fmaf(a.smag_coef * sq, inv, a.tau * a.tau);
-        te = 0.5f * (a.tau + disc * rsqrtf(disc));                  // (tau + sqrt(disc)) / 2
-        omega = __fdividef(1.0f, te);
+        c.te = 0.5f * (a.tau + disc * rsqrtf(disc));                // (tau + sqrt(disc)) / 2
+        c.omega = __fdividef(1.0f, c.te);
     }
-    // ---- immersed moving boundary (Sec. 2.3): total solid ratio of the node, then
-    // per-particle weights B_p = B eps_p / sum eps, solid-velocity moments, force
-    float B = 0.0f;
-    float m1x = 0.0f, m1y = 0.0f, m2xx = 0.0f, m2xy = 0.0f, m2yy = 0.0f;
-    if (mask) {
-        const bool exact = a.eps_mode == EPS_EXACT;
-        float esum = 0.0f;
-        int ns = 0;
-        for (unsigned m = mask; m; m &= m - 1u) {
-            const int s = __ffs(m) - 1;
+}
+
+// Solid-velocity moments of the particles covering a node, weighted by B_p.
+struct SolidMoments {
+    float B, m1x, m1y, m2xx, m2xy, m2yy;
+};
+
+// Collision (Eq. 13) -- fluid part weighted 1 - B, solid part (Eq. 12 summed over the
+// covering particles) by B -- and store of the post-collision populations.
+template <typename S>
+__device__ __forceinline__ void node_collide_store(const float (&d)[9], const NodeState &c,
+                                                   const SolidMoments &sm, S *__restrict__ outp,
+                                                   const LatticeArgs &a, const bool forced) {
+    const float B = sm.B;
+    const float fl = 1.0f - B;
+    const float sf = 1.0f - 0.5f * c.omega;
+    // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u)), with
+    // sum_p B_p f^eq_q(u_s,p) - B f^eq_q(u) = rho w_q (3 c.A1 + 4.5 c.A2.c - 1.5 tr A2)
+    const float a1x = sm.m1x - B * c.ux, a1y = sm.m1y - B * c.uy;
+    const float a2xx = sm.m2xx - B * c.ux * c.ux, a2yy = sm.m2yy - B * c.uy * c.uy;
+    const float a2xy = sm.m2xy - B * c.ux * c.uy;
+    const float tra2 = a2xx + a2yy;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
+        float upd = -c.omega * c.n[q];
+        if (forced) {  // Guo forcing term
+            const float cu = cxq * c.ux + cyq * c.uy;
+            const float S_q = w_of(q) * (3.0f * ((cxq - c.ux) * a.Fx + (cyq - c.uy) * a.Fy) +
+                                         9.0f * cu * (cxq * a.Fx + cyq * a.Fy));
+            upd = fmaf(sf, S_q, upd);
+        }
+        upd *= fl;
+        if (B > 0.0f) {
+            const float ca1 = cxq * a1x + cyq * a1y;
+            const float ca2c = cxq * cxq * a2xx + 2.0f * cxq * cyq * a2xy + cyq * cyq * a2yy;
+            upd += B * (c.n[opp_of(q)] - c.n[q]) + c.rho * w_of(q) * (3.0f * ca1 + 4.5f * ca2c - 1.5f * tra2);
+        }
+        Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);
+    }
+}
+
+// Immersed moving boundary at one node (Sec. 2.3): the node at tile offset (xl, yy)
+// is covered by the candidates of `mask` (a subset of the warp-uniform `uni`).  Total
+// solid ratio -> B (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps ->
+// solid-velocity moments; the per-particle force and torque (Eqs. 15-16) are reduced
+// over the warp into part[s] (lane 0, warp-private).
+__device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned mask,
+                                         const unsigned uni, const bool act, const PRec *__restrict__ cand,
+                                         const int *__restrict__ cid, float (*part)[3], const LatticeArgs &a,
+                                         SolidMoments &sm) {
+    const int lane = threadIdx.x & 31;
+    const bool exact = a.eps_mode == EPS_EXACT;
+    sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
+    float esum = 0.0f;
+    int ns = 0;
+    for (unsigned m = uni; m; m &= m - 1u) {
+        const int s = __ffs(m) - 1;
+        if (!act || !((mask >> s) & 1u)) continue;
+        const PRec &P = cand[s];
+        bool cov;
+        const float e = cand_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w,
+                                 a.tab_h, exact, cov);
+        if (cov) {
+            esum += e;
+            ++ns;
+        }
+    }
+    if (ns > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
+    if (esum > 0.0f) {
+        const float eps = fminf(esum, 1.0f);
+        const float tm = c.te - 0.5f;
+        sm.B = eps * tm / ((1.0f - eps) + tm);                  // Eq. 14
+    }
+    const float Bs = sm.B > 0.0f ? __fdividef(sm.B, esum) : 0.0f;
+    for (unsigned m = uni; m; m &= m - 1u) {
+        const int s = __ffs(m) - 1;
+        float Bp = 0.0f, vx = 0.0f, vy = 0.0f, vt = 0.0f;
+        if (act && ((mask >> s) & 1u) && Bs > 0.0f) {
             const PRec &P = cand[s];
+            const int di = xl - P.ci, dk = yy - P.cj;
             bool cov;
-            const float e = cand_eps(P, lane - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride,
-                                     a.tab_w, a.tab_h, exact, cov);
-            if (xin && cov) {
-                esum += e;
-                ++ns;
-            }
-        }
-        if (ns > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
-        if (esum > 0.0f) {
-            const float eps = fminf(esum, 1.0f);
-            const float tm = te - 0.5f;
-            B = eps * tm / ((1.0f - eps) + tm);                 // Eq. 14
-        }
-        if (__any_sync(FULL, B > 0.0f)) {
-            const float Bs = B > 0.0f ? B / esum : 0.0f;
-            for (unsigned m = mask; m; m &= m - 1u) {
-                const int s = __ffs(m) - 1;
-                const PRec &P = cand[s];
-                const int di = lane - P.ci, dk = yy - P.cj;
-                bool cov;
-                const float e = cand_eps(P, di, dk, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w,
-                                         a.tab_h, exact, cov);
-                const float Bp = (xin && cov) ? Bs * e : 0.0f;
+            const float e = cand_eps(P, di, dk, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
+                                     exact, cov);
+            if (cov) {
+                Bp = Bs * e;
                 const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
                 const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
                 const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
-                m1x += Bp * usx;
-                m1y += Bp * usy;
-                m2xx += Bp * usx * usx;
-                m2xy += Bp * usx * usy;
-                m2yy += Bp * usy * usy;
-                if (!__any_sync(FULL, Bp > 0.0f)) continue;
+                sm.m1x += Bp * usx;
+                sm.m1y += Bp * usy;
+                sm.m2xx += Bp * usx * usx;
+                sm.m2xy += Bp * usx * usy;
+                sm.m2yy += Bp * usy * usy;
                 // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
-                float vx = Bp * (jx - rho * usx - a.Fx);
-                float vy = Bp * (jy - rho * usy - a.Fy);
-                float vt = rx * vy - ry * vx;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    vx += __shfl_xor_sync(FULL, vx, o);
-                    vy += __shfl_xor_sync(FULL, vy, o);
-                    vt += __shfl_xor_sync(FULL, vt, o);
-                }
-                if (lane == 0) {
-                    part[s][0] += vx;
-                    part[s][1] += vy;
-                    part[s][2] += vt;
-                }
+                vx = Bp * (c.jx - c.rho * usx - a.Fx);
+                vy = Bp * (c.jy - c.rho * usy - a.Fy);
+                vt = rx * vy - ry * vx;
             }
         }
-    }
-    // ---- collision and store (Eq. 13): fluid part weighted 1 - B, solid part by B
-    if (xin) {
-        const float fl = 1.0f - B;
-        const float sf = 1.0f - 0.5f * omega;
-        // Eq. 12 summed over the covering particles:
-        // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u)), with
-        // sum_p B_p f^eq_q(u_s,p) - B f^eq_q(u) = rho w_q (3 c.A1 + 4.5 c.A2.c - 1.5 tr A2)
-        const float a1x = m1x - B * ux, a1y = m1y - B * uy;
-        const float a2xx = m2xx - B * ux * ux, a2yy = m2yy - B * uy * uy, a2xy = m2xy - B * ux * uy;
-        const float tra2 = a2xx + a2yy;
-        S *outp = fout + (size_t)y * a.pitch + x;
+        if (!__any_sync(FULL, Bp > 0.0f)) continue;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-            float upd = -omega * n[q];
-            if (forced) {  // Guo forcing term
-                const float cu = cxq * ux + cyq * uy;
-                const float S_q = w_of(q) * (3.0f * ((cxq - ux) * a.Fx + (cyq - uy) * a.Fy) +
-                                             9.0f * cu * (cxq * a.Fx + cyq * a.Fy));
-                upd = fmaf(sf, S_q, upd);
-            }
-            upd *= fl;
-            if (B > 0.0f) {
-                const float ca1 = cxq * a1x + cyq * a1y;
-                const float ca2c = cxq * cxq * a2xx + 2.0f * cxq * cyq * a2xy + cyq * cyq * a2yy;
-                upd += B * (n[opp_of(q)] - n[q]) + rho * w_of(q) * (3.0f * ca1 + 4.5f * ca2c - 1.5f * tra2);
-            }
-            Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);
+        for (int o = 16; o > 0; o >>= 1) {
+            vx += __shfl_xor_sync(FULL, vx, o);
+            vy += __shfl_xor_sync(FULL, vy, o);
+            vt += __shfl_xor_sync(FULL, vt, o);
+        }
+        if (lane == 0) {
+            part[s][0] += vx;
+            part[s][1] += vy;
+            part[s][2] += vt;
         }
     }
 }
@@ -416,7 +432,9 @@ template <typename S> struct Box {
     static constexpr int POP_BYTES = 9 * BYTES;
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
     static constexpr int PART_FLOATS = 2 * WARPS * TILE_CAND * 3;
-    static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + PART_FLOATS * 4 + 16;
+    static constexpr int QUEUE_SHORTS = WARPS * (TILE / WARPS) * 32;   // immersed cells per warp
+    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QUEUE_SHORTS * 2 + WARPS * (TILE / WARPS) * 4;
+    static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + EXTRA_BYTES + 16;
 };
 static_assert(Box<float>::BYTES % 128 == 0 && Box<__half>::BYTES % 128 == 0, "TMA boxes stay 128-B aligned");
 
@@ -435,8 +453,13 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
                  const LatticeArgs a, const TileCand *__restrict__ tiles, const int ntiles) {
     using G = Box<S>;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * G::STAGE_BYTES + G::EXTRA_BYTES);
     float *part_base = reinterpret_cast<float *>(smem + 2 * G::STAGE_BYTES);
+    short *queue = reinterpret_cast<short *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4) +
+                   (threadIdx.x >> 5) * (TILE / WARPS) * 32;
+    unsigned *rmask = reinterpret_cast<unsigned *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4 +
+                                                   G::QUEUE_SHORTS * 2) +
+                      (threadIdx.x >> 5) * (TILE / WARPS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nbx = a.nbx;
     const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
@@ -485,27 +508,72 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
         const int nc = ok ? min(tc->n, TILE_CAND) : 0;
         const S *pop = stage_pop(st);
         float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + (st * WARPS + warp) * TILE_CAND * 3);
-        const int x = x0 + lane;
-        const bool xin = x < a.nx;
-#pragma unroll 1
-        for (int rr = 0; rr < TILE / WARPS; ++rr) {
-            const int yy = warp + WARPS * rr;
-            const int y = y0 + yy;
-            if (y >= a.ny) break;
-            float d[9];
+        auto load_node = [&](int xl, int yy, float (&d)[9]) {
             if (in) {
 #pragma unroll
                 for (int q = 0; q < 9; ++q)
-                    d[q] = Store<S>::lds(pop + q * (G::W * TILE) + yy * G::W + lane + G::HALO - cx_of(q));
-            } else if (xin) {
-                pull_cell(fin, a, x, y, d);
+                    d[q] = Store<S>::lds(pop + q * (G::W * TILE) + yy * G::W + xl + G::HALO - cx_of(q));
+            } else if (x0 + xl < a.nx) {
+                pull_cell(fin, a, x0 + xl, y0 + yy, d);
             } else {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) d[q] = 0.0f;
             }
+        };
+        // pass A: every row of the warp; fluid nodes collide and store here, nodes that
+        // a disk reaches into are queued (tile row * 32 + lane)
+        const int x = x0 + lane;
+        const bool xin = x < a.nx;
+        int nq = 0;
+        unsigned uni = 0u;
+#pragma unroll 1
+        for (int rr = 0; rr < TILE / WARPS; ++rr) {
+            const int yy = warp + WARPS * rr;
+            const int y = y0 + yy;
+            if (y >= a.ny) {
+                if (lane == 0) rmask[rr] = 0u;
+                continue;
+            }
+            float d[9];
+            load_node(lane, yy, d);
             const unsigned mask = nc ? row_mask(tc->p, nc, yy, true) : 0u;
-            collide_store_row(d, lane, yy, x, y, xin, mask, tc->p, tc->id, part, fout, a, forced, smag,
-                              unstable);
+            if (lane == 0) rmask[rr] = mask;
+            uni |= mask;
+            bool imb = false;
+            for (unsigned m = mask; m; m &= m - 1u) {
+                const PRec &P = tc->p[__ffs(m) - 1];
+                imb |= covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r);
+            }
+            imb = imb && xin;
+            const unsigned ib = __ballot_sync(FULL, imb);
+            if (imb) queue[nq + __popc(ib & ((1u << lane) - 1u))] = (short)(yy * 32 + lane);
+            nq += __popc(ib);
+            if (ib != FULL) {
+                NodeState c;
+                node_state(d, a, forced, smag, c);
+                if (xin && !(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+                if (xin && !imb) {
+                    const SolidMoments none = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                    node_collide_store(d, c, none, fout + (size_t)y * a.pitch + x, a, forced);
+                }
+            }
+        }
+        __syncwarp();
+        // pass B: the queued immersed-boundary nodes, 32 at a time
+#pragma unroll 1
+        for (int base = 0; base < nq; base += 32) {
+            const bool act = base + lane < nq;
+            const int e = queue[act ? base + lane : base];
+            const int yy = e >> 5, xl = e & 31;
+            const unsigned mask = rmask[(yy - warp) / WARPS];
+            float d[9];
+            load_node(xl, yy, d);
+            NodeState c;
+            node_state(d, a, forced, smag, c);
+            SolidMoments sm;
+            node_imb(c, xl, yy, mask, uni, act, tc->p, tc->id, part, a, sm);
+            if (act)
+                node_collide_store(d, c, sm, fout + (size_t)(y0 + yy) * a.pitch + (x0 + xl), a, forced);
         }
         // the threads that flush this tile's forces take their particle id before the
         // stage is handed back to the copy engine
@@ -561,44 +629,61 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
 }
 
 // The map step of the coupling cycle (Sec. 2.4) for the partially covered cells: one
-// block per particle lists the cells of its bounding box that the disk covers only in
-// part, then computes their solid ratios lane-compacted into the particle's table
-// (row dk + th, column di + th for the cell at offset (di, dk) from the centre cell).
-// In cell-decomposition mode fully covered cells are tabulated too.
-__global__ void __launch_bounds__(128) k_particle_eps(const PRec *__restrict__ prec, int np, int eps_mode,
-                                                      int n_sub, float *tab, int tw, int th, int stride) {
-    __shared__ short s_off[2][1024];
-    __shared__ int s_n;
-    const int p = blockIdx.x;
+// warp per particle lists the cells of its bounding box that the disk covers only in
+// part (ballot compaction, row by row), then computes their solid ratios with all 32
+// lanes busy, into the particle's table (row dk + th, column di + th for the cell at
+// offset (di, dk) from the centre cell).  In cell-decomposition mode fully covered
+// cells are tabulated too.
+constexpr int EPS_WARPS = 4;
+constexpr int EPS_LIST = 256;
+
+__device__ __forceinline__ void eps_flush(const PRec &P, bool exact, int n_sub, float *out, int tw, int th,
+                                          const short *lst, int n) {
+    for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
+        const int di = lst[2 * k], dk = lst[2 * k + 1];
+        const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
+        out[(dk + th) * tw + (di + th)] = exact ? cell_disk_area(lox, loy, P.r)
+                                                : cell_subcell_ratio(lox, loy, P.r, n_sub);
+    }
+}
+
+__global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_eps(const PRec *__restrict__ prec, int np,
+                                                                 int eps_mode, int n_sub, float *tab, int tw,
+                                                                 int th, int stride) {
+    __shared__ short s_lst[EPS_WARPS][2 * EPS_LIST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * EPS_WARPS + warp;
     if (p >= np) return;
     const PRec P = prec[p];
     const bool exact = eps_mode == EPS_EXACT;
     const int span = (int)ceilf(P.r) + 1;
-    const int side = 2 * span + 1;
     float *out = tab + (size_t)p * stride;
-    for (int base = 0; base < side * side; base += 1024) {
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        const int end = min(base + 1024, side * side);
-        for (int k = base + threadIdx.x; k < end; k += blockDim.x) {
-            const int di = k % side - span, dk = k / side - span;
-            const int st = cover_state(__fsub_rn((float)di, P.fx), __fsub_rn((float)dk, P.fy), P.r);
-            if (st == 1 || (st == 2 && !exact)) {
-                const int slot = atomicAdd(&s_n, 1);
-                s_off[0][slot] = (short)di;
-                s_off[1][slot] = (short)dk;
+    short *lst = s_lst[warp];
+    int n = 0;
+    for (int dk = -span; dk <= span; ++dk) {
+        const float loy = __fsub_rn((float)dk, P.fy);
+        for (int di0 = -span; di0 <= span; di0 += 32) {
+            const int di = di0 + lane;
+            int st = 0;
+            if (di <= span) st = cover_state(__fsub_rn((float)di, P.fx), loy, P.r);
+            const bool take = st == 1 || (st == 2 && !exact);
+            const unsigned bal = __ballot_sync(FULL, take);
+            if (n + __popc(bal) > EPS_LIST) {   // list full: evaluate what is queued
+                __syncwarp();
+                eps_flush(P, exact, n_sub, out, tw, th, lst, n);
+                __syncwarp();
+                n = 0;
             }
+            if (take) {
+                const int pos = n + __popc(bal & ((1u << lane) - 1u));
+                lst[2 * pos] = (short)di;
+                lst[2 * pos + 1] = (short)dk;
+            }
+            n += __popc(bal);
         }
-        __syncthreads();
-        const int n = s_n;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int di = s_off[0][k], dk = s_off[1][k];
-            const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
-            out[(dk + th) * tw + (di + th)] = exact ? cell_disk_area(lox, loy, P.r)
-                                                    : cell_subcell_ratio(lox, loy, P.r, n_sub);
-        }
-        __syncthreads();
     }
+    __syncwarp();
+    eps_flush(P, exact, n_sub, out, tw, th, lst, n);
 }
 
 // ------------------------------------------------------------- gather
@@ -733,8 +818,8 @@ cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_
     k_tile_lists<<<(ntiles + WARPS - 1) / WARPS, BLOCK, 0, s>>>(a, tiles, ntiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.np == 0) return e;
-    k_particle_eps<<<a.np, 128, 0, s>>>(a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h,
-                                       a.tab_stride);
+    k_particle_eps<<<(a.np + EPS_WARPS - 1) / EPS_WARPS, 32 * EPS_WARPS, 0, s>>>(
+        a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h, a.tab_stride);
     return cudaGetLastError();
 }
 

@@ -71,43 +71,43 @@ __global__ void k_particle_table(const double *__restrict__ x, const double *__r
     }
 }
 
-// Exclusive scan of the bin counts by one block: warps reduce coalesced 32-bin
-// segments, the block scans the segment sums, warps write the prefixes back.
-// Also resets the counts and fill cursors (and the DEM list counters) for reuse.
+// Exclusive scan of the bin counts by one block: each thread owns 32 consecutive
+// bins (eight 16-byte loads in flight), the block scans the per-thread sums.  Also
+// resets the counts and fill cursors (and the DEM list counters) for reuse.  The
+// bin arrays are padded to a multiple of 32 entries.
 __global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *start, int nbins,
                                                    int *dem_counters) {
-    __shared__ int seg[4096];
     __shared__ int wsum[32];
     __shared__ int s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_carry = 0;
-    const int nseg = (nbins + 31) / 32;
-    for (int base = 0; base < nseg; base += 4096) {
-        const int nchunk = min(4096, nseg - base);
-        for (int sg = warp; sg < nchunk; sg += 32) {
-            const int b = (base + sg) * 32 + lane;
-            int v = b < nbins ? count[b] : 0;
+    const int nchunks = (nbins + 32 * 1024 - 1) / (32 * 1024);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int b0 = (ch * 1024 + threadIdx.x) * 32;
+        int v[32];
+        if (b0 < nbins) {
+            const int4 *src = reinterpret_cast<const int4 *>(count + b0);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) seg[sg] = v;
-        }
-        __syncthreads();
-        // block scan of the segment sums: each thread owns 4 consecutive segments
-        const int per = 4;
-        int loc[per], tot = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int4 t = src[k];
+                v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < per; ++k) {
-            const int sg = threadIdx.x * per + k;
-            loc[k] = sg < nchunk ? seg[sg] : 0;
-            tot += loc[k];
+            for (int k = 0; k < 32; ++k) v[k] = 0;
         }
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) tot += (b0 + k < nbins) ? v[k] : 0;
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
+        __syncthreads();   // s_carry of the previous chunk and wsum are free again
         if (lane == 31) wsum[warp] = incl;
+        const int carry = s_carry;
         __syncthreads();
         if (warp == 0) {
             int w = wsum[lane];
@@ -119,34 +119,25 @@ __global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *s
             wsum[lane] = w;
         }
         __syncthreads();
-        const int carry = s_carry;
         int run = carry + (warp ? wsum[warp - 1] : 0) + incl - tot;
+        if (b0 < nbins) {
+            int4 *dst = reinterpret_cast<int4 *>(start + b0);
+            int4 *zc = reinterpret_cast<int4 *>(count + b0);
+            int4 *zf = reinterpret_cast<int4 *>(fill + b0);
 #pragma unroll
-        for (int k = 0; k < per; ++k) {
-            const int sg = threadIdx.x * per + k;
-            if (sg < nchunk) seg[sg] = run;
-            run += loc[k];
-        }
-        __syncthreads();
-        for (int sg = warp; sg < nchunk; sg += 32) {
-            const int b = (base + sg) * 32 + lane;
-            const int v = b < nbins ? count[b] : 0;
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += t;
+            for (int k = 0; k < 8; ++k) {
+                int4 o;
+                o.x = run; run += v[4 * k];
+                o.y = run; run += v[4 * k + 1];
+                o.z = run; run += v[4 * k + 2];
+                o.w = run; run += v[4 * k + 3];
+                dst[k] = o;
+                zc[k] = make_int4(0, 0, 0, 0);
+                zf[k] = make_int4(0, 0, 0, 0);
             }
-            if (b < nbins) {
-                start[b] = seg[sg] + x - v;
-                count[b] = 0;
-                fill[b] = 0;
-            }
-            if (b == nbins - 1) start[nbins] = seg[sg] + x;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + wsum[31];
-        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = carry + wsum[31];
+        if (b0 <= nbins - 1 && nbins - 1 < b0 + 32) start[nbins] = run;   // padded counts are zero
     }
     if (threadIdx.x == 0 && dem_counters) {
         dem_counters[0] = 0;
@@ -308,34 +299,53 @@ __global__ void k_dem_free(const DemArgs d) {
         const double ax0 = (0.0 + d.F[2 * p]) / mp + d.gx_eff;
         const double ay0 = (0.0 + d.F[2 * p + 1]) / mp + d.gy_eff;
         const double al0 = (0.0 + d.T[p]) / d.I[p];
-        const bool walls = d.bc_x == BC_WALL || d.bc_y == BC_WALL;
-        for (int s = 0; s < d.N_sub; ++s) {
-            bool touching = false;
-            if (walls) {
-                const double m_ = rp;
-                touching = (d.bc_x == BC_WALL && (px < m_ || (double)d.nx - px < m_)) ||
-                           (d.bc_y == BC_WALL && (py < m_ || (double)d.ny - py < m_));
-            }
-            if (touching) {
-                double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
-                wall_contacts(d, p, px, py, vx, vy, w, rp, mp, xiw, Fcx, Fcy, Tc);
-                integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
-            } else {
-                // a released wall spring (wall_contacts would zero it)
+        // largest excursion of a free particle within one coupling cycle (unit time):
+        // |x(t) - x(0)| <= |v| + |a| / 2 per axis, plus a margin
+        const double ex = fabs(vx) + 0.5 * fabs(ax0) + 1e-6, ey = fabs(vy) + 0.5 * fabs(ay0) + 1e-6;
+        const bool quiet =
+            (d.bc_x != BC_WALL || (px - rp > ex && ((double)d.nx - px) - rp > ex)) &&
+            (d.bc_y != BC_WALL || (py - rp > ey && ((double)d.ny - py) - rp > ey)) &&
+            (d.bc_x != BC_PERIODIC || (px > ex && px < (double)d.nx - ex)) &&
+            (d.bc_y != BC_PERIODIC || (py > ey && py < (double)d.ny - ey));
+        if (quiet) {
+            // no wall within reach and no periodic crossing: the same updates as below
 #pragma unroll
-                for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
+            for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
+            for (int s = 0; s < d.N_sub; ++s) {
                 vx = vx + ax0 * d.dt;
                 vy = vy + ay0 * d.dt;
                 w = w + al0 * d.dt;
                 px = px + vx * d.dt;
                 py = py + vy * d.dt;
-                if (d.bc_x == BC_PERIODIC) {
-                    if (px >= d.nx) px -= d.nx;
-                    else if (px < 0.0) px += d.nx;
-                }
-                if (d.bc_y == BC_PERIODIC) {
-                    if (py >= d.ny) py -= d.ny;
-                    else if (py < 0.0) py += d.ny;
+            }
+        } else {
+            const bool walls = d.bc_x == BC_WALL || d.bc_y == BC_WALL;
+            for (int s = 0; s < d.N_sub; ++s) {
+                bool touching = false;
+                if (walls)
+                    touching = (d.bc_x == BC_WALL && (px < rp || (double)d.nx - px < rp)) ||
+                               (d.bc_y == BC_WALL && (py < rp || (double)d.ny - py < rp));
+                if (touching) {
+                    double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+                    wall_contacts(d, p, px, py, vx, vy, w, rp, mp, xiw, Fcx, Fcy, Tc);
+                    integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+                } else {
+                    // a released wall spring (wall_contacts would zero it)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
+                    vx = vx + ax0 * d.dt;
+                    vy = vy + ay0 * d.dt;
+                    w = w + al0 * d.dt;
+                    px = px + vx * d.dt;
+                    py = py + vy * d.dt;
+                    if (d.bc_x == BC_PERIODIC) {
+                        if (px >= d.nx) px -= d.nx;
+                        else if (px < 0.0) px += d.nx;
+                    }
+                    if (d.bc_y == BC_PERIODIC) {
+                        if (py >= d.ny) py -= d.ny;
+                        else if (py < 0.0) py += d.ny;
+                    }
                 }
             }
         }
