@@ -58,18 +58,27 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--nx", type=int, default=None, help="smaller lattice at the same disk density")
     ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--particles", type=int, default=None, help="override the disk count (0 = fluid only)")
+    ap.add_argument("--csmag", type=float, default=None, help="override the Smagorinsky constant")
     return ap.parse_args()
 
 
-def make_workload(name, nx=None, ny=None):
+def make_workload(name, nx=None, ny=None, particles=None, csmag=None):
     if name == "c1":
-        return W.c1()
-    if name == "c2":
-        return W.c2()
-    if nx or ny:
+        w = W.c1()
+    elif name == "c2":
+        w = W.c2()
+    elif nx or ny or particles is not None:
         nx, ny = nx or 8192, ny or 4096
-        return W.c3(n=int(round(20000 * nx * ny / (8192 * 4096))), nx=nx, ny=ny)
-    return W.c3()
+        n = int(round(20000 * nx * ny / (8192 * 4096))) if particles is None else particles
+        w = W.c3(n=n, nx=nx, ny=ny)
+        if n == 0:
+            w = w.with_(name=f"c3_fluid_only_{nx}x{ny}")
+    else:
+        w = W.c3()
+    if csmag is not None:
+        w = w.with_(C_smag=csmag, name=w.name + f"_C{csmag:g}")
+    return w
 
 
 # --------------------------------------------------------------- distributed
@@ -248,7 +257,7 @@ def run_reference(args):
     rank, world, _ = dist_init(args.gpus)
     if rank != 0:
         return
-    w = make_workload(args.workload, args.nx, args.ny)
+    w = make_workload(args.workload, args.nx, args.ny, args.particles, args.csmag)
     mlups, cpu = time_oracle(target_s=max(5.0, min(60.0, 0.05 * (args.steps + args.warmup))))
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -267,7 +276,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     import paper_1809_07008_gb300 as imb
     imb.load()
-    w = make_workload(args.workload, args.nx, args.ny)
+    w = make_workload(args.workload, args.nx, args.ny, args.particles, args.csmag)
     lat = imb.Lattice.from_workload(w, storage=args.storage)
     ts = torch.cuda.Stream()
     lat.set_stream(ts.cuda_stream)

@@ -39,6 +39,8 @@ struct imb_ctx {
     int nbr_cur = 0;
     double *wall_xi = nullptr;
     int *free_ids = nullptr, *coupled_ids = nullptr, *counters = nullptr;
+    int *parent = nullptr, *label = nullptr, *isz = nullptr, *ifill = nullptr, *istart = nullptr;
+    int *members = nullptr, *roots = nullptr, *big_ids = nullptr;
     int *pbin = nullptr;
     PRec *prec = nullptr;
     // bins
@@ -50,7 +52,7 @@ struct imb_ctx {
     float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
     size_t eps_tab_cap = 0;
     int tab_w = 0, tab_h = 0;
-    CUtensorMap tmap[2];            // TMA descriptors of the two population buffers
+    CUtensorMap tmap[2][2];         // TMA descriptors [buffer][narrow, wide] of the populations
     // parameters derived on the host
     double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
     // timing / accounting
@@ -184,6 +186,14 @@ static DemArgs dem_args(imb_ctx *c) {
     d.free_ids = c->free_ids;
     d.coupled_ids = c->coupled_ids;
     d.counters = c->counters;
+    d.parent = c->parent;
+    d.label = c->label;
+    d.isz = c->isz;
+    d.ifill = c->ifill;
+    d.istart = c->istart;
+    d.members = c->members;
+    d.roots = c->roots;
+    d.big_ids = c->big_ids;
     d.bin_start = c->bin_start;
     d.bin_ids = c->bin_ids;
     d.pbin = c->pbin;
@@ -199,7 +209,8 @@ static void free_particles(imb_ctx *c) {
                      &c->x1, &c->v1, &c->w1, &c->xs, &c->nbr_xi[0], &c->nbr_xi[1], &c->wall_xi};
     for (double **q : dp) { dfree(*q); *q = nullptr; }
     int **ip[] = {&c->nbr_cnt[0], &c->nbr_cnt[1], &c->nbr_id[0], &c->nbr_id[1], &c->free_ids,
-                  &c->coupled_ids, &c->pbin, &c->bin_ids};
+                  &c->coupled_ids, &c->pbin, &c->bin_ids, &c->parent, &c->label, &c->isz, &c->ifill,
+                  &c->istart, &c->members, &c->roots, &c->big_ids};
     for (int **q : ip) { dfree(*q); *q = nullptr; }
     dfree(c->prec);
     c->prec = nullptr;
@@ -227,8 +238,8 @@ extern "C" void imb_destroy(imb_ctx *c) {
 }
 
 // TMA descriptor of one population buffer: a 3D tensor (x over the padded row,
-// y, plane) read in boxes of (32 + 2 halo) x 32 x 1 elements.
-static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map) {
+// y, plane) read in boxes of 32 (narrow) or 32 + halo (wide) x 16 x 1 elements.
+static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map, int wide) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -244,7 +255,7 @@ static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map) {
                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, 9};
     cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->elem, (cuuint64_t)c->plane * c->elem};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage), (cuuint32_t)TILE, 1};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(map, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -305,17 +316,19 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     // bin arrays padded to a multiple of 32 entries (the scan moves 16-byte vectors)
     const int nbins_pad = (c->nbins + 31) / 32 * 32;
     if ((e = dalloc(&c->bin_count, nbins_pad)) != cudaSuccess || (e = dalloc(&c->bin_fill, nbins_pad)) != cudaSuccess ||
-        (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 2)) != cudaSuccess ||
+        (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 4)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
     cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
     for (int b = 0; b < 2; ++b)
-        if ((e = make_tensor_map(c, c->fbuf[b], &c->tmap[b])) != cudaSuccess) return bail(e, "TMA descriptor");
+        for (int wide = 0; wide < 2; ++wide)
+            if ((e = make_tensor_map(c, c->fbuf[b], &c->tmap[b][wide], wide)) != cudaSuccess)
+                return bail(e, "TMA descriptor");
     cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins_pad, c->stream);
     cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * nbins_pad, c->stream);
     cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (nbins_pad + 32), c->stream);
-    cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream);
+    cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->barrier, 0, sizeof(GridBarrier), c->stream);
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
     LatticeArgs a = lattice_args(c);
@@ -388,6 +401,14 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
         if (e == cudaSuccess) e = dalloc(&c->pbin, N);
         if (e == cudaSuccess) e = dalloc(&c->bin_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->prec, N);
+        const size_t Np = (N + 31) / 32 * 32;
+        int **ia[] = {&c->parent, &c->label, &c->members, &c->roots, &c->big_ids};
+        for (int **q : ia) if (e == cudaSuccess) e = dalloc(q, N);
+        if (e == cudaSuccess) e = dalloc(&c->isz, Np);
+        if (e == cudaSuccess) e = dalloc(&c->ifill, Np);
+        if (e == cudaSuccess) e = dalloc(&c->istart, Np + 32);
+        if (e == cudaSuccess) e = cudaMemset(c->isz, 0, 4 * Np);
+        if (e == cudaSuccess) e = cudaMemset(c->ifill, 0, 4 * Np);
         if (e != cudaSuccess) {
             free_particles(c);
             return cuda_fail(c, e, "particle buffers");
@@ -427,7 +448,7 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
         CK(cudaMemset(c->F, 0, 16 * (size_t)n), "reset forces");
         CK(cudaMemset(c->T, 0, 8 * (size_t)n), "reset torques");
     }
-    CK(cudaMemset(c->counters, 0, 8), "reset counters");
+    CK(cudaMemset(c->counters, 0, 16), "reset counters");
     int rc = rebuild_table(c, nullptr, false);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -451,9 +472,11 @@ extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, 
 static int dem_cycle(imb_ctx *c, bool zero_forces) {
     DemArgs d = dem_args(c);
     CK(launch_dem_neighbours(d, c->stream), "dem neighbours");
+    CK(launch_dem_islands_setup(d, c->stream), "dem islands");
     CK(launch_dem_free(d, c->stream), "dem free");
+    CK(launch_dem_islands(d, c->stream), "dem islands");
     CK(launch_dem_coupled(d, dem_coupled_blocks(), c->stream), "dem coupled");
-    c->launches += 3;
+    c->launches += 8;
     c->nbr_cur ^= 1;
     return rebuild_table(c, c->xs, zero_forces);
 }
@@ -476,8 +499,8 @@ static int lattice_step(imb_ctx *c) {
         c->ev_used += 2;
         CK(cudaEventRecord(e0, c->stream), "event record");
     }
-    CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur],
-                             c->tiles, c->stream),
+    CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur][0],
+                             &c->tmap[c->cur][1], c->tiles, c->stream),
        "stream-collide");
     c->launches++;
     if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");

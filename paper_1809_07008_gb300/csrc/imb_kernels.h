@@ -47,7 +47,10 @@ struct DemArgs {
     double *nbr_xi_old, *nbr_xi;      // [np * MAX_NBR]
     double *wall_xi;                  // [np * 4]
     int *free_ids, *coupled_ids;      // [np]
-    int *counters;                    // [0] free, [1] coupled
+    int *counters;                    // [0] free, [1] coupled, [2] small islands, [3] big-island particles
+    int *parent, *label;              // [np] union-find forest and island of each particle
+    int *isz, *ifill, *istart;        // island sizes / fill cursors / starts (padded to 32, +32)
+    int *members, *roots, *big_ids;   // [np] island members, roots of small islands, big-island particles
     const int *bin_start, *bin_ids;   // bins of the positions at cycle start
     int *pbin;                        // [np]
     int nbx, nby;
@@ -59,9 +62,11 @@ struct DemArgs {
 cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, float rho0, float ux0,
                                     float uy0, cudaStream_t s);
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
-                                  const CUtensorMap *tmap_in, const TileCand *tiles, cudaStream_t s);
+                                  const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
+                                  const TileCand *tiles, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
-int tma_box_width(int storage);
+int tma_box_width(int storage, int wide);
+int tma_box_rows();
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s);
 cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);
@@ -79,6 +84,8 @@ cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *b
 cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s);
+cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s);
+cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
                             int bc_y, const int *bin_start, const int *bin_ids, const int *pbin,
                             int nbx, int nby, int reach, int *pair_cnt, int *pairs, int max_per,

@@ -423,43 +423,63 @@ __device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int 
     return __ballot_sync(FULL, rel);
 }
 
-// TMA box geometry per storage type: the box starts HALO cells left of the tile so
-// that its x coordinate is 16-byte aligned, and spans the tile plus both halos.
+// Work unit of the persistent kernel: HROWS rows of a tile (a full 32 x 32 tile by
+// default); NST units are in flight per block.  TMA boxes: the x start must be 16-byte aligned, so the six planes
+// pulled from x - 1 or x + 1 (c_x = +-1) take a box HALO cells wider than the tile
+// (starting HALO cells left of the tile for c_x = +1), the three with c_x = 0 exactly
+// the tile width.
+constexpr int HROWS = TILE;              // rows per work unit
+constexpr int UPT = TILE / HROWS;        // work units per tile
+constexpr int NST = 2;                   // pipeline stages per block
+constexpr int RPW = HROWS / WARPS;       // rows per warp per unit
+
 template <typename S> struct Box {
     static constexpr int HALO = 16 / (int)sizeof(S);
-    static constexpr int W = TILE + 2 * HALO;
-    static constexpr int BYTES = W * TILE * (int)sizeof(S);
-    static constexpr int POP_BYTES = 9 * BYTES;
+    static constexpr int WN = TILE, WW = TILE + HALO;
+    __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
+    __host__ __device__ static constexpr int offset(int q) {   // elements before plane q
+        int o = 0;
+        for (int k = 0; k < q; ++k) o += width(k) * HROWS;
+        return o;
+    }
+    // shared-memory column of lane xl's source x - c_x in plane q's box
+    __host__ __device__ static constexpr int col(int q, int xl) {
+        return xl - cx_of(q) + (cx_of(q) == 1 ? HALO : 0);
+    }
+    static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
     static constexpr int PART_FLOATS = 2 * WARPS * TILE_CAND * 3;
-    static constexpr int QUEUE_SHORTS = WARPS * (TILE / WARPS) * 32;   // immersed cells per warp
-    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QUEUE_SHORTS * 2 + WARPS * (TILE / WARPS) * 4;
-    static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + EXTRA_BYTES + 16;
+    static constexpr int QUEUE_SHORTS = WARPS * RPW * 32;   // immersed cells per warp and unit
+    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QUEUE_SHORTS * 2 + WARPS * RPW * 4;
+    static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
-static_assert(Box<float>::BYTES % 128 == 0 && Box<__half>::BYTES % 128 == 0, "TMA boxes stay 128-B aligned");
+static_assert((Box<float>::WN * HROWS * 4) % 128 == 0 && (Box<float>::WW * HROWS * 4) % 128 == 0 &&
+                  (Box<__half>::WN * HROWS * 2) % 128 == 0 && (Box<__half>::WW * HROWS * 2) % 128 == 0,
+              "TMA boxes stay 128-byte aligned in shared memory");
 
 __device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
     // every neighbour read of the tile lies inside the lattice: no boundary rule applies
     return bx >= 1 && by >= 1 && (bx + 1) * TILE <= nx - 1 && (by + 1) * TILE <= ny - 1;
 }
 
-// Persistent fused stream-collide.  Each block walks tiles t = blockIdx.x + k * gridDim.x.
-// Thread 0 keeps two tiles in flight: for interior tiles nine TMA boxes (one per
-// population plane, shifted by -c_i) plus the tile's candidate block; boundary tiles
-// take the candidate block only and pull their populations with the boundary rules.
+// Persistent fused stream-collide.  Block b walks the half tiles of tiles
+// t = b + j * gridDim.x.  Thread 0 keeps NST units in flight: for interior tiles nine
+// TMA boxes (one per population plane, rows shifted by -c_y) plus the tile's candidate
+// block; boundary tiles take the candidate block only and pull their populations with
+// the boundary rules.
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 2)
-k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__ fin, S *__restrict__ fout,
-                 const LatticeArgs a, const TileCand *__restrict__ tiles, const int ntiles) {
+k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_constant__ CUtensorMap tmap_w,
+                 const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
+                 const TileCand *__restrict__ tiles, const int ntiles) {
     using G = Box<S>;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * G::STAGE_BYTES + G::EXTRA_BYTES);
-    float *part_base = reinterpret_cast<float *>(smem + 2 * G::STAGE_BYTES);
-    short *queue = reinterpret_cast<short *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4) +
-                   (threadIdx.x >> 5) * (TILE / WARPS) * 32;
-    unsigned *rmask = reinterpret_cast<unsigned *>(smem + 2 * G::STAGE_BYTES + G::PART_FLOATS * 4 +
-                                                   G::QUEUE_SHORTS * 2) +
-                      (threadIdx.x >> 5) * (TILE / WARPS);
+    unsigned char *extra = smem + NST * G::STAGE_BYTES;
+    float *part_base = reinterpret_cast<float *>(extra);
+    short *queue = reinterpret_cast<short *>(extra + G::PART_FLOATS * 4) + (threadIdx.x >> 5) * RPW * 32;
+    unsigned *rmask = reinterpret_cast<unsigned *>(extra + G::PART_FLOATS * 4 + G::QUEUE_SHORTS * 2) +
+                      (threadIdx.x >> 5) * RPW;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(extra + G::EXTRA_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nbx = a.nbx;
     const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
@@ -467,8 +487,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
 
     for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part_base[i] = 0.0f;
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < NST; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -478,41 +497,41 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
         return reinterpret_cast<TileCand *>(smem + st * G::STAGE_BYTES + G::POP_BYTES);
     };
     auto issue = [&](int k, int st) {
-        const int t = blockIdx.x + k * gridDim.x;
+        const int t = blockIdx.x + (k / UPT) * gridDim.x;
         if (t >= ntiles) return;
         const int bx = t % nbx, by = t / nbx;
         const bool in = tma_tile(bx, by, a.nx, a.ny);
         mbar_arrive_expect_tx(&mbar[st], (uint32_t)sizeof(TileCand) + (in ? (uint32_t)G::POP_BYTES : 0u));
         bulk_load(stage_cand(st), &tiles[t], (uint32_t)sizeof(TileCand), &mbar[st]);
         if (in) {
+            const int x0 = bx * TILE, yb = by * TILE + (k % UPT) * HROWS;
 #pragma unroll
             for (int q = 0; q < 9; ++q)
-                tma_load_3d(stage_pop(st) + q * (G::W * TILE), &tmap, bx * TILE - G::HALO,
-                            by * TILE - cy_of(q), q, &mbar[st]);
+                tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
+                            cx_of(q) == 1 ? x0 - G::HALO : x0, yb - cy_of(q), q, &mbar[st]);
         }
     };
-    if (threadIdx.x == 0) {
-        issue(0, 0);
-        issue(1, 1);
-    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NST; ++k) issue(k, k);
     bool unstable = false;
     for (int k = 0;; ++k) {
-        const int t = blockIdx.x + k * gridDim.x;
+        const int t = blockIdx.x + (k / UPT) * gridDim.x;
         if (t >= ntiles) break;
-        const int st = k & 1;
-        const bool ok = mbar_wait(&mbar[st], (uint32_t)((k >> 1) & 1));
+        const int h = k % UPT;
+        const int st = k % NST;
+        const bool ok = mbar_wait(&mbar[st], (uint32_t)((k / NST) & 1));
         const int bx = t % nbx, by = t / nbx;
         const int x0 = bx * TILE, y0 = by * TILE;
         const bool in = tma_tile(bx, by, a.nx, a.ny);
         const TileCand *tc = stage_cand(st);
         const int nc = ok ? min(tc->n, TILE_CAND) : 0;
         const S *pop = stage_pop(st);
-        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + (st * WARPS + warp) * TILE_CAND * 3);
+        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + ((k & 1) * WARPS + warp) * TILE_CAND * 3);
         auto load_node = [&](int xl, int yy, float (&d)[9]) {
             if (in) {
+                const int r = yy - h * HROWS;
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    d[q] = Store<S>::lds(pop + q * (G::W * TILE) + yy * G::W + xl + G::HALO - cx_of(q));
+                for (int q = 0; q < 9; ++q) d[q] = Store<S>::lds(pop + G::offset(q) + r * G::width(q) + G::col(q, xl));
             } else if (x0 + xl < a.nx) {
                 pull_cell(fin, a, x0 + xl, y0 + yy, d);
             } else {
@@ -527,8 +546,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
         int nq = 0;
         unsigned uni = 0u;
 #pragma unroll 1
-        for (int rr = 0; rr < TILE / WARPS; ++rr) {
-            const int yy = warp + WARPS * rr;
+        for (int rr = 0; rr < RPW; ++rr) {
+            const int yy = h * HROWS + warp + WARPS * rr;
             const int y = y0 + yy;
             if (y >= a.ny) {
                 if (lane == 0) rmask[rr] = 0u;
@@ -565,7 +584,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
             const bool act = base + lane < nq;
             const int e = queue[act ? base + lane : base];
             const int yy = e >> 5, xl = e & 31;
-            const unsigned mask = rmask[(yy - warp) / WARPS];
+            const unsigned mask = rmask[(yy - h * HROWS - warp) / WARPS];
             float d[9];
             load_node(xl, yy, d);
             NodeState c;
@@ -581,11 +600,11 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap, const S *__restrict__
         const int bad = __syncthreads_or(!ok);
         if (threadIdx.x == 0 && !bad) {
             fence_proxy_async_smem();
-            issue(k + 2, st);
+            issue(k + NST, st);
         }
         if (fid >= 0) {
             const int s = threadIdx.x / 3, c = threadIdx.x - 3 * s;
-            float *pb = part_base + st * WARPS * TILE_CAND * 3 + s * 3 + c;
+            float *pb = part_base + (k & 1) * WARPS * TILE_CAND * 3 + s * 3 + c;
             double acc = 0.0;
 #pragma unroll
             for (int w = 0; w < WARPS; ++w) {
@@ -802,13 +821,14 @@ static int stream_collide_grid(int ntiles) {
 }
 
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
-                                  const CUtensorMap *tmap_in, const TileCand *tiles, cudaStream_t s) {
+                                  const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
+                                  const TileCand *tiles, cudaStream_t s) {
     const int ntiles = a.nbx * a.nby;
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         const int grid = stream_collide_grid<S>(ntiles);
-        k_stream_collide<S><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(*tmap_in, (const S *)fin, (S *)fout, a,
-                                                                   tiles, ntiles);
+        k_stream_collide<S><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(*tmap_narrow, *tmap_wide, (const S *)fin,
+                                                                   (S *)fout, a, tiles, ntiles);
         return cudaGetLastError();
     });
 }
@@ -823,9 +843,11 @@ cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_
     return cudaGetLastError();
 }
 
-int tma_box_width(int storage) {
-    return storage == 0 ? Box<float>::W : Box<__half>::W;
+int tma_box_width(int storage, int wide) {
+    if (storage == 0) return wide ? Box<float>::WW : Box<float>::WN;
+    return wide ? Box<__half>::WW : Box<__half>::WN;
 }
+int tma_box_rows() { return HROWS; }
 
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s) {

@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *s
     if (threadIdx.x == 0 && dem_counters) {
         dem_counters[0] = 0;
         dem_counters[1] = 0;
+        dem_counters[2] = 0;
+        dem_counters[3] = 0;
     }
 }
 
@@ -281,6 +283,7 @@ __global__ void k_dem_neighbours(const DemArgs d) {
         d.nbr_xi[p * MAX_NBR + j] = xi;
     }
     d.nbr_cnt[p] = n;
+    d.parent[p] = p;
     if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
     else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
 }
@@ -359,11 +362,50 @@ __global__ void k_dem_free(const DemArgs d) {
     }
 }
 
+// One sub-cycle of particle p (Eqs. 7-11): contact forces from the candidate list in
+// ascending id order, then the walls, then the leapfrog update.  nb(j, q, ...) yields
+// the state of the j-th candidate q at the start of the sub-cycle.
+template <typename NB>
+__device__ __forceinline__ void particle_substep(const DemArgs &d, const int p, double &px, double &py,
+                                                 double &vx, double &vy, double &w, NB &&nb) {
+    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
+    const double rp = d.r[p], mp = d.m[p];
+    double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+    const int n = d.nbr_cnt[p];
+    for (int j = 0; j < n; ++j) {
+        const int q = d.nbr_id[p * MAX_NBR + j];
+        double &xi = d.nbr_xi[p * MAX_NBR + j];
+        double qx, qy, qvx, qvy, qw;
+        nb(j, q, qx, qy, qvx, qvy, qw);
+        const double dx = min_image(qx - px, perx, d.nx);
+        const double dy = min_image(qy - py, pery, d.ny);
+        const double d2 = dx * dx + dy * dy;
+        const double R = rp + d.r[q];
+        if (!(d2 < R * R)) {  // Eq. 7: no overlap, the spring is released
+            xi = 0.0;
+            continue;
+        }
+        const double dist = sqrt(d2);
+        const double nxv = dx / dist, nyv = dy / dist;
+        const double mq = d.m[q];
+        const double mstar = mp * mq / (mp + mq);
+        const double rot = w * rp + qw * d.r[q];
+        double fx, fy, Ft;
+        contact_law(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, mstar, xi, fx, fy, Ft);
+        Fcx += fx;
+        Fcy += fy;
+        Tc += rp * Ft;
+    }
+    wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
+    integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+}
+
+// Particles of islands larger than a warp: all blocks step them together, one bounded
+// grid barrier per sub-cycle (cooperative launch), state exchanged through L2.
 __global__ void k_dem_coupled(const DemArgs d) {
-    const int ncpl = d.counters[1];
+    const int ncpl = d.counters[3];
     const int nb_active = min((int)gridDim.x, (ncpl + (int)blockDim.x - 1) / (int)blockDim.x);
     if (ncpl == 0 || (int)blockIdx.x >= nb_active) return;
-    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
     const int stride = nb_active * blockDim.x;
     for (int s = 0; s < d.N_sub; ++s) {
         const double *xc = (s & 1) ? d.x1 : d.x;
@@ -373,38 +415,17 @@ __global__ void k_dem_coupled(const DemArgs d) {
         double *vn = (s & 1) ? d.v : d.v1;
         double *wn = (s & 1) ? d.w : d.w1;
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += stride) {
-            const int p = d.coupled_ids[c];
+            const int p = d.big_ids[c];
             double px = __ldcg(&xc[2 * p]), py = __ldcg(&xc[2 * p + 1]);
             double vx = __ldcg(&vc[2 * p]), vy = __ldcg(&vc[2 * p + 1]), w = __ldcg(&wc[p]);
-            const double rp = d.r[p], mp = d.m[p];
-            double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
-            const int n = d.nbr_cnt[p];
-            for (int j = 0; j < n; ++j) {
-                const int q = d.nbr_id[p * MAX_NBR + j];
-                double &xi = d.nbr_xi[p * MAX_NBR + j];
-                const double qx = __ldcg(&xc[2 * q]), qy = __ldcg(&xc[2 * q + 1]);
-                const double dx = min_image(qx - px, perx, d.nx);
-                const double dy = min_image(qy - py, pery, d.ny);
-                const double d2 = dx * dx + dy * dy;
-                const double R = rp + d.r[q];
-                if (!(d2 < R * R)) {  // Eq. 7: no overlap, the spring is released
-                    xi = 0.0;
-                    continue;
-                }
-                const double dist = sqrt(d2);
-                const double nxv = dx / dist, nyv = dy / dist;
-                const double mq = d.m[q];
-                const double mstar = mp * mq / (mp + mq);
-                const double rot = w * rp + __ldcg(&wc[q]) * d.r[q];
-                double fx, fy, Ft;
-                contact_law(d, nxv, nyv, R - dist, __ldcg(&vc[2 * q]) - vx, __ldcg(&vc[2 * q + 1]) - vy,
-                            rot, mstar, xi, fx, fy, Ft);
-                Fcx += fx;
-                Fcy += fy;
-                Tc += rp * Ft;
-            }
-            wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
-            integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+            particle_substep(d, p, px, py, vx, vy, w,
+                             [&](int, int q, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
+                                 qx = __ldcg(&xc[2 * q]);
+                                 qy = __ldcg(&xc[2 * q + 1]);
+                                 qvx = __ldcg(&vc[2 * q]);
+                                 qvy = __ldcg(&vc[2 * q + 1]);
+                                 qw = __ldcg(&wc[q]);
+                             });
             __stcg(&xn[2 * p], px);
             __stcg(&xn[2 * p + 1], py);
             __stcg(&vn[2 * p], vx);
@@ -419,13 +440,141 @@ __global__ void k_dem_coupled(const DemArgs d) {
     }
     if (d.N_sub & 1) {  // the last sub-cycle wrote the second buffer
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += stride) {
-            const int p = d.coupled_ids[c];
+            const int p = d.big_ids[c];
             d.x[2 * p] = __ldcg(&d.x1[2 * p]);
             d.x[2 * p + 1] = __ldcg(&d.x1[2 * p + 1]);
             d.v[2 * p] = __ldcg(&d.v1[2 * p]);
             d.v[2 * p + 1] = __ldcg(&d.v1[2 * p + 1]);
             d.w[p] = __ldcg(&d.w1[p]);
         }
+    }
+}
+
+// ------------------------------------------------------------ islands
+// Particles that can touch during a coupling cycle form the connected components
+// ("islands") of the candidate graph; islands evolve independently.  Lock-free
+// union-find: roots hook under the smaller index, finds halve paths.
+__device__ __forceinline__ int uf_find(int *parent, int x) {
+    volatile int *par = parent;
+    for (;;) {
+        const int p = par[x];
+        if (p == x) return x;
+        const int g = par[p];
+        if (g == p) return p;
+        par[x] = g;
+        x = g;
+    }
+}
+
+__global__ void k_uf_link(const DemArgs d) {
+    const int ncpl = d.counters[1];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
+        const int p = d.coupled_ids[c];
+        const int n = d.nbr_cnt[p];
+        for (int j = 0; j < n; ++j) {
+            const int q = d.nbr_id[p * MAX_NBR + j];
+            if (q < p) continue;
+            int a = p, b = q;
+            for (;;) {
+                a = uf_find(d.parent, a);
+                b = uf_find(d.parent, b);
+                if (a == b) break;
+                if (a < b) { const int t = a; a = b; b = t; }
+                if (atomicCAS(&d.parent[a], a, b) == a) break;
+            }
+        }
+    }
+}
+
+__global__ void k_uf_label(const DemArgs d) {
+    const int ncpl = d.counters[1];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
+        const int p = d.coupled_ids[c];
+        const int r = uf_find(d.parent, p);
+        d.label[p] = r;
+        atomicAdd(&d.isz[r], 1);
+    }
+}
+
+__global__ void k_island_fill(const DemArgs d) {
+    const int ncpl = d.counters[1];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
+        const int p = d.coupled_ids[c];
+        const int r = d.label[p];
+        const int b = d.istart[r], size = d.istart[r + 1] - b;
+        d.members[b + atomicAdd(&d.ifill[r], 1)] = p;
+        if (size <= 32) {
+            if (p == r) d.roots[atomicAdd(&d.counters[2], 1)] = r;
+        } else {
+            d.big_ids[atomicAdd(&d.counters[3], 1)] = p;
+        }
+    }
+}
+
+// One warp per island of at most 32 particles: all N_sub sub-cycles with the island
+// state in shared memory (double-buffered), lanes synchronised by __syncwarp.
+constexpr int ISL_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d) {
+    __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
+    __shared__ int s_id[ISL_WARPS][32];
+    __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nisl = d.counters[2];
+    for (int i = blockIdx.x * ISL_WARPS + warp; i < nisl; i += gridDim.x * ISL_WARPS) {
+        const int r = d.roots[i];
+        const int b = d.istart[r], n = d.istart[r + 1] - b;
+        const bool act = lane < n;
+        const int p = act ? d.members[b + lane] : -1;
+        s_id[warp][lane] = p;
+        __syncwarp();
+        if (act) {
+            const int nn = d.nbr_cnt[p];
+            for (int j = 0; j < nn; ++j) {
+                const int q = d.nbr_id[p * MAX_NBR + j];
+                int l = 0;
+                while (l < n - 1 && s_id[warp][l] != q) ++l;   // q is in the same island
+                s_nl[warp][lane][j] = (unsigned char)l;
+            }
+            s_st[warp][0][0][lane] = d.x[2 * p];
+            s_st[warp][0][1][lane] = d.x[2 * p + 1];
+            s_st[warp][0][2][lane] = d.v[2 * p];
+            s_st[warp][0][3][lane] = d.v[2 * p + 1];
+            s_st[warp][0][4][lane] = d.w[p];
+        }
+        __syncwarp();
+        for (int s = 0; s < d.N_sub; ++s) {
+            const int cur = s & 1;
+            if (act) {
+                double px = s_st[warp][cur][0][lane], py = s_st[warp][cur][1][lane];
+                double vx = s_st[warp][cur][2][lane], vy = s_st[warp][cur][3][lane];
+                double w = s_st[warp][cur][4][lane];
+                particle_substep(d, p, px, py, vx, vy, w,
+                                 [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
+                                     const int l = s_nl[warp][lane][j];
+                                     qx = s_st[warp][cur][0][l];
+                                     qy = s_st[warp][cur][1][l];
+                                     qvx = s_st[warp][cur][2][l];
+                                     qvy = s_st[warp][cur][3][l];
+                                     qw = s_st[warp][cur][4][l];
+                                 });
+                s_st[warp][cur ^ 1][0][lane] = px;
+                s_st[warp][cur ^ 1][1][lane] = py;
+                s_st[warp][cur ^ 1][2][lane] = vx;
+                s_st[warp][cur ^ 1][3][lane] = vy;
+                s_st[warp][cur ^ 1][4][lane] = w;
+            }
+            __syncwarp();
+        }
+        if (act) {
+            const int fin = d.N_sub & 1;
+            d.x[2 * p] = s_st[warp][fin][0][lane];
+            d.x[2 * p + 1] = s_st[warp][fin][1][lane];
+            d.v[2 * p] = s_st[warp][fin][2][lane];
+            d.v[2 * p + 1] = s_st[warp][fin][3][lane];
+            d.w[p] = s_st[warp][fin][4][lane];
+        }
+        __syncwarp();
     }
 }
 
@@ -520,6 +669,23 @@ cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s) {
     DemArgs copy = d;
     void *args[] = {&copy};
     return cudaLaunchCooperativeKernel((const void *)k_dem_coupled, dim3(nblocks), dim3(32), args, 0, s);
+}
+
+cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s) {
+    if (d.np == 0) return cudaSuccess;
+    const int g = blocks_for(d.np, 128);
+    k_uf_link<<<g, 128, 0, s>>>(d);
+    k_uf_label<<<g, 128, 0, s>>>(d);
+    cudaError_t e = launch_bin_scan(d.isz, d.ifill, d.istart, d.np, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_island_fill<<<g, 128, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s) {
+    if (d.np == 0) return cudaSuccess;
+    k_dem_islands<<<blocks_for(d.np, 32 * ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
