@@ -165,6 +165,27 @@ long long imb_launch_count(imb_ctx *ctx);
  * (9 loads + 9 stores of one population). */
 double imb_bytes_per_cell(imb_ctx *ctx);
 
+/* Particle-to-bin map into caller-owned device buffers, allocating nothing.  The
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc (code
+ * running under CUDA graph capture, hosts whose device memory belongs to their own
+ * pool, real-time loops that must not touch the allocator).
+ * d_x: DEVICE pointer to 2n doubles (x, y of each centre, inside [0,nx) x [0,ny));
+ * d_bin_start: DEVICE pointer to nbins + 1 ints, nbins = ceil(nx/32) * ceil(ny/32);
+ * d_bin_ids: DEVICE pointer to n ints, the particle ids grouped by bin (bin = by * nbx
+ * + bx, bx = floor(x/32) clamped to the lattice), ascending within each bin -- the same
+ * result as imb_get_bins for the same centres.  stream: a cudaStream_t or NULL; the
+ * call only queues work on it.
+ * Scratch (per-bin counts and fill cursors) lives in one fixed device array of
+ * 2 * IMB_NOALLOC_MAX_BINS ints inside the library, held by every GPU that loads it
+ * until process exit; nbins > IMB_NOALLOC_MAX_BINS returns IMB_E_INVALID_ARG.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress, with that
+ * device current), so make that first call before any stream capture.  Every call
+ * shares the array and clears the part it uses; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller. */
+#define IMB_NOALLOC_MAX_BINS 65536
+int imb_bin_particles_noalloc(const double *d_x, int n, int nx, int ny, int *d_bin_start,
+                              int *d_bin_ids, void *stream);
+
 /* Last error message of ctx (or of the last failed imb_init_lattice when ctx is
  * NULL).  Valid until the next call on the same context. */
 const char *imb_last_error(imb_ctx *ctx);

@@ -31,8 +31,16 @@ EXPORTS = (
     "imb_get_macro", "imb_get_forces", "imb_set_forces", "imb_get_particles",
     "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
-    "imb_last_error", "imb_destroy",
+    "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc",
 )
+
+
+def bin_particles_noalloc(d_x: int, n: int, nx: int, ny: int, d_bin_start: int, d_bin_ids: int,
+                          stream: int = 0) -> int:
+    """imb_bin_particles_noalloc on raw device addresses (e.g. tensor.data_ptr()); returns
+    the IMB_* code.  For callers that cannot allocate: nothing is allocated."""
+    return load().imb_bin_particles_noalloc(_vp(d_x), int(n), int(nx), int(ny), _vp(d_bin_start),
+                                           _vp(d_bin_ids), _vp(stream) if stream else None)
 
 
 class ImbError(RuntimeError):
@@ -104,6 +112,7 @@ def load(build_if_missing: bool = True):
     L.imb_last_error.restype = C.c_char_p
     L.imb_destroy.argtypes = [_vp]
     L.imb_destroy.restype = None
+    L.imb_bin_particles_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]
     _lib = L
     return L
 

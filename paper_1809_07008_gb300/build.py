@@ -26,6 +26,7 @@ UNITS = {
     "imb_lbm.cu": [],
     "imb_particles.cu": ["--fmad=false"],
     "imb_api.cu": [],
+    "imb_noalloc.cu": [],
 }
 
 
