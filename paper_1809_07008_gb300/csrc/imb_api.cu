@@ -36,11 +36,14 @@ struct imb_ctx {
     double *F = nullptr, *T = nullptr, *x1 = nullptr, *v1 = nullptr, *w1 = nullptr, *xs = nullptr;
     int *nbr_cnt[2] = {nullptr, nullptr}, *nbr_id[2] = {nullptr, nullptr};
     double *nbr_xi[2] = {nullptr, nullptr};
+    double *nbr_cn[2] = {nullptr, nullptr};
     int nbr_cur = 0;
     double *wall_xi = nullptr;
     int *free_ids = nullptr, *coupled_ids = nullptr, *counters = nullptr;
     int *parent = nullptr, *label = nullptr, *isz = nullptr, *ifill = nullptr, *istart = nullptr;
     int *members = nullptr, *roots = nullptr, *big_ids = nullptr;
+    int *loud = nullptr, *iloud = nullptr;
+    double *exc = nullptr;
     int *pbin = nullptr;
     PRec *prec = nullptr;
     // bins
@@ -182,6 +185,8 @@ static DemArgs dem_args(imb_ctx *c) {
     d.nbr_id = c->nbr_id[c->nbr_cur];
     d.nbr_xi_old = c->nbr_xi[c->nbr_cur ^ 1];
     d.nbr_xi = c->nbr_xi[c->nbr_cur];
+    d.nbr_cn_old = c->nbr_cn[c->nbr_cur ^ 1];
+    d.nbr_cn = c->nbr_cn[c->nbr_cur];
     d.wall_xi = c->wall_xi;
     d.free_ids = c->free_ids;
     d.coupled_ids = c->coupled_ids;
@@ -193,6 +198,9 @@ static DemArgs dem_args(imb_ctx *c) {
     d.istart = c->istart;
     d.members = c->members;
     d.roots = c->roots;
+    d.exc = c->exc;
+    d.loud = c->loud;
+    d.iloud = c->iloud;
     d.big_ids = c->big_ids;
     d.bin_start = c->bin_start;
     d.bin_ids = c->bin_ids;
@@ -206,11 +214,12 @@ static DemArgs dem_args(imb_ctx *c) {
 
 static void free_particles(imb_ctx *c) {
     double **dp[] = {&c->x, &c->v, &c->w, &c->r, &c->m, &c->I, &c->F, &c->T,
-                     &c->x1, &c->v1, &c->w1, &c->xs, &c->nbr_xi[0], &c->nbr_xi[1], &c->wall_xi};
+                     &c->x1, &c->v1, &c->w1, &c->xs, &c->nbr_xi[0], &c->nbr_xi[1], &c->wall_xi,
+                     &c->nbr_cn[0], &c->nbr_cn[1], &c->exc};
     for (double **q : dp) { dfree(*q); *q = nullptr; }
     int **ip[] = {&c->nbr_cnt[0], &c->nbr_cnt[1], &c->nbr_id[0], &c->nbr_id[1], &c->free_ids,
                   &c->coupled_ids, &c->pbin, &c->bin_ids, &c->parent, &c->label, &c->isz, &c->ifill,
-                  &c->istart, &c->members, &c->roots, &c->big_ids};
+                  &c->istart, &c->members, &c->roots, &c->big_ids, &c->loud, &c->iloud};
     for (int **q : ip) { dfree(*q); *q = nullptr; }
     dfree(c->prec);
     c->prec = nullptr;
@@ -316,7 +325,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     // bin arrays padded to a multiple of 32 entries (the scan moves 16-byte vectors)
     const int nbins_pad = (c->nbins + 31) / 32 * 32;
     if ((e = dalloc(&c->bin_count, nbins_pad)) != cudaSuccess || (e = dalloc(&c->bin_fill, nbins_pad)) != cudaSuccess ||
-        (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 4)) != cudaSuccess ||
+        (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
@@ -328,7 +337,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins_pad, c->stream);
     cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * nbins_pad, c->stream);
     cudaMemsetAsync(c->bin_start, 0, sizeof(int) * (nbins_pad + 32), c->stream);
-    cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream);
+    cudaMemsetAsync(c->counters, 0, sizeof(int) * 8, c->stream);
     cudaMemsetAsync(c->barrier, 0, sizeof(GridBarrier), c->stream);
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
     LatticeArgs a = lattice_args(c);
@@ -357,7 +366,7 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
     CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
-    c->launches += 4;
+    c->launches += 5;   // table, scan, fill, tile lists, solid-ratio map
     return IMB_OK;
 }
 
@@ -396,16 +405,19 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
             if (e == cudaSuccess) e = dalloc(&c->nbr_xi[b], N * MAX_NBR);
         }
         if (e == cudaSuccess) e = dalloc(&c->wall_xi, 4 * N);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dalloc(&c->nbr_cn[b], N * MAX_NBR);
         if (e == cudaSuccess) e = dalloc(&c->free_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->coupled_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->pbin, N);
         if (e == cudaSuccess) e = dalloc(&c->bin_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->prec, N);
         const size_t Np = (N + 31) / 32 * 32;
-        int **ia[] = {&c->parent, &c->label, &c->members, &c->roots, &c->big_ids};
+        int **ia[] = {&c->parent, &c->label, &c->members, &c->roots, &c->big_ids, &c->loud};
         for (int **q : ia) if (e == cudaSuccess) e = dalloc(q, N);
         if (e == cudaSuccess) e = dalloc(&c->isz, Np);
         if (e == cudaSuccess) e = dalloc(&c->ifill, Np);
+        if (e == cudaSuccess) e = dalloc(&c->iloud, Np);
+        if (e == cudaSuccess) e = dalloc(&c->exc, 2 * N);
         if (e == cudaSuccess) e = dalloc(&c->istart, Np + 32);
         if (e == cudaSuccess) e = cudaMemset(c->isz, 0, 4 * Np);
         if (e == cudaSuccess) e = cudaMemset(c->ifill, 0, 4 * Np);
@@ -448,7 +460,7 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
         CK(cudaMemset(c->F, 0, 16 * (size_t)n), "reset forces");
         CK(cudaMemset(c->T, 0, 8 * (size_t)n), "reset torques");
     }
-    CK(cudaMemset(c->counters, 0, 16), "reset counters");
+    CK(cudaMemset(c->counters, 0, 32), "reset counters");
     int rc = rebuild_table(c, nullptr, false);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -476,7 +488,7 @@ static int dem_cycle(imb_ctx *c, bool zero_forces) {
     CK(launch_dem_free(d, c->stream), "dem free");
     CK(launch_dem_islands(d, c->stream), "dem islands");
     CK(launch_dem_coupled(d, dem_coupled_blocks(), c->stream), "dem coupled");
-    c->launches += 8;
+    c->launches += 9;   // neighbours, link, label, alloc, fill, free, small + medium islands, coupled
     c->nbr_cur ^= 1;
     return rebuild_table(c, c->xs, zero_forces);
 }

@@ -45,11 +45,16 @@ struct DemArgs {
     int *nbr_cnt_old, *nbr_cnt;       // [np]
     int *nbr_id_old, *nbr_id;         // [np * MAX_NBR]
     double *nbr_xi_old, *nbr_xi;      // [np * MAX_NBR]
+    double *nbr_cn_old, *nbr_cn;      // [np * MAX_NBR] normal damping of each candidate pair
+    double *exc;                      // [np][2] excursion bounds of contact-free motion in the cycle
+    int *loud;                        // [np] 1 if p may touch a wall or a candidate within the cycle
+    int *iloud;                       // [np] per island root: 1 if any member is loud
     double *wall_xi;                  // [np * 4]
     int *free_ids, *coupled_ids;      // [np]
-    int *counters;                    // [0] free, [1] coupled, [2] small islands, [3] big-island particles
+    int *counters;                    // [0] free, [1] coupled, [2] small islands, [3] big-island
+                                      // particles, [4] member-list cursor, [5] medium islands
     int *parent, *label;              // [np] union-find forest and island of each particle
-    int *isz, *ifill, *istart;        // island sizes / fill cursors / starts (padded to 32, +32)
+    int *isz, *ifill, *istart;        // per root: island size, fill cursor, start in members
     int *members, *roots, *big_ids;   // [np] island members, roots of small islands, big-island particles
     const int *bin_start, *bin_ids;   // bins of the positions at cycle start
     int *pbin;                        // [np]

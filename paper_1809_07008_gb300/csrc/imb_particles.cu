@@ -144,6 +144,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *s
         dem_counters[1] = 0;
         dem_counters[2] = 0;
         dem_counters[3] = 0;
+        dem_counters[4] = 0;
+        dem_counters[5] = 0;
     }
 }
 
@@ -159,13 +161,17 @@ __global__ void k_bin_fill(const int *__restrict__ pbin, int np, int *fill, cons
 // Linear spring-dashpot contact seen from particle a (Eqs. 7-9): n from a to the
 // partner, t = z x n, (dvx, dvy) partner minus a, rot = w_a r_a + w_b r_b.
 // Returns the force on a and the tangential force magnitude.
-__device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double nyv, double delta,
-                                            double dvx, double dvy, double rot, double mstar,
-                                            double &xi, double &fx, double &fy, double &Ft) {
+// Normal damping of a pair of reduced mass m* (set from the restitution coefficient).
+__device__ __forceinline__ double damping_cn(const DemArgs &d, double mstar) {
+    return 2.0 * d.zeta * sqrt(mstar * d.kn);
+}
+
+__device__ __forceinline__ void contact_law_cn(const DemArgs &d, double nxv, double nyv, double delta,
+                                               double dvx, double dvy, double rot, double cn,
+                                               double &xi, double &fx, double &fy, double &Ft) {
     const double tx = -nyv, ty = nxv;
     const double vn = dvx * nxv + dvy * nyv;
     const double vt = (dvx * tx + dvy * ty) - rot;
-    const double cn = 2.0 * d.zeta * sqrt(mstar * d.kn);
     const double ct = d.ct_ratio * cn;
     xi = xi + vt * d.dt;                     // incremental tangential spring (Eq. 9)
     const double Fn = d.kn * delta - cn * vn; // Eq. 8, repulsive when positive
@@ -178,6 +184,38 @@ __device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double
     fx = -Fn * nxv + F_t * tx;
     fy = -Fn * nyv + F_t * ty;
     Ft = F_t;
+}
+
+__device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double nyv, double delta,
+                                            double dvx, double dvy, double rot, double mstar,
+                                            double &xi, double &fx, double &fy, double &Ft) {
+    contact_law_cn(d, nxv, nyv, delta, dvx, dvy, rot, damping_cn(d, mstar), xi, fx, fy, Ft);
+}
+
+// Force of candidate slot j on particle p (seen from p), the pair's damping constant
+// cached in the neighbour list.  Returns false (and releases the spring) without overlap.
+__device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const int j, const double px,
+                                           const double py, const double w, const double qx, const double qy,
+                                           const double qvx, const double qvy, const double qw,
+                                           const double vx, const double vy, double &fx, double &fy,
+                                           double &Ft) {
+    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
+    const int q = d.nbr_id[p * MAX_NBR + j];
+    double &xi = d.nbr_xi[p * MAX_NBR + j];
+    const double rp = d.r[p];
+    const double dx = min_image(qx - px, perx, d.nx);
+    const double dy = min_image(qy - py, pery, d.ny);
+    const double d2 = dx * dx + dy * dy;
+    const double R = rp + d.r[q];
+    if (!(d2 < R * R)) {  // Eq. 7: no overlap, the spring is released
+        xi = 0.0;
+        return false;
+    }
+    const double dist = sqrt(d2);
+    const double nxv = dx / dist, nyv = dy / dist;
+    const double rot = w * rp + qw * d.r[q];
+    contact_law_cn(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, d.nbr_cn[p * MAX_NBR + j], xi, fx, fy, Ft);
+    return true;
 }
 
 // Walls on the domain edges of non-periodic axes, an immovable partner (m* = m).
@@ -224,6 +262,58 @@ __device__ __forceinline__ void integrate(const DemArgs &d, int p, double Fcx, d
         if (py >= d.ny) py -= d.ny;
         else if (py < 0.0) py += d.ny;
     }
+}
+
+// Motion of particle p over one coupling cycle when it touches nothing: the accelerations
+// are evaluated once, with exactly the operations integrate() uses on zero contact sums.
+struct FreeMotion {
+    double ax, ay, al;   // accelerations
+    double ex, ey;       // bounds on |x(t) - x(0)| per axis within the cycle
+};
+
+__device__ __forceinline__ FreeMotion free_motion(const DemArgs &d, int p, double vx, double vy) {
+    FreeMotion f;
+    f.ax = (0.0 + d.F[2 * p]) / d.m[p] + d.gx_eff;
+    f.ay = (0.0 + d.F[2 * p + 1]) / d.m[p] + d.gy_eff;
+    f.al = (0.0 + d.T[p]) / d.I[p];
+    // constant a over N sub-cycles of dt = 1/N: after k of them the drift is
+    // v k dt + a dt^2 k (k + 1) / 2, so |dx| <= |v| + |a| (N + 1) / (2N) <= |v| + |a|;
+    // the margin covers the rounding of the updates
+    f.ex = fabs(vx) + fabs(f.ax) + 1e-6;
+    f.ey = fabs(vy) + fabs(f.ay) + 1e-6;
+    return f;
+}
+
+// No wall within reach and no periodic crossing during the cycle.
+__device__ __forceinline__ bool free_of_edges(const DemArgs &d, const FreeMotion &f, double px, double py,
+                                              double rp) {
+    return (d.bc_x != BC_WALL || (px - rp > f.ex && ((double)d.nx - px) - rp > f.ex)) &&
+           (d.bc_y != BC_WALL || (py - rp > f.ey && ((double)d.ny - py) - rp > f.ey)) &&
+           (d.bc_x != BC_PERIODIC || (px > f.ex && px < (double)d.nx - f.ex)) &&
+           (d.bc_y != BC_PERIODIC || (py > f.ey && py < (double)d.ny - f.ey));
+}
+
+// The N_sub sub-cycles of a particle that touches nothing: the updates of integrate().
+__device__ __forceinline__ void free_run(const DemArgs &d, const FreeMotion &f, double &px, double &py,
+                                         double &vx, double &vy, double &w) {
+    for (int s = 0; s < d.N_sub; ++s) {
+        vx = vx + f.ax * d.dt;
+        vy = vy + f.ay * d.dt;
+        w = w + f.al * d.dt;
+        px = px + vx * d.dt;
+        py = py + vy * d.dt;
+    }
+}
+
+// Candidate pair (p, q) cannot overlap within the cycle if both move freely: the gap
+// exceeds the sum of their excursion bounds.
+__device__ __forceinline__ bool pair_apart(const DemArgs &d, double px, double py, double rp, double exp_,
+                                           double eyp, double qx, double qy, double rq, double exq,
+                                           double eyq) {
+    const double dx = min_image(qx - px, d.bc_x == BC_PERIODIC, d.nx);
+    const double dy = min_image(qy - py, d.bc_y == BC_PERIODIC, d.ny);
+    const double M = rp + rq + (exp_ + exq) + (eyp + eyq);
+    return dx * dx + dy * dy > M * M;
 }
 
 __global__ void k_dem_neighbours(const DemArgs d) {
@@ -276,14 +366,31 @@ __global__ void k_dem_neighbours(const DemArgs d) {
         }
     const int nold = d.nbr_cnt_old[p];
     for (int j = 0; j < n; ++j) {
-        double xi = 0.0;
+        double xi = 0.0, cn = -1.0;
         for (int k = 0; k < nold; ++k)
-            if (d.nbr_id_old[p * MAX_NBR + k] == ids[j]) xi = d.nbr_xi_old[p * MAX_NBR + k];
+            if (d.nbr_id_old[p * MAX_NBR + k] == ids[j]) {
+                xi = d.nbr_xi_old[p * MAX_NBR + k];
+                cn = d.nbr_cn_old[p * MAX_NBR + k];
+            }
+        if (cn < 0.0) {   // a new candidate pair: its damping constant, once
+            const double mq = d.m[ids[j]], mp = d.m[p];
+            cn = damping_cn(d, mp * mq / (mp + mq));
+        }
         d.nbr_id[p * MAX_NBR + j] = ids[j];
         d.nbr_xi[p * MAX_NBR + j] = xi;
+        d.nbr_cn[p * MAX_NBR + j] = cn;
     }
     d.nbr_cnt[p] = n;
     d.parent[p] = p;
+    d.isz[p] = 0;
+    d.ifill[p] = 0;
+    d.iloud[p] = 0;
+    if (n > 0) {
+        const FreeMotion f = free_motion(d, p, d.v[2 * p], d.v[2 * p + 1]);
+        d.exc[2 * p] = f.ex;
+        d.exc[2 * p + 1] = f.ey;
+        d.loud[p] = !free_of_edges(d, f, px, py, rp);
+    }
     if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
     else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
 }
@@ -297,30 +404,14 @@ __global__ void k_dem_free(const DemArgs d) {
         double xiw[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) xiw[k] = d.wall_xi[4 * p + k];
-        // without a wall contact the accelerations are the same every sub-cycle:
-        // evaluate them once, with exactly the operations integrate() would use
-        const double ax0 = (0.0 + d.F[2 * p]) / mp + d.gx_eff;
-        const double ay0 = (0.0 + d.F[2 * p + 1]) / mp + d.gy_eff;
-        const double al0 = (0.0 + d.T[p]) / d.I[p];
-        // largest excursion of a free particle within one coupling cycle (unit time):
-        // |x(t) - x(0)| <= |v| + |a| / 2 per axis, plus a margin
-        const double ex = fabs(vx) + 0.5 * fabs(ax0) + 1e-6, ey = fabs(vy) + 0.5 * fabs(ay0) + 1e-6;
-        const bool quiet =
-            (d.bc_x != BC_WALL || (px - rp > ex && ((double)d.nx - px) - rp > ex)) &&
-            (d.bc_y != BC_WALL || (py - rp > ey && ((double)d.ny - py) - rp > ey)) &&
-            (d.bc_x != BC_PERIODIC || (px > ex && px < (double)d.nx - ex)) &&
-            (d.bc_y != BC_PERIODIC || (py > ey && py < (double)d.ny - ey));
-        if (quiet) {
-            // no wall within reach and no periodic crossing: the same updates as below
+        // candidate partners of a quiet island stay out of reach: their springs are released
+        for (int j = 0, nn = d.nbr_cnt[p]; j < nn; ++j) d.nbr_xi[p * MAX_NBR + j] = 0.0;
+        const FreeMotion f = free_motion(d, p, vx, vy);
+        const double ax0 = f.ax, ay0 = f.ay, al0 = f.al;
+        if (free_of_edges(d, f, px, py, rp)) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
-            for (int s = 0; s < d.N_sub; ++s) {
-                vx = vx + ax0 * d.dt;
-                vy = vy + ay0 * d.dt;
-                w = w + al0 * d.dt;
-                px = px + vx * d.dt;
-                py = py + vy * d.dt;
-            }
+            free_run(d, f, px, py, vx, vy, w);
         } else {
             const bool walls = d.bc_x == BC_WALL || d.bc_y == BC_WALL;
             for (int s = 0; s < d.N_sub; ++s) {
@@ -368,30 +459,14 @@ __global__ void k_dem_free(const DemArgs d) {
 template <typename NB>
 __device__ __forceinline__ void particle_substep(const DemArgs &d, const int p, double &px, double &py,
                                                  double &vx, double &vy, double &w, NB &&nb) {
-    const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
     const double rp = d.r[p], mp = d.m[p];
     double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
     const int n = d.nbr_cnt[p];
     for (int j = 0; j < n; ++j) {
-        const int q = d.nbr_id[p * MAX_NBR + j];
-        double &xi = d.nbr_xi[p * MAX_NBR + j];
         double qx, qy, qvx, qvy, qw;
-        nb(j, q, qx, qy, qvx, qvy, qw);
-        const double dx = min_image(qx - px, perx, d.nx);
-        const double dy = min_image(qy - py, pery, d.ny);
-        const double d2 = dx * dx + dy * dy;
-        const double R = rp + d.r[q];
-        if (!(d2 < R * R)) {  // Eq. 7: no overlap, the spring is released
-            xi = 0.0;
-            continue;
-        }
-        const double dist = sqrt(d2);
-        const double nxv = dx / dist, nyv = dy / dist;
-        const double mq = d.m[q];
-        const double mstar = mp * mq / (mp + mq);
-        const double rot = w * rp + qw * d.r[q];
+        nb(j, d.nbr_id[p * MAX_NBR + j], qx, qy, qvx, qvy, qw);
         double fx, fy, Ft;
-        contact_law(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, mstar, xi, fx, fy, Ft);
+        if (!pair_force(d, p, j, px, py, w, qx, qy, qvx, qvy, qw, vx, vy, fx, fy, Ft)) continue;
         Fcx += fx;
         Fcy += fy;
         Tc += rp * Ft;
@@ -471,8 +546,13 @@ __global__ void k_uf_link(const DemArgs d) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
         const int n = d.nbr_cnt[p];
+        const double px = d.x[2 * p], py = d.x[2 * p + 1], rp = d.r[p];
+        const double exp_ = d.exc[2 * p], eyp = d.exc[2 * p + 1];
+        int loud = d.loud[p];
         for (int j = 0; j < n; ++j) {
             const int q = d.nbr_id[p * MAX_NBR + j];
+            loud |= !pair_apart(d, px, py, rp, exp_, eyp, d.x[2 * q], d.x[2 * q + 1], d.r[q], d.exc[2 * q],
+                                d.exc[2 * q + 1]);
             if (q < p) continue;
             int a = p, b = q;
             for (;;) {
@@ -483,6 +563,7 @@ __global__ void k_uf_link(const DemArgs d) {
                 if (atomicCAS(&d.parent[a], a, b) == a) break;
             }
         }
+        d.loud[p] = loud;
     }
 }
 
@@ -493,6 +574,20 @@ __global__ void k_uf_label(const DemArgs d) {
         const int r = uf_find(d.parent, p);
         d.label[p] = r;
         atomicAdd(&d.isz[r], 1);
+        if (d.loud[p]) atomicOr(&d.iloud[r], 1);
+    }
+}
+
+constexpr int ISL_SMALL = 4;           // islands up to this size share a warp, 8 to a warp
+constexpr int ISL_WARPS = 4;
+constexpr int ISL_PAIRS = 96;          // pair-parallel up to this many candidate pairs
+
+// Roots reserve a contiguous range of the member list for their island.
+__global__ void k_island_alloc(const DemArgs d) {
+    const int ncpl = d.counters[1];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
+        const int p = d.coupled_ids[c];
+        if (d.label[p] == p) d.istart[p] = atomicAdd(&d.counters[4], d.isz[p]);
     }
 }
 
@@ -501,40 +596,133 @@ __global__ void k_island_fill(const DemArgs d) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
         const int r = d.label[p];
-        const int b = d.istart[r], size = d.istart[r + 1] - b;
-        d.members[b + atomicAdd(&d.ifill[r], 1)] = p;
-        if (size <= 32) {
+        if (!d.iloud[r]) {   // nothing in the island can touch within the cycle: free particles
+            d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
+            continue;
+        }
+        const int size = d.isz[r];
+        d.members[d.istart[r] + atomicAdd(&d.ifill[r], 1)] = p;
+        if (size <= ISL_SMALL) {
             if (p == r) d.roots[atomicAdd(&d.counters[2], 1)] = r;
+        } else if (size <= 32) {
+            if (p == r) d.roots[d.np - 1 - atomicAdd(&d.counters[5], 1)] = r;   // filled from the end
         } else {
             d.big_ids[atomicAdd(&d.counters[3], 1)] = p;
         }
     }
 }
 
-// One warp per island of at most 32 particles: all N_sub sub-cycles with the island
-// state in shared memory (double-buffered), lanes synchronised by __syncwarp.
-constexpr int ISL_WARPS = 4;
+// Islands of at most ISL_SMALL particles, eight per warp in lane groups of ISL_SMALL:
+// all N_sub sub-cycles with the state in shared memory, the whole warp in lockstep.
+constexpr int SMALL_PER_WARP = 32 / ISL_SMALL;
 
-__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d) {
+__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemArgs d) {
     __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
     __shared__ int s_id[ISL_WARPS][32];
     __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / ISL_SMALL, k = lane % ISL_SMALL, g0 = grp * ISL_SMALL;
     const int nisl = d.counters[2];
-    for (int i = blockIdx.x * ISL_WARPS + warp; i < nisl; i += gridDim.x * ISL_WARPS) {
+    const int i = (blockIdx.x * ISL_WARPS + warp) * SMALL_PER_WARP + grp;
+    if ((blockIdx.x * ISL_WARPS + warp) * SMALL_PER_WARP >= nisl) return;   // whole warp idle
+    int p = -1, n = 0;
+    if (i < nisl) {
         const int r = d.roots[i];
-        const int b = d.istart[r], n = d.istart[r + 1] - b;
+        n = d.isz[r];
+        if (k < n) p = d.members[d.istart[r] + k];
+    }
+    const bool act = p >= 0;
+    s_id[warp][lane] = p;
+    __syncwarp();
+    if (act) {
+        const int nn = d.nbr_cnt[p];
+        for (int j = 0; j < nn; ++j) {
+            const int q = d.nbr_id[p * MAX_NBR + j];
+            int l = g0;
+            while (l < g0 + n - 1 && s_id[warp][l] != q) ++l;   // q is in the same island
+            s_nl[warp][lane][j] = (unsigned char)l;
+        }
+        s_st[warp][0][0][lane] = d.x[2 * p];
+        s_st[warp][0][1][lane] = d.x[2 * p + 1];
+        s_st[warp][0][2][lane] = d.v[2 * p];
+        s_st[warp][0][3][lane] = d.v[2 * p + 1];
+        s_st[warp][0][4][lane] = d.w[p];
+    }
+    __syncwarp();
+    for (int s = 0; s < d.N_sub; ++s) {
+        const int cur = s & 1;
+        const double(*st)[32] = s_st[warp][cur];
+        if (act) {
+            double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], w = st[4][lane];
+            particle_substep(d, p, px, py, vx, vy, w,
+                             [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
+                                 const int l = s_nl[warp][lane][j];
+                                 qx = st[0][l];
+                                 qy = st[1][l];
+                                 qvx = st[2][l];
+                                 qvy = st[3][l];
+                                 qw = st[4][l];
+                             });
+            s_st[warp][cur ^ 1][0][lane] = px;
+            s_st[warp][cur ^ 1][1][lane] = py;
+            s_st[warp][cur ^ 1][2][lane] = vx;
+            s_st[warp][cur ^ 1][3][lane] = vy;
+            s_st[warp][cur ^ 1][4][lane] = w;
+        }
+        __syncwarp();
+    }
+    if (act) {
+        const int fin = d.N_sub & 1;
+        d.x[2 * p] = s_st[warp][fin][0][lane];
+        d.x[2 * p + 1] = s_st[warp][fin][1][lane];
+        d.v[2 * p] = s_st[warp][fin][2][lane];
+        d.v[2 * p + 1] = s_st[warp][fin][3][lane];
+        d.w[p] = s_st[warp][fin][4][lane];
+    }
+}
+
+// One warp per island of at most 32 particles: all N_sub sub-cycles with the island
+// state in shared memory (double-buffered), lanes synchronised by __syncwarp.  Each
+// sub-cycle first evaluates the island's candidate pairs one per lane (the force of
+// slot j on particle i), then lane i sums its pairs in slot order -- the order of a
+// sequential evaluation -- adds the walls and integrates.
+
+__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d) {
+    __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
+    __shared__ double s_f[ISL_WARPS][3][ISL_PAIRS];     // fx, fy, Ft per pair
+    __shared__ int s_id[ISL_WARPS][32];
+    __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
+    __shared__ unsigned char s_pi[ISL_WARPS][ISL_PAIRS], s_pj[ISL_WARPS][ISL_PAIRS], s_on[ISL_WARPS][ISL_PAIRS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nisl = d.counters[5];
+    for (int i = blockIdx.x * ISL_WARPS + warp; i < nisl; i += gridDim.x * ISL_WARPS) {
+        const int r = d.roots[d.np - 1 - i];
+        const int b = d.istart[r], n = d.isz[r];
         const bool act = lane < n;
         const int p = act ? d.members[b + lane] : -1;
+        const int nn = act ? d.nbr_cnt[p] : 0;
         s_id[warp][lane] = p;
+        // pairs of lane i occupy [off, off + nn)
+        int off = nn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += t;
+        }
+        const int npairs = __shfl_sync(0xffffffffu, off, 31);
+        off -= nn;
+        const bool pairwise = npairs <= ISL_PAIRS;
         __syncwarp();
         if (act) {
-            const int nn = d.nbr_cnt[p];
             for (int j = 0; j < nn; ++j) {
                 const int q = d.nbr_id[p * MAX_NBR + j];
                 int l = 0;
                 while (l < n - 1 && s_id[warp][l] != q) ++l;   // q is in the same island
                 s_nl[warp][lane][j] = (unsigned char)l;
+                if (pairwise) {
+                    s_pi[warp][off + j] = (unsigned char)lane;
+                    s_pj[warp][off + j] = (unsigned char)j;
+                }
             }
             s_st[warp][0][0][lane] = d.x[2 * p];
             s_st[warp][0][1][lane] = d.x[2 * p + 1];
@@ -545,19 +733,44 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d)
         __syncwarp();
         for (int s = 0; s < d.N_sub; ++s) {
             const int cur = s & 1;
+            const double(*st)[32] = s_st[warp][cur];
+            if (pairwise) {
+                for (int k = lane; k < npairs; k += 32) {
+                    const int li = s_pi[warp][k], j = s_pj[warp][k];
+                    const int l = s_nl[warp][li][j];
+                    double fx = 0.0, fy = 0.0, Ft = 0.0;
+                    s_on[warp][k] = pair_force(d, s_id[warp][li], j, st[0][li], st[1][li], st[4][li], st[0][l],
+                                               st[1][l], st[2][l], st[3][l], st[4][l], st[2][li], st[3][li], fx, fy, Ft);
+                    s_f[warp][0][k] = fx;
+                    s_f[warp][1][k] = fy;
+                    s_f[warp][2][k] = Ft;
+                }
+                __syncwarp();
+            }
             if (act) {
-                double px = s_st[warp][cur][0][lane], py = s_st[warp][cur][1][lane];
-                double vx = s_st[warp][cur][2][lane], vy = s_st[warp][cur][3][lane];
-                double w = s_st[warp][cur][4][lane];
-                particle_substep(d, p, px, py, vx, vy, w,
-                                 [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
-                                     const int l = s_nl[warp][lane][j];
-                                     qx = s_st[warp][cur][0][l];
-                                     qy = s_st[warp][cur][1][l];
-                                     qvx = s_st[warp][cur][2][l];
-                                     qvy = s_st[warp][cur][3][l];
-                                     qw = s_st[warp][cur][4][l];
-                                 });
+                double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], w = st[4][lane];
+                if (pairwise) {
+                    const double rp = d.r[p], mp = d.m[p];
+                    double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+                    for (int j = 0; j < nn; ++j) {
+                        if (!s_on[warp][off + j]) continue;
+                        Fcx += s_f[warp][0][off + j];
+                        Fcy += s_f[warp][1][off + j];
+                        Tc += rp * s_f[warp][2][off + j];
+                    }
+                    wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
+                    integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+                } else {
+                    particle_substep(d, p, px, py, vx, vy, w,
+                                     [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
+                                         const int l = s_nl[warp][lane][j];
+                                         qx = st[0][l];
+                                         qy = st[1][l];
+                                         qvx = st[2][l];
+                                         qvy = st[3][l];
+                                         qw = st[4][l];
+                                     });
+                }
                 s_st[warp][cur ^ 1][0][lane] = px;
                 s_st[warp][cur ^ 1][1][lane] = py;
                 s_st[warp][cur ^ 1][2][lane] = vx;
@@ -676,15 +889,17 @@ cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s) {
     const int g = blocks_for(d.np, 128);
     k_uf_link<<<g, 128, 0, s>>>(d);
     k_uf_label<<<g, 128, 0, s>>>(d);
-    cudaError_t e = launch_bin_scan(d.isz, d.ifill, d.istart, d.np, nullptr, s);
-    if (e != cudaSuccess) return e;
+    k_island_alloc<<<g, 128, 0, s>>>(d);
     k_island_fill<<<g, 128, 0, s>>>(d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
-    k_dem_islands<<<blocks_for(d.np, 32 * ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
+    // enough warps for every island at once: at most np/2 islands of two or more particles,
+    // at most np/5 of five or more
+    k_dem_small_islands<<<blocks_for(blocks_for(d.np / 2 + 1, SMALL_PER_WARP), ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
+    k_dem_islands<<<blocks_for(d.np / 5 + 1, ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
     return cudaGetLastError();
 }
 

@@ -184,6 +184,34 @@ def test_dem_only_with_frozen_fluid_force_bit_exact(orc, imb):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("bc_x", [W.BC_WALL, W.BC_PERIODIC])
+def test_dem_gas_quiet_and_touching_islands_bit_exact(orc, imb, bc_x):
+    # a dilute gas of disks: candidate pairs far enough apart to move freely through the
+    # cycle, pairs that collide, separate again and cross the periodic edge, all bit for bit
+    nx, ny, n, R = 160, 120, 100, 5.0
+    x, r = W.random_sequential_addition(nx, ny, n, lambda g: R + g.uniform_range(-0.5, 0.5), 11, gap=0.3,
+                                        periodic_x=bc_x == W.BC_PERIODIC, wall_gap=0.3)
+    v = W.random_directions(n, 0.06, 12)
+    w = W.Workload(name="gas", nx=nx, ny=ny, tau=0.6, bc_x=bc_x, bc_y=W.BC_WALL, dem_on=1, N_sub=20,
+                   gravity=(0.0, -1e-4), e_rest=0.7, mu=0.3, x=x, v=v, omega=np.zeros(n), r=r)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    rng = np.random.default_rng(3)
+    F = 1e-1 * rng.standard_normal((n, 2))
+    T = 1e-1 * rng.standard_normal(n)
+    o.set_forces(F, T)
+    g.set_forces(F, T)
+    touched = 0
+    for cycle in range(240):
+        o.dem_substeps(w.N_sub)
+        g.dem_step(1)
+        touched += len(o.contacts()) > 0
+        if cycle % 20 == 19:
+            for a, b in zip(o.particles(), g.particles()):
+                assert np.array_equal(a, b)
+    assert touched >= 10
+
+
 def test_moving_particles_coupled_parity(orc, imb):
     # c3 at the same density on 256 x 192: DEM + IMB + Smagorinsky, tau = 0.51
     w = W.c3sub(steps=0, nx=256, ny=192)
