@@ -51,6 +51,7 @@ struct imb_ctx {
     int *bin_count = nullptr, *bin_fill = nullptr, *bin_start = nullptr, *bin_ids = nullptr;
     GridBarrier *barrier = nullptr;
     unsigned *err = nullptr;
+    unsigned *tile_ctr = nullptr;
     TileCand *tiles = nullptr;      // per 32 x 32 tile: particles that can reach it
     float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
     size_t eps_tab_cap = 0;
@@ -147,6 +148,7 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.F = c->F;
     a.T = c->T;
     a.err = c->err;
+    a.tile_ctr = c->tile_ctr;
     return a;
 }
 
@@ -239,6 +241,7 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->counters);
     dfree(c->barrier);
     dfree(c->err);
+    dfree(c->tile_ctr);
     dfree(c->tiles);
     dfree(c->eps_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -327,7 +330,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     if ((e = dalloc(&c->bin_count, nbins_pad)) != cudaSuccess || (e = dalloc(&c->bin_fill, nbins_pad)) != cudaSuccess ||
         (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
-        (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
+        (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
     cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
     for (int b = 0; b < 2; ++b)
@@ -340,6 +343,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     cudaMemsetAsync(c->counters, 0, sizeof(int) * 8, c->stream);
     cudaMemsetAsync(c->barrier, 0, sizeof(GridBarrier), c->stream);
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream);
+    cudaMemsetAsync(c->tile_ctr, 0, 2 * sizeof(unsigned), c->stream);
     LatticeArgs a = lattice_args(c);
     for (int b = 0; b < 2; ++b) {
         if ((e = launch_init_populations(c->fbuf[b], p.storage, a, (float)p.rho0, (float)p.ux0,
@@ -561,6 +565,7 @@ extern "C" int imb_sync(imb_ctx *c) {
     if (bits & ERR_TILE_LIST) return fail(c, IMB_E_OVERFLOW, "more than 32 particles touch one tile");
     if (bits & ERR_NEIGHBOURS) return fail(c, IMB_E_OVERFLOW, "DEM neighbour list full (16)");
     if (bits & ERR_BARRIER) return fail(c, IMB_E_TIMEOUT, "DEM grid barrier timed out");
+    if (bits & ERR_TMA) return fail(c, IMB_E_TIMEOUT, "wait on a stream-collide tile copy timed out");
     if (bits & ERR_SKIN) return fail(c, IMB_E_SKIN, "a particle moved more than skin/2 in one step");
     return fail(c, IMB_E_CUDA, "unknown device error flag");
 }

@@ -31,6 +31,7 @@ struct LatticeArgs {
     double *F;                 // [2 np] hydrodynamic force accumulators
     double *T;                 // [np]   hydrodynamic torque accumulators
     unsigned *err;
+    unsigned *tile_ctr;        // [2] tiles handed out and blocks finished (zero between launches)
 };
 
 // DEM state and parameters (FP64).

@@ -240,19 +240,6 @@ __device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared
 }
 
 // ------------------------------------------------- fused stream-collide
-// Solid ratio of the cell at offset (di, dk) from the centre cell of tile candidate
-// P: 0 when the disk does not reach in, 1 when the cell is fully covered (exact-area
-// mode), else the value that k_particle_eps stored for this particle and offset.
-__device__ __forceinline__ float cand_eps(const PRec &P, int di, int dk, const float *__restrict__ tab,
-                                          int tw, int th, bool exact, bool &covered) {
-    const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
-    const int st = cover_state(lox, loy, P.r);
-    covered = st != 0;
-    if (st == 0) return 0.0f;
-    if (st == 2 && exact) return 1.0f;
-    return __ldg(tab + (dk + th) * tw + (di + th));
-}
-
 // Macroscopic state of one node (Eqs. 2-4) and its relaxation rate.
 struct NodeState {
     float drho, rho, jx, jy, ux, uy, usq, te, omega;
@@ -335,63 +322,69 @@ __device__ __forceinline__ void node_collide_store(const float (&d)[9], const No
     }
 }
 
-// Immersed moving boundary at one node (Sec. 2.3): the node at tile offset (xl, yy)
-// is covered by the candidates of `mask` (a subset of the warp-uniform `uni`).  Total
-// solid ratio -> B (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps ->
-// solid-velocity moments; the per-particle force and torque (Eqs. 15-16) are reduced
-// over the warp into part[s] (lane 0, warp-private).
-__device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned mask,
-                                         const unsigned uni, const bool act, const PRec *__restrict__ cand,
-                                         const int *__restrict__ cid, float (*part)[3], const LatticeArgs &a,
-                                         SolidMoments &sm) {
+// Solid ratio of a node that candidate P is known to reach into (covers() true):
+// 1 when the cell is fully covered in exact-area mode, else the value k_particle_eps
+// stored for this particle and offset.
+__device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const float *__restrict__ tab, int tw,
+                                          int th, bool exact) {
+    if (exact && fully_covered(__fsub_rn((float)di, P.fx), __fsub_rn((float)dk, P.fy), P.r)) return 1.0f;
+    return __ldg(tab + (dk + th) * tw + (di + th));
+}
+
+// Immersed moving boundary at one node (Sec. 2.3).  Bit s of `cm` is set when tile
+// candidate s reaches into the node; `U` is the warp-uniform union of the batch's cm;
+// e0 and e1 are the solid ratios of the node's first two candidates (looked up while the
+// node was queued).  Total solid ratio -> B (Eq. 14) -> per-particle weights
+// B_p = B eps_p / sum eps -> solid-velocity moments; the per-particle force and torque
+// (Eqs. 15-16) are reduced over the warp into part[s] by lane 0 of each warp.
+__device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
+                                         const unsigned U, const float e0, const float e1,
+                                         const PRec *__restrict__ cand, const int *__restrict__ cid,
+                                         float (*part)[3], const LatticeArgs &a, SolidMoments &sm) {
     const int lane = threadIdx.x & 31;
     const bool exact = a.eps_mode == EPS_EXACT;
     sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
-    float esum = 0.0f;
-    int ns = 0;
-    for (unsigned m = uni; m; m &= m - 1u) {
-        const int s = __ffs(m) - 1;
-        if (!act || !((mask >> s) & 1u)) continue;
-        const PRec &P = cand[s];
-        bool cov;
-        const float e = cand_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w,
-                                 a.tab_h, exact, cov);
-        if (cov) {
-            esum += e;
-            ++ns;
-        }
-    }
+    const int ns = __popc(cm);
     if (ns > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
+    auto eps_of = [&](unsigned below, int s) {   // solid ratio of slot s; `below` = cm bits under s
+        const int i = __popc(below);
+        if (i == 0) return e0;
+        if (i == 1) return e1;
+        const PRec &P = cand[s];
+        return slot_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
+                        exact);
+    };
+    float esum = e0;   // summed in slot order
+    if (ns > 1) esum += e1;
+    for (unsigned m = (cm & (cm - 1u)) & ((cm & (cm - 1u)) - 1u); m; m &= m - 1u) {
+        const int s = __ffs(m) - 1;
+        esum += eps_of(cm & ((1u << s) - 1u), s);
+    }
     if (esum > 0.0f) {
         const float eps = fminf(esum, 1.0f);
         const float tm = c.te - 0.5f;
         sm.B = eps * tm / ((1.0f - eps) + tm);                  // Eq. 14
     }
     const float Bs = sm.B > 0.0f ? __fdividef(sm.B, esum) : 0.0f;
-    for (unsigned m = uni; m; m &= m - 1u) {
+    for (unsigned m = U; m; m &= m - 1u) {
         const int s = __ffs(m) - 1;
         float Bp = 0.0f, vx = 0.0f, vy = 0.0f, vt = 0.0f;
-        if (act && ((mask >> s) & 1u) && Bs > 0.0f) {
+        if (((cm >> s) & 1u) && Bs > 0.0f) {
             const PRec &P = cand[s];
             const int di = xl - P.ci, dk = yy - P.cj;
-            bool cov;
-            const float e = cand_eps(P, di, dk, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
-                                     exact, cov);
-            if (cov) {
-                Bp = Bs * e;
-                const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
-                const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
-                const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
-                sm.m1x += Bp * usx;
-                sm.m1y += Bp * usy;
-                sm.m2xx += Bp * usx * usx;
-                sm.m2xy += Bp * usx * usy;
-                sm.m2yy += Bp * usy * usy;
-                // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
-                vx = Bp * (c.jx - c.rho * usx - a.Fx);
-                vy = Bp * (c.jy - c.rho * usy - a.Fy);
-                vt = rx * vy - ry * vx;
-            }
+            Bp = Bs * eps_of(cm & ((1u << s) - 1u), s);
+            const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
+            const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
+            const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
+            sm.m1x += Bp * usx;
+            sm.m1y += Bp * usy;
+            sm.m2xx += Bp * usx * usx;
+            sm.m2xy += Bp * usx * usy;
+            sm.m2yy += Bp * usy * usy;
+            // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
+            vx = Bp * (c.jx - c.rho * usx - a.Fx);
+            vy = Bp * (c.jy - c.rho * usy - a.Fy);
+            vt = rx * vy - ry * vx;
         }
         if (!__any_sync(FULL, Bp > 0.0f)) continue;
 #pragma unroll
@@ -423,18 +416,18 @@ __device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int 
     return __ballot_sync(FULL, rel);
 }
 
-// Work unit of the persistent kernel: HROWS rows of a tile (a full 32 x 32 tile by
-// default); NST units are in flight per block.  TMA boxes: the x start must be 16-byte aligned, so the six planes
-// pulled from x - 1 or x + 1 (c_x = +-1) take a box HALO cells wider than the tile
-// (starting HALO cells left of the tile for c_x = +1), the three with c_x = 0 exactly
-// the tile width.
-constexpr int HROWS = TILE;              // rows per work unit
-constexpr int UPT = TILE / HROWS;        // work units per tile
-constexpr int NST = 2;                   // pipeline stages per block
+// Work unit of the persistent kernel: HROWS rows of a 32 x 32 tile; NST units are in
+// flight per block, so that NST - 1 of them are loading while one is computed.  TMA
+// boxes: the x start must be 16-byte aligned, so the six planes pulled from x - 1 or
+// x + 1 (c_x = +-1) take a box HALO cells wider than the tile (starting HALO cells left
+// of the tile for c_x = +1), the three with c_x = 0 exactly the tile width.
+constexpr int HROWS = TILE;              // rows per work unit (one tile)
 constexpr int RPW = HROWS / WARPS;       // rows per warp per unit
+constexpr int QCAP = HROWS * 32;         // immersed-node queue of a unit
 
 template <typename S> struct Box {
     static constexpr int HALO = 16 / (int)sizeof(S);
+    static constexpr int NST = sizeof(S) == 4 ? 2 : 3;   // units in flight per block
     static constexpr int WN = TILE, WW = TILE + HALO;
     __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
     __host__ __device__ static constexpr int offset(int q) {   // elements before plane q
@@ -449,43 +442,54 @@ template <typename S> struct Box {
     static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
     static constexpr int PART_FLOATS = 2 * WARPS * TILE_CAND * 3;
-    static constexpr int QUEUE_SHORTS = WARPS * RPW * 32;   // immersed cells per warp and unit
-    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QUEUE_SHORTS * 2 + WARPS * RPW * 4;
+    // force partials (two units), queue (solid ratios, cover masks, node offsets), two
+    // queue counters, the tile of each stage (index, column, row, spare)
+    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 8 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
 static_assert((Box<float>::WN * HROWS * 4) % 128 == 0 && (Box<float>::WW * HROWS * 4) % 128 == 0 &&
                   (Box<__half>::WN * HROWS * 2) % 128 == 0 && (Box<__half>::WW * HROWS * 2) % 128 == 0,
               "TMA boxes stay 128-byte aligned in shared memory");
+static_assert(Box<float>::EXTRA_BYTES % 8 == 0 && Box<__half>::EXTRA_BYTES % 8 == 0, "mbarrier alignment");
+static_assert(2 * (Box<float>::SMEM_BYTES + 1024) <= 228 * 1024 && 2 * (Box<__half>::SMEM_BYTES + 1024) <= 228 * 1024,
+              "two blocks per SM");
 
 __device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
     // every neighbour read of the tile lies inside the lattice: no boundary rule applies
     return bx >= 1 && by >= 1 && (bx + 1) * TILE <= nx - 1 && (by + 1) * TILE <= ny - 1;
 }
 
-// Persistent fused stream-collide.  Block b walks the half tiles of tiles
-// t = b + j * gridDim.x.  Thread 0 keeps NST units in flight: for interior tiles nine
-// TMA boxes (one per population plane, rows shifted by -c_y) plus the tile's candidate
-// block; boundary tiles take the candidate block only and pull their populations with
-// the boundary rules.
+// Persistent fused stream-collide.  Tiles are handed out dynamically (a counter in
+// global memory), so that blocks finish together whatever their mix of interior and
+// boundary tiles.  Thread 0 keeps NST tiles in flight: for interior tiles nine TMA boxes
+// (one per population plane, rows shifted by -c_y) plus the tile's candidate block;
+// boundary tiles take the candidate block only and pull their populations with the
+// boundary rules.  Pass A collides the fluid nodes and queues, block-wide, the nodes a
+// disk reaches into with their candidate mask; pass B spreads the queue over the warps.
+// A stage is handed back, and the forces of its tile flushed, once every warp has
+// passed the top of the next tile.
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 2)
 k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_constant__ CUtensorMap tmap_w,
                  const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
                  const TileCand *__restrict__ tiles, const int ntiles) {
     using G = Box<S>;
+    constexpr int NST = G::NST;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
     float *part_base = reinterpret_cast<float *>(extra);
-    short *queue = reinterpret_cast<short *>(extra + G::PART_FLOATS * 4) + (threadIdx.x >> 5) * RPW * 32;
-    unsigned *rmask = reinterpret_cast<unsigned *>(extra + G::PART_FLOATS * 4 + G::QUEUE_SHORTS * 2) +
-                      (threadIdx.x >> 5) * RPW;
+    float2 *q_e = reinterpret_cast<float2 *>(extra + G::PART_FLOATS * 4);
+    unsigned *q_cm = reinterpret_cast<unsigned *>(q_e + QCAP);
+    unsigned short *q_node = reinterpret_cast<unsigned short *>(q_cm + QCAP);
+    int *q_count = reinterpret_cast<int *>(q_node + QCAP);
+    int4 *stage_tile = reinterpret_cast<int4 *>(q_count + 4);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(extra + G::EXTRA_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nbx = a.nbx;
     const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
     const bool smag = a.smag_coef > 0.0f;
 
     for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part_base[i] = 0.0f;
+    if (threadIdx.x < 2) q_count[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
@@ -496,37 +500,79 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     auto stage_cand = [&](int st) {
         return reinterpret_cast<TileCand *>(smem + st * G::STAGE_BYTES + G::POP_BYTES);
     };
-    auto issue = [&](int k, int st) {
-        const int t = blockIdx.x + (k / UPT) * gridDim.x;
-        if (t >= ntiles) return;
-        const int bx = t % nbx, by = t / nbx;
+    // producer (thread 0): takes the next tile and starts its copies into the next stage;
+    // after the first tile past the end it hands out nothing more
+    int pk = 0;
+    bool pdone = false;
+    int next_t = threadIdx.x == 0 ? (int)atomicAdd(&a.tile_ctr[0], 1u) : 0;   // taken one tile ahead
+    auto issue_next = [&]() {
+        if (pdone) return;
+        const int st = pk++ % NST;
+        const int t = next_t;
+        if (t >= ntiles) {
+            pdone = true;
+            stage_tile[st] = make_int4(-1, 0, 0, 0);
+            mbar_arrive_expect_tx(&mbar[st], 0u);
+            return;
+        }
+        next_t = (int)atomicAdd(&a.tile_ctr[0], 1u);
+        const int bx = t % a.nbx, by = t / a.nbx;
+        stage_tile[st] = make_int4(t, bx, by, 0);
         const bool in = tma_tile(bx, by, a.nx, a.ny);
         mbar_arrive_expect_tx(&mbar[st], (uint32_t)sizeof(TileCand) + (in ? (uint32_t)G::POP_BYTES : 0u));
         bulk_load(stage_cand(st), &tiles[t], (uint32_t)sizeof(TileCand), &mbar[st]);
         if (in) {
-            const int x0 = bx * TILE, yb = by * TILE + (k % UPT) * HROWS;
+            const int x0 = bx * TILE, y0 = by * TILE;
 #pragma unroll
             for (int q = 0; q < 9; ++q)
                 tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
-                            cx_of(q) == 1 ? x0 - G::HALO : x0, yb - cy_of(q), q, &mbar[st]);
+                            cx_of(q) == 1 ? x0 - G::HALO : x0, y0 - cy_of(q), q, &mbar[st]);
         }
     };
     if (threadIdx.x == 0)
-        for (int k = 0; k < NST; ++k) issue(k, k);
+        for (int k = 0; k < NST; ++k) issue_next();
     bool unstable = false;
+    int fid = -1;   // particle whose force component this thread flushes for the previous tile
     for (int k = 0;; ++k) {
-        const int t = blockIdx.x + (k / UPT) * gridDim.x;
-        if (t >= ntiles) break;
-        const int h = k % UPT;
         const int st = k % NST;
+        const int qc = k & 1;
         const bool ok = mbar_wait(&mbar[st], (uint32_t)((k / NST) & 1));
-        const int bx = t % nbx, by = t / nbx;
-        const int x0 = bx * TILE, y0 = by * TILE;
-        const bool in = tma_tile(bx, by, a.nx, a.ny);
+        const int4 ti = stage_tile[st];
+        const int bad = __syncthreads_or(!ok);
+        // every warp is past the previous tile: its stage goes back to the copy engine
+        // and its forces are flushed
+        if (k > 0) {
+            if (threadIdx.x == 0 && !bad) {
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            if (fid >= 0) {
+                const int s = threadIdx.x / 3, c = threadIdx.x - 3 * s;
+                float *pb = part_base + (qc ^ 1) * WARPS * TILE_CAND * 3 + s * 3 + c;
+                double acc = 0.0;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) {
+                    acc += (double)pb[w * TILE_CAND * 3];
+                    pb[w * TILE_CAND * 3] = 0.0f;
+                }
+                if (acc != 0.0) {
+                    if (c < 2) atomicAdd(&a.F[2 * fid + c], acc);
+                    else atomicAdd(&a.T[fid], acc);
+                }
+            }
+        }
+        if (bad) {
+            if (threadIdx.x == 0) set_err(a.err, ERR_TMA);
+            break;
+        }
+        if (ti.x < 0) break;   // past the last tile (the same value in every thread)
+        const int h = 0;
+        const int x0 = ti.y * TILE, y0 = ti.z * TILE;
+        const bool in = tma_tile(ti.y, ti.z, a.nx, a.ny);
         const TileCand *tc = stage_cand(st);
-        const int nc = ok ? min(tc->n, TILE_CAND) : 0;
+        const int nc = min(tc->n, TILE_CAND);
         const S *pop = stage_pop(st);
-        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + ((k & 1) * WARPS + warp) * TILE_CAND * 3);
+        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + (qc * WARPS + warp) * TILE_CAND * 3);
         auto load_node = [&](int xl, int yy, float (&d)[9]) {
             if (in) {
                 const int r = yy - h * HROWS;
@@ -539,89 +585,98 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 for (int q = 0; q < 9; ++q) d[q] = 0.0f;
             }
         };
-        // pass A: every row of the warp; fluid nodes collide and store here, nodes that
-        // a disk reaches into are queued (tile row * 32 + lane)
+        // pass A: the warp's rows; fluid nodes collide and store here, nodes that a disk
+        // reaches into are queued with the mask of the candidates that reach them
         const int x = x0 + lane;
         const bool xin = x < a.nx;
-        int nq = 0;
-        unsigned uni = 0u;
 #pragma unroll 1
         for (int rr = 0; rr < RPW; ++rr) {
             const int yy = h * HROWS + warp + WARPS * rr;
             const int y = y0 + yy;
-            if (y >= a.ny) {
-                if (lane == 0) rmask[rr] = 0u;
-                continue;
-            }
+            if (y >= a.ny) continue;
             float d[9];
             load_node(lane, yy, d);
             const unsigned mask = nc ? row_mask(tc->p, nc, yy, true) : 0u;
-            if (lane == 0) rmask[rr] = mask;
-            uni |= mask;
-            bool imb = false;
+            unsigned cm = 0u;
             for (unsigned m = mask; m; m &= m - 1u) {
-                const PRec &P = tc->p[__ffs(m) - 1];
-                imb |= covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r);
+                const int s = __ffs(m) - 1;
+                const PRec &P = tc->p[s];
+                if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
+                    cm |= 1u << s;
             }
-            imb = imb && xin;
-            const unsigned ib = __ballot_sync(FULL, imb);
-            if (imb) queue[nq + __popc(ib & ((1u << lane) - 1u))] = (short)(yy * 32 + lane);
-            nq += __popc(ib);
+            if (!xin) cm = 0u;
+            const unsigned ib = __ballot_sync(FULL, cm != 0u);
+            if (ib) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&q_count[qc], __popc(ib));
+                base = __shfl_sync(FULL, base, 0);
+                if (cm) {
+                    const int i = base + __popc(ib & ((1u << lane) - 1u));
+                    // solid ratios of the first two candidates, fetched now so that the
+                    // table reads overlap the rest of this pass
+                    float2 e = make_float2(0.0f, 0.0f);
+                    const bool exact = a.eps_mode == EPS_EXACT;
+                    const int sa = __ffs(cm) - 1;
+                    const PRec &Pa = tc->p[sa];
+                    e.x = slot_eps(Pa, lane - Pa.ci, yy - Pa.cj, a.eps_tab + (size_t)tc->id[sa] * a.tab_stride,
+                                   a.tab_w, a.tab_h, exact);
+                    const unsigned rest = cm & (cm - 1u);
+                    if (rest) {
+                        const int sb = __ffs(rest) - 1;
+                        const PRec &Pb = tc->p[sb];
+                        e.y = slot_eps(Pb, lane - Pb.ci, yy - Pb.cj,
+                                       a.eps_tab + (size_t)tc->id[sb] * a.tab_stride, a.tab_w, a.tab_h, exact);
+                    }
+                    q_e[i] = e;
+                    q_cm[i] = cm;
+                    q_node[i] = (unsigned short)((yy - h * HROWS) * 32 + lane);
+                }
+            }
             if (ib != FULL) {
                 NodeState c;
                 node_state(d, a, forced, smag, c);
                 if (xin && !(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
-                if (xin && !imb) {
+                if (xin && !cm) {
                     const SolidMoments none = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
                     node_collide_store(d, c, none, fout + (size_t)y * a.pitch + x, a, forced);
                 }
             }
         }
-        __syncwarp();
-        // pass B: the queued immersed-boundary nodes, 32 at a time
+        __syncthreads();   // the unit's queue is complete
+        const int nq = min(q_count[qc], QCAP);
+        if (threadIdx.x == 0) q_count[qc ^ 1] = 0;   // the next unit's counter, last read a unit ago
+        // pass B: the queued immersed-boundary nodes, 32 per warp at a time
 #pragma unroll 1
-        for (int base = 0; base < nq; base += 32) {
+        for (int base = warp * 32; base < nq; base += WARPS * 32) {
             const bool act = base + lane < nq;
-            const int e = queue[act ? base + lane : base];
-            const int yy = e >> 5, xl = e & 31;
-            const unsigned mask = rmask[(yy - h * HROWS - warp) / WARPS];
+            const int i = act ? base + lane : base;
+            const unsigned cm = act ? q_cm[i] : 0u;
+            const float2 qe = q_e[i];
+            const int e = q_node[i];
+            const int yy = h * HROWS + (e >> 5), xl = e & 31;
             float d[9];
             load_node(xl, yy, d);
             NodeState c;
             node_state(d, a, forced, smag, c);
             SolidMoments sm;
-            node_imb(c, xl, yy, mask, uni, act, tc->p, tc->id, part, a, sm);
+            node_imb(c, xl, yy, cm, __reduce_or_sync(FULL, cm), qe.x, qe.y, tc->p, tc->id, part, a, sm);
             if (act)
                 node_collide_store(d, c, sm, fout + (size_t)(y0 + yy) * a.pitch + (x0 + xl), a, forced);
         }
-        // the threads that flush this tile's forces take their particle id before the
-        // stage is handed back to the copy engine
-        const int fid = threadIdx.x < nc * 3 ? tc->id[threadIdx.x / 3] : -1;
-        const int bad = __syncthreads_or(!ok);
-        if (threadIdx.x == 0 && !bad) {
-            fence_proxy_async_smem();
-            issue(k + NST, st);
-        }
-        if (fid >= 0) {
-            const int s = threadIdx.x / 3, c = threadIdx.x - 3 * s;
-            float *pb = part_base + (k & 1) * WARPS * TILE_CAND * 3 + s * 3 + c;
-            double acc = 0.0;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) {
-                acc += (double)pb[w * TILE_CAND * 3];
-                pb[w * TILE_CAND * 3] = 0.0f;
-            }
-            if (acc != 0.0) {
-                if (c < 2) atomicAdd(&a.F[2 * fid + c], acc);
-                else atomicAdd(&a.T[fid], acc);
-            }
-        }
-        if (bad) {
-            if (threadIdx.x == 0) set_err(a.err, ERR_TMA);
-            break;
-        }
+        // the threads that flush this tile's forces take their particle id now, while the
+        // stage still holds the tile's candidate block
+        fid = threadIdx.x < nc * 3 ? tc->id[threadIdx.x / 3] : -1;
     }
     if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
+    // the last block to finish leaves the tile counter at zero for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.tile_ctr[1], 1u) == gridDim.x - 1) {
+            atomicExch(&a.tile_ctr[0], 0u);
+            atomicExch(&a.tile_ctr[1], 0u);
+        }
+    }
 }
 
 // Per-tile candidate lists: one warp per tile gathers the particles of the 3 x 3
