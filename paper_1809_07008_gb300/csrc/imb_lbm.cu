@@ -331,72 +331,56 @@ __device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const f
     return __ldg(tab + (dk + th) * tw + (di + th));
 }
 
-// Immersed moving boundary at one node (Sec. 2.3).  Bit s of `cm` is set when tile
-// candidate s reaches into the node; `U` is the warp-uniform union of the batch's cm;
-// e0 and e1 are the solid ratios of the node's first two candidates (looked up while the
-// node was queued).  Total solid ratio -> B (Eq. 14) -> per-particle weights
-// B_p = B eps_p / sum eps -> solid-velocity moments; the per-particle force and torque
-// (Eqs. 15-16) are reduced over the warp into part[s] by lane 0 of each warp.
+// Immersed moving boundary at one node (Sec. 2.3), all within the lane.  Bit s of
+// `cm` is set when tile candidate s reaches into the node.  Total solid ratio -> B
+// (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps -> solid-velocity moments;
+// the per-particle force and torque (Eqs. 15-16) go to the lane's own column of
+// part[s][c][lane], summed over the lanes when the tile's forces are flushed.
 __device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
-                                         const unsigned U, const float e0, const float e1,
                                          const PRec *__restrict__ cand, const int *__restrict__ cid,
-                                         float (*part)[3], const LatticeArgs &a, SolidMoments &sm) {
+                                         float *__restrict__ part, const LatticeArgs &a, SolidMoments &sm) {
     const int lane = threadIdx.x & 31;
     const bool exact = a.eps_mode == EPS_EXACT;
     sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
-    const int ns = __popc(cm);
-    if (ns > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
-    auto eps_of = [&](unsigned below, int s) {   // solid ratio of slot s; `below` = cm bits under s
-        const int i = __popc(below);
-        if (i == 0) return e0;
-        if (i == 1) return e1;
+    if (__popc(cm) > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
+    auto eps_of = [&](int s) {
         const PRec &P = cand[s];
         return slot_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
                         exact);
     };
+    // the common case of a single candidate keeps its solid ratio in a register
+    const int s0 = cm ? __ffs(cm) - 1 : 0;
+    const float e0 = cm ? eps_of(s0) : 0.0f;
     float esum = e0;   // summed in slot order
-    if (ns > 1) esum += e1;
-    for (unsigned m = (cm & (cm - 1u)) & ((cm & (cm - 1u)) - 1u); m; m &= m - 1u) {
-        const int s = __ffs(m) - 1;
-        esum += eps_of(cm & ((1u << s) - 1u), s);
-    }
+    for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += eps_of(__ffs(m) - 1);
     if (esum > 0.0f) {
         const float eps = fminf(esum, 1.0f);
         const float tm = c.te - 0.5f;
         sm.B = eps * tm / ((1.0f - eps) + tm);                  // Eq. 14
     }
-    const float Bs = sm.B > 0.0f ? __fdividef(sm.B, esum) : 0.0f;
-    for (unsigned m = U; m; m &= m - 1u) {
+    if (!(sm.B > 0.0f)) return;
+    const float Bs = __fdividef(sm.B, esum);
+    for (unsigned m = cm; m; m &= m - 1u) {
         const int s = __ffs(m) - 1;
-        float Bp = 0.0f, vx = 0.0f, vy = 0.0f, vt = 0.0f;
-        if (((cm >> s) & 1u) && Bs > 0.0f) {
-            const PRec &P = cand[s];
-            const int di = xl - P.ci, dk = yy - P.cj;
-            Bp = Bs * eps_of(cm & ((1u << s) - 1u), s);
-            const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
-            const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
-            const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
-            sm.m1x += Bp * usx;
-            sm.m1y += Bp * usy;
-            sm.m2xx += Bp * usx * usx;
-            sm.m2xy += Bp * usx * usy;
-            sm.m2yy += Bp * usy * usy;
+        const PRec &P = cand[s];
+        const int di = xl - P.ci, dk = yy - P.cj;
+        const float Bp = Bs * (s == s0 ? e0 : eps_of(s));
+        const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
+        const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
+        const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
+        sm.m1x += Bp * usx;
+        sm.m1y += Bp * usy;
+        sm.m2xx += Bp * usx * usx;
+        sm.m2xy += Bp * usx * usy;
+        sm.m2yy += Bp * usy * usy;
+        if (Bp > 0.0f) {
             // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
-            vx = Bp * (c.jx - c.rho * usx - a.Fx);
-            vy = Bp * (c.jy - c.rho * usy - a.Fy);
-            vt = rx * vy - ry * vx;
-        }
-        if (!__any_sync(FULL, Bp > 0.0f)) continue;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vx += __shfl_xor_sync(FULL, vx, o);
-            vy += __shfl_xor_sync(FULL, vy, o);
-            vt += __shfl_xor_sync(FULL, vt, o);
-        }
-        if (lane == 0) {
-            part[s][0] += vx;
-            part[s][1] += vy;
-            part[s][2] += vt;
+            const float vx = Bp * (c.jx - c.rho * usx - a.Fx);
+            const float vy = Bp * (c.jy - c.rho * usy - a.Fy);
+            float *pp = part + s * 96 + lane;
+            atomicAdd(pp, vx);
+            atomicAdd(pp + 32, vy);
+            atomicAdd(pp + 64, rx * vy - ry * vx);
         }
     }
 }
@@ -441,10 +425,10 @@ template <typename S> struct Box {
     }
     static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
-    static constexpr int PART_FLOATS = 2 * WARPS * TILE_CAND * 3;
-    // force partials (two units), queue (solid ratios, cover masks, node offsets), two
-    // queue counters, the tile of each stage (index, column, row, spare)
-    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 8 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
+    static constexpr int PART_FLOATS = TILE_CAND * 3 * 32;
+    // force partials (per candidate, component and lane), queue (cover masks, node
+    // offsets), two queue counters, the tile of each stage (index, column, row, spare)
+    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
 static_assert((Box<float>::WN * HROWS * 4) % 128 == 0 && (Box<float>::WW * HROWS * 4) % 128 == 0 &&
@@ -477,9 +461,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     constexpr int NST = G::NST;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
-    float *part_base = reinterpret_cast<float *>(extra);
-    float2 *q_e = reinterpret_cast<float2 *>(extra + G::PART_FLOATS * 4);
-    unsigned *q_cm = reinterpret_cast<unsigned *>(q_e + QCAP);
+    float *part = reinterpret_cast<float *>(extra);
+    unsigned *q_cm = reinterpret_cast<unsigned *>(extra + G::PART_FLOATS * 4);
     unsigned short *q_node = reinterpret_cast<unsigned short *>(q_cm + QCAP);
     int *q_count = reinterpret_cast<int *>(q_node + QCAP);
     int4 *stage_tile = reinterpret_cast<int4 *>(q_count + 4);
@@ -488,7 +471,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
     const bool smag = a.smag_coef > 0.0f;
 
-    for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part_base[i] = 0.0f;
+    for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part[i] = 0.0f;
     if (threadIdx.x < 2) q_count[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&mbar[i], 1);
@@ -546,18 +529,19 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 fence_proxy_async_smem();
                 issue_next();
             }
-            if (fid >= 0) {
-                const int s = threadIdx.x / 3, c = threadIdx.x - 3 * s;
-                float *pb = part_base + (qc ^ 1) * WARPS * TILE_CAND * 3 + s * 3 + c;
-                double acc = 0.0;
+            if (fid >= 0) {   // thread 3 s + c sums component c of candidate s over the lanes
+                float *pb = part + threadIdx.x * 32;
+                float acc = 0.0f;
 #pragma unroll
-                for (int w = 0; w < WARPS; ++w) {
-                    acc += (double)pb[w * TILE_CAND * 3];
-                    pb[w * TILE_CAND * 3] = 0.0f;
+                for (int l = 0; l < 32; ++l) {
+                    const int j = (l + threadIdx.x) & 31;   // staggered: no bank conflicts
+                    acc += pb[j];
+                    pb[j] = 0.0f;
                 }
-                if (acc != 0.0) {
-                    if (c < 2) atomicAdd(&a.F[2 * fid + c], acc);
-                    else atomicAdd(&a.T[fid], acc);
+                if (acc != 0.0f) {
+                    const int c = threadIdx.x % 3;
+                    if (c < 2) atomicAdd(&a.F[2 * fid + c], (double)acc);
+                    else atomicAdd(&a.T[fid], (double)acc);
                 }
             }
         }
@@ -572,7 +556,6 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         const TileCand *tc = stage_cand(st);
         const int nc = min(tc->n, TILE_CAND);
         const S *pop = stage_pop(st);
-        float(*part)[3] = reinterpret_cast<float(*)[3]>(part_base + (qc * WARPS + warp) * TILE_CAND * 3);
         auto load_node = [&](int xl, int yy, float (&d)[9]) {
             if (in) {
                 const int r = yy - h * HROWS;
@@ -612,22 +595,6 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 base = __shfl_sync(FULL, base, 0);
                 if (cm) {
                     const int i = base + __popc(ib & ((1u << lane) - 1u));
-                    // solid ratios of the first two candidates, fetched now so that the
-                    // table reads overlap the rest of this pass
-                    float2 e = make_float2(0.0f, 0.0f);
-                    const bool exact = a.eps_mode == EPS_EXACT;
-                    const int sa = __ffs(cm) - 1;
-                    const PRec &Pa = tc->p[sa];
-                    e.x = slot_eps(Pa, lane - Pa.ci, yy - Pa.cj, a.eps_tab + (size_t)tc->id[sa] * a.tab_stride,
-                                   a.tab_w, a.tab_h, exact);
-                    const unsigned rest = cm & (cm - 1u);
-                    if (rest) {
-                        const int sb = __ffs(rest) - 1;
-                        const PRec &Pb = tc->p[sb];
-                        e.y = slot_eps(Pb, lane - Pb.ci, yy - Pb.cj,
-                                       a.eps_tab + (size_t)tc->id[sb] * a.tab_stride, a.tab_w, a.tab_h, exact);
-                    }
-                    q_e[i] = e;
                     q_cm[i] = cm;
                     q_node[i] = (unsigned short)((yy - h * HROWS) * 32 + lane);
                 }
@@ -651,7 +618,6 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             const bool act = base + lane < nq;
             const int i = act ? base + lane : base;
             const unsigned cm = act ? q_cm[i] : 0u;
-            const float2 qe = q_e[i];
             const int e = q_node[i];
             const int yy = h * HROWS + (e >> 5), xl = e & 31;
             float d[9];
@@ -659,7 +625,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             NodeState c;
             node_state(d, a, forced, smag, c);
             SolidMoments sm;
-            node_imb(c, xl, yy, cm, __reduce_or_sync(FULL, cm), qe.x, qe.y, tc->p, tc->id, part, a, sm);
+            node_imb(c, xl, yy, cm, tc->p, tc->id, part, a, sm);
             if (act)
                 node_collide_store(d, c, sm, fout + (size_t)(y0 + yy) * a.pitch + (x0 + xl), a, forced);
         }
