@@ -332,31 +332,34 @@ __device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const f
 }
 
 // Immersed moving boundary at one node (Sec. 2.3), all within the lane.  Bit s of
-// `cm` is set when tile candidate s reaches into the node.  Total solid ratio -> B
-// (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps -> solid-velocity moments;
-// the per-particle force and torque (Eqs. 15-16) go to the lane's own column of
-// part[s][c][lane], summed over the lanes when the tile's forces are flushed.
+// `cm` is set when tile candidate s reaches into the node; e0 is the solid ratio of its
+// first candidate s0 (fetched by the caller ahead of the node's moments).  Total solid
+// ratio -> B (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps -> solid-velocity
+// moments; the per-particle force and torque (Eqs. 15-16) of the first PSLOTS
+// candidates go to the lane's own column of the warp's partials part[s][c][lane] (no
+// other thread touches it), those of later candidates straight to the particle.
+constexpr int PSLOTS = 4;
+
+__device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
+                                               int s, int xl, int yy, const LatticeArgs &a) {
+    const PRec &P = cand[s];
+    return slot_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
+                    a.eps_mode == EPS_EXACT);
+}
+
 __device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
-                                         const PRec *__restrict__ cand, const int *__restrict__ cid,
-                                         float *__restrict__ part, const LatticeArgs &a, SolidMoments &sm) {
+                                         const int s0, const float e0, const PRec *__restrict__ cand,
+                                         const int *__restrict__ cid, float *__restrict__ part,
+                                         const LatticeArgs &a, SolidMoments &sm) {
     const int lane = threadIdx.x & 31;
-    const bool exact = a.eps_mode == EPS_EXACT;
     sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
     if (__popc(cm) > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
-    auto eps_of = [&](int s) {
-        const PRec &P = cand[s];
-        return slot_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
-                        exact);
-    };
-    // the common case of a single candidate keeps its solid ratio in a register
-    const int s0 = cm ? __ffs(cm) - 1 : 0;
-    const float e0 = cm ? eps_of(s0) : 0.0f;
     float esum = e0;   // summed in slot order
-    for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += eps_of(__ffs(m) - 1);
+    for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += cand_slot_eps(cand, cid, __ffs(m) - 1, xl, yy, a);
     if (esum > 0.0f) {
         const float eps = fminf(esum, 1.0f);
         const float tm = c.te - 0.5f;
-        sm.B = eps * tm / ((1.0f - eps) + tm);                  // Eq. 14
+        sm.B = __fdividef(eps * tm, (1.0f - eps) + tm);       // Eq. 14
     }
     if (!(sm.B > 0.0f)) return;
     const float Bs = __fdividef(sm.B, esum);
@@ -364,7 +367,7 @@ __device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const
         const int s = __ffs(m) - 1;
         const PRec &P = cand[s];
         const int di = xl - P.ci, dk = yy - P.cj;
-        const float Bp = Bs * (s == s0 ? e0 : eps_of(s));
+        const float Bp = Bs * (s == s0 ? e0 : cand_slot_eps(cand, cid, s, xl, yy, a));
         const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
         const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
         const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
@@ -377,10 +380,17 @@ __device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const
             // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
             const float vx = Bp * (c.jx - c.rho * usx - a.Fx);
             const float vy = Bp * (c.jy - c.rho * usy - a.Fy);
-            float *pp = part + s * 96 + lane;
-            atomicAdd(pp, vx);
-            atomicAdd(pp + 32, vy);
-            atomicAdd(pp + 64, rx * vy - ry * vx);
+            const float vt = rx * vy - ry * vx;
+            if (s < PSLOTS) {
+                float *pp = part + s * 96 + lane;
+                pp[0] += vx;
+                pp[32] += vy;
+                pp[64] += vt;
+            } else {   // a crowded tile: later candidates add straight to the particle
+                atomicAdd(&a.F[2 * cid[s]], (double)vx);
+                atomicAdd(&a.F[2 * cid[s] + 1], (double)vy);
+                atomicAdd(&a.T[cid[s]], (double)vt);
+            }
         }
     }
 }
@@ -425,8 +435,8 @@ template <typename S> struct Box {
     }
     static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
-    static constexpr int PART_FLOATS = TILE_CAND * 3 * 32;
-    // force partials (per candidate, component and lane), queue (cover masks, node
+    static constexpr int PART_FLOATS = WARPS * PSLOTS * 3 * 32;
+    // force partials (per warp, candidate, component and lane), queue (cover masks, node
     // offsets), two queue counters, the tile of each stage (index, column, row, spare)
     static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
@@ -529,14 +539,13 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 fence_proxy_async_smem();
                 issue_next();
             }
-            if (fid >= 0) {   // thread 3 s + c sums component c of candidate s over the lanes
+            if (fid >= 0) {   // thread 3 s + c sums component c of candidate s over the warps
                 float *pb = part + threadIdx.x * 32;
                 float acc = 0.0f;
 #pragma unroll
-                for (int l = 0; l < 32; ++l) {
-                    const int j = (l + threadIdx.x) & 31;   // staggered: no bank conflicts
-                    acc += pb[j];
-                    pb[j] = 0.0f;
+                for (int w = 0; w < WARPS; ++w) {
+                    acc += pb[w * PSLOTS * 96];
+                    pb[w * PSLOTS * 96] = 0.0f;
                 }
                 if (acc != 0.0f) {
                     const int c = threadIdx.x % 3;
@@ -613,6 +622,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         const int nq = min(q_count[qc], QCAP);
         if (threadIdx.x == 0) q_count[qc ^ 1] = 0;   // the next unit's counter, last read a unit ago
         // pass B: the queued immersed-boundary nodes, 32 per warp at a time
+        float *part_w = part + warp * PSLOTS * 96;
+        unsigned used = 0u;   // candidates this lane's nodes gave force to
 #pragma unroll 1
         for (int base = warp * 32; base < nq; base += WARPS * 32) {
             const bool act = base + lane < nq;
@@ -620,18 +631,35 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             const unsigned cm = act ? q_cm[i] : 0u;
             const int e = q_node[i];
             const int yy = h * HROWS + (e >> 5), xl = e & 31;
+            // the first candidate's solid ratio is fetched before the moments so that the
+            // table read overlaps them
+            const int s0 = cm ? __ffs(cm) - 1 : 0;
+            const float e0 = cm ? cand_slot_eps(tc->p, tc->id, s0, xl, yy, a) : 0.0f;
+            used |= cm;
             float d[9];
             load_node(xl, yy, d);
             NodeState c;
             node_state(d, a, forced, smag, c);
             SolidMoments sm;
-            node_imb(c, xl, yy, cm, tc->p, tc->id, part, a, sm);
+            node_imb(c, xl, yy, cm, s0, e0, tc->p, tc->id, part_w, a, sm);
             if (act)
                 node_collide_store(d, c, sm, fout + (size_t)(y0 + yy) * a.pitch + (x0 + xl), a, forced);
         }
+        // the warp's partials: sum over the lanes into lane 0's column
+        for (unsigned m = __reduce_or_sync(FULL, used) & ((1u << PSLOTS) - 1u); m; m &= m - 1u) {
+            float *pp = part_w + (__ffs(m) - 1) * 96 + lane;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                float v = pp[32 * cc];
+                pp[32 * cc] = 0.0f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if (lane == 0) pp[32 * cc] = v;
+            }
+        }
         // the threads that flush this tile's forces take their particle id now, while the
         // stage still holds the tile's candidate block
-        fid = threadIdx.x < nc * 3 ? tc->id[threadIdx.x / 3] : -1;
+        fid = threadIdx.x < min(nc, PSLOTS) * 3 ? tc->id[threadIdx.x / 3] : -1;
     }
     if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
     // the last block to finish leaves the tile counter at zero for the next launch
