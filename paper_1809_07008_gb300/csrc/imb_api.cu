@@ -49,6 +49,7 @@ struct imb_ctx {
     // bins
     int nbx = 0, nby = 0, nbins = 0;
     int *bin_count = nullptr, *bin_fill = nullptr, *bin_start = nullptr, *bin_ids = nullptr;
+    int *bin_bsum = nullptr;   // per-block totals of the bin scan
     GridBarrier *barrier = nullptr;
     unsigned *err = nullptr;
     unsigned *tile_ctr = nullptr;
@@ -238,6 +239,7 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->bin_count);
     dfree(c->bin_fill);
     dfree(c->bin_start);
+    dfree(c->bin_bsum);
     dfree(c->counters);
     dfree(c->barrier);
     dfree(c->err);
@@ -330,7 +332,8 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     if ((e = dalloc(&c->bin_count, nbins_pad)) != cudaSuccess || (e = dalloc(&c->bin_fill, nbins_pad)) != cudaSuccess ||
         (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
-        (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess)
+        (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess ||
+        (e = dalloc(&c->bin_bsum, c->nbins / 1024 + 1)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
     cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
     for (int b = 0; b < 2; ++b)
@@ -366,11 +369,11 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
                              0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
                              c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
        "particle table");
-    CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->counters, c->stream),
+    CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->bin_bsum, c->counters, c->stream),
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
     CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
-    c->launches += 5;   // table, scan, fill, tile lists, solid-ratio map
+    c->launches += 6;   // table, scan (two passes), fill, tile lists, solid-ratio map
     return IMB_OK;
 }
 

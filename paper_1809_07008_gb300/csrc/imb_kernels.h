@@ -83,7 +83,7 @@ cudaError_t launch_particle_table(const double *x, const double *r, const double
                                   int nby, int *bin_count, int *pbin, PRec *prec, const double *v,
                                   const double *w, double *F, double *T, unsigned *err,
                                   cudaStream_t s);
-cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins,
+cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins, int *bsum,
                             int *dem_counters, cudaStream_t s);
 cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *bin_start,
                             int *bin_ids, cudaStream_t s);

@@ -703,22 +703,56 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
 // offset (di, dk) from the centre cell).  In cell-decomposition mode fully covered
 // cells are tabulated too.
 constexpr int EPS_WARPS = 4;
-constexpr int EPS_LIST = 256;
 
-__device__ __forceinline__ void eps_flush(const PRec &P, bool exact, int n_sub, float *out, int tw, int th,
-                                          const short *lst, int n) {
-    for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
-        const int di = lst[2 * k], dk = lst[2 * k + 1];
-        const float lox = __fsub_rn((float)di, P.fx), loy = __fsub_rn((float)dk, P.fy);
-        out[(dk + th) * tw + (di + th)] = exact ? cell_disk_area(lox, loy, P.r)
-                                                : cell_subcell_ratio(lox, loy, P.r, n_sub);
-    }
+// Cells of one row (cell rows [dk, dk + 1) relative to a disk centre at fractional
+// offset (fx, fy) in its centre cell) that the disk reaches into, [L, H], and that it
+// covers completely, [L2, H2] (empty when L > H).  Along a row the nearest and the
+// farthest point of a cell move monotonically away from the centre on either side, so
+// both sets are intervals; the ends are estimated from the chord half-widths and then
+// settled with covers() and fully_covered() themselves.
+__device__ __forceinline__ void row_reach(float fx, float loy, float r, int &L, int &H) {
+    const float hiy = __fadd_rn(loy, 1.0f);
+    const float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
+    const float r2 = __fmul_rn(r, r), dy2 = __fmul_rn(dy, dy);
+    L = 1;
+    H = 0;
+    if (!(dy2 < r2)) return;
+    auto in = [&](int l) { return covers(__fsub_rn((float)l, fx), loy, r); };
+    const float w = sqrtf(r2 - dy2);
+    L = (int)floorf(fx - w);
+    H = (int)floorf(fx + w);
+    for (int i = 0; i < 3 && in(L - 1); ++i) --L;
+    for (int i = 0; i < 3 && L <= H && !in(L); ++i) ++L;
+    for (int i = 0; i < 3 && in(H + 1); ++i) ++H;
+    for (int i = 0; i < 3 && H >= L && !in(H); ++i) --H;
 }
+
+__device__ __forceinline__ void row_full(float fx, float loy, float r, int &L, int &H) {
+    const float fy = fmaxf(fabsf(loy), fabsf(__fadd_rn(loy, 1.0f)));
+    const float r2 = __fmul_rn(r, r), fy2 = __fmul_rn(fy, fy);
+    L = 1;
+    H = 0;
+    if (!(fy2 <= r2)) return;
+    auto in = [&](int l) { return fully_covered(__fsub_rn((float)l, fx), loy, r); };
+    const float w = sqrtf(r2 - fy2);
+    L = (int)ceilf(fx - w);
+    H = (int)floorf(fx + w - 1.0f);
+    for (int i = 0; i < 3 && in(L - 1); ++i) --L;
+    for (int i = 0; i < 3 && L <= H && !in(L); ++i) ++L;
+    for (int i = 0; i < 3 && in(H + 1); ++i) ++H;
+    for (int i = 0; i < 3 && H >= L && !in(H); ++i) --H;
+}
+
+// Solid-ratio table of one particle, a warp per particle: the cells the disk reaches into
+// but does not cover completely (exact area), or all cells it reaches into (cell
+// decomposition).  A lane per cell row finds the row's cells, they are listed in shared
+// memory, and the lanes share the list's area evaluations evenly.
+constexpr int EPS_LIST = 256;
 
 __global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_eps(const PRec *__restrict__ prec, int np,
                                                                  int eps_mode, int n_sub, float *tab, int tw,
                                                                  int th, int stride) {
-    __shared__ short s_lst[EPS_WARPS][2 * EPS_LIST];
+    __shared__ short2 s_lst[EPS_WARPS][EPS_LIST];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * EPS_WARPS + warp;
     if (p >= np) return;
@@ -726,32 +760,47 @@ __global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_eps(const PRec *__r
     const bool exact = eps_mode == EPS_EXACT;
     const int span = (int)ceilf(P.r) + 1;
     float *out = tab + (size_t)p * stride;
-    short *lst = s_lst[warp];
-    int n = 0;
-    for (int dk = -span; dk <= span; ++dk) {
+    short2 *lst = s_lst[warp];
+    for (int dk0 = -span; dk0 <= span; dk0 += 32) {
+        const int dk = dk0 + lane;
         const float loy = __fsub_rn((float)dk, P.fy);
-        for (int di0 = -span; di0 <= span; di0 += 32) {
-            const int di = di0 + lane;
-            int st = 0;
-            if (di <= span) st = cover_state(__fsub_rn((float)di, P.fx), loy, P.r);
-            const bool take = st == 1 || (st == 2 && !exact);
-            const unsigned bal = __ballot_sync(FULL, take);
-            if (n + __popc(bal) > EPS_LIST) {   // list full: evaluate what is queued
-                __syncwarp();
-                eps_flush(P, exact, n_sub, out, tw, th, lst, n);
-                __syncwarp();
-                n = 0;
+        int L = 1, H = 0, L2 = 1, H2 = 0;
+        if (dk <= span) {
+            row_reach(P.fx, loy, P.r, L, H);
+            if (exact) row_full(P.fx, loy, P.r, L2, H2);
+        }
+        // the row's tabulated cells: [L, H] minus the fully covered run [L2, H2]
+        const bool split = L2 <= H2 && L2 >= L && H2 <= H;
+        const int cnt = H < L ? 0 : (H - L + 1) - (split ? H2 - L2 + 1 : 0);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int base = 0; base < total; base += EPS_LIST) {
+            // this lane's cells with list positions in [base, base + EPS_LIST)
+            int pos = incl - cnt;
+            for (int di = L; di <= H && pos < base + EPS_LIST; ++di) {
+                if (split && di >= L2 && di <= H2) {
+                    di = H2;
+                    continue;
+                }
+                if (pos >= base) lst[pos - base] = make_short2((short)di, (short)dk);
+                ++pos;
             }
-            if (take) {
-                const int pos = n + __popc(bal & ((1u << lane) - 1u));
-                lst[2 * pos] = (short)di;
-                lst[2 * pos + 1] = (short)dk;
+            __syncwarp();
+            const int n = min(total - base, EPS_LIST);
+            for (int k = lane; k < n; k += 32) {
+                const short2 c = lst[k];
+                const float lox = __fsub_rn((float)c.x, P.fx), ly = __fsub_rn((float)c.y, P.fy);
+                out[(c.y + th) * tw + (c.x + th)] = exact ? cell_disk_area(lox, ly, P.r)
+                                                          : cell_subcell_ratio(lox, ly, P.r, n_sub);
             }
-            n += __popc(bal);
+            __syncwarp();
         }
     }
-    __syncwarp();
-    eps_flush(P, exact, n_sub, out, tw, th, lst, n);
 }
 
 // ------------------------------------------------------------- gather

@@ -75,78 +75,78 @@ __global__ void k_particle_table(const double *__restrict__ x, const double *__r
 // bins (eight 16-byte loads in flight), the block scans the per-thread sums.  Also
 // resets the counts and fill cursors (and the DEM list counters) for reuse.  The
 // bin arrays are padded to a multiple of 32 entries.
-__global__ void __launch_bounds__(1024) k_bin_scan(int *count, int *fill, int *start, int nbins,
-                                                   int *dem_counters) {
-    __shared__ int wsum[32];
-    __shared__ int s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    const int nchunks = (nbins + 32 * 1024 - 1) / (32 * 1024);
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int b0 = (ch * 1024 + threadIdx.x) * 32;
-        int v[32];
-        if (b0 < nbins) {
-            const int4 *src = reinterpret_cast<const int4 *>(count + b0);
+// Exclusive scan of the bin counts in two passes over blocks of SCAN_BINS bins: each
+// block scans its bins and records their total, then adds the totals of the blocks
+// before it.  Both passes also clear the counters that the next binning accumulates.
+constexpr int SCAN_BINS = 1024;   // 256 threads x 4 bins
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int4 t = src[k];
-                v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] = 0;
-        }
-        int tot = 0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) tot += (b0 + k < nbins) ? v[k] : 0;
-        int incl = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
         }
-        __syncthreads();   // s_carry of the previous chunk and wsum are free again
-        if (lane == 31) wsum[warp] = incl;
-        const int carry = s_carry;
-        __syncthreads();
-        if (warp == 0) {
-            int w = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += t;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        int run = carry + (warp ? wsum[warp - 1] : 0) + incl - tot;
-        if (b0 < nbins) {
-            int4 *dst = reinterpret_cast<int4 *>(start + b0);
-            int4 *zc = reinterpret_cast<int4 *>(count + b0);
-            int4 *zf = reinterpret_cast<int4 *>(fill + b0);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                int4 o;
-                o.x = run; run += v[4 * k];
-                o.y = run; run += v[4 * k + 1];
-                o.z = run; run += v[4 * k + 2];
-                o.w = run; run += v[4 * k + 3];
-                dst[k] = o;
-                zc[k] = make_int4(0, 0, 0, 0);
-                zf[k] = make_int4(0, 0, 0, 0);
-            }
-        }
-        if (threadIdx.x == 1023) s_carry = carry + wsum[31];
-        if (b0 <= nbins - 1 && nbins - 1 < b0 + 32) start[nbins] = run;   // padded counts are zero
+        if (lane < nw) wsum[lane] = w;
     }
-    if (threadIdx.x == 0 && dem_counters) {
-        dem_counters[0] = 0;
-        dem_counters[1] = 0;
-        dem_counters[2] = 0;
-        dem_counters[3] = 0;
-        dem_counters[4] = 0;
-        dem_counters[5] = 0;
+    __syncthreads();
+    total = wsum[nw - 1];
+    return (warp ? wsum[warp - 1] : 0) + incl - v;
+}
+
+__global__ void __launch_bounds__(256) k_bin_scan_local(int *count, int *start, int nbins, int *bsum,
+                                                        int *dem_counters) {
+    __shared__ int wsum[8];
+    const int b0 = blockIdx.x * SCAN_BINS + threadIdx.x * 4;
+    int4 v = make_int4(0, 0, 0, 0);
+    if (b0 < nbins) v = *reinterpret_cast<const int4 *>(count + b0);   // counts padded to 32
+    int total;
+    int run = block_exclusive_scan(v.x + v.y + v.z + v.w, wsum, total);
+    if (b0 < nbins) {
+        int4 o;
+        o.x = run; run += v.x;
+        o.y = run; run += v.y;
+        o.z = run; run += v.z;
+        o.w = run;
+        *reinterpret_cast<int4 *>(start + b0) = o;
+        *reinterpret_cast<int4 *>(count + b0) = make_int4(0, 0, 0, 0);
     }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+    if (blockIdx.x == 0 && threadIdx.x < 6 && dem_counters) dem_counters[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_bin_scan_add(int *fill, int *start, int nbins, const int *bsum) {
+    __shared__ int s_off;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {   // totals of the blocks before this one
+        int acc = 0;
+        for (int i = lane; i < (int)blockIdx.x; i += 32) acc += bsum[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_off = acc;
+    }
+    __syncthreads();
+    const int off = s_off;
+    const int b0 = blockIdx.x * SCAN_BINS + threadIdx.x * 4;
+    if (b0 < nbins) {
+        int4 *p = reinterpret_cast<int4 *>(start + b0);
+        int4 o = *p;
+        o.x += off; o.y += off; o.z += off; o.w += off;
+        *p = o;
+        *reinterpret_cast<int4 *>(fill + b0) = make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[nbins] = off + bsum[blockIdx.x];
 }
 
 __global__ void k_bin_fill(const int *__restrict__ pbin, int np, int *fill, const int *__restrict__ start,
@@ -316,83 +316,120 @@ __device__ __forceinline__ bool pair_apart(const DemArgs &d, double px, double p
     return dx * dx + dy * dy > M * M;
 }
 
-__global__ void k_dem_neighbours(const DemArgs d) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Candidate lists, one warp per particle: lanes 0-8 take the 3 x 3 bins around the
+// particle's bin, then every lane tests candidates from the flattened bins (pairs within
+// r_p + r_q + skin), the hits are ranked by id (the list is in ascending id order), and
+// each kept pair carries its tangential spring and damping constant over from the
+// previous list.
+constexpr int NB_WARPS = 4;
+constexpr int NB_HITS = 64;   // hits a warp can hold before the overflow is reported
+
+__global__ void __launch_bounds__(32 * NB_WARPS) k_dem_neighbours(const DemArgs d) {
+    __shared__ int s_hit[NB_WARPS][NB_HITS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.x * NB_WARPS + warp;
     if (p >= d.np) return;
+    const unsigned FULLM = 0xffffffffu;
     const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
     const double px = d.x[2 * p], py = d.x[2 * p + 1], rp = d.r[p];
-    d.x_start[2 * p] = px;
-    d.x_start[2 * p + 1] = py;
+    if (lane == 0) {
+        d.x_start[2 * p] = px;
+        d.x_start[2 * p + 1] = py;
+    }
     const int b = d.pbin[p];
     const int bx = b % d.nbx, by = b / d.nbx;
-    int ids[MAX_NBR];
-    int n = 0;
-    int seen[9];
-    int nseen = 0;
-    for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-            int ix = bx + ox, iy = by + oy;
-            if (ix < 0 || ix >= d.nbx) {
-                if (!perx) continue;
-                ix = (ix + d.nbx) % d.nbx;
-            }
-            if (iy < 0 || iy >= d.nby) {
-                if (!pery) continue;
-                iy = (iy + d.nby) % d.nby;
-            }
-            const int bb = iy * d.nbx + ix;
-            bool dup = false;
-            for (int k = 0; k < nseen; ++k) dup |= seen[k] == bb;
-            if (dup) continue;
-            seen[nseen++] = bb;
-            for (int k = d.bin_start[bb]; k < d.bin_start[bb + 1]; ++k) {
-                const int q = d.bin_ids[k];
-                if (q == p) continue;
-                const double dx = min_image(d.x[2 * q] - px, perx, d.nx);
-                const double dy = min_image(d.x[2 * q + 1] - py, pery, d.ny);
-                const double R = rp + d.r[q] + d.skin;
-                if (!(dx * dx + dy * dy < R * R)) continue;
-                if (n == MAX_NBR) {
-                    set_err(d.err, ERR_NEIGHBOURS);
-                    continue;
-                }
-                int j = n++;  // insertion keeps the list in ascending id order
-                while (j > 0 && ids[j - 1] > q) {
-                    ids[j] = ids[j - 1];
-                    --j;
-                }
-                ids[j] = q;
-            }
+    int bb = -1;
+    if (lane < 9) {
+        int ix = bx + lane % 3 - 1, iy = by + lane / 3 - 1;
+        bool ok = true;
+        if (ix < 0 || ix >= d.nbx) {
+            if (perx) ix = (ix + d.nbx) % d.nbx;
+            else ok = false;
         }
+        if (iy < 0 || iy >= d.nby) {
+            if (pery) iy = (iy + d.nby) % d.nby;
+            else ok = false;
+        }
+        if (ok) bb = iy * d.nbx + ix;
+    }
+    const unsigned same = __match_any_sync(FULLM, bb);   // a bin met twice on a tiny periodic lattice
+    if (bb >= 0 && __ffs(same) - 1 != lane) bb = -1;
+    int beg = 0, cnt = 0;
+    if (bb >= 0) {
+        beg = d.bin_start[bb];
+        cnt = d.bin_start[bb + 1] - beg;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULLM, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(FULLM, incl, 31);
+    const int excl = incl - cnt;
+    int nh = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int k = base + lane;
+        int q = -1;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int e = __shfl_sync(FULLM, excl, j), c = __shfl_sync(FULLM, cnt, j);
+            const int g = __shfl_sync(FULLM, beg, j);
+            if (k >= e && k < e + c) q = d.bin_ids[g + k - e];
+        }
+        bool hit = false;
+        if (q >= 0 && q != p) {
+            const double dx = min_image(d.x[2 * q] - px, perx, d.nx);
+            const double dy = min_image(d.x[2 * q + 1] - py, pery, d.ny);
+            const double R = rp + d.r[q] + d.skin;
+            hit = dx * dx + dy * dy < R * R;
+        }
+        const unsigned hb = __ballot_sync(FULLM, hit);
+        const int pos = nh + __popc(hb & ((1u << lane) - 1u));
+        if (hit && pos < NB_HITS) s_hit[warp][pos] = q;
+        nh += __popc(hb);
+    }
+    __syncwarp();
+    if (nh > MAX_NBR) {
+        if (lane == 0) set_err(d.err, ERR_NEIGHBOURS);
+    }
+    const int nkeep = min(nh, NB_HITS);
+    const int n = min(nh, MAX_NBR);
     const int nold = d.nbr_cnt_old[p];
-    for (int j = 0; j < n; ++j) {
+    for (int j = lane; j < nkeep; j += 32) {
+        const int q = s_hit[warp][j];
+        int rank = 0;
+        for (int i = 0; i < nkeep; ++i) rank += s_hit[warp][i] < q;
+        if (rank >= MAX_NBR) continue;
         double xi = 0.0, cn = -1.0;
         for (int k = 0; k < nold; ++k)
-            if (d.nbr_id_old[p * MAX_NBR + k] == ids[j]) {
+            if (d.nbr_id_old[p * MAX_NBR + k] == q) {
                 xi = d.nbr_xi_old[p * MAX_NBR + k];
                 cn = d.nbr_cn_old[p * MAX_NBR + k];
             }
         if (cn < 0.0) {   // a new candidate pair: its damping constant, once
-            const double mq = d.m[ids[j]], mp = d.m[p];
+            const double mq = d.m[q], mp = d.m[p];
             cn = damping_cn(d, mp * mq / (mp + mq));
         }
-        d.nbr_id[p * MAX_NBR + j] = ids[j];
-        d.nbr_xi[p * MAX_NBR + j] = xi;
-        d.nbr_cn[p * MAX_NBR + j] = cn;
+        d.nbr_id[p * MAX_NBR + rank] = q;
+        d.nbr_xi[p * MAX_NBR + rank] = xi;
+        d.nbr_cn[p * MAX_NBR + rank] = cn;
     }
-    d.nbr_cnt[p] = n;
-    d.parent[p] = p;
-    d.isz[p] = 0;
-    d.ifill[p] = 0;
-    d.iloud[p] = 0;
-    if (n > 0) {
-        const FreeMotion f = free_motion(d, p, d.v[2 * p], d.v[2 * p + 1]);
-        d.exc[2 * p] = f.ex;
-        d.exc[2 * p + 1] = f.ey;
-        d.loud[p] = !free_of_edges(d, f, px, py, rp);
+    if (lane == 0) {
+        d.nbr_cnt[p] = n;
+        d.parent[p] = p;
+        d.isz[p] = 0;
+        d.ifill[p] = 0;
+        d.iloud[p] = 0;
+        if (n > 0) {
+            const FreeMotion f = free_motion(d, p, d.v[2 * p], d.v[2 * p + 1]);
+            d.exc[2 * p] = f.ex;
+            d.exc[2 * p + 1] = f.ey;
+            d.loud[p] = !free_of_edges(d, f, px, py, rp);
+        }
+        if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
+        else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
     }
-    if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
-    else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
 }
 
 __global__ void k_dem_free(const DemArgs d) {
@@ -840,9 +877,11 @@ cudaError_t launch_particle_table(const double *x, const double *r, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins,
+cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins, int *bsum,
                             int *dem_counters, cudaStream_t s) {
-    k_bin_scan<<<1, 1024, 0, s>>>(bin_count, bin_fill, bin_start, nbins, dem_counters);
+    const int nb = (nbins + SCAN_BINS - 1) / SCAN_BINS;
+    k_bin_scan_local<<<nb, 256, 0, s>>>(bin_count, bin_start, nbins, bsum, dem_counters);
+    k_bin_scan_add<<<nb, 256, 0, s>>>(bin_fill, bin_start, nbins, bsum);
     return cudaGetLastError();
 }
 
@@ -855,7 +894,7 @@ cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *b
 
 cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
-    k_dem_neighbours<<<blocks_for(d.np, 64), 64, 0, s>>>(d);
+    k_dem_neighbours<<<blocks_for(d.np, NB_WARPS), 32 * NB_WARPS, 0, s>>>(d);
     return cudaGetLastError();
 }
 
