@@ -421,7 +421,8 @@ constexpr int QCAP = HROWS * 32;         // immersed-node queue of a unit
 
 template <typename S> struct Box {
     static constexpr int HALO = 16 / (int)sizeof(S);
-    static constexpr int NST = sizeof(S) == 4 ? 2 : 3;   // units in flight per block
+    static constexpr int NST = 2;                            // units in flight per block
+    static constexpr int BLOCKS_PER_SM = sizeof(S) == 4 ? 2 : 3;
     static constexpr int WN = TILE, WW = TILE + HALO;
     __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
     __host__ __device__ static constexpr int offset(int q) {   // elements before plane q
@@ -445,8 +446,9 @@ static_assert((Box<float>::WN * HROWS * 4) % 128 == 0 && (Box<float>::WW * HROWS
                   (Box<__half>::WN * HROWS * 2) % 128 == 0 && (Box<__half>::WW * HROWS * 2) % 128 == 0,
               "TMA boxes stay 128-byte aligned in shared memory");
 static_assert(Box<float>::EXTRA_BYTES % 8 == 0 && Box<__half>::EXTRA_BYTES % 8 == 0, "mbarrier alignment");
-static_assert(2 * (Box<float>::SMEM_BYTES + 1024) <= 228 * 1024 && 2 * (Box<__half>::SMEM_BYTES + 1024) <= 228 * 1024,
-              "two blocks per SM");
+static_assert(Box<float>::BLOCKS_PER_SM * (Box<float>::SMEM_BYTES + 1024) <= 228 * 1024 &&
+                  Box<__half>::BLOCKS_PER_SM * (Box<__half>::SMEM_BYTES + 1024) <= 228 * 1024,
+              "resident blocks per SM fit in shared memory");
 
 __device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
     // every neighbour read of the tile lies inside the lattice: no boundary rule applies
@@ -463,7 +465,7 @@ __device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
 // A stage is handed back, and the forces of its tile flushed, once every warp has
 // passed the top of the next tile.
 template <typename S>
-__global__ void __launch_bounds__(BLOCK, 2)
+__global__ void __launch_bounds__(BLOCK, Box<S>::BLOCKS_PER_SM)
 k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_constant__ CUtensorMap tmap_w,
                  const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
                  const TileCand *__restrict__ tiles, const int ntiles) {
