@@ -269,7 +269,7 @@ static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map, int 
                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, 9};
     cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->elem, (cuuint64_t)c->plane * c->elem};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(), 1};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(c->p.storage), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(map, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

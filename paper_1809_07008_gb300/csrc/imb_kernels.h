@@ -72,7 +72,7 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
                                   const TileCand *tiles, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
 int tma_box_width(int storage, int wide);
-int tma_box_rows();
+int tma_box_rows(int storage);
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s);
 cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);

@@ -415,14 +415,14 @@ __device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int 
 // boxes: the x start must be 16-byte aligned, so the six planes pulled from x - 1 or
 // x + 1 (c_x = +-1) take a box HALO cells wider than the tile (starting HALO cells left
 // of the tile for c_x = +1), the three with c_x = 0 exactly the tile width.
-constexpr int HROWS = TILE;              // rows per work unit (one tile)
-constexpr int RPW = HROWS / WARPS;       // rows per warp per unit
-constexpr int QCAP = HROWS * 32;         // immersed-node queue of a unit
-
 template <typename S> struct Box {
+    static constexpr int HROWS = sizeof(S) == 4 ? 16 : 32;  // rows per work unit
+    static constexpr int UPT = TILE / HROWS;                 // work units per tile
+    static constexpr int RPW = HROWS / WARPS;                // rows per warp per unit
+    static constexpr int QCAP = HROWS * 32;                  // immersed-node queue of a unit
     static constexpr int HALO = 16 / (int)sizeof(S);
     static constexpr int NST = 2;                            // units in flight per block
-    static constexpr int BLOCKS_PER_SM = sizeof(S) == 4 ? 2 : 3;
+    static constexpr int BLOCKS_PER_SM = 3;
     static constexpr int WN = TILE, WW = TILE + HALO;
     __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
     __host__ __device__ static constexpr int offset(int q) {   // elements before plane q
@@ -442,8 +442,10 @@ template <typename S> struct Box {
     static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
-static_assert((Box<float>::WN * HROWS * 4) % 128 == 0 && (Box<float>::WW * HROWS * 4) % 128 == 0 &&
-                  (Box<__half>::WN * HROWS * 2) % 128 == 0 && (Box<__half>::WW * HROWS * 2) % 128 == 0,
+static_assert((Box<float>::WN * Box<float>::HROWS * 4) % 128 == 0 &&
+                  (Box<float>::WW * Box<float>::HROWS * 4) % 128 == 0 &&
+                  (Box<__half>::WN * Box<__half>::HROWS * 2) % 128 == 0 &&
+                  (Box<__half>::WW * Box<__half>::HROWS * 2) % 128 == 0,
               "TMA boxes stay 128-byte aligned in shared memory");
 static_assert(Box<float>::EXTRA_BYTES % 8 == 0 && Box<__half>::EXTRA_BYTES % 8 == 0, "mbarrier alignment");
 static_assert(Box<float>::BLOCKS_PER_SM * (Box<float>::SMEM_BYTES + 1024) <= 228 * 1024 &&
@@ -470,7 +472,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                  const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
                  const TileCand *__restrict__ tiles, const int ntiles) {
     using G = Box<S>;
-    constexpr int NST = G::NST;
+    constexpr int NST = G::NST, HROWS = G::HROWS, UPT = G::UPT, RPW = G::RPW, QCAP = G::QCAP;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
     float *part = reinterpret_cast<float *>(extra);
@@ -497,31 +499,35 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     };
     // producer (thread 0): takes the next tile and starts its copies into the next stage;
     // after the first tile past the end it hands out nothing more
-    int pk = 0;
+    int pk = 0, cur_t = 0;
     bool pdone = false;
     int next_t = threadIdx.x == 0 ? (int)atomicAdd(&a.tile_ctr[0], 1u) : 0;   // taken one tile ahead
     auto issue_next = [&]() {
         if (pdone) return;
-        const int st = pk++ % NST;
-        const int t = next_t;
+        const int st = pk % NST, h = pk % UPT;
+        ++pk;
+        if (h == 0) {
+            cur_t = next_t;
+            if (cur_t < ntiles) next_t = (int)atomicAdd(&a.tile_ctr[0], 1u);
+        }
+        const int t = cur_t;
         if (t >= ntiles) {
             pdone = true;
             stage_tile[st] = make_int4(-1, 0, 0, 0);
             mbar_arrive_expect_tx(&mbar[st], 0u);
             return;
         }
-        next_t = (int)atomicAdd(&a.tile_ctr[0], 1u);
         const int bx = t % a.nbx, by = t / a.nbx;
-        stage_tile[st] = make_int4(t, bx, by, 0);
+        stage_tile[st] = make_int4(t, bx, by, h);
         const bool in = tma_tile(bx, by, a.nx, a.ny);
         mbar_arrive_expect_tx(&mbar[st], (uint32_t)sizeof(TileCand) + (in ? (uint32_t)G::POP_BYTES : 0u));
         bulk_load(stage_cand(st), &tiles[t], (uint32_t)sizeof(TileCand), &mbar[st]);
         if (in) {
-            const int x0 = bx * TILE, y0 = by * TILE;
+            const int x0 = bx * TILE, yb = by * TILE + h * HROWS;
 #pragma unroll
             for (int q = 0; q < 9; ++q)
                 tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
-                            cx_of(q) == 1 ? x0 - G::HALO : x0, y0 - cy_of(q), q, &mbar[st]);
+                            cx_of(q) == 1 ? x0 - G::HALO : x0, yb - cy_of(q), q, &mbar[st]);
         }
     };
     if (threadIdx.x == 0)
@@ -561,7 +567,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             break;
         }
         if (ti.x < 0) break;   // past the last tile (the same value in every thread)
-        const int h = 0;
+        const int h = ti.w;   // half of the tile, for units of 16 rows
         const int x0 = ti.y * TILE, y0 = ti.z * TILE;
         const bool in = tma_tile(ti.y, ti.z, a.nx, a.ny);
         const TileCand *tc = stage_cand(st);
@@ -947,7 +953,7 @@ int tma_box_width(int storage, int wide) {
     if (storage == 0) return wide ? Box<float>::WW : Box<float>::WN;
     return wide ? Box<__half>::WW : Box<__half>::WN;
 }
-int tma_box_rows() { return HROWS; }
+int tma_box_rows(int storage) { return storage == 0 ? Box<float>::HROWS : Box<__half>::HROWS; }
 
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s) {
