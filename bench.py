@@ -341,7 +341,7 @@ def run_gpu(args):
         lat.step(1)
         if n:
             lat.forces(F, T)
-            hx[:], hv[:], hw[:] = lat.particles()
+            lat.particles(hx, hv, hw)
     t1 = time.perf_counter()
     e2e_s = max_over_ranks(t1 - t0, world)
     e2e_mlups = sum_over_ranks(float(cells) * e2e_steps, world) / e2e_s / 1e6

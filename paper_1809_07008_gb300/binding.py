@@ -236,8 +236,10 @@ class Lattice:
         F, T = _f64(F, 2 * self.np), _f64(T, self.np)
         self._check(self._L.imb_set_forces(self.h, _d(F), _d(T)))
 
-    def particles(self):
-        x, v, w = np.zeros((self.np, 2)), np.zeros((self.np, 2)), np.zeros(self.np)
+    def particles(self, x=None, v=None, w=None):
+        x = np.zeros((self.np, 2)) if x is None else x
+        v = np.zeros((self.np, 2)) if v is None else v
+        w = np.zeros(self.np) if w is None else w
         self._check(self._L.imb_get_particles(self.h, _d(x), _d(v), _d(w)))
         return x, v, w
 

@@ -53,6 +53,7 @@ struct imb_ctx {
     GridBarrier *barrier = nullptr;
     unsigned *err = nullptr;
     unsigned *tile_ctr = nullptr;
+    unsigned *h_err = nullptr;   // pinned host copy of the error word
     TileCand *tiles = nullptr;      // per 32 x 32 tile: particles that can reach it
     float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
     size_t eps_tab_cap = 0;
@@ -244,6 +245,7 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->barrier);
     dfree(c->err);
     dfree(c->tile_ctr);
+    if (c->h_err) cudaFreeHost(c->h_err);
     dfree(c->tiles);
     dfree(c->eps_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -333,6 +335,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
         (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&c->h_err, sizeof(unsigned))) != cudaSuccess ||
         (e = dalloc(&c->bin_bsum, c->nbins / 1024 + 1)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
     cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream);
@@ -542,25 +545,28 @@ static int queue_steps(imb_ctx *c, int n) {
     return IMB_OK;
 }
 
+// Wait for the stream with a deadline: poll without sleeping for the first 2 ms (the usual
+// wait of a coupling cycle), then with 20 us sleeps.
 static int bounded_wait(imb_ctx *c) {
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(c->stream);
         if (e == cudaSuccess) return IMB_OK;
         if (e != cudaErrorNotReady) return cuda_fail(c, e, "stream");
-        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
-                      std::chrono::steady_clock::now() - t0).count();
-        if (ms > c->p.timeout_ms) return fail(c, IMB_E_TIMEOUT, "timed out waiting for the GPU");
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if (us > 1000LL * c->p.timeout_ms) return fail(c, IMB_E_TIMEOUT, "timed out waiting for the GPU");
+        if (us > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
 extern "C" int imb_sync(imb_ctx *c) {
     if (!c) return IMB_E_INVALID_ARG;
+    // the error word travels with the stream's work, into pinned host memory
+    CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "read error flags");
     int rc = bounded_wait(c);
     if (rc) return rc;
-    unsigned bits = 0;
-    CK(cudaMemcpy(&bits, c->err, sizeof(bits), cudaMemcpyDeviceToHost), "read error flags");
+    const unsigned bits = *c->h_err;
     if (!bits) return IMB_OK;
     CK(cudaMemset(c->err, 0, sizeof(unsigned)), "clear error flags");
     if (bits & ERR_UNSTABLE) return fail(c, IMB_E_UNSTABLE, "NaN or |u| >= 0.3 (Mach guard)");
