@@ -589,7 +589,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         // reaches into are queued with the mask of the candidates that reach them
         const int x = x0 + lane;
         const bool xin = x < a.nx;
-#pragma unroll 1
+#pragma unroll 2
         for (int rr = 0; rr < RPW; ++rr) {
             const int yy = h * HROWS + warp + WARPS * rr;
             const int y = y0 + yy;
