@@ -703,3 +703,179 @@ double orc_wall_contact_xi(const orc_sim *s, int p, int wall)
 {
     return s->xiw[(size_t)p * 4 + wall];
 }
+
+/* ------------------------------------------------------------ adjoint
+ * Gradient of the time-averaged drag J = (1/T) sum_{t<T} sum_p F_x,p(t) of T
+ * steps taken from the current state, with respect to the inlet velocity, the
+ * relaxation time and the particle centres, by reverse-mode differentiation of
+ * the steps above (the chain rule through collide and stream in reverse order).
+ * Scope: fixed particles (DEM off, v = w = 0, so u_s = 0 in Eq. 12), plain BGK
+ * (C_smag = 0), no body force, exact-area solid ratio.  Then the solid term
+ * summed over a cell's particles is B (f_{-i} - f^eq_{-i}(rho, u) + w_i rho - f_i)
+ * (Eqs. 12-13 with sum_p B_p = B), the cell's drag is B j_x (Eq. 15 with
+ * sum_i c_i Omega^s_i = -j), and J depends on the particle positions only through
+ * the summed solid ratio E of each cell (Eq. 14). */
+
+/* vertical chord of the disk (centre at the origin, radius r) on the line x = a,
+ * clipped to [b0, b1] */
+static double chord_len(double a, double b0, double b1, double r)
+{
+    if (!(fabs(a) < r)) return 0.0;
+    double h = sqrt(r * r - a * a);
+    double lo = fmax(b0, -h), hi = fmin(b1, h);
+    return hi > lo ? hi - lo : 0.0;
+}
+
+/* adjoint of stream(): lam holds d J / d f(t+1) on entry (modified), lamg gets
+ * d J / d f*(t); fn is f(t+1) (for the inlet density) */
+static void stream_adjoint(const orc_sim *s, double *lam, const double *fn, double *lamg, double *g_uin)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    if (s->p.bc_x == ORC_INLET_OUTLET) {
+        const double ux = s->p.u_in_x, uy = s->p.u_in_y, usq = ux * ux + uy * uy;
+        for (int k = 0; k < ny; ++k) {
+            /* outlet: f(nx-1) = f(nx-2) */
+            for (int q = 0; q < 9; ++q) {
+                lam[IDX(s, q, k, nx - 2)] += lam[IDX(s, q, k, nx - 1)];
+                lam[IDX(s, q, k, nx - 1)] = 0.0;
+            }
+            /* inlet: f(0) = f^eq(rho1, u_in), rho1 = sum_q f(1) */
+            double rho1 = 0.0;
+            for (int q = 0; q < 9; ++q) rho1 += fn[IDX(s, q, k, 1)];
+            double lr = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                double cu = CX[q] * ux + CY[q] * uy, l0 = lam[IDX(s, q, k, 0)];
+                lr += l0 * W[q] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                *g_uin += l0 * W[q] * rho1 * (3.0 * CX[q] + 9.0 * cu * CX[q] - 3.0 * ux);
+                lam[IDX(s, q, k, 0)] = 0.0;
+            }
+            for (int q = 0; q < 9; ++q) lam[IDX(s, q, k, 1)] += lr;
+        }
+    }
+    for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < nx; ++i)
+            for (int q = 0; q < 9; ++q) {
+                double g = 0.0;
+                int xn = i + CX[q], yn = k + CY[q], wall = 0, gone = 0;
+                if (yn < 0 || yn >= ny) {
+                    if (s->p.bc_y == ORC_PERIODIC) yn = (yn + ny) % ny;
+                    else wall = 1;
+                }
+                if (!wall && (xn < 0 || xn >= nx)) {
+                    if (s->p.bc_x == ORC_PERIODIC) xn = (xn + nx) % nx;
+                    else if (s->p.bc_x == ORC_WALL) wall = 1;
+                    else gone = 1;
+                }
+                if (wall) g = lam[IDX(s, OPP[q], k, i)];
+                else if (!gone) g = lam[IDX(s, q, yn, xn)];
+                lamg[IDX(s, q, k, i)] = g;
+            }
+}
+
+/* adjoint of collide() at the state f(t) = f: lamg (d J / d f*) -> lam (d J / d f),
+ * plus the drag's own dependence on f; accumulates d J / d tau and d J / d E */
+static void collide_adjoint(const orc_sim *s, const double *f_all, const double *lamg, double *lam,
+                            double inv_T, double *g_tau, double *gE)
+{
+    const int nx = s->p.nx, ny = s->p.ny;
+    const double tau = s->p.tau, t = tau - 0.5;
+    for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < nx; ++i) {
+            double f[9], fe[9], lg[9];
+            for (int q = 0; q < 9; ++q) {
+                f[q] = f_all[IDX(s, q, k, i)];
+                lg[q] = lamg[IDX(s, q, k, i)];
+            }
+            double rho, ux, uy;
+            moments(f, 0.0, 0.0, &rho, &ux, &uy);
+            orc_feq(rho, ux, uy, fe);
+            double jx = rho * ux, usq = ux * ux + uy * uy;
+            size_t c = (size_t)k * nx + i;
+            double E = 0.0;
+            for (int sl = 0; sl < s->cnt[c]; ++sl) E += s->eps[c * ORC_MAX_SLOTS + sl];
+            double e = E < 1.0 ? E : 1.0;
+            double B = (s->cnt[c] > 0 && E > 0.0) ? orc_B(e, tau) : 0.0;
+            double a = (1.0 - B) / tau;
+            double lf[9], mu[9], nu = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                lf[q] = lg[q] * (1.0 - a - B) + B * lg[OPP[q]] + inv_T * B * CX[q];
+                mu[q] = a * lg[q] - B * lg[OPP[q]];
+                nu += B * W[q] * lg[q];
+            }
+            double lr = nu, ljx = 0.0, ljy = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                double cu = CX[q] * ux + CY[q] * uy;
+                lr += mu[q] * W[q] * (1.0 - 4.5 * cu * cu + 1.5 * usq);
+                ljx += mu[q] * W[q] * (3.0 * CX[q] + 9.0 * cu * CX[q] - 3.0 * ux);
+                ljy += mu[q] * W[q] * (3.0 * CY[q] + 9.0 * cu * CY[q] - 3.0 * uy);
+            }
+            for (int q = 0; q < 9; ++q)
+                lam[IDX(s, q, k, i)] = lf[q] + lr + CX[q] * ljx + CY[q] * ljy;
+            double gt = 0.0;
+            for (int q = 0; q < 9; ++q) gt += lg[q] * (1.0 - B) * (f[q] - fe[q]) / (tau * tau);
+            if (B > 0.0) {
+                double lB = inv_T * jx;
+                for (int q = 0; q < 9; ++q)
+                    lB += lg[q] * ((f[q] - fe[q]) / tau + (f[OPP[q]] - fe[OPP[q]] + W[q] * rho - f[q]));
+                double den = (1.0 - e) + t;
+                gt += lB * e * (1.0 - e) / (den * den);
+                if (E < 1.0) gE[c] += lB * t * (1.0 + t) / (den * den);
+            }
+            *g_tau += gt;
+        }
+}
+
+int orc_drag_adjoint(orc_sim *s, int T, double *J, double *dJ_duin, double *dJ_dtau, double *dJ_dx)
+{
+    if (T < 1 || s->p.dem_on || s->p.C_smag != 0.0 || s->p.Fx != 0.0 || s->p.Fy != 0.0 ||
+        s->p.eps_mode != ORC_EPS_EXACT)
+        return -3;
+    for (int p = 0; p < s->np; ++p)
+        if (s->vx[p] != 0.0 || s->vy[p] != 0.0 || s->w[p] != 0.0) return -3;
+    const int nx = s->p.nx, ny = s->p.ny;
+    const size_t N = (size_t)9 * nx * ny, NC = (size_t)nx * ny;
+    int rc = map_particles(s);
+    if (rc) return rc;
+    /* forward, keeping f(t) of every step */
+    double *tape = (double *)malloc(sizeof(double) * N * (size_t)(T + 1));
+    if (!tape) return -4;
+    double sum = 0.0;
+    for (int t = 0; t < T; ++t) {
+        memcpy(tape + (size_t)t * N, s->f, sizeof(double) * N);
+        collide(s);
+        for (int p = 0; p < s->np; ++p) sum += s->Ffx[p];
+        stream(s);
+    }
+    memcpy(tape + (size_t)T * N, s->f, sizeof(double) * N);
+    *J = sum / T;
+    /* reverse */
+    double *lam = (double *)calloc(N, sizeof(double));
+    double *lamg = (double *)calloc(N, sizeof(double));
+    double *gE = (double *)calloc(NC, sizeof(double));
+    double g_uin = 0.0, g_tau = 0.0;
+    for (int t = T - 1; t >= 0; --t) {
+        stream_adjoint(s, lam, tape + (size_t)(t + 1) * N, lamg, &g_uin);
+        collide_adjoint(s, tape + (size_t)t * N, lamg, lam, 1.0 / T, &g_tau, gE);
+    }
+    *dJ_duin = g_uin;
+    *dJ_dtau = g_tau;
+    /* d E / d (centre) per covered cell: chord lengths on the cell's edges */
+    const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
+    for (int p = 0; p < s->np; ++p) dJ_dx[2 * p] = dJ_dx[2 * p + 1] = 0.0;
+    for (int k = 0; k < ny; ++k)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = (size_t)k * nx + i;
+            for (int sl = 0; sl < s->cnt[c]; ++sl) {
+                int p = s->ids[c * ORC_MAX_SLOTS + sl];
+                double cx = s->px[p], cy = s->py[p], r = s->r[p];
+                int ci = (int)floor(cx), cj = (int)floor(cy);
+                int ri = rel_index(i, ci, perx, nx), rk = rel_index(k, cj, pery, ny);
+                double a0 = (double)ri - (cx - ci), b0 = (double)rk - (cy - cj);
+                /* moving the centre by +d moves the cell by -d relative to the disk */
+                dJ_dx[2 * p] += gE[c] * (chord_len(a0, b0, b0 + 1.0, r) - chord_len(a0 + 1.0, b0, b0 + 1.0, r));
+                dJ_dx[2 * p + 1] += gE[c] * (chord_len(b0, a0, a0 + 1.0, r) - chord_len(b0 + 1.0, a0, a0 + 1.0, r));
+            }
+        }
+    free(tape); free(lam); free(lamg); free(gE);
+    return 0;
+}

@@ -70,6 +70,14 @@ int      orc_bins(const orc_sim *s, int bin, int *bin_start, int *bin_ids);
 int      orc_dem_substeps(orc_sim *s, int nsub);
 double   orc_wall_contact_xi(const orc_sim *s, int p, int wall);
 
+/* Time-averaged drag J = (1/T) sum_{t<T} sum_p F_x,p(t) over T steps from the
+ * current state (which advances by T steps) and its gradient with respect to
+ * u_in_x, tau and the particle centres (dJ_dx[2p], dJ_dx[2p+1]), by reverse-mode
+ * differentiation of the steps.  Scope: DEM off, particles at rest, C_smag = 0,
+ * no body force, exact-area solid ratio; returns -3 outside it.  Keeps every
+ * state in memory (small cases only). */
+int      orc_drag_adjoint(orc_sim *s, int T, double *J, double *dJ_duin, double *dJ_dtau, double *dJ_dx);
+
 #ifdef __cplusplus
 }
 #endif

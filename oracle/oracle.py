@@ -90,6 +90,7 @@ def lib():
         L.orc_dem_substeps.argtypes = [C.c_void_p, C.c_int]
         L.orc_wall_contact_xi.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_wall_contact_xi.restype = C.c_double
+        L.orc_drag_adjoint.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -254,3 +255,21 @@ class Sim:
 
     def wall_xi(self, p, wall):
         return lib().orc_wall_contact_xi(self.h, p, wall)
+
+    def drag_adjoint(self, T):
+        """Time-averaged drag over T steps from the current state and its gradient with
+        respect to u_in_x, tau and the particle centres (reverse mode; see the C source)."""
+        J, gu, gt = (C.c_double(0.0) for _ in range(3))
+        gx = np.zeros((max(self.np, 1), 2))
+        rc = lib().orc_drag_adjoint(self.h, int(T), C.byref(J), C.byref(gu), C.byref(gt), _d(gx))
+        if rc:
+            raise ValueError(f"drag adjoint outside its scope or failed ({rc})")
+        return J.value, gu.value, gt.value, gx[:self.np]
+
+    def drag_average(self, T):
+        """Time-averaged total drag sum_p F_x,p over T steps from the current state."""
+        s = 0.0
+        for _ in range(T):
+            self.step(1)
+            s += self.forces()[0][:, 0].sum()
+        return s / T
