@@ -139,6 +139,22 @@ int imb_get_particles(imb_ctx *ctx, double *x, double *v, double *omega);
  * order (-1 in unused slots) and each one's solid ratio eps[ny*nx*4]. */
 int imb_get_cell_map(imb_ctx *ctx, int *count, int *ids, float *eps);
 
+/* Time-averaged drag on disks held at rest, J = (1/T) sum_{t<T} sum_p F_x,p(t) over
+ * T steps from the current state (Eq. 15 forces, summed over the disks), and its
+ * gradient by reverse-mode differentiation of the steps (the adjoint of the pull
+ * streaming, Eq. 1, and of the collision, Eqs. 1-2 and 12-14): dJ_duin (inlet
+ * velocity x component; 0 without an inlet), dJ_dtau, and dJ_dx[2n] (each disk
+ * centre, through the exact overlap area of every cell it covers).  The forward
+ * states are kept every `checkpoint_every` steps and the states in between
+ * recomputed one segment at a time (device memory about T / checkpoint_every +
+ * checkpoint_every + 4 copies of the populations, allocated for the call and freed
+ * after it).  On return the lattice has advanced T steps, as imb_step(ctx, T)
+ * would.  Needs DEM off, v = omega = 0, C_smag = 0, no body force, the exact solid
+ * ratio and FP32 storage, else IMB_E_INVALID_ARG; IMB_E_NOMEM / IMB_E_CUDA on
+ * device failures.  All pointers are host memory owned by the caller. */
+int imb_drag_gradient(imb_ctx *ctx, int T, int checkpoint_every, double *J, double *dJ_duin,
+                      double *dJ_dtau, double *dJ_dx);
+
 /* Pairs (a < b) of particles in contact (Eq. 7: overlap > 0) at the current
  * positions, ascending; writes min(max_pairs, total) pairs and *n_pairs = total. */
 int imb_get_contacts(imb_ctx *ctx, int max_pairs, int *pairs, int *n_pairs);

@@ -3,7 +3,8 @@
 The compute path is the CUDA library ``libimblbm.so`` (C ABI in
 ``include/imblbm.h``); :mod:`.binding` is its ctypes binding.  Importing this
 package loads nothing: the library is built and loaded on first use and every
-call fails loudly when it or a CUDA device is missing.
+call fails loudly when it or a CUDA device is missing.  :mod:`.autodiff` wraps the
+library's drag gradient as a ``torch.autograd.Function`` (imported on demand).
 """
 from .binding import (BC_INLET_OUTLET, BC_PERIODIC, BC_WALL, EPS_EXACT, EPS_SUBCELL, EXPORTS,
                       STORE_BF16, STORE_FP16, STORE_FP32, ImbError, Lattice, default_params,

@@ -31,7 +31,7 @@ EXPORTS = (
     "imb_get_macro", "imb_get_forces", "imb_set_forces", "imb_get_particles",
     "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
-    "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc",
+    "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
 )
 
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
     L.imb_destroy.argtypes = [_vp]
     L.imb_destroy.restype = None
     L.imb_bin_particles_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]
+    L.imb_drag_gradient.argtypes = [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
     _lib = L
     return L
 
@@ -242,6 +243,15 @@ class Lattice:
         w = np.zeros(self.np) if w is None else w
         self._check(self._L.imb_get_particles(self.h, _d(x), _d(v), _d(w)))
         return x, v, w
+
+    def drag_gradient(self, T, checkpoint_every=100):
+        """Time-averaged drag over T steps from the current state and its gradient with respect
+        to the inlet velocity, tau and the disk centres (imb_drag_gradient)."""
+        J, gu, gt = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+        gx = np.zeros((max(self.np, 1), 2))
+        self._check(self._L.imb_drag_gradient(self.h, int(T), int(checkpoint_every), C.byref(J), C.byref(gu),
+                                              C.byref(gt), _d(gx)))
+        return J.value, gu.value, gt.value, gx[:self.np]
 
     def cell_map(self):
         count = np.zeros((self.ny, self.nx), dtype=np.int32)

@@ -27,6 +27,7 @@ UNITS = {
     "imb_particles.cu": ["--fmad=false"],
     "imb_api.cu": [],
     "imb_noalloc.cu": [],
+    "imb_adjoint.cu": [],
 }
 
 

@@ -769,3 +769,111 @@ extern "C" double imb_bytes_per_cell(imb_ctx *c) { return c ? 18.0 * (double)c->
 extern "C" const char *imb_last_error(imb_ctx *c) {
     return c ? c->msg.c_str() : g_init_error.c_str();
 }
+
+// ------------------------------------------------------------------ drag gradient
+extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double *J, double *dJ_duin,
+                                 double *dJ_dtau, double *dJ_dx) {
+    if (!c || !J || !dJ_duin || !dJ_dtau || (c->np > 0 && !dJ_dx)) return IMB_E_INVALID_ARG;
+    if (T < 1 || checkpoint_every < 1) return fail(c, IMB_E_INVALID_ARG, "T and checkpoint_every must be >= 1");
+    if (c->p.dem_on || c->C_smag != 0.0 || c->p.Fx != 0.0 || c->p.Fy != 0.0 || c->p.eps_mode != IMB_EPS_EXACT ||
+        c->p.storage != IMB_STORE_FP32)
+        return fail(c, IMB_E_INVALID_ARG,
+                    "drag gradient needs DEM off, C_smag = 0, no body force, exact solid ratio, FP32 storage");
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int np = c->np, K = checkpoint_every;
+    if (np > 0) {   // disks at rest
+        std::vector<double> hv(2 * (size_t)np), hw(np);
+        CK(cudaMemcpy(hv.data(), c->v, 16 * (size_t)np, cudaMemcpyDeviceToHost), "read v");
+        CK(cudaMemcpy(hw.data(), c->w, 8 * (size_t)np, cudaMemcpyDeviceToHost), "read w");
+        for (int i = 0; i < np; ++i)
+            if (hv[2 * i] != 0.0 || hv[2 * i + 1] != 0.0 || hw[i] != 0.0)
+                return fail(c, IMB_E_INVALID_ARG, "drag gradient needs disks at rest");
+    }
+    const size_t ncell = (size_t)c->nx * c->ny, state = 9 * c->plane;   // floats per state
+    const int nck = (T + K - 1) / K;
+    DevTmp<float> ck, seg, lam, Eb, fin;
+    DevTmp<double> acc, gE, gx, Fsave;
+    DevTmp<int> cnt, ids;
+    DevTmp<float> epsb;
+    CK(dalloc(&ck.p, state * nck), "checkpoints");
+    CK(dalloc(&seg.p, state * (size_t)std::min(K, T)), "segment states");
+    CK(dalloc(&lam.p, 2 * state), "adjoint buffers");
+    CK(dalloc(&fin.p, state), "final state");
+    CK(dalloc(&Eb.p, ncell), "solid ratio");
+    CK(dalloc(&gE.p, ncell), "solid-ratio gradient");
+    CK(dalloc(&acc.p, 4), "accumulators");
+    CK(dalloc(&gx.p, 2 * (size_t)std::max(np, 1)), "position gradient");
+    CK(dalloc(&Fsave.p, 3 * (size_t)std::max(np, 1)), "force copy");
+    CK(dalloc(&cnt.p, ncell), "cell map");
+    CK(dalloc(&ids.p, ncell * MAX_SLOTS), "cell map");
+    CK(dalloc(&epsb.p, ncell * MAX_SLOTS), "cell map");
+    cudaStream_t s = c->stream;
+    const size_t sb = state * sizeof(float);
+    CK(cudaMemsetAsync(acc.p, 0, 4 * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(gE.p, 0, ncell * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(gx.p, 0, 2 * (size_t)std::max(np, 1) * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(lam.p, 0, 2 * sb, s), "clear");
+    CK(cudaMemsetAsync(Eb.p, 0, ncell * sizeof(float), s), "clear");
+    LatticeArgs a = lattice_args(c);
+    if (np > 0) {
+        CK(launch_cell_map(a, cnt.p, ids.p, epsb.p, s), "cell map");
+        CK(launch_cell_E(cnt.p, epsb.p, ncell, Eb.p, s), "solid ratio");
+        c->launches += 2;
+    }
+    // forward: every K-th state kept, the drag of every step summed
+    for (int t = 0; t < T; ++t) {
+        if (t % K == 0)
+            CK(cudaMemcpyAsync(ck.p + state * (t / K), c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "checkpoint");
+        if ((rc = lattice_step(c))) return rc;
+        if (np > 0) {
+            CK(launch_drag_sum(c->F, np, acc.p, s), "drag");
+            c->launches++;
+        }
+    }
+    CK(cudaMemcpyAsync(fin.p, c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "final state");
+    if (np > 0) {
+        CK(cudaMemcpyAsync(Fsave.p, c->F, 16 * (size_t)np, cudaMemcpyDeviceToDevice, s), "forces");
+        CK(cudaMemcpyAsync(Fsave.p + 2 * (size_t)np, c->T, 8 * (size_t)np, cudaMemcpyDeviceToDevice, s), "torques");
+    }
+    // backward, one checkpoint segment at a time: recompute its states, then walk back
+    float *lam1 = lam.p, *lam0 = lam.p + state;   // d J / d f(t+1), d J / d f(t)
+    const float inv_T = 1.0f / (float)T;
+    for (int j = nck - 1; j >= 0; --j) {
+        const int t0 = j * K, t1 = std::min(T, t0 + K);
+        CK(cudaMemcpyAsync(c->fbuf[c->cur], ck.p + state * j, sb, cudaMemcpyDeviceToDevice, s), "restore");
+        for (int t = t0; t < t1; ++t) {
+            CK(cudaMemcpyAsync(seg.p + state * (t - t0), c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "segment");
+            if (t + 1 < t1 && (rc = lattice_step(c))) return rc;
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const float *S1 = t + 1 < t1 ? seg.p + state * (t + 1 - t0) : (t + 1 == T ? fin.p : ck.p + state * (j + 1));
+            if (c->p.bc_x == IMB_BC_INLET_OUTLET && t + 1 < T) {
+                CK(launch_adjoint_inlet(lam1, S1, a, acc.p + 2, s), "adjoint inlet");
+                c->launches++;
+            }
+            CK(launch_adjoint_step(lam1, seg.p + state * (t - t0), lam0, a, Eb.p, gE.p, inv_T, acc.p + 1, s),
+               "adjoint step");
+            c->launches++;
+            std::swap(lam1, lam0);
+        }
+    }
+    // the state and forces after the T forward steps
+    CK(cudaMemcpyAsync(c->fbuf[c->cur], fin.p, sb, cudaMemcpyDeviceToDevice, s), "restore final state");
+    if (np > 0) {
+        CK(cudaMemcpyAsync(c->F, Fsave.p, 16 * (size_t)np, cudaMemcpyDeviceToDevice, s), "forces");
+        CK(cudaMemcpyAsync(c->T, Fsave.p + 2 * (size_t)np, 8 * (size_t)np, cudaMemcpyDeviceToDevice, s), "torques");
+        CK(launch_position_grad(cnt.p, ids.p, gE.p, c->x, c->r, c->nx, c->ny, c->p.bc_x, c->p.bc_y, gx.p, s),
+           "position gradient");
+        c->launches++;
+    }
+    double h[4];
+    CK(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "accumulators");
+    if (np > 0) CK(cudaMemcpyAsync(dJ_dx, gx.p, 16 * (size_t)np, cudaMemcpyDeviceToHost, s), "gradient");
+    if ((rc = imb_sync(c))) return rc;
+    *J = h[0] / T;
+    *dJ_dtau = h[1];
+    *dJ_duin = h[2];
+    return IMB_OK;
+}

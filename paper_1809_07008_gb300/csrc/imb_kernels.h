@@ -76,6 +76,16 @@ int tma_box_rows(int storage);
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s);
 cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);
+// drag gradient (imb_adjoint.cu)
+cudaError_t launch_drag_sum(const double *F, int np, double *acc, cudaStream_t s);
+cudaError_t launch_cell_E(const int *count, const float *eps, size_t ncell, float *E, cudaStream_t s);
+cudaError_t launch_adjoint_inlet(float *lam, const float *S1, const LatticeArgs &a, double *g_uin,
+                                 cudaStream_t s);
+cudaError_t launch_adjoint_step(const float *lam1, const float *S0, float *lam0, const LatticeArgs &a,
+                                const float *E, double *gE, float inv_T, double *g_tau, cudaStream_t s);
+cudaError_t launch_position_grad(const int *count, const int *ids, const double *gE, const double *x,
+                                 const double *r, int nx, int ny, int bc_x, int bc_y, double *dJ_dx,
+                                 cudaStream_t s);
 
 // particle kernels (imb_particles.cu)
 cudaError_t launch_particle_table(const double *x, const double *r, const double *x_start, int np,

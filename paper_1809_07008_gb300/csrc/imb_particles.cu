@@ -296,10 +296,12 @@ __device__ __forceinline__ bool free_of_edges(const DemArgs &d, const FreeMotion
 // The N_sub sub-cycles of a particle that touches nothing: the updates of integrate().
 __device__ __forceinline__ void free_run(const DemArgs &d, const FreeMotion &f, double &px, double &py,
                                          double &vx, double &vy, double &w) {
+    // the velocity increments a dt round to the same value every sub-cycle
+    const double dvx = f.ax * d.dt, dvy = f.ay * d.dt, dw = f.al * d.dt;
     for (int s = 0; s < d.N_sub; ++s) {
-        vx = vx + f.ax * d.dt;
-        vy = vy + f.ay * d.dt;
-        w = w + f.al * d.dt;
+        vx = vx + dvx;
+        vy = vy + dvy;
+        w = w + dw;
         px = px + vx * d.dt;
         py = py + vy * d.dt;
     }
@@ -444,7 +446,7 @@ __global__ void k_dem_free(const DemArgs d) {
         // candidate partners of a quiet island stay out of reach: their springs are released
         for (int j = 0, nn = d.nbr_cnt[p]; j < nn; ++j) d.nbr_xi[p * MAX_NBR + j] = 0.0;
         const FreeMotion f = free_motion(d, p, vx, vy);
-        const double ax0 = f.ax, ay0 = f.ay, al0 = f.al;
+        const double dvx0 = f.ax * d.dt, dvy0 = f.ay * d.dt, dw0 = f.al * d.dt;   // as integrate() rounds them
         if (free_of_edges(d, f, px, py, rp)) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
@@ -464,9 +466,9 @@ __global__ void k_dem_free(const DemArgs d) {
                     // a released wall spring (wall_contacts would zero it)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
-                    vx = vx + ax0 * d.dt;
-                    vy = vy + ay0 * d.dt;
-                    w = w + al0 * d.dt;
+                    vx = vx + dvx0;
+                    vy = vy + dvy0;
+                    w = w + dw0;
                     px = px + vx * d.dt;
                     py = py + vy * d.dt;
                     if (d.bc_x == BC_PERIODIC) {

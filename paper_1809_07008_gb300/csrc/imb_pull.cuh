@@ -1,0 +1,69 @@
+// imb_pull.cuh -- the pull half of the stream step (Eq. 1 LHS) with the boundary rules:
+// periodic wrap, halfway bounce-back walls, velocity inlet / zero-gradient outlet.  Shared by
+// the stream-collide kernel and its adjoint.
+#pragma once
+#include "imb_device.cuh"
+#include "imb_kernels.h"
+
+namespace imb {
+
+// ---------------------------------------------------------------- pulls
+template <typename S>
+__device__ __forceinline__ void pull_generic(const S *__restrict__ fin, const LatticeArgs &a, int x,
+                                             int y, float (&d)[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        int xs = x - cx_of(q), ys = y - cy_of(q);
+        const size_t self_opp = (size_t)opp_of(q) * a.plane + (size_t)y * a.pitch + x;
+        if (ys < 0 || ys >= a.ny) {
+            if (a.bc_y == BC_PERIODIC) {
+                ys = ys < 0 ? ys + a.ny : ys - a.ny;
+            } else {  // halfway bounce-back: what left (x,y) towards the wall comes back
+                d[q] = Store<S>::ld(fin + self_opp);
+                continue;
+            }
+        }
+        if (xs < 0 || xs >= a.nx) {
+            if (a.bc_x == BC_PERIODIC) {
+                xs = xs < 0 ? xs + a.nx : xs - a.nx;
+            } else if (a.bc_x == BC_WALL) {
+                d[q] = Store<S>::ld(fin + self_opp);
+                continue;
+            } else {  // inlet / outlet column, rebuilt by pull_cell
+                d[q] = 0.0f;
+                continue;
+            }
+        }
+        d[q] = Store<S>::ld(fin + (size_t)q * a.plane + (size_t)ys * a.pitch + xs);
+    }
+}
+
+// shifted equilibrium f^eq_q - w_q = w_q (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2))   (Eq. 2)
+__device__ __forceinline__ void equilibrium_shifted(float drho, float rho, float ux, float uy,
+                                                    float (&d)[9]) {
+    const float usq = ux * ux + uy * uy;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        d[q] = w_of(q) * (drho + rho * (cu * (3.0f + 4.5f * cu) - 1.5f * usq));
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ void pull_cell(const S *__restrict__ fin, const LatticeArgs &a, int x,
+                                          int y, float (&d)[9]) {
+    if (a.bc_x == BC_INLET_OUTLET && (x == 0 || x == a.nx - 1)) {
+        // inlet: f^eq(rho of column 1, u_in); outlet: copy of column nx-2 (zero gradient)
+        pull_generic(fin, a, x == 0 ? 1 : a.nx - 2, y, d);
+        if (x == 0) {
+            float drho = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) drho += d[q];
+            equilibrium_shifted(drho, 1.0f + drho, a.u_in_x, a.u_in_y, d);
+        }
+        return;
+    }
+    pull_generic(fin, a, x, y, d);
+}
+
+}  // namespace imb

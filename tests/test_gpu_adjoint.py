@@ -1,0 +1,126 @@
+"""GPU reverse-mode drag gradient (imb_drag_gradient) against the FP64 oracle's adjoint and
+against central finite differences of the GPU's own forward steps.
+
+* Same warm state on both sides (20 steps from rest), then T steps: J, d J / d tau and
+  d J / d (disk centres) against the oracle's reverse mode (FP32 tolerances: 1e-5 on J, 2e-3 on
+  the gradients relative to their largest component).  The inlet-velocity component differs by
+  design here (the oracle holds f(x, t) fixed, the GPU pulls f(x, t) from the previous
+  post-collision field with the inlet rule), so it is checked against differences instead.
+* The 512 x 256 channel with 16 fixed disks (the drag-gradient case): d J / d u_in and
+  d J / d tau against central differences with h = 1e-4 of J from rest (FP32 forward:
+  2e-2), and the checkpoint interval changes nothing (the recomputed states are the same; the
+  order in which a tile's immersed nodes are summed into the forces is not fixed, which leaves
+  differences of ~1e-10 in J and ~1e-12 in the gradient).
+* The torch.autograd wrapper hands back the library's gradient.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imb():
+    import paper_1809_07008_gb300 as imb
+    imb.load()
+    return imb
+
+
+def _small(kind, u=0.02, tau=0.6):
+    x = np.array([[20.3, 15.7], [33.6, 17.2]])
+    common = dict(x=x, v=np.zeros((2, 2)), omega=np.zeros(2), r=np.array([5.23, 4.37]), dem_on=0)
+    if kind == "channel":
+        return W.Workload(name="adj_channel", nx=52, ny=32, tau=tau, bc_x=W.BC_INLET_OUTLET,
+                          bc_y=W.BC_WALL, u_in=(u, 0.0), **common)
+    # the library wants a periodic extent of at least 2 (32 + r_max + 2) cells
+    return W.Workload(name="adj_periodic", nx=96, ny=32, tau=tau, bc_x=W.BC_PERIODIC, bc_y=W.BC_WALL,
+                      u0=(0.02, 0.0), **common)
+
+
+@pytest.mark.parametrize("kind", ["channel", "periodic"])
+def test_drag_gradient_matches_oracle_adjoint(orc, imb, kind):
+    w = _small(kind)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    o.step(20)
+    g.step(20)
+    T = 60
+    Jo, _, gto, gxo = o.drag_adjoint(T)
+    Jg, _, gtg, gxg = g.drag_gradient(T, checkpoint_every=16)
+    assert Jg == pytest.approx(Jo, rel=1e-5)
+    assert gtg == pytest.approx(gto, rel=2e-3)
+    scale = np.abs(gxo).max()
+    assert np.abs(gxg - gxo).max() < 2e-3 * scale, (gxg, gxo)
+    # the lattice advanced T steps, as imb_step would have
+    o.step(3)
+    g.step(3)
+    assert np.abs(g.populations() - o.f()).max() < 1e-5
+
+
+def _J_from_rest(imb, w, T):
+    g = imb.Lattice.from_workload(w)
+    s = 0.0
+    for _ in range(T):
+        g.step(1)
+        s += g.forces()[0][:, 0].sum()
+    g.close()
+    return s / T
+
+
+def test_inlet_and_tau_gradient_against_differences_small(imb):
+    w = _small("channel")
+    T, h = 200, 1e-4
+    g = imb.Lattice.from_workload(w)
+    J, g_u, g_tau, _ = g.drag_gradient(T, checkpoint_every=32)
+    assert J == pytest.approx(_J_from_rest(imb, w, T), rel=1e-6)
+    fd_u = (_J_from_rest(imb, _small("channel", u=0.02 + h), T) - _J_from_rest(imb, _small("channel", u=0.02 - h), T)) / (2 * h)
+    fd_t = (_J_from_rest(imb, _small("channel", tau=0.6 + h), T) - _J_from_rest(imb, _small("channel", tau=0.6 - h), T)) / (2 * h)
+    assert g_u == pytest.approx(fd_u, rel=2e-2)
+    assert g_tau == pytest.approx(fd_t, rel=2e-2)
+
+
+def test_channel_16_disks_gradient(imb):
+    w = W.c4()
+    T, h = 4000, 1e-4
+    g = imb.Lattice.from_workload(w)
+    J, g_u, g_tau, g_x = g.drag_gradient(T, checkpoint_every=100)
+    g.close()
+    assert np.isfinite([J, g_u, g_tau]).all() and np.isfinite(g_x).all()
+    assert J > 0.0 and np.abs(g_x).max() > 0.0
+    # the checkpoint interval only changes what is recomputed
+    g2 = imb.Lattice.from_workload(w)
+    J2, g_u2, g_tau2, g_x2 = g2.drag_gradient(T, checkpoint_every=37)
+    g2.close()
+    assert J2 == pytest.approx(J, rel=1e-8) and g_u2 == pytest.approx(g_u, rel=1e-12)
+    assert g_tau2 == pytest.approx(g_tau, rel=1e-12)
+    assert np.abs(g_x2 - g_x).max() <= 1e-12 * np.abs(g_x).max()
+
+    def J_of(**kw):
+        g3 = imb.Lattice.from_workload(W.c4(**kw))
+        out = g3.drag_gradient(T, checkpoint_every=T)[0]
+        g3.close()
+        return out
+
+    fd_u = (J_of(u_in=0.02 + h) - J_of(u_in=0.02 - h)) / (2 * h)
+    fd_t = (J_of(tau=0.6 + h) - J_of(tau=0.6 - h)) / (2 * h)
+    assert g_u == pytest.approx(fd_u, rel=2e-2)
+    assert g_tau == pytest.approx(fd_t, rel=2e-2)
+
+
+def test_autograd_wrapper_returns_the_library_gradient(imb):
+    torch = pytest.importorskip("torch")
+    from paper_1809_07008_gb300.autodiff import drag_mean
+    w = _small("channel")
+    u = torch.tensor(0.02, dtype=torch.float64, requires_grad=True)
+    tau = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    x = torch.tensor(w.x, dtype=torch.float64, requires_grad=True)
+    J = drag_mean(u, tau, x, w, 50, checkpoint_every=10)
+    J.backward()
+    g = imb.Lattice.from_workload(w)
+    Jr, g_u, g_tau, g_x = g.drag_gradient(50, checkpoint_every=10)
+    assert J.item() == pytest.approx(Jr, rel=1e-8)
+    assert u.grad.item() == pytest.approx(g_u, rel=1e-12)
+    assert tau.grad.item() == pytest.approx(g_tau, rel=1e-12)
+    assert np.abs(x.grad.numpy() - g_x).max() <= 1e-12 * np.abs(g_x).max()

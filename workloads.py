@@ -238,10 +238,26 @@ def c3sub(steps=1000, nx=512, ny=512, seed=7008) -> Workload:
     return w.with_(name=f"c3sub_suspension_{nx}x{ny}_{n}disks")
 
 
+def c4(steps=4000, nx=512, ny=256, n_side=4, d=20.0, seed=1809, u_in=0.02, tau=0.6) -> Workload:
+    """Channel with n_side x n_side fixed disks on a jittered grid (velocity inlet, zero-gradient
+    outlet, walls), the case of the drag-gradient computation."""
+    rng = SplitMix64(seed)
+    sx, sy = nx / (n_side + 1), ny / (n_side + 1)
+    xs = []
+    for j in range(n_side):
+        for i in range(n_side):
+            xs.append(((i + 1) * sx + rng.uniform_range(-0.15 * sx, 0.15 * sx),
+                       (j + 1) * sy + rng.uniform_range(-0.15 * sy, 0.15 * sy)))
+    n = len(xs)
+    return Workload(name=f"c4_channel_{nx}x{ny}_{n}disks", nx=nx, ny=ny, tau=tau, C_smag=0.0,
+                    bc_x=BC_INLET_OUTLET, bc_y=BC_WALL, u_in=(u_in, 0.0), dem_on=0, steps=steps,
+                    x=np.array(xs), v=np.zeros((n, 2)), omega=np.zeros(n), r=np.full(n, d / 2.0))
+
+
 def poiseuille(H=32, nx=4, tau=0.6, g=1.0e-6, steps=20000) -> Workload:
     """Body-force driven channel, periodic in x, walls at y = 0 and y = H, no particles."""
     return Workload(name=f"poiseuille_H{H}", nx=nx, ny=H, tau=tau, bc_x=BC_PERIODIC, bc_y=BC_WALL,
                     force=(g, 0.0), steps=steps)
 
 
-WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c3sub": c3sub}
+WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c3sub": c3sub, "c4": c4}
