@@ -15,7 +15,10 @@ Prints ONE JSON line.  ``value`` = lattice updates per second of whole steps
 uploaded and forces/torques read back every step); ``roofline`` = the
 stream-collide kernel's algorithmic bytes per launch over its event-timed
 duration against the measured HBM copy bandwidth; ``cpu_baseline`` = the FP64
-oracle on a bounded sample, timed on this host.
+oracle on a bounded sample, timed on this host; ``storage_variants`` = the same
+workload with FP16 / BF16 population storage; ``drag_gradient`` = one reverse-mode
+gradient of the time-averaged drag on the 512 x 256 channel with 16 fixed disks
+over 4000 steps (imb_drag_gradient), timed on the host clock.
 
   python bench.py [--gpus N --steps K --warmup W] [--workload c3|c2|c1]
                   [--storage fp32|fp16|bf16] [--impl reference]
@@ -55,6 +58,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="skip the drag-gradient line (512 x 256 channel, 16 fixed disks, 4000 steps)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--nx", type=int, default=None, help="smaller lattice at the same disk density")
     ap.add_argument("--ny", type=int, default=None)
@@ -230,6 +235,25 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+def time_drag_gradient(imb, T=4000, checkpoint_every=100):
+    """Reverse-mode gradient of the time-averaged drag on the 512 x 256 channel with 16 fixed
+    disks: one call of imb_drag_gradient (forward, checkpointed recomputation, backward)."""
+    w = W.c4(steps=T)
+    warm = imb.Lattice.from_workload(w)
+    warm.drag_gradient(200, checkpoint_every)
+    warm.close()
+    lat = imb.Lattice.from_workload(w)
+    t0 = time.perf_counter()
+    J, g_u, g_tau, g_x = lat.drag_gradient(T, checkpoint_every)
+    dt = time.perf_counter() - t0
+    lat.close()
+    cells = w.nx * w.ny
+    return {"workload": w.name, "steps": T, "checkpoint_every": checkpoint_every, "seconds": round(dt, 4),
+            "mlups": round(cells * T / dt / 1e6, 1), "note": "lattice updates of the forward horizon per second "
+            "of the whole gradient (forward, recomputation and adjoint)", "J": J, "dJ_duin": g_u,
+            "dJ_dtau": g_tau, "dJ_dx_max": float(np.abs(g_x).max())}
+
+
 def oracle_sample_workload():
     # bounded sample: the 512 x 512 subdomain of the suspension at the same disk density
     return W.c3sub(steps=0)
@@ -376,6 +400,10 @@ def run_gpu(args):
             del lv
             torch.cuda.synchronize()
 
+    gradient = None
+    if not args.no_gradient and rank == 0:
+        gradient = time_drag_gradient(imb)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu = time_oracle()
@@ -394,6 +422,8 @@ def run_gpu(args):
                 "clocks": clocks}
         if variants:
             line["storage_variants"] = variants
+        if gradient:
+            line["drag_gradient"] = gradient
         print(json.dumps(line), flush=True)
 
 

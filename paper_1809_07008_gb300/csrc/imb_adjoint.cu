@@ -46,43 +46,54 @@ __global__ void k_cell_E(const int *__restrict__ count, const float *__restrict_
 }
 
 // adjoint of the inlet and outlet columns of the pull, applied in place to the adjoint of
-// f(t+1) before the step-t kernel gathers from it; S1 is P(t), from which f(t+1) is pulled
+// f(t+1) before the step-t kernel gathers from it; S1 is P(t), from which f(t+1) is pulled.
+// One warp per row, lane q < 9 for population q.
 __global__ void k_adjoint_inlet(float *__restrict__ lam, const float *__restrict__ S1, const LatticeArgs a,
                                 double *g_uin) {
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    double gu = 0.0;
-    if (y < a.ny) {
-        const size_t row = (size_t)y * a.pitch;
-        // outlet: f(nx-1) = f(nx-2)
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            float *l = lam + (size_t)q * a.plane + row;
-            l[a.nx - 2] += l[a.nx - 1];
-            l[a.nx - 1] = 0.0f;
-        }
-        // inlet: f(0) = f^eq(rho1, u_in), rho1 the density of the column-1 pull
-        float d[9];
-        pull_generic(S1, a, 1, y, d);
-        float rho1 = 1.0f;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) rho1 += d[q];
-        const float ux = a.u_in_x, uy = a.u_in_y, usq = ux * ux + uy * uy;
-        float lr = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            float *l = lam + (size_t)q * a.plane + row;
-            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-            const float cu = cxq * ux + cyq * uy;
-            lr += l[0] * w_of(q) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
-            gu += (double)(l[0] * w_of(q) * rho1 * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux));
-            l[0] = 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) lam[(size_t)q * a.plane + row + 1] += lr;
+    const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), q = threadIdx.x & 31;
+    if (y >= a.ny) return;   // whole warp
+    const bool on = q < 9;
+    const size_t row = (size_t)y * a.pitch;
+    float *l = lam + (size_t)(on ? q : 0) * a.plane + row;
+    // outlet: f(nx-1) = f(nx-2)
+    if (on) {
+        l[a.nx - 2] += l[a.nx - 1];
+        l[a.nx - 1] = 0.0f;
     }
+    // inlet: f(0) = f^eq(rho1, u_in), rho1 = 1 + the pulled shifted populations of column 1
+    float dq = 0.0f;
+    if (on) {
+        int ys = y - cy_of(q);
+        size_t src;
+        if (ys < 0 || ys >= a.ny) {
+            if (a.bc_y == BC_PERIODIC) {
+                ys = ys < 0 ? ys + a.ny : ys - a.ny;
+                src = (size_t)q * a.plane + (size_t)ys * a.pitch + (1 - cx_of(q));
+            } else {
+                src = (size_t)opp_of(q) * a.plane + row + 1;   // halfway bounce-back
+            }
+        } else {
+            src = (size_t)q * a.plane + (size_t)ys * a.pitch + (1 - cx_of(q));
+        }
+        dq = S1[src];
+    }
+    const float ux = a.u_in_x, uy = a.u_in_y, usq = ux * ux + uy * uy;
+    const float cxq = on ? (float)cx_of(q) : 0.0f, cyq = on ? (float)cy_of(q) : 0.0f;
+    const float wq = on ? w_of(q) : 0.0f, cu = cxq * ux + cyq * uy;
+    const float l0 = on ? l[0] : 0.0f;
+    float lr = l0 * wq * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
+    float gq = l0 * wq * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) gu += __shfl_xor_sync(0xffffffffu, gu, o);
-    if ((threadIdx.x & 31) == 0 && gu != 0.0) atomicAdd(g_uin, gu);
+    for (int o = 16; o > 0; o >>= 1) {
+        dq += __shfl_xor_sync(0xffffffffu, dq, o);
+        lr += __shfl_xor_sync(0xffffffffu, lr, o);
+        gq += __shfl_xor_sync(0xffffffffu, gq, o);
+    }
+    if (on) {
+        l[0] = 0.0f;
+        l[1] += lr;
+    }
+    if (q == 0 && gq != 0.0f) atomicAdd(g_uin, (double)(gq * (1.0f + dq)));
 }
 
 // One step backwards: lam1 = d J / d f(t+1) (columns already transposed), S0 = P(t-1)
@@ -221,7 +232,7 @@ cudaError_t launch_cell_E(const int *count, const float *eps, size_t ncell, floa
 
 cudaError_t launch_adjoint_inlet(float *lam, const float *S1, const LatticeArgs &a, double *g_uin,
                                  cudaStream_t s) {
-    k_adjoint_inlet<<<(a.ny + 127) / 128, 128, 0, s>>>(lam, S1, a, g_uin);
+    k_adjoint_inlet<<<(a.ny + 7) / 8, 256, 0, s>>>(lam, S1, a, g_uin);
     return cudaGetLastError();
 }
 
