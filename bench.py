@@ -235,10 +235,10 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def time_drag_gradient(imb, T=4000, checkpoint_every=100):
+def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256):
     """Reverse-mode gradient of the time-averaged drag on the 512 x 256 channel with 16 fixed
     disks: one call of imb_drag_gradient (forward, checkpointed recomputation, backward)."""
-    w = W.c4(steps=T)
+    w = W.c4(steps=T, nx=nx, ny=ny)
     warm = imb.Lattice.from_workload(w)
     warm.drag_gradient(200, checkpoint_every)
     warm.close()

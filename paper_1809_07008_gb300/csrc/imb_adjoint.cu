@@ -105,28 +105,38 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const float *__restrict__ 
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     double gt = 0.0;
     if (x < a.nx) {
-        // adjoint of P(t) at (x, y): who pulled P_q(x, y)
-        float L[9];
+        // adjoint of P(t) at (x, y): who pulled P_q(x, y); and f(t) at (x, y), pulled from
+        // P(t-1) (shifted populations d = f - w).  Away from the edges no boundary rule applies.
+        float L[9], d[9];
+        const bool inner = x >= 1 && x <= a.nx - 2 && y >= 1 && y <= a.ny - 2;
+        if (inner) {
+            const size_t c0 = (size_t)y * a.pitch + x;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            int xd = x + cx_of(q), yd = y + cy_of(q);
-            bool bounce = false, gone = false;
-            if (yd < 0 || yd >= a.ny) {
-                if (a.bc_y == BC_PERIODIC) yd = yd < 0 ? yd + a.ny : yd - a.ny;
-                else bounce = true;
+            for (int q = 0; q < 9; ++q) {
+                const ptrdiff_t off = (ptrdiff_t)cy_of(q) * a.pitch + cx_of(q);
+                L[q] = lam1[(size_t)q * a.plane + c0 + off];
+                d[q] = S0[(size_t)q * a.plane + c0 - off];
             }
-            if (!bounce && (xd < 0 || xd >= a.nx)) {
-                if (a.bc_x == BC_PERIODIC) xd = xd < 0 ? xd + a.nx : xd - a.nx;
-                else if (a.bc_x == BC_WALL) bounce = true;
-                else gone = true;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                int xd = x + cx_of(q), yd = y + cy_of(q);
+                bool bounce = false, gone = false;
+                if (yd < 0 || yd >= a.ny) {
+                    if (a.bc_y == BC_PERIODIC) yd = yd < 0 ? yd + a.ny : yd - a.ny;
+                    else bounce = true;
+                }
+                if (!bounce && (xd < 0 || xd >= a.nx)) {
+                    if (a.bc_x == BC_PERIODIC) xd = xd < 0 ? xd + a.nx : xd - a.nx;
+                    else if (a.bc_x == BC_WALL) bounce = true;
+                    else gone = true;
+                }
+                L[q] = gone ? 0.0f
+                       : bounce ? lam1[(size_t)opp_of(q) * a.plane + (size_t)y * a.pitch + x]
+                                : lam1[(size_t)q * a.plane + (size_t)yd * a.pitch + xd];
             }
-            L[q] = gone ? 0.0f
-                   : bounce ? lam1[(size_t)opp_of(q) * a.plane + (size_t)y * a.pitch + x]
-                            : lam1[(size_t)q * a.plane + (size_t)yd * a.pitch + xd];
+            pull_cell(S0, a, x, y, d);
         }
-        // f(t) at (x, y) and its moments (shifted populations d = f - w)
-        float d[9];
-        pull_cell(S0, a, x, y, d);
         float drho = 0.0f, jx = 0.0f, jy = 0.0f;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
