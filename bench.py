@@ -229,7 +229,7 @@ def committed_traffic(kernel_src_hash, workload, storage):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("imb_lbm.cu", "imb_device.cuh", "imb_pull.cuh"):
+    for f in ("imb_lbm.cu", "imb_device.cuh", "imb_pull.cuh", "imb_node.cuh"):
         with open(os.path.join(ROOT, "paper_1809_07008_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

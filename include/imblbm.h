@@ -155,6 +155,51 @@ int imb_get_cell_map(imb_ctx *ctx, int *count, int *ids, float *eps);
 int imb_drag_gradient(imb_ctx *ctx, int T, int checkpoint_every, double *J, double *dJ_duin,
                       double *dJ_dtau, double *dJ_dx);
 
+/* ---- many independent domains (the parameter sweeps of Sec. 3 as one batch) ----
+ * Each domain d is an nx[d] x ny[d] lattice, periodic in x and y, at rest at t = 0
+ * (rho = 1), driven by the body force (Fx[d], Fy[d]) (Guo forcing), with relaxation
+ * time tau[d] (plain BGK) and n_disks[d] disks held at rest: their centres are
+ * disk_xy[2j], disk_xy[2j+1] in the domain's cell units and radii disk_r[j], the
+ * disks of domain 0 first, then those of domain 1, and so on.  Populations are
+ * stored as f - w in `storage` (IMB_STORE_*).  Every step advances all domains
+ * with the collision of Eq. 13 (B of Eq. 14 from the summed exact overlap area of
+ * each cell, u_s = 0) and adds each domain's drag (Eq. 15, summed over its disks)
+ * to an accumulator.  The library owns the batch; host arrays are copied.
+ * Returns IMB_E_INVALID_ARG for a bad size, tau <= 0.5, a disk outside its domain
+ * or wider than it minus four cells; IMB_E_NOMEM / IMB_E_CUDA on device failures
+ * (then *out holds a batch to destroy, with the message in imb_batch_last_error). */
+typedef struct imb_batch imb_batch;
+int imb_batch_create(imb_batch **out, int n_domains, const int *nx, const int *ny, const double *tau,
+                     const double *Fx, const double *Fy, const int *n_disks, const double *disk_xy,
+                     const double *disk_r, int storage);
+
+/* Advance every domain by `steps` steps (two steps at a time as a replayed CUDA graph
+ * of two launches) and wait; IMB_E_UNSTABLE when a node went NaN or |u| >= 0.3. */
+int imb_batch_run(imb_batch *b, int steps);
+
+/* Time `steps_per_trial` steps of each launch shape (blocks of 128, 256 or
+ * 512 threads; one or two cells per lane along a row) on the batch itself, keep the
+ * fastest, and put the state and the drag accumulators back as they were.  Outputs
+ * (each may be NULL): the chosen block size, cells per lane and its ms per step. */
+int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block, int *cells_per_lane,
+                       double *best_ms_per_step);
+
+/* Mean drag of every domain over the steps run so far: Fx_mean[n_domains],
+ * Fy_mean[n_domains] (the force on the domain's disks, summed over them). */
+int imb_batch_mean_drag(imb_batch *b, double *Fx_mean, double *Fy_mean);
+
+/* f(x, t) of one domain, [9][ny][nx] in FP64 (as imb_get_populations). */
+int imb_batch_get_populations(imb_batch *b, int domain, double *f);
+
+/* Lattice cells of all domains together. */
+long long imb_batch_cells(const imb_batch *b);
+
+/* Message of the last failed call on this batch. */
+const char *imb_batch_last_error(const imb_batch *b);
+
+/* Free the batch; NULL is ignored. */
+void imb_batch_destroy(imb_batch *b);
+
 /* Pairs (a < b) of particles in contact (Eq. 7: overlap > 0) at the current
  * positions, ascending; writes min(max_pairs, total) pairs and *n_pairs = total. */
 int imb_get_contacts(imb_ctx *ctx, int max_pairs, int *pairs, int *n_pairs);

@@ -32,6 +32,8 @@ EXPORTS = (
     "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
     "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
+    "imb_batch_create", "imb_batch_run", "imb_batch_autotune", "imb_batch_mean_drag",
+    "imb_batch_get_populations", "imb_batch_cells", "imb_batch_last_error", "imb_batch_destroy",
 )
 
 
@@ -114,6 +116,17 @@ def load(build_if_missing: bool = True):
     L.imb_destroy.restype = None
     L.imb_bin_particles_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]
     L.imb_drag_gradient.argtypes = [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+    L.imb_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _ip, _ip, _dp, _dp, _dp, _ip, _dp, _dp, C.c_int]
+    L.imb_batch_run.argtypes = [_vp, C.c_int]
+    L.imb_batch_autotune.argtypes = [_vp, C.c_int, _ip, _ip, _dp]
+    L.imb_batch_mean_drag.argtypes = [_vp, _dp, _dp]
+    L.imb_batch_get_populations.argtypes = [_vp, C.c_int, _dp]
+    L.imb_batch_cells.argtypes = [_vp]
+    L.imb_batch_cells.restype = C.c_longlong
+    L.imb_batch_last_error.argtypes = [_vp]
+    L.imb_batch_last_error.restype = C.c_char_p
+    L.imb_batch_destroy.argtypes = [_vp]
+    L.imb_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -297,3 +310,73 @@ class Lattice:
 
     def bytes_per_cell(self) -> float:
         return float(self._L.imb_bytes_per_cell(self.h))
+
+
+class Batch:
+    """Many independent periodic domains with fixed disks, stepped together (imb_batch_*).
+
+    ``domains`` is a sequence of workloads (``workloads.Workload``, periodic in x and y, DEM
+    off, disks at rest); their sizes, tau, body force and disks define the batch."""
+
+    def __init__(self, domains, storage="fp16"):
+        self._L = load()
+        n = len(domains)
+        nx = np.array([w.nx for w in domains], dtype=np.int32)
+        ny = np.array([w.ny for w in domains], dtype=np.int32)
+        tau = np.array([w.tau for w in domains], dtype=np.float64)
+        fx = np.array([w.force[0] for w in domains], dtype=np.float64)
+        fy = np.array([w.force[1] for w in domains], dtype=np.float64)
+        nd = np.array([w.n_particles for w in domains], dtype=np.int32)
+        xy = np.ascontiguousarray(np.concatenate([np.asarray(w.x, dtype=np.float64).reshape(-1, 2)
+                                                  for w in domains] + [np.zeros((0, 2))]))
+        r = np.ascontiguousarray(np.concatenate([np.asarray(w.r, dtype=np.float64).reshape(-1)
+                                                 for w in domains] + [np.zeros(0)]))
+        if xy.shape[0] == 0:
+            xy, r = np.zeros((1, 2)), np.zeros(1)
+        st = STORAGE_NAMES[storage] if isinstance(storage, str) else storage
+        h = _vp()
+        rc = self._L.imb_batch_create(C.byref(h), n, nx.ctypes.data_as(_ip), ny.ctypes.data_as(_ip), _d(tau),
+                                      _d(fx), _d(fy), nd.ctypes.data_as(_ip), _d(xy), _d(r), st)
+        self.h = h
+        self.n = n
+        self.shapes = [(int(a), int(b)) for a, b in zip(ny, nx)]
+        self._check(rc)
+
+    def _check(self, rc):
+        if rc != IMB_OK:
+            msg = self._L.imb_batch_last_error(self.h).decode() if self.h else ""
+            raise ImbError(rc, msg)
+
+    def run(self, steps):
+        self._check(self._L.imb_batch_run(self.h, int(steps)))
+
+    def autotune(self, steps_per_trial=20):
+        blk, cpl, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        self._check(self._L.imb_batch_autotune(self.h, int(steps_per_trial), C.byref(blk), C.byref(cpl),
+                                               C.byref(ms)))
+        return blk.value, cpl.value, ms.value
+
+    def mean_drag(self):
+        fx, fy = np.zeros(self.n), np.zeros(self.n)
+        self._check(self._L.imb_batch_mean_drag(self.h, _d(fx), _d(fy)))
+        return fx, fy
+
+    def populations(self, domain):
+        ny, nx = self.shapes[domain]
+        out = np.zeros((9, ny, nx))
+        self._check(self._L.imb_batch_get_populations(self.h, int(domain), _d(out)))
+        return out
+
+    def cells(self):
+        return int(self._L.imb_batch_cells(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.imb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

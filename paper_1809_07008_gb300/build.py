@@ -28,6 +28,7 @@ UNITS = {
     "imb_api.cu": [],
     "imb_noalloc.cu": [],
     "imb_adjoint.cu": [],
+    "imb_batch.cu": [],
 }
 
 

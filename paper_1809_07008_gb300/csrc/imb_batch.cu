@@ -1,0 +1,473 @@
+// imb_batch.cu -- many independent small periodic domains stepped together.
+//
+// A sweep over resolution, solid fraction, relaxation time and driving force (the paper's
+// parameter studies, Sec. 3) is a set of independent lattices.  Each is periodic in x and y,
+// driven by a body force (Guo forcing, as in the single-lattice path), and holds fixed disks
+// whose summed solid ratio E per cell (exact overlap area, Sec. 2.3) is computed once.  One
+// launch advances every domain by one step: its warps take rows of the domains in turn (a
+// row is a work item; a warp finds the row's domain by binary search in the domains' first
+// items), pull with the periodic wrap of their domain (Eq. 1), collide with the blend of
+// Eq. 13 (B from Eq. 14, u_s = 0 for disks at rest) and add the row's drag B (j - F) (Eq. 15)
+// to the domain's accumulator.  Steps run as a replayed CUDA graph of two launches (A -> B,
+// B -> A); the block size and the cells per lane are chosen by timing the candidates on the
+// batch itself.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/imblbm.h"
+#include "imb_device.cuh"
+#include "imb_kernels.h"
+#include "imb_node.cuh"
+
+namespace imb {
+
+struct BatchDomain {
+    int nx, ny;
+    int item0;          // first work item (row) of the domain
+    int pad;
+    size_t off;         // element offset of the domain's plane 0 in the population buffers
+    size_t plane;       // nx * ny
+    size_t e_off;       // offset of the domain's solid ratios (cells)
+    float tau, omega0, Fx, Fy;
+};
+
+template <typename S, int CPL>
+__global__ void k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
+                             int ndom, int nitems, const float *__restrict__ E, double *drag, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    bool unstable = false;
+    for (int it = gw; it < nitems; it += nw) {
+        int lo = 0, hi = ndom - 1;   // the domain of this row
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (dom[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchDomain D = dom[lo];
+        const int y = it - D.item0, nx = D.nx, ny = D.ny;
+        LatticeArgs a;
+        a.plane = D.plane;
+        a.tau = D.tau;
+        a.omega0 = D.omega0;
+        a.smag_coef = 0.0f;
+        a.Fx = D.Fx;
+        a.Fy = D.Fy;
+        const bool forced = D.Fx != 0.0f || D.Fy != 0.0f;
+        const S *src = fin + D.off;
+        S *dst = fout + D.off;
+        const float *Ed = E + D.e_off;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        float fx_acc = 0.0f, fy_acc = 0.0f;
+        for (int x0 = 0; x0 < nx; x0 += 32 * CPL) {
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const int x = x0 + 32 * k + lane;
+                if (x >= nx) continue;
+                const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+                float d[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {   // pull from x - c_q with the periodic wrap
+                    const int xs = cx_of(q) == 0 ? x : (cx_of(q) == 1 ? xm : xp);
+                    const int ys = cy_of(q) == 0 ? y : (cy_of(q) == 1 ? ym : yp);
+                    d[q] = Store<S>::ld(src + (size_t)q * D.plane + (size_t)ys * nx + xs);
+                }
+                NodeState c;
+                node_state(d, a, forced, false, c);
+                if (!(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+                const float e = Ed[(size_t)y * nx + x];
+                SolidMoments sm = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                if (e > 0.0f) {
+                    const float ec = fminf(e, 1.0f), tm = c.te - 0.5f;
+                    sm.B = __fdividef(ec * tm, (1.0f - ec) + tm);   // Eq. 14
+                    fx_acc += sm.B * (c.jx - D.Fx);                // Eq. 15 with u_s = 0
+                    fy_acc += sm.B * (c.jy - D.Fy);
+                }
+                node_collide_store(d, c, sm, dst + (size_t)y * nx + x, a, forced);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx_acc += __shfl_xor_sync(0xffffffffu, fx_acc, o);
+            fy_acc += __shfl_xor_sync(0xffffffffu, fy_acc, o);
+        }
+        if (lane == 0 && (fx_acc != 0.0f || fy_acc != 0.0f)) {
+            atomicAdd(&drag[2 * lo], (double)fx_acc);
+            atomicAdd(&drag[2 * lo + 1], (double)fy_acc);
+        }
+    }
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) set_err(err, ERR_UNSTABLE);
+}
+
+// summed solid ratio: one thread per (disk, cell of its bounding box)
+__global__ void k_batch_solid(const BatchDomain *__restrict__ dom, const int *__restrict__ disk_dom,
+                              const double *__restrict__ xy, const double *__restrict__ r, int ndisk, int span,
+                              float *E) {
+    const int w = 2 * span + 1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ndisk * w * w) return;
+    const int j = (int)(t / (w * w)), cell = (int)(t % (w * w));
+    const BatchDomain D = dom[disk_dom[j]];
+    const double cx = xy[2 * j], cy = xy[2 * j + 1];
+    const int ci = (int)floor(cx), cj = (int)floor(cy);
+    const float fx = (float)(cx - ci), fy = (float)(cy - cj), rf = (float)r[j];
+    const int di = cell % w - span, dk = cell / w - span;
+    const float lox = __fsub_rn((float)di, fx), loy = __fsub_rn((float)dk, fy);
+    if (!covers(lox, loy, rf)) return;
+    const int i = ((ci + di) % D.nx + D.nx) % D.nx, k = ((cj + dk) % D.ny + D.ny) % D.ny;
+    atomicAdd(&E[D.e_off + (size_t)k * D.nx + i], cell_disk_area(lox, loy, rf));
+}
+
+// f(x, t) of one domain (the pull of its post-collision field), as FP64 f = w + (f - w)
+template <typename S>
+__global__ void k_batch_gather(const S *__restrict__ fin, const BatchDomain *__restrict__ dom, int d,
+                               double *out) {
+    const BatchDomain D = dom[d];
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.plane) return;
+    const int x = (int)(c % D.nx), y = (int)(c / D.nx);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int xs = (x - cx_of(q) + D.nx) % D.nx, ys = (y - cy_of(q) + D.ny) % D.ny;
+        out[(size_t)q * D.plane + c] =
+            (double)w_of(q) + (double)Store<S>::ld(fin + D.off + (size_t)q * D.plane + (size_t)ys * D.nx + xs);
+    }
+}
+
+}  // namespace imb
+
+using namespace imb;
+
+struct imb_batch {
+    int device = 0, storage = 0, elem = 4, ndom = 0, nitems = 0, ndisk = 0;
+    size_t total = 0;          // elements per population buffer
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;               // buffer holding the current post-collision field
+    BatchDomain *dom = nullptr;
+    std::vector<BatchDomain> hdom;
+    float *E = nullptr;
+    double *drag = nullptr;
+    unsigned *err = nullptr;
+    long long steps_run = 0;
+    cudaStream_t stream = nullptr;
+    int block = 256, cpl = 1, grid = 0;
+    bool grid_only = false;    // launch_step only sizes the grid
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // two steps starting from buffer 0 / 1
+    std::string last_error;
+};
+
+namespace {
+
+int bfail(imb_batch *b, int code, const std::string &msg) {
+    if (b) b->last_error = msg;
+    return code;
+}
+
+#define BCK(call, what)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? IMB_E_NOMEM : IMB_E_CUDA,       \
+                         std::string(what) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+template <typename F>
+cudaError_t by_storage_b(int storage, F &&fn) {
+    switch (storage) {
+    case IMB_STORE_FP32: return fn((float *)nullptr);
+    case IMB_STORE_FP16: return fn((__half *)nullptr);
+    case IMB_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S, int CPL>
+cudaError_t launch_step_t(imb_batch *b, int from) {
+    auto k = k_batch_step<S, CPL>;
+    if (b->grid == 0) {   // resident blocks of this configuration (set before any capture)
+        int per = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, b->block, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        const int need = (b->nitems * 32 + b->block - 1) / b->block;
+        b->grid = std::max(1, std::min(need, std::max(per, 1) * sms));
+        if (b->grid_only) return cudaSuccess;
+    }
+    if (b->grid_only) return cudaSuccess;
+    k<<<b->grid, b->block, 0, b->stream>>>((const S *)b->buf[from], (S *)b->buf[from ^ 1], b->dom, b->ndom,
+                                           b->nitems, b->E, b->drag, b->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(imb_batch *b, int from) {
+    return by_storage_b(b->storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return b->cpl == 2 ? launch_step_t<S, 2>(b, from) : launch_step_t<S, 1>(b, from);
+    });
+}
+
+void drop_graphs(imb_batch *b) {
+    for (auto &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+int batch_wait(imb_batch *b) {
+    BCK(cudaStreamSynchronize(b->stream), "batch stream");
+    unsigned bits = 0;
+    BCK(cudaMemcpy(&bits, b->err, sizeof(bits), cudaMemcpyDeviceToHost), "error flags");
+    if (bits & ERR_UNSTABLE) {
+        cudaMemset(b->err, 0, sizeof(unsigned));
+        return bfail(b, IMB_E_UNSTABLE, "NaN or |u| >= 0.3 in a batch domain (Mach guard)");
+    }
+    return IMB_OK;
+}
+
+}  // namespace
+
+extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, const int *ny, const double *tau,
+                                const double *Fx, const double *Fy, const int *n_disks, const double *disk_xy,
+                                const double *disk_r, int storage) {
+    if (!out) return IMB_E_INVALID_ARG;
+    *out = nullptr;
+    if (n_domains < 1 || !nx || !ny || !tau || !Fx || !Fy || !n_disks || storage < 0 || storage > 2)
+        return IMB_E_INVALID_ARG;
+    auto *b = new imb_batch();
+    b->storage = storage;
+    b->elem = storage == IMB_STORE_FP32 ? 4 : 2;
+    b->ndom = n_domains;
+    double rmax = 0.0;
+    size_t cells = 0;
+    int items = 0, ndisk = 0;
+    for (int d = 0; d < n_domains; ++d) {
+        if (nx[d] < 3 || ny[d] < 3 || !(tau[d] > 0.5) || n_disks[d] < 0) {
+            delete b;
+            return IMB_E_INVALID_ARG;
+        }
+        BatchDomain D{};
+        D.nx = nx[d];
+        D.ny = ny[d];
+        D.item0 = items;
+        D.plane = (size_t)nx[d] * ny[d];
+        D.off = 9 * cells;
+        D.e_off = cells;
+        D.tau = (float)tau[d];
+        D.omega0 = (float)(1.0 / tau[d]);
+        D.Fx = (float)Fx[d];
+        D.Fy = (float)Fy[d];
+        b->hdom.push_back(D);
+        cells += D.plane;
+        items += ny[d];
+        ndisk += n_disks[d];
+    }
+    if (ndisk > 0 && (!disk_xy || !disk_r)) {
+        delete b;
+        return IMB_E_INVALID_ARG;
+    }
+    std::vector<int> ddom(std::max(ndisk, 1));
+    for (int d = 0, j = 0; d < n_domains; ++d)
+        for (int k = 0; k < n_disks[d]; ++k, ++j) {
+            ddom[j] = d;
+            const double x = disk_xy[2 * j], y = disk_xy[2 * j + 1], r = disk_r[j];
+            if (!(r > 0.0) || !(x >= 0.0 && x < nx[d] && y >= 0.0 && y < ny[d]) || 2.0 * r + 4.0 > std::min(nx[d], ny[d])) {
+                delete b;
+                return IMB_E_INVALID_ARG;
+            }
+            rmax = std::max(rmax, r);
+        }
+    b->nitems = items;
+    b->ndisk = ndisk;
+    b->total = 9 * cells;
+    cudaGetDevice(&b->device);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&b->buf[0], b->total * b->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&b->buf[1], b->total * b->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&b->dom, sizeof(BatchDomain) * n_domains)) != cudaSuccess ||
+        (e = cudaMalloc(&b->E, sizeof(float) * std::max(cells, (size_t)1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->drag, sizeof(double) * 2 * n_domains)) != cudaSuccess ||
+        (e = cudaMalloc(&b->err, sizeof(unsigned))) != cudaSuccess) {
+        *out = b;
+        return bfail(b, e == cudaErrorMemoryAllocation ? IMB_E_NOMEM : IMB_E_CUDA, "batch buffers");
+    }
+    *out = b;
+    // fluid at rest with rho = 1: f = w, i.e. zero shifted populations
+    BCK(cudaMemsetAsync(b->buf[0], 0, b->total * b->elem, b->stream), "clear");
+    BCK(cudaMemsetAsync(b->buf[1], 0, b->total * b->elem, b->stream), "clear");
+    BCK(cudaMemsetAsync(b->E, 0, sizeof(float) * cells, b->stream), "clear");
+    BCK(cudaMemsetAsync(b->drag, 0, sizeof(double) * 2 * n_domains, b->stream), "clear");
+    BCK(cudaMemsetAsync(b->err, 0, sizeof(unsigned), b->stream), "clear");
+    BCK(cudaMemcpyAsync(b->dom, b->hdom.data(), sizeof(BatchDomain) * n_domains, cudaMemcpyHostToDevice, b->stream),
+        "domains");
+    if (ndisk > 0) {
+        int *d_dd = nullptr;
+        double *d_xy = nullptr, *d_r = nullptr;
+        BCK(cudaMalloc(&d_dd, sizeof(int) * ndisk), "disks");
+        BCK(cudaMalloc(&d_xy, sizeof(double) * 2 * ndisk), "disks");
+        BCK(cudaMalloc(&d_r, sizeof(double) * ndisk), "disks");
+        BCK(cudaMemcpyAsync(d_dd, ddom.data(), sizeof(int) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        BCK(cudaMemcpyAsync(d_xy, disk_xy, sizeof(double) * 2 * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        BCK(cudaMemcpyAsync(d_r, disk_r, sizeof(double) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;
+        const long long nthreads = (long long)ndisk * w * w;
+        k_batch_solid<<<(unsigned)((nthreads + 127) / 128), 128, 0, b->stream>>>(b->dom, d_dd, d_xy, d_r, ndisk,
+                                                                               span, b->E);
+        BCK(cudaGetLastError(), "solid ratio");
+        BCK(cudaStreamSynchronize(b->stream), "solid ratio");
+        cudaFree(d_dd);
+        cudaFree(d_xy);
+        cudaFree(d_r);
+    }
+    return batch_wait(b);
+}
+
+extern "C" int imb_batch_run(imb_batch *b, int steps) {
+    if (!b) return IMB_E_INVALID_ARG;
+    if (steps < 0) return bfail(b, IMB_E_INVALID_ARG, "steps must be >= 0");
+    BCK(cudaSetDevice(b->device), "cudaSetDevice");
+    for (int s = 0; s + 1 < steps; s += 2) {
+        cudaGraphExec_t &g = b->graph[b->cur];
+        if (!g) {   // two steps from the current buffer, captured once
+            if (b->grid == 0) {
+                b->grid_only = true;
+                launch_step(b, b->cur);
+                b->grid_only = false;
+            }
+            cudaGraph_t gr;
+            BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "capture");
+            cudaError_t e1 = launch_step(b, b->cur);
+            cudaError_t e2 = launch_step(b, b->cur ^ 1);
+            BCK(cudaStreamEndCapture(b->stream, &gr), "capture");
+            BCK(e1, "capture launch");
+            BCK(e2, "capture launch");
+            BCK(cudaGraphInstantiate(&g, gr, 0), "graph");
+            cudaGraphDestroy(gr);
+        }
+        BCK(cudaGraphLaunch(g, b->stream), "graph launch");
+    }
+    if (steps % 2) {
+        BCK(launch_step(b, b->cur), "batch step");
+        b->cur ^= 1;
+    }
+    b->steps_run += steps;
+    return batch_wait(b);
+}
+
+extern "C" int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block, int *cells_per_lane,
+                                  double *best_ms_per_step) {
+    if (!b || steps_per_trial < 1) return IMB_E_INVALID_ARG;
+    BCK(cudaSetDevice(b->device), "cudaSetDevice");
+    // work on a copy of the state, put it back afterwards
+    void *save = nullptr;
+    BCK(cudaMalloc(&save, b->total * b->elem), "autotune copy");
+    BCK(cudaMemcpyAsync(save, b->buf[b->cur], b->total * b->elem, cudaMemcpyDeviceToDevice, b->stream), "copy");
+    double *dsave = nullptr;
+    BCK(cudaMalloc(&dsave, sizeof(double) * 2 * b->ndom), "autotune copy");
+    BCK(cudaMemcpyAsync(dsave, b->drag, sizeof(double) * 2 * b->ndom, cudaMemcpyDeviceToDevice, b->stream), "copy");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks[3] = {128, 256, 512}, cpls[2] = {1, 2};
+    float best = 1e30f;
+    int bb = b->block, bc = b->cpl;
+    for (int bl : blocks)
+        for (int cp : cpls) {
+            b->block = bl;
+            b->cpl = cp;
+            b->grid = 0;
+            int from = b->cur;
+            BCK(launch_step(b, from), "trial");   // warm-up
+            from ^= 1;
+            cudaEventRecord(e0, b->stream);
+            for (int s = 0; s < steps_per_trial; ++s, from ^= 1) BCK(launch_step(b, from), "trial");
+            cudaEventRecord(e1, b->stream);
+            BCK(cudaEventSynchronize(e1), "trial");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bb = bl;
+                bc = cp;
+            }
+            BCK(cudaMemcpyAsync(b->buf[b->cur], save, b->total * b->elem, cudaMemcpyDeviceToDevice, b->stream),
+                "restore");
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->block = bb;
+    b->cpl = bc;
+    b->grid = 0;
+    drop_graphs(b);
+    BCK(cudaMemcpyAsync(b->drag, dsave, sizeof(double) * 2 * b->ndom, cudaMemcpyDeviceToDevice, b->stream), "copy");
+    BCK(cudaStreamSynchronize(b->stream), "autotune");
+    cudaFree(save);
+    cudaFree(dsave);
+    BCK(cudaMemset(b->err, 0, sizeof(unsigned)), "clear");
+    if (block) *block = bb;
+    if (cells_per_lane) *cells_per_lane = bc;
+    if (best_ms_per_step) *best_ms_per_step = best / steps_per_trial;
+    return IMB_OK;
+}
+
+extern "C" int imb_batch_mean_drag(imb_batch *b, double *Fx_mean, double *Fy_mean) {
+    if (!b || !Fx_mean || !Fy_mean) return IMB_E_INVALID_ARG;
+    int rc = batch_wait(b);
+    if (rc) return rc;
+    std::vector<double> h(2 * (size_t)b->ndom);
+    BCK(cudaMemcpy(h.data(), b->drag, sizeof(double) * h.size(), cudaMemcpyDeviceToHost), "drag");
+    const double n = b->steps_run > 0 ? (double)b->steps_run : 1.0;
+    for (int d = 0; d < b->ndom; ++d) {
+        Fx_mean[d] = h[2 * d] / n;
+        Fy_mean[d] = h[2 * d + 1] / n;
+    }
+    return IMB_OK;
+}
+
+extern "C" int imb_batch_get_populations(imb_batch *b, int domain, double *f) {
+    if (!b || !f || domain < 0 || domain >= b->ndom) return IMB_E_INVALID_ARG;
+    int rc = batch_wait(b);
+    if (rc) return rc;
+    const size_t n = 9 * b->hdom[domain].plane;
+    double *t = nullptr;
+    BCK(cudaMalloc(&t, sizeof(double) * n), "readback buffer");
+    cudaError_t e = by_storage_b(b->storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        k_batch_gather<S><<<(unsigned)((b->hdom[domain].plane + 255) / 256), 256, 0, b->stream>>>(
+            (const S *)b->buf[b->cur], b->dom, domain, t);
+        return cudaGetLastError();
+    });
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, t, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(t);
+    BCK(e, "populations");
+    return IMB_OK;
+}
+
+extern "C" long long imb_batch_cells(const imb_batch *b) {
+    return b ? (long long)(b->total / 9) : 0;
+}
+
+extern "C" const char *imb_batch_last_error(const imb_batch *b) {
+    return b ? b->last_error.c_str() : "null batch";
+}
+
+extern "C" void imb_batch_destroy(imb_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->dom);
+    cudaFree(b->E);
+    cudaFree(b->drag);
+    cudaFree(b->err);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}

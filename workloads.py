@@ -254,6 +254,63 @@ def c4(steps=4000, nx=512, ny=256, n_side=4, d=20.0, seed=1809, u_in=0.02, tau=0
                     x=np.array(xs), v=np.zeros((n, 2)), omega=np.zeros(n), r=np.full(n, d / 2.0))
 
 
+def rsa_periodic(nx, ny, n, r, seed, gap=1.0, attempts_per_disk=40):
+    """Up to ``n`` disks of radius ``r`` by random sequential addition in a box periodic in x and
+    y, each at least 2 r + gap from every other (minimum image); stops after
+    ``attempts_per_disk * n`` attempts (dense arrays jam below the requested count)."""
+    rng = SplitMix64(seed)
+    pts = np.zeros((0, 2))
+    dmin2 = (2.0 * r + gap) ** 2
+    for _ in range(attempts_per_disk * n):
+        if len(pts) == n:
+            break
+        c = np.array([rng.uniform_range(0.0, float(nx)), rng.uniform_range(0.0, float(ny))])
+        if len(pts):
+            d = pts - c
+            d[:, 0] -= nx * np.round(d[:, 0] / nx)
+            d[:, 1] -= ny * np.round(d[:, 1] / ny)
+            if ((d * d).sum(axis=1) < dmin2).any():
+                continue
+        pts = np.vstack([pts, c])
+    return pts
+
+
+def c5_domain(k, nx, ny, d, phi, tau, Re, seed):
+    """One domain of the batched sweep: periodic box with fixed disks of diameter d at solid
+    fraction ~phi, driven along x by the body force that a Kozeny-Carman permeability
+    k = d^2 (1 - phi)^3 / (180 phi^2) turns into the mean speed U = Re nu / d (U capped at
+    0.03 for the Mach number)."""
+    r = d / 2.0
+    n = max(1, int(round(phi * nx * ny / (np.pi * r * r))))
+    x = rsa_periodic(nx, ny, n, r, seed)
+    phi_got = len(x) * np.pi * r * r / (nx * ny)
+    nu = (tau - 0.5) / 3.0
+    U = min(Re * nu / d, 0.03)
+    perm = d * d * (1.0 - phi_got) ** 3 / (180.0 * phi_got * phi_got)
+    F = nu * U / perm
+    m = len(x)
+    return Workload(name=f"c5_{k}_{nx}x{ny}", nx=nx, ny=ny, tau=tau, C_smag=0.0, bc_x=BC_PERIODIC,
+                    bc_y=BC_PERIODIC, force=(F, 0.0), dem_on=0, x=x, v=np.zeros((m, 2)), omega=np.zeros(m),
+                    r=np.full(m, r))
+
+
+def c5(n_domains=256, seed=1809):
+    """Batched sweep: ``n_domains`` independent periodic domains, sizes 128..512 x 128..256 (in
+    steps of 32), disk diameter 10..30, solid fraction 0.1..0.5, tau 0.51..1.0, Re 0.1..100
+    (log-uniform), all drawn from one seeded generator."""
+    rng = SplitMix64(seed)
+    out = []
+    for k in range(n_domains):
+        nx = 128 + 32 * int(rng.uniform() * 13)
+        ny = 128 + 32 * int(rng.uniform() * 5)
+        d = rng.uniform_range(10.0, 30.0)
+        phi = rng.uniform_range(0.1, 0.5)
+        tau = rng.uniform_range(0.51, 1.0)
+        Re = 10.0 ** rng.uniform_range(-1.0, 2.0)
+        out.append(c5_domain(k, nx, ny, d, phi, tau, Re, seed * 1000 + k))
+    return out
+
+
 def poiseuille(H=32, nx=4, tau=0.6, g=1.0e-6, steps=20000) -> Workload:
     """Body-force driven channel, periodic in x, walls at y = 0 and y = H, no particles."""
     return Workload(name=f"poiseuille_H{H}", nx=nx, ny=H, tau=tau, bc_x=BC_PERIODIC, bc_y=BC_WALL,
