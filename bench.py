@@ -18,7 +18,8 @@ duration against the measured HBM copy bandwidth; ``cpu_baseline`` = the FP64
 oracle on a bounded sample, timed on this host; ``storage_variants`` = the same
 workload with FP16 / BF16 population storage; ``drag_gradient`` = one reverse-mode
 gradient of the time-averaged drag on the 512 x 256 channel with 16 fixed disks
-over 4000 steps (imb_drag_gradient), timed on the host clock.
+over 4000 steps (imb_drag_gradient), timed on the host clock; ``batched_sweep`` =
+256 independent periodic domains with fixed disks (FP16, 5000 steps, imb_batch_*).
 
   python bench.py [--gpus N --steps K --warmup W] [--workload c3|c2|c1]
                   [--storage fp32|fp16|bf16] [--impl reference]
@@ -60,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the drag-gradient line (512 x 256 channel, 16 fixed disks, 4000 steps)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the batched-sweep line (256 periodic domains, FP16, 5000 steps)")
+    ap.add_argument("--sweep-steps", type=int, default=5000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--nx", type=int, default=None, help="smaller lattice at the same disk density")
     ap.add_argument("--ny", type=int, default=None)
@@ -254,6 +258,31 @@ def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256):
             "dJ_dtau": g_tau, "dJ_dx_max": float(np.abs(g_x).max())}
 
 
+def time_batched_sweep(imb, steps=5000, n_domains=256, storage="fp16"):
+    """The batched sweep: ``n_domains`` periodic domains (128..512 x 128..256, fixed disks,
+    body-force driven) in FP16 storage, launch shape tuned on the batch, then ``steps`` steps
+    timed with CUDA events on the batch's own stream (graph replays)."""
+    doms = W.c5(n_domains)
+    b = imb.Batch(doms, storage=storage)
+    blk, cpl, _ = b.autotune(steps_per_trial=20)
+    b.run(4)   # warm-up: graph capture
+    cells = b.cells()
+    t0 = time.perf_counter()   # imb_batch_run waits for its stream before returning
+    b.run(steps)
+    dt = time.perf_counter() - t0
+    fx, _ = b.mean_drag()
+    b.close()
+    bpc = 36.0 if storage != "fp32" else 72.0
+    peak, kind = measured_hbm_peak()
+    gbs = bpc * cells * steps / dt / 1e9
+    return {"domains": n_domains, "cells": cells, "storage": storage, "steps": steps, "seconds": round(dt, 4),
+            "mlups": round(cells * steps / dt / 1e6, 1), "ms_per_step": round(dt / steps * 1e3, 4),
+            "block": blk, "cells_per_lane": cpl, "bytes_per_cell": bpc, "achieved_gbs": round(gbs, 1),
+            "frac": round(gbs / peak, 4), "peak_source": kind,
+            "mean_drag_range": [float(fx.min()), float(fx.max())],
+            "note": "host clock around imb_batch_run (graph replays, one sync at the end)"}
+
+
 def oracle_sample_workload():
     # bounded sample: the 512 x 512 subdomain of the suspension at the same disk density
     return W.c3sub(steps=0)
@@ -403,6 +432,9 @@ def run_gpu(args):
     gradient = None
     if not args.no_gradient and rank == 0:
         gradient = time_drag_gradient(imb)
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = time_batched_sweep(imb, args.sweep_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -424,6 +456,8 @@ def run_gpu(args):
             line["storage_variants"] = variants
         if gradient:
             line["drag_gradient"] = gradient
+        if sweep:
+            line["batched_sweep"] = sweep
         print(json.dumps(line), flush=True)
 
 

@@ -165,20 +165,20 @@ int imb_drag_gradient(imb_ctx *ctx, int T, int checkpoint_every, double *J, doub
  * with the collision of Eq. 13 (B of Eq. 14 from the summed exact overlap area of
  * each cell, u_s = 0) and adds each domain's drag (Eq. 15, summed over its disks)
  * to an accumulator.  The library owns the batch; host arrays are copied.
- * Returns IMB_E_INVALID_ARG for a bad size, tau <= 0.5, a disk outside its domain
+ * Returns IMB_E_INVALID_ARG for a bad size, tau <= 0.5, C_smag < 0, a disk outside its domain
  * or wider than it minus four cells; IMB_E_NOMEM / IMB_E_CUDA on device failures
  * (then *out holds a batch to destroy, with the message in imb_batch_last_error). */
 typedef struct imb_batch imb_batch;
 int imb_batch_create(imb_batch **out, int n_domains, const int *nx, const int *ny, const double *tau,
-                     const double *Fx, const double *Fy, const int *n_disks, const double *disk_xy,
-                     const double *disk_r, int storage);
+                     const double *C_smag, const double *Fx, const double *Fy, const int *n_disks,
+                     const double *disk_xy, const double *disk_r, int storage);
 
 /* Advance every domain by `steps` steps (two steps at a time as a replayed CUDA graph
  * of two launches) and wait; IMB_E_UNSTABLE when a node went NaN or |u| >= 0.3. */
 int imb_batch_run(imb_batch *b, int steps);
 
 /* Time `steps_per_trial` steps of each launch shape (blocks of 128, 256 or
- * 512 threads; one or two cells per lane along a row) on the batch itself, keep the
+ * 512 threads, where the kernel can launch them; one or two cells per lane along a row) on the batch itself, keep the
  * fastest, and put the state and the drag accumulators back as they were.  Outputs
  * (each may be NULL): the chosen block size, cells per lane and its ms per step. */
 int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block, int *cells_per_lane,

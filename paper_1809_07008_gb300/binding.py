@@ -116,7 +116,7 @@ def load(build_if_missing: bool = True):
     L.imb_destroy.restype = None
     L.imb_bin_particles_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]
     L.imb_drag_gradient.argtypes = [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
-    L.imb_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _ip, _ip, _dp, _dp, _dp, _ip, _dp, _dp, C.c_int]
+    L.imb_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _dp, _dp, C.c_int]
     L.imb_batch_run.argtypes = [_vp, C.c_int]
     L.imb_batch_autotune.argtypes = [_vp, C.c_int, _ip, _ip, _dp]
     L.imb_batch_mean_drag.argtypes = [_vp, _dp, _dp]
@@ -316,7 +316,8 @@ class Batch:
     """Many independent periodic domains with fixed disks, stepped together (imb_batch_*).
 
     ``domains`` is a sequence of workloads (``workloads.Workload``, periodic in x and y, DEM
-    off, disks at rest); their sizes, tau, body force and disks define the batch."""
+    off, disks at rest); their sizes, tau, Smagorinsky constant, body force and disks define
+    the batch."""
 
     def __init__(self, domains, storage="fp16"):
         self._L = load()
@@ -324,6 +325,7 @@ class Batch:
         nx = np.array([w.nx for w in domains], dtype=np.int32)
         ny = np.array([w.ny for w in domains], dtype=np.int32)
         tau = np.array([w.tau for w in domains], dtype=np.float64)
+        csm = np.array([w.C_smag for w in domains], dtype=np.float64)
         fx = np.array([w.force[0] for w in domains], dtype=np.float64)
         fy = np.array([w.force[1] for w in domains], dtype=np.float64)
         nd = np.array([w.n_particles for w in domains], dtype=np.int32)
@@ -336,7 +338,7 @@ class Batch:
         st = STORAGE_NAMES[storage] if isinstance(storage, str) else storage
         h = _vp()
         rc = self._L.imb_batch_create(C.byref(h), n, nx.ctypes.data_as(_ip), ny.ctypes.data_as(_ip), _d(tau),
-                                      _d(fx), _d(fy), nd.ctypes.data_as(_ip), _d(xy), _d(r), st)
+                                      _d(csm), _d(fx), _d(fy), nd.ctypes.data_as(_ip), _d(xy), _d(r), st)
         self.h = h
         self.n = n
         self.shapes = [(int(a), int(b)) for a, b in zip(ny, nx)]

@@ -3,7 +3,8 @@
 // A sweep over resolution, solid fraction, relaxation time and driving force (the paper's
 // parameter studies, Sec. 3) is a set of independent lattices.  Each is periodic in x and y,
 // driven by a body force (Guo forcing, as in the single-lattice path), and holds fixed disks
-// whose summed solid ratio E per cell (exact overlap area, Sec. 2.3) is computed once.  One
+// whose summed solid ratio E per cell (exact overlap area, Sec. 2.3) is computed once; its
+// relaxation time may carry the Smagorinsky closure of the single-lattice path.  One
 // launch advances every domain by one step: its warps take rows of the domains in turn (a
 // row is a work item; a warp finds the row's domain by binary search in the domains' first
 // items), pull with the periodic wrap of their domain (Eq. 1), collide with the blend of
@@ -33,6 +34,8 @@ struct BatchDomain {
     size_t plane;       // nx * ny
     size_t e_off;       // offset of the domain's solid ratios (cells)
     float tau, omega0, Fx, Fy;
+    float smag_coef;    // 18 sqrt(2) C^2 of the Smagorinsky closure (0: plain BGK)
+    float pad2;
 };
 
 template <typename S, int CPL>
@@ -55,7 +58,7 @@ __global__ void k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, co
         a.plane = D.plane;
         a.tau = D.tau;
         a.omega0 = D.omega0;
-        a.smag_coef = 0.0f;
+        a.smag_coef = D.smag_coef;
         a.Fx = D.Fx;
         a.Fy = D.Fy;
         const bool forced = D.Fx != 0.0f || D.Fy != 0.0f;
@@ -78,7 +81,7 @@ __global__ void k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, co
                     d[q] = Store<S>::ld(src + (size_t)q * D.plane + (size_t)ys * nx + xs);
                 }
                 NodeState c;
-                node_state(d, a, forced, false, c);
+                node_state(d, a, forced, D.smag_coef > 0.0f, c);
                 if (!(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
                 const float e = Ed[(size_t)y * nx + x];
                 SolidMoments sm = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -203,6 +206,20 @@ cudaError_t launch_step_t(imb_batch *b, int from) {
     return cudaGetLastError();
 }
 
+// largest block the kernel of this storage and cells-per-lane can launch (its registers)
+int max_block(imb_batch *b) {
+    int m = 0;
+    by_storage_b(b->storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        cudaFuncAttributes fa{};
+        cudaError_t e = b->cpl == 2 ? cudaFuncGetAttributes(&fa, k_batch_step<S, 2>)
+                                    : cudaFuncGetAttributes(&fa, k_batch_step<S, 1>);
+        m = e == cudaSuccess ? fa.maxThreadsPerBlock : 0;
+        return e;
+    });
+    return m;
+}
+
 cudaError_t launch_step(imb_batch *b, int from) {
     return by_storage_b(b->storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
@@ -232,11 +249,11 @@ int batch_wait(imb_batch *b) {
 }  // namespace
 
 extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, const int *ny, const double *tau,
-                                const double *Fx, const double *Fy, const int *n_disks, const double *disk_xy,
-                                const double *disk_r, int storage) {
+                                const double *C_smag, const double *Fx, const double *Fy, const int *n_disks,
+                                const double *disk_xy, const double *disk_r, int storage) {
     if (!out) return IMB_E_INVALID_ARG;
     *out = nullptr;
-    if (n_domains < 1 || !nx || !ny || !tau || !Fx || !Fy || !n_disks || storage < 0 || storage > 2)
+    if (n_domains < 1 || !nx || !ny || !tau || !C_smag || !Fx || !Fy || !n_disks || storage < 0 || storage > 2)
         return IMB_E_INVALID_ARG;
     auto *b = new imb_batch();
     b->storage = storage;
@@ -246,7 +263,7 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
     size_t cells = 0;
     int items = 0, ndisk = 0;
     for (int d = 0; d < n_domains; ++d) {
-        if (nx[d] < 3 || ny[d] < 3 || !(tau[d] > 0.5) || n_disks[d] < 0) {
+        if (nx[d] < 3 || ny[d] < 3 || !(tau[d] > 0.5) || !(C_smag[d] >= 0.0) || n_disks[d] < 0) {
             delete b;
             return IMB_E_INVALID_ARG;
         }
@@ -261,6 +278,7 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
         D.omega0 = (float)(1.0 / tau[d]);
         D.Fx = (float)Fx[d];
         D.Fy = (float)Fy[d];
+        D.smag_coef = (float)(18.0 * std::sqrt(2.0) * C_smag[d] * C_smag[d]);
         b->hdom.push_back(D);
         cells += D.plane;
         items += ny[d];
@@ -381,6 +399,7 @@ extern "C" int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block,
             b->block = bl;
             b->cpl = cp;
             b->grid = 0;
+            if (max_block(b) < bl) continue;   // too many registers for this block size
             int from = b->cur;
             BCK(launch_step(b, from), "trial");   // warm-up
             from ^= 1;

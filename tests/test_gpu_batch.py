@@ -1,8 +1,8 @@
 """Batched sweep of independent periodic domains (imb_batch_*) against the FP64 oracle run on
 each domain by itself.
 
-* Three domains of different sizes, disk diameters, solid fractions, relaxation times and body
-  forces, 300 steps from rest: populations of every domain (FP32 storage: 1e-6; FP16: 2e-4,
+* Three domains of different sizes, disk diameters, solid fractions, relaxation times, body
+  forces and Smagorinsky constants (0 and 0.1), 300 steps from rest: populations of every domain (FP32 storage: 1e-6; FP16: 2e-4,
   the rounding of the stored deviation f - w accumulated over the steps) and the per-domain
   mean drag (FP32: 1e-4 of the drag scale; FP16: 1 %, the storage bar the single-lattice tests
   use).
@@ -26,8 +26,8 @@ def imb():
 
 
 def _domains():
-    return [W.c5_domain(0, 96, 64, 12.0, 0.2, 0.7, 1.0, 11),
-            W.c5_domain(1, 128, 96, 16.0, 0.3, 0.55, 10.0, 12),
+    return [W.c5_domain(0, 96, 64, 12.0, 0.2, 0.7, 1.0, 11, C_smag=0.0),
+            W.c5_domain(1, 128, 96, 16.0, 0.3, 0.52, 30.0, 12),
             W.c5_domain(2, 64, 64, 10.0, 0.12, 1.0, 0.5, 13)]
 
 
