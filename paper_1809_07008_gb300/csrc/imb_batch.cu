@@ -39,7 +39,7 @@ struct BatchDomain {
 };
 
 template <typename S, int CPL>
-__global__ void k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
+__global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
                              int ndom, int nitems, const float *__restrict__ E, double *drag, unsigned *err) {
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
