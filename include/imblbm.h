@@ -158,7 +158,8 @@ int imb_drag_gradient(imb_ctx *ctx, int T, int checkpoint_every, double *J, doub
 /* ---- many independent domains (the parameter sweeps of Sec. 3 as one batch) ----
  * Each domain d is an nx[d] x ny[d] lattice, periodic in x and y, at rest at t = 0
  * (rho = 1), driven by the body force (Fx[d], Fy[d]) (Guo forcing), with relaxation
- * time tau[d] (plain BGK) and n_disks[d] disks held at rest: their centres are
+ * time tau[d] and Smagorinsky constant C_smag[d] (0: plain BGK; the closure of the
+ * single-lattice path), and n_disks[d] disks held at rest: their centres are
  * disk_xy[2j], disk_xy[2j+1] in the domain's cell units and radii disk_r[j], the
  * disks of domain 0 first, then those of domain 1, and so on.  Populations are
  * stored as f - w in `storage` (IMB_STORE_*).  Every step advances all domains
