@@ -22,7 +22,6 @@
 #include "../../include/imblbm.h"
 #include "imb_device.cuh"
 #include "imb_kernels.h"
-#include "imb_node.cuh"
 
 namespace imb {
 
@@ -37,6 +36,66 @@ struct BatchDomain {
     float smag_coef;    // 18 sqrt(2) C^2 of the Smagorinsky closure (0: plain BGK)
     float pad2;
 };
+
+// One node of a domain whose disks are at rest.  With u_s = 0 the solid operator of Eq. 12
+// summed over the covering disks is B (f_{-q} - f^eq_{-q}(u) + f^eq_q(0) - f_q); in the
+// shifted variables d_q = f_q - w_q and n_q = d_q - (f^eq_q(u) - w_q) this is
+// B (n_{-q} - d_q + w_q drho), and Eq. 13 becomes
+//   d*_q = d_q + (1 - B) [-omega n_q + (1 - omega / 2) w_q S_q] + B (n_{-q} - d_q + w_q drho)
+// with S_q / w_q = 3 (c_q - u).F + 9 (c_q.u)(c_q.F) (Guo forcing).  The same algebra as the
+// general collision with every solid-velocity moment zero, with fewer operations.
+struct RestNode {
+    float B, jx, jy;      // drag weight of the node (Eq. 14); jx, jy include the half-force shift
+    bool ok;              // |u|^2 below the Mach guard (false for NaN)
+};
+
+template <typename S>
+__device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, const BatchDomain &D, S *__restrict__ outp) {
+    RestNode r;
+    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const float rho = 1.0f + drho;
+    const float jx = fmaf(0.5f, D.Fx, (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]));   // Eqs. 3-4
+    const float jy = fmaf(0.5f, D.Fy, (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]));
+    const float inv = __fdividef(1.0f, rho);
+    const float ux = jx * inv, uy = jy * inv;
+    const float usq = ux * ux + uy * uy;
+    const float t = fmaf(-1.5f * rho, usq, drho);
+    float n[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {   // non-equilibrium parts (Eq. 2)
+        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        n[q] = d[q] - w_of(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+    }
+    float omega = D.omega0, te = D.tau;
+    if (D.smag_coef > 0.0f) {       // Smagorinsky closure, as in the single-lattice path
+        const float pxx = (n[1] + n[3]) + (n[5] + n[6]) + (n[7] + n[8]);
+        const float pyy = (n[2] + n[4]) + (n[5] + n[6]) + (n[7] + n[8]);
+        const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
+        const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
+        const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;
+        const float disc = fmaf(D.smag_coef * sq, inv, D.tau * D.tau);
+        te = 0.5f * (D.tau + disc * rsqrtf(disc));
+        omega = __fdividef(1.0f, te);
+    }
+    const float ec = fminf(e, 1.0f), tm = te - 0.5f;
+    const float B = __fdividef(ec * tm, (1.0f - ec) + tm);   // Eq. 14 (0 in uncovered cells)
+    const float fl = 1.0f - B, sf = 1.0f - 0.5f * omega;
+    const float g = -3.0f * (ux * D.Fx + uy * D.Fy);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        const float cF = (float)cx_of(q) * D.Fx + (float)cy_of(q) * D.Fy;
+        const float Sq = fmaf(9.0f * cu, cF, fmaf(3.0f, cF, g));
+        const float fluid = fmaf(sf * w_of(q), Sq, -omega * n[q]);
+        const float solid = fmaf(w_of(q), drho, n[opp_of(q)]) - d[q];
+        Store<S>::st(outp + (size_t)q * D.plane, fmaf(B, solid, fmaf(fl, fluid, d[q])));
+    }
+    r.B = B;
+    r.jx = jx;
+    r.jy = jy;
+    r.ok = usq < 0.09f;
+    return r;
+}
 
 template <typename S, int CPL>
 __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
@@ -53,19 +112,11 @@ __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin
             else hi = mid - 1;
         }
         const BatchDomain D = dom[lo];
-        const int y = it - D.item0, nx = D.nx, ny = D.ny;
-        LatticeArgs a;
-        a.plane = D.plane;
-        a.tau = D.tau;
-        a.omega0 = D.omega0;
-        a.smag_coef = D.smag_coef;
-        a.Fx = D.Fx;
-        a.Fy = D.Fy;
-        const bool forced = D.Fx != 0.0f || D.Fy != 0.0f;
+        const int y = it - D.item0, nx = D.nx, ny = D.ny, plane = (int)D.plane;
         const S *src = fin + D.off;
-        S *dst = fout + D.off;
-        const float *Ed = E + D.e_off;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const float *Er = E + D.e_off + (size_t)y * nx;
+        S *dst = fout + D.off + (size_t)y * nx;
+        const int rm = (y == 0 ? ny - 1 : y - 1) * nx, r0 = y * nx, rp = (y == ny - 1 ? 0 : y + 1) * nx;
         float fx_acc = 0.0f, fy_acc = 0.0f;
         for (int x0 = 0; x0 < nx; x0 += 32 * CPL) {
 #pragma unroll
@@ -75,23 +126,15 @@ __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin
                 const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
                 float d[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {   // pull from x - c_q with the periodic wrap
+                for (int q = 0; q < 9; ++q) {   // pull from x - c_q with the periodic wrap (Eq. 1)
                     const int xs = cx_of(q) == 0 ? x : (cx_of(q) == 1 ? xm : xp);
-                    const int ys = cy_of(q) == 0 ? y : (cy_of(q) == 1 ? ym : yp);
-                    d[q] = Store<S>::ld(src + (size_t)q * D.plane + (size_t)ys * nx + xs);
+                    const int ys = cy_of(q) == 0 ? r0 : (cy_of(q) == 1 ? rm : rp);
+                    d[q] = Store<S>::ld(src + (q * plane + ys + xs));
                 }
-                NodeState c;
-                node_state(d, a, forced, D.smag_coef > 0.0f, c);
-                if (!(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
-                const float e = Ed[(size_t)y * nx + x];
-                SolidMoments sm = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                if (e > 0.0f) {
-                    const float ec = fminf(e, 1.0f), tm = c.te - 0.5f;
-                    sm.B = __fdividef(ec * tm, (1.0f - ec) + tm);   // Eq. 14
-                    fx_acc += sm.B * (c.jx - D.Fx);                // Eq. 15 with u_s = 0
-                    fy_acc += sm.B * (c.jy - D.Fy);
-                }
-                node_collide_store(d, c, sm, dst + (size_t)y * nx + x, a, forced);
+                const RestNode c = rest_node(d, Er[x], D, dst + x);
+                if (!c.ok) unstable = true;   // Mach guard, also catches NaN
+                fx_acc = fmaf(c.B, c.jx - D.Fx, fx_acc);   // Eq. 15 with u_s = 0
+                fy_acc = fmaf(c.B, c.jy - D.Fy, fy_acc);
             }
         }
 #pragma unroll
@@ -263,7 +306,8 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
     size_t cells = 0;
     int items = 0, ndisk = 0;
     for (int d = 0; d < n_domains; ++d) {
-        if (nx[d] < 3 || ny[d] < 3 || !(tau[d] > 0.5) || !(C_smag[d] >= 0.0) || n_disks[d] < 0) {
+        if (nx[d] < 3 || ny[d] < 3 || 9.0 * nx[d] * ny[d] > 2147483647.0 || !(tau[d] > 0.5) ||
+            !(C_smag[d] >= 0.0) || n_disks[d] < 0) {
             delete b;
             return IMB_E_INVALID_ARG;
         }
