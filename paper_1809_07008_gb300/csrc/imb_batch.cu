@@ -5,11 +5,11 @@
 // driven by a body force (Guo forcing, as in the single-lattice path), and holds fixed disks
 // whose summed solid ratio E per cell (exact overlap area, Sec. 2.3) is computed once; its
 // relaxation time may carry the Smagorinsky closure of the single-lattice path.  One
-// launch advances every domain by one step: its warps take rows of the domains in turn (a
-// row is a work item; a warp finds the row's domain by binary search in the domains' first
-// items), pull with the periodic wrap of their domain (Eq. 1), collide with the blend of
-// Eq. 13 (B from Eq. 14, u_s = 0 for disks at rest) and add the row's drag B (j - F) (Eq. 15)
-// to the domain's accumulator.  Steps run as a replayed CUDA graph of two launches (A -> B,
+// launch advances every domain by one step: each warp takes an equal run of row segments
+// (finding the domain of its first segment by binary search in the domains' first items),
+// pulls with the periodic wrap of the domain (Eq. 1), collides with the blend of Eq. 13
+// (B from Eq. 14, u_s = 0 for disks at rest) and adds the drag B (j - F) (Eq. 15) of the
+// nodes it stepped to the domain's accumulator.  Steps run as a replayed CUDA graph of two launches (A -> B,
 // B -> A); the block size and the cells per lane are chosen by timing the candidates on the
 // batch itself.
 #include <algorithm>
@@ -27,8 +27,7 @@ namespace imb {
 
 struct BatchDomain {
     int nx, ny;
-    int item0;          // first work item (row) of the domain
-    int pad;
+    int item0[2];       // first work item of the domain: row segments of 32 / 64 cells
     size_t off;         // element offset of the domain's plane 0 in the population buffers
     size_t plane;       // nx * ny
     size_t e_off;       // offset of the domain's solid ratios (cells)
@@ -97,54 +96,79 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     return r;
 }
 
+// A work item is a segment of 32 CPL cells of one row (the last segment of a row may be
+// shorter); items are numbered domain by domain, row by row.  Each warp takes an equal run of
+// consecutive items, so the warps finish together whatever the domain sizes, the rows a warp
+// visits one after another share their neighbour rows in L1, and the drag of a domain is
+// summed in registers until the warp leaves the domain.
 template <typename S, int CPL>
 __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
                              int ndom, int nitems, const float *__restrict__ E, double *drag, unsigned *err) {
+    constexpr int SEG = 32 * CPL;
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int per = nitems / nw, rem = nitems % nw;
+    int it = gw * per + min(gw, rem);
+    const int end = it + per + (gw < rem ? 1 : 0);
+    if (it >= end) return;   // the whole warp: gw is the same on every lane
+    int lo = 0, hi = ndom - 1;   // the domain of the first item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (dom[mid].item0[CPL - 1] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    int dd = lo;
+    BatchDomain D = dom[dd];
+    int nseg = (D.nx + SEG - 1) / SEG;
+    int y = (it - D.item0[CPL - 1]) / nseg;
+    int sg = it - D.item0[CPL - 1] - y * nseg;
     bool unstable = false;
-    for (int it = gw; it < nitems; it += nw) {
-        int lo = 0, hi = ndom - 1;   // the domain of this row
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (dom[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchDomain D = dom[lo];
-        const int y = it - D.item0, nx = D.nx, ny = D.ny, plane = (int)D.plane;
+    float fx_acc = 0.0f, fy_acc = 0.0f;
+    for (;;) {
+        const int nx = D.nx, ny = D.ny, plane = (int)D.plane;
         const S *src = fin + D.off;
         const float *Er = E + D.e_off + (size_t)y * nx;
         S *dst = fout + D.off + (size_t)y * nx;
         const int rm = (y == 0 ? ny - 1 : y - 1) * nx, r0 = y * nx, rp = (y == ny - 1 ? 0 : y + 1) * nx;
-        float fx_acc = 0.0f, fy_acc = 0.0f;
-        for (int x0 = 0; x0 < nx; x0 += 32 * CPL) {
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int x = x0 + 32 * k + lane;
-                if (x >= nx) continue;
-                const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-                float d[9];
+        for (int k = 0; k < CPL; ++k) {
+            const int x = sg * SEG + 32 * k + lane;
+            if (x >= nx) continue;
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            float d[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {   // pull from x - c_q with the periodic wrap (Eq. 1)
-                    const int xs = cx_of(q) == 0 ? x : (cx_of(q) == 1 ? xm : xp);
-                    const int ys = cy_of(q) == 0 ? r0 : (cy_of(q) == 1 ? rm : rp);
-                    d[q] = Store<S>::ld(src + (q * plane + ys + xs));
-                }
-                const RestNode c = rest_node(d, Er[x], D, dst + x);
-                if (!c.ok) unstable = true;   // Mach guard, also catches NaN
-                fx_acc = fmaf(c.B, c.jx - D.Fx, fx_acc);   // Eq. 15 with u_s = 0
-                fy_acc = fmaf(c.B, c.jy - D.Fy, fy_acc);
+            for (int q = 0; q < 9; ++q) {   // pull from x - c_q with the periodic wrap (Eq. 1)
+                const int xs = cx_of(q) == 0 ? x : (cx_of(q) == 1 ? xm : xp);
+                const int ys = cy_of(q) == 0 ? r0 : (cy_of(q) == 1 ? rm : rp);
+                d[q] = Store<S>::ld(src + (q * plane + ys + xs));
             }
+            const RestNode c = rest_node(d, Er[x], D, dst + x);
+            if (!c.ok) unstable = true;   // Mach guard, also catches NaN
+            fx_acc = fmaf(c.B, c.jx - D.Fx, fx_acc);   // Eq. 15 with u_s = 0
+            fy_acc = fmaf(c.B, c.jy - D.Fy, fy_acc);
         }
+        ++it;
+        if (++sg == nseg) {
+            sg = 0;
+            ++y;
+        }
+        const bool last = it == end;
+        if (last || y == ny) {   // leaving the domain: add its drag
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fx_acc += __shfl_xor_sync(0xffffffffu, fx_acc, o);
-            fy_acc += __shfl_xor_sync(0xffffffffu, fy_acc, o);
-        }
-        if (lane == 0 && (fx_acc != 0.0f || fy_acc != 0.0f)) {
-            atomicAdd(&drag[2 * lo], (double)fx_acc);
-            atomicAdd(&drag[2 * lo + 1], (double)fy_acc);
+            for (int o = 16; o > 0; o >>= 1) {
+                fx_acc += __shfl_xor_sync(0xffffffffu, fx_acc, o);
+                fy_acc += __shfl_xor_sync(0xffffffffu, fy_acc, o);
+            }
+            if (lane == 0 && (fx_acc != 0.0f || fy_acc != 0.0f)) {
+                atomicAdd(&drag[2 * dd], (double)fx_acc);
+                atomicAdd(&drag[2 * dd + 1], (double)fy_acc);
+            }
+            fx_acc = fy_acc = 0.0f;
+            if (last) break;
+            D = dom[++dd];
+            nseg = (D.nx + SEG - 1) / SEG;
+            y = 0;
         }
     }
     if (__any_sync(0xffffffffu, unstable) && lane == 0) set_err(err, ERR_UNSTABLE);
@@ -190,7 +214,7 @@ __global__ void k_batch_gather(const S *__restrict__ fin, const BatchDomain *__r
 using namespace imb;
 
 struct imb_batch {
-    int device = 0, storage = 0, elem = 4, ndom = 0, nitems = 0, ndisk = 0;
+    int device = 0, storage = 0, elem = 4, ndom = 0, nitems[2] = {0, 0}, ndisk = 0;
     size_t total = 0;          // elements per population buffer
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;               // buffer holding the current post-collision field
@@ -239,13 +263,13 @@ cudaError_t launch_step_t(imb_batch *b, int from) {
         int per = 0, sms = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, b->block, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        const int need = (b->nitems * 32 + b->block - 1) / b->block;
-        b->grid = std::max(1, std::min(need, std::max(per, 1) * sms));
+        const long long need = ((long long)b->nitems[CPL - 1] * 32 + b->block - 1) / b->block;
+        b->grid = (int)std::max(1LL, std::min(need, (long long)std::max(per, 1) * sms));
         if (b->grid_only) return cudaSuccess;
     }
     if (b->grid_only) return cudaSuccess;
     k<<<b->grid, b->block, 0, b->stream>>>((const S *)b->buf[from], (S *)b->buf[from ^ 1], b->dom, b->ndom,
-                                           b->nitems, b->E, b->drag, b->err);
+                                           b->nitems[CPL - 1], b->E, b->drag, b->err);
     return cudaGetLastError();
 }
 
@@ -304,7 +328,8 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
     b->ndom = n_domains;
     double rmax = 0.0;
     size_t cells = 0;
-    int items = 0, ndisk = 0;
+    long long items = 0, items2 = 0;   // row segments of 32 and of 64 cells
+    int ndisk = 0;
     for (int d = 0; d < n_domains; ++d) {
         if (nx[d] < 3 || ny[d] < 3 || 9.0 * nx[d] * ny[d] > 2147483647.0 || !(tau[d] > 0.5) ||
             !(C_smag[d] >= 0.0) || n_disks[d] < 0) {
@@ -314,7 +339,8 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
         BatchDomain D{};
         D.nx = nx[d];
         D.ny = ny[d];
-        D.item0 = items;
+        D.item0[0] = (int)items;
+        D.item0[1] = (int)items2;
         D.plane = (size_t)nx[d] * ny[d];
         D.off = 9 * cells;
         D.e_off = cells;
@@ -325,7 +351,8 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
         D.smag_coef = (float)(18.0 * std::sqrt(2.0) * C_smag[d] * C_smag[d]);
         b->hdom.push_back(D);
         cells += D.plane;
-        items += ny[d];
+        items += (long long)ny[d] * ((nx[d] + 31) / 32);
+        items2 += (long long)ny[d] * ((nx[d] + 63) / 64);
         ndisk += n_disks[d];
     }
     if (ndisk > 0 && (!disk_xy || !disk_r)) {
@@ -343,7 +370,12 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
             }
             rmax = std::max(rmax, r);
         }
-    b->nitems = items;
+    if (items > 2147483647LL) {
+        delete b;
+        return IMB_E_INVALID_ARG;
+    }
+    b->nitems[0] = (int)items;
+    b->nitems[1] = (int)items2;
     b->ndisk = ndisk;
     b->total = 9 * cells;
     cudaGetDevice(&b->device);
