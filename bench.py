@@ -239,9 +239,10 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256):
+def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256, snapshots=40):
     """Reverse-mode gradient of the time-averaged drag on the 512 x 256 channel with 16 fixed
-    disks: one call of imb_drag_gradient (forward, checkpointed recomputation, backward)."""
+    disks: one call of imb_drag_gradient (forward, checkpointed recomputation, backward), and
+    one of imb_drag_gradient_binomial with ``snapshots`` snapshots."""
     w = W.c4(steps=T, nx=nx, ny=ny)
     warm = imb.Lattice.from_workload(w)
     warm.drag_gradient(200, checkpoint_every)
@@ -251,11 +252,21 @@ def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256):
     J, g_u, g_tau, g_x = lat.drag_gradient(T, checkpoint_every)
     dt = time.perf_counter() - t0
     lat.close()
+    # binomial checkpointing with 40 snapshots (41 states held instead of ~140)
+    lat = imb.Lattice.from_workload(w)
+    t0 = time.perf_counter()
+    Jb, g_ub, g_taub, g_xb = lat.drag_gradient(T, snapshots=snapshots)
+    dtb = time.perf_counter() - t0
+    lat.close()
+    _, fwd_b = imb.binomial_schedule(T, snapshots)
     cells = w.nx * w.ny
     return {"workload": w.name, "steps": T, "checkpoint_every": checkpoint_every, "seconds": round(dt, 4),
             "mlups": round(cells * T / dt / 1e6, 1), "note": "lattice updates of the forward horizon per second "
             "of the whole gradient (forward, recomputation and adjoint)", "J": J, "dJ_duin": g_u,
-            "dJ_dtau": g_tau, "dJ_dx_max": float(np.abs(g_x).max())}
+            "dJ_dtau": g_tau, "dJ_dx_max": float(np.abs(g_x).max()),
+            "binomial": {"snapshots": snapshots, "seconds": round(dtb, 4), "forward_steps": fwd_b + 1,
+                         "states_held": snapshots + 1, "J_rel_diff": abs(Jb - J) / abs(J),
+                         "dJ_dtau_rel_diff": abs(g_taub - g_tau) / abs(g_tau)}}
 
 
 def time_batched_sweep(imb, steps=5000, n_domains=256, storage="fp16"):

@@ -155,6 +155,31 @@ int imb_get_cell_map(imb_ctx *ctx, int *count, int *ids, float *eps);
 int imb_drag_gradient(imb_ctx *ctx, int T, int checkpoint_every, double *J, double *dJ_duin,
                       double *dJ_dtau, double *dJ_dx);
 
+/* The same gradient with binomial checkpointing: `snapshots` + 1 copies of the
+ * populations (the start state and `snapshots` more, capped at T - 1) placed by the
+ * recursive binomial schedule of imb_binomial_schedule, which recomputes the fewest
+ * forward steps that memory allows (about r T for the least r with
+ * C(snapshots + 1 + r, r) >= T).  Every step's drag enters J the first time the
+ * schedule steps over it; the last step is taken once more to give the final
+ * state.  Same requirements, outputs and errors as imb_drag_gradient; snapshots < 0
+ * is IMB_E_INVALID_ARG. */
+int imb_drag_gradient_binomial(imb_ctx *ctx, int T, int snapshots, double *J, double *dJ_duin,
+                               double *dJ_dtau, double *dJ_dx);
+
+/* Operations of the binomial checkpointing schedule (host only, no GPU call): the
+ * reversal of T steps with `snapshots` free snapshot slots (1 .. snapshots; slot 0
+ * holds the start state).  ops receives pairs (kind, argument): IMB_CK_ADVANCE n
+ * (step the working state n times), IMB_CK_STORE k (copy it to slot k),
+ * IMB_CK_RESTORE k (copy slot k back), IMB_CK_ADJOINT t (adjoint of step t from the
+ * working state, which then holds state t).  At most max_ops pairs are written;
+ * *n_ops receives the full count and *n_advances (may be NULL) the forward steps.
+ * IMB_E_INVALID_ARG for T < 1, snapshots < 0 or missing outputs. */
+#define IMB_CK_ADVANCE 1
+#define IMB_CK_STORE 2
+#define IMB_CK_RESTORE 3
+#define IMB_CK_ADJOINT 4
+int imb_binomial_schedule(int T, int snapshots, int *ops, int max_ops, int *n_ops, long long *n_advances);
+
 /* ---- many independent domains (the parameter sweeps of Sec. 3 as one batch) ----
  * Each domain d is an nx[d] x ny[d] lattice, periodic in x and y, at rest at t = 0
  * (rho = 1), driven by the body force (Fx[d], Fy[d]) (Guo forcing), with relaxation

@@ -32,9 +32,29 @@ EXPORTS = (
     "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
     "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
+    "imb_drag_gradient_binomial", "imb_binomial_schedule",
     "imb_batch_create", "imb_batch_run", "imb_batch_autotune", "imb_batch_mean_drag",
     "imb_batch_get_populations", "imb_batch_cells", "imb_batch_last_error", "imb_batch_destroy",
 )
+
+
+CK_ADVANCE, CK_STORE, CK_RESTORE, CK_ADJOINT = 1, 2, 3, 4
+
+
+def binomial_schedule(T: int, snapshots: int):
+    """imb_binomial_schedule: the operations [(kind, argument), ...] of the binomial
+    checkpointing schedule for reversing T steps with ``snapshots`` free snapshot slots, and
+    the number of forward steps it takes.  Host only (no GPU)."""
+    L = load()
+    n, adv = C.c_int(0), C.c_longlong(0)
+    rc = L.imb_binomial_schedule(int(T), int(snapshots), None, 0, C.byref(n), C.byref(adv))
+    if rc:
+        raise ImbError(rc, "imb_binomial_schedule")
+    ops = np.zeros(2 * max(n.value, 1), dtype=np.int32)
+    rc = L.imb_binomial_schedule(int(T), int(snapshots), ops.ctypes.data_as(_ip), n.value, C.byref(n), None)
+    if rc:
+        raise ImbError(rc, "imb_binomial_schedule")
+    return [(int(ops[2 * k]), int(ops[2 * k + 1])) for k in range(n.value)], adv.value
 
 
 def bin_particles_noalloc(d_x: int, n: int, nx: int, ny: int, d_bin_start: int, d_bin_ids: int,
@@ -116,6 +136,8 @@ def load(build_if_missing: bool = True):
     L.imb_destroy.restype = None
     L.imb_bin_particles_noalloc.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]
     L.imb_drag_gradient.argtypes = [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+    L.imb_drag_gradient_binomial.argtypes = [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+    L.imb_binomial_schedule.argtypes = [C.c_int, C.c_int, _ip, C.c_int, _ip, C.POINTER(C.c_longlong)]
     L.imb_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _dp, _dp, C.c_int]
     L.imb_batch_run.argtypes = [_vp, C.c_int]
     L.imb_batch_autotune.argtypes = [_vp, C.c_int, _ip, _ip, _dp]
@@ -257,13 +279,20 @@ class Lattice:
         self._check(self._L.imb_get_particles(self.h, _d(x), _d(v), _d(w)))
         return x, v, w
 
-    def drag_gradient(self, T, checkpoint_every=100):
+    def drag_gradient(self, T, checkpoint_every=100, snapshots=None):
         """Time-averaged drag over T steps from the current state and its gradient with respect
-        to the inlet velocity, tau and the disk centres (imb_drag_gradient)."""
+        to the inlet velocity, tau and the disk centres: uniform checkpoints every
+        ``checkpoint_every`` steps (imb_drag_gradient), or binomial checkpointing with
+        ``snapshots`` snapshots when that is given (imb_drag_gradient_binomial)."""
         J, gu, gt = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
         gx = np.zeros((max(self.np, 1), 2))
-        self._check(self._L.imb_drag_gradient(self.h, int(T), int(checkpoint_every), C.byref(J), C.byref(gu),
-                                              C.byref(gt), _d(gx)))
+        if snapshots is None:
+            rc = self._L.imb_drag_gradient(self.h, int(T), int(checkpoint_every), C.byref(J), C.byref(gu),
+                                           C.byref(gt), _d(gx))
+        else:
+            rc = self._L.imb_drag_gradient_binomial(self.h, int(T), int(snapshots), C.byref(J), C.byref(gu),
+                                                    C.byref(gt), _d(gx))
+        self._check(rc)
         return J.value, gu.value, gt.value, gx[:self.np]
 
     def cell_map(self):

@@ -771,10 +771,24 @@ extern "C" const char *imb_last_error(imb_ctx *c) {
 }
 
 // ------------------------------------------------------------------ drag gradient
-extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double *J, double *dJ_duin,
-                                 double *dJ_dtau, double *dJ_dx) {
-    if (!c || !J || !dJ_duin || !dJ_dtau || (c->np > 0 && !dJ_dx)) return IMB_E_INVALID_ARG;
-    if (T < 1 || checkpoint_every < 1) return fail(c, IMB_E_INVALID_ARG, "T and checkpoint_every must be >= 1");
+// Reverse-mode gradient of the time-averaged drag J = (1/T) sum_t sum_p F_x,p(t) of T steps
+// (Eq. 15 forces) with respect to the inlet velocity, tau and the disk centres.  The adjoint
+// of step t needs the post-collision field the step starts from ("state t"); how the states
+// are kept is the checkpointing scheme: uniform (every K-th state, a segment recomputed at a
+// time) or binomial (a fixed number of snapshots placed by the recursive binomial schedule).
+namespace {
+
+struct GradBufs {
+    size_t ncell = 0, state = 0, sb = 0;   // cells, floats per state, bytes per state
+    DevTmp<float> lam, Eb, fin;
+    DevTmp<double> acc, gE, gx, Fsave;
+    DevTmp<int> cnt, ids;
+    DevTmp<float> epsb;
+    float *lam1 = nullptr, *lam0 = nullptr;   // d J / d f(t+1), d J / d f(t)
+    float inv_T = 0.0f;
+};
+
+int grad_prepare(imb_ctx *c, int T, GradBufs &g) {
     if (c->p.dem_on || c->C_smag != 0.0 || c->p.Fx != 0.0 || c->p.Fy != 0.0 || c->p.eps_mode != IMB_EPS_EXACT ||
         c->p.storage != IMB_STORE_FP32)
         return fail(c, IMB_E_INVALID_ARG,
@@ -782,7 +796,7 @@ extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double
     int rc = imb_sync(c);
     if (rc) return rc;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int np = c->np, K = checkpoint_every;
+    const int np = c->np;
     if (np > 0) {   // disks at rest
         std::vector<double> hv(2 * (size_t)np), hw(np);
         CK(cudaMemcpy(hv.data(), c->v, 16 * (size_t)np, cudaMemcpyDeviceToHost), "read v");
@@ -791,55 +805,213 @@ extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double
             if (hv[2 * i] != 0.0 || hv[2 * i + 1] != 0.0 || hw[i] != 0.0)
                 return fail(c, IMB_E_INVALID_ARG, "drag gradient needs disks at rest");
     }
-    const size_t ncell = (size_t)c->nx * c->ny, state = 9 * c->plane;   // floats per state
-    const int nck = (T + K - 1) / K;
-    DevTmp<float> ck, seg, lam, Eb, fin;
-    DevTmp<double> acc, gE, gx, Fsave;
-    DevTmp<int> cnt, ids;
-    DevTmp<float> epsb;
-    CK(dalloc(&ck.p, state * nck), "checkpoints");
-    CK(dalloc(&seg.p, state * (size_t)std::min(K, T)), "segment states");
-    CK(dalloc(&lam.p, 2 * state), "adjoint buffers");
-    CK(dalloc(&fin.p, state), "final state");
-    CK(dalloc(&Eb.p, ncell), "solid ratio");
-    CK(dalloc(&gE.p, ncell), "solid-ratio gradient");
-    CK(dalloc(&acc.p, 4), "accumulators");
-    CK(dalloc(&gx.p, 2 * (size_t)std::max(np, 1)), "position gradient");
-    CK(dalloc(&Fsave.p, 3 * (size_t)std::max(np, 1)), "force copy");
-    CK(dalloc(&cnt.p, ncell), "cell map");
-    CK(dalloc(&ids.p, ncell * MAX_SLOTS), "cell map");
-    CK(dalloc(&epsb.p, ncell * MAX_SLOTS), "cell map");
+    g.ncell = (size_t)c->nx * c->ny;
+    g.state = 9 * c->plane;
+    g.sb = g.state * sizeof(float);
+    g.inv_T = 1.0f / (float)T;
+    CK(dalloc(&g.lam.p, 2 * g.state), "adjoint buffers");
+    CK(dalloc(&g.fin.p, g.state), "final state");
+    CK(dalloc(&g.Eb.p, g.ncell), "solid ratio");
+    CK(dalloc(&g.gE.p, g.ncell), "solid-ratio gradient");
+    CK(dalloc(&g.acc.p, 4), "accumulators");
+    CK(dalloc(&g.gx.p, 2 * (size_t)std::max(np, 1)), "position gradient");
+    CK(dalloc(&g.Fsave.p, 3 * (size_t)std::max(np, 1)), "force copy");
+    CK(dalloc(&g.cnt.p, g.ncell), "cell map");
+    CK(dalloc(&g.ids.p, g.ncell * MAX_SLOTS), "cell map");
+    CK(dalloc(&g.epsb.p, g.ncell * MAX_SLOTS), "cell map");
     cudaStream_t s = c->stream;
-    const size_t sb = state * sizeof(float);
-    CK(cudaMemsetAsync(acc.p, 0, 4 * sizeof(double), s), "clear");
-    CK(cudaMemsetAsync(gE.p, 0, ncell * sizeof(double), s), "clear");
-    CK(cudaMemsetAsync(gx.p, 0, 2 * (size_t)std::max(np, 1) * sizeof(double), s), "clear");
-    CK(cudaMemsetAsync(lam.p, 0, 2 * sb, s), "clear");
-    CK(cudaMemsetAsync(Eb.p, 0, ncell * sizeof(float), s), "clear");
-    LatticeArgs a = lattice_args(c);
+    CK(cudaMemsetAsync(g.acc.p, 0, 4 * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(g.gE.p, 0, g.ncell * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(g.gx.p, 0, 2 * (size_t)std::max(np, 1) * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(g.lam.p, 0, 2 * g.sb, s), "clear");
+    CK(cudaMemsetAsync(g.Eb.p, 0, g.ncell * sizeof(float), s), "clear");
+    g.lam1 = g.lam.p;
+    g.lam0 = g.lam.p + g.state;
     if (np > 0) {
-        CK(launch_cell_map(a, cnt.p, ids.p, epsb.p, s), "cell map");
-        CK(launch_cell_E(cnt.p, epsb.p, ncell, Eb.p, s), "solid ratio");
+        LatticeArgs a = lattice_args(c);
+        CK(launch_cell_map(a, g.cnt.p, g.ids.p, g.epsb.p, s), "cell map");
+        CK(launch_cell_E(g.cnt.p, g.epsb.p, g.ncell, g.Eb.p, s), "solid ratio");
         c->launches += 2;
     }
+    return IMB_OK;
+}
+
+// one forward step whose drag enters J
+int grad_forward_step(imb_ctx *c, GradBufs &g) {
+    int rc = lattice_step(c);
+    if (rc) return rc;
+    if (c->np > 0) {
+        CK(launch_drag_sum(c->F, c->np, g.acc.p, c->stream), "drag");
+        c->launches++;
+    }
+    return IMB_OK;
+}
+
+// the state after the T steps and its forces, kept for the end of the call
+int grad_keep_final(imb_ctx *c, GradBufs &g) {
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpyAsync(g.fin.p, c->fbuf[c->cur], g.sb, cudaMemcpyDeviceToDevice, s), "final state");
+    if (c->np > 0) {
+        CK(cudaMemcpyAsync(g.Fsave.p, c->F, 16 * (size_t)c->np, cudaMemcpyDeviceToDevice, s), "forces");
+        CK(cudaMemcpyAsync(g.Fsave.p + 2 * (size_t)c->np, c->T, 8 * (size_t)c->np, cudaMemcpyDeviceToDevice, s),
+           "torques");
+    }
+    return IMB_OK;
+}
+
+// Adjoint of step t from state t (S0): d J / d f(t+1) -> d J / d f(t), plus the tau and
+// solid-ratio terms; then, for t >= 1, the transpose of the inlet/outlet rule that produced
+// f(t) from state t (it adds the inlet-velocity term), so that the next unit starts from the
+// full d J / d f(t).
+int grad_unit(imb_ctx *c, GradBufs &g, int t, const float *S0) {
+    LatticeArgs a = lattice_args(c);
+    cudaStream_t s = c->stream;
+    CK(launch_adjoint_step(g.lam1, S0, g.lam0, a, g.Eb.p, g.gE.p, g.inv_T, g.acc.p + 1, s), "adjoint step");
+    c->launches++;
+    std::swap(g.lam1, g.lam0);
+    if (t >= 1 && c->p.bc_x == IMB_BC_INLET_OUTLET) {
+        CK(launch_adjoint_inlet(g.lam1, S0, a, g.acc.p + 2, s), "adjoint inlet");
+        c->launches++;
+    }
+    return IMB_OK;
+}
+
+int grad_finish(imb_ctx *c, GradBufs &g, int T, double *J, double *dJ_duin, double *dJ_dtau, double *dJ_dx) {
+    cudaStream_t s = c->stream;
+    const int np = c->np;
+    CK(cudaMemcpyAsync(c->fbuf[c->cur], g.fin.p, g.sb, cudaMemcpyDeviceToDevice, s), "restore final state");
+    if (np > 0) {
+        CK(cudaMemcpyAsync(c->F, g.Fsave.p, 16 * (size_t)np, cudaMemcpyDeviceToDevice, s), "forces");
+        CK(cudaMemcpyAsync(c->T, g.Fsave.p + 2 * (size_t)np, 8 * (size_t)np, cudaMemcpyDeviceToDevice, s), "torques");
+        CK(launch_position_grad(g.cnt.p, g.ids.p, g.gE.p, c->x, c->r, c->nx, c->ny, c->p.bc_x, c->p.bc_y, g.gx.p, s),
+           "position gradient");
+        c->launches++;
+    }
+    double h[4];
+    CK(cudaMemcpyAsync(h, g.acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "accumulators");
+    if (np > 0) CK(cudaMemcpyAsync(dJ_dx, g.gx.p, 16 * (size_t)np, cudaMemcpyDeviceToHost, s), "gradient");
+    int rc = imb_sync(c);
+    if (rc) return rc;
+    *J = h[0] / T;
+    *dJ_dtau = h[1];
+    *dJ_duin = h[2];
+    return IMB_OK;
+}
+
+// ---- binomial checkpointing schedule (Griewank's recursive reversal) ----
+// C(s + r, s), saturated far above any step count
+long long binom_beta(int s, int r) {
+    if (r < 0) return 0;
+    long double v = 1.0L;
+    for (int k = 1; k <= s; ++k) {
+        v = v * (long double)(r + k) / (long double)k;
+        if (v > 4.0e18L) return (long long)4e18;
+    }
+    return (long long)(v + 0.5L);
+}
+
+struct Sched {
+    std::vector<int> ops;   // (kind, argument) pairs
+    long long advances = 0;
+    int cur = 0;            // time of the state in the working buffer
+    std::vector<int> slot_t, free_slots;
+    void emit(int k, int v) {
+        ops.push_back(k);
+        ops.push_back(v);
+    }
+    void restore(int slot) {
+        if (cur != slot_t[slot]) {
+            emit(IMB_CK_RESTORE, slot);
+            cur = slot_t[slot];
+        }
+    }
+    void advance(int n) {
+        emit(IMB_CK_ADVANCE, n);
+        cur += n;
+        advances += n;
+    }
+    // adjoints of steps b-1 .. a; state a is in `slot`, s snapshots are free
+    void reverse(int a, int b, int s, int slot) {
+        const int l = b - a;
+        if (l == 1) {
+            restore(slot);
+            emit(IMB_CK_ADJOINT, a);
+            return;
+        }
+        if (s == 0) {   // no snapshot left: recompute every state from state a
+            for (int t = b - 1; t >= a; --t) {
+                restore(slot);
+                if (t > a) advance(t - a);
+                emit(IMB_CK_ADJOINT, t);
+            }
+            return;
+        }
+        // repetition number r: the least with C(s + 1 + r, r) >= l; then a first snapshot j
+        // steps on, the left part [a, a + j) reversed with the same snapshots, the right part
+        // with one fewer, both within their repetition budgets (r - 1 and r)
+        int r = 0;
+        while (binom_beta(s + 1, r) < l) ++r;
+        long long j = std::max(binom_beta(s + 1, r - 2), (long long)l - binom_beta(s, r));
+        j = std::max(1LL, std::min(j, (long long)l - 1));
+        restore(slot);
+        advance((int)j);
+        const int sl = free_slots.back();
+        free_slots.pop_back();
+        slot_t[sl] = cur;
+        emit(IMB_CK_STORE, sl);
+        reverse(a + (int)j, b, s - 1, sl);
+        free_slots.push_back(sl);
+        reverse(a, a + (int)j, s, slot);
+    }
+};
+
+void binomial_schedule(int T, int snapshots, Sched &sc) {
+    const int s = std::max(0, std::min(snapshots, T - 1));
+    sc.slot_t.assign(s + 1, -1);
+    for (int k = s; k >= 1; --k) sc.free_slots.push_back(k);
+    sc.slot_t[0] = 0;
+    sc.emit(IMB_CK_STORE, 0);
+    sc.reverse(0, T, s, 0);
+}
+
+}  // namespace
+
+extern "C" int imb_binomial_schedule(int T, int snapshots, int *ops, int max_ops, int *n_ops,
+                                     long long *n_advances) {
+    if (T < 1 || snapshots < 0 || max_ops < 0 || (max_ops > 0 && !ops) || !n_ops) return IMB_E_INVALID_ARG;
+    Sched sc;
+    binomial_schedule(T, snapshots, sc);
+    const int n = (int)(sc.ops.size() / 2);
+    for (int k = 0; k < std::min(n, max_ops); ++k) {
+        ops[2 * k] = sc.ops[2 * k];
+        ops[2 * k + 1] = sc.ops[2 * k + 1];
+    }
+    *n_ops = n;
+    if (n_advances) *n_advances = sc.advances;
+    return IMB_OK;
+}
+
+extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double *J, double *dJ_duin,
+                                 double *dJ_dtau, double *dJ_dx) {
+    if (!c || !J || !dJ_duin || !dJ_dtau || (c->np > 0 && !dJ_dx)) return IMB_E_INVALID_ARG;
+    if (T < 1 || checkpoint_every < 1) return fail(c, IMB_E_INVALID_ARG, "T and checkpoint_every must be >= 1");
+    GradBufs g;
+    int rc = grad_prepare(c, T, g);
+    if (rc) return rc;
+    const int K = checkpoint_every, nck = (T + K - 1) / K;
+    const size_t state = g.state, sb = g.sb;
+    DevTmp<float> ck, seg;
+    CK(dalloc(&ck.p, state * nck), "checkpoints");
+    CK(dalloc(&seg.p, state * (size_t)std::min(K, T)), "segment states");
+    cudaStream_t s = c->stream;
     // forward: every K-th state kept, the drag of every step summed
     for (int t = 0; t < T; ++t) {
         if (t % K == 0)
             CK(cudaMemcpyAsync(ck.p + state * (t / K), c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "checkpoint");
-        if ((rc = lattice_step(c))) return rc;
-        if (np > 0) {
-            CK(launch_drag_sum(c->F, np, acc.p, s), "drag");
-            c->launches++;
-        }
+        if ((rc = grad_forward_step(c, g))) return rc;
     }
-    CK(cudaMemcpyAsync(fin.p, c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "final state");
-    if (np > 0) {
-        CK(cudaMemcpyAsync(Fsave.p, c->F, 16 * (size_t)np, cudaMemcpyDeviceToDevice, s), "forces");
-        CK(cudaMemcpyAsync(Fsave.p + 2 * (size_t)np, c->T, 8 * (size_t)np, cudaMemcpyDeviceToDevice, s), "torques");
-    }
+    if ((rc = grad_keep_final(c, g))) return rc;
     // backward, one checkpoint segment at a time: recompute its states, then walk back
-    float *lam1 = lam.p, *lam0 = lam.p + state;   // d J / d f(t+1), d J / d f(t)
-    const float inv_T = 1.0f / (float)T;
     for (int j = nck - 1; j >= 0; --j) {
         const int t0 = j * K, t1 = std::min(T, t0 + K);
         CK(cudaMemcpyAsync(c->fbuf[c->cur], ck.p + state * j, sb, cudaMemcpyDeviceToDevice, s), "restore");
@@ -847,33 +1019,55 @@ extern "C" int imb_drag_gradient(imb_ctx *c, int T, int checkpoint_every, double
             CK(cudaMemcpyAsync(seg.p + state * (t - t0), c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "segment");
             if (t + 1 < t1 && (rc = lattice_step(c))) return rc;
         }
-        for (int t = t1 - 1; t >= t0; --t) {
-            const float *S1 = t + 1 < t1 ? seg.p + state * (t + 1 - t0) : (t + 1 == T ? fin.p : ck.p + state * (j + 1));
-            if (c->p.bc_x == IMB_BC_INLET_OUTLET && t + 1 < T) {
-                CK(launch_adjoint_inlet(lam1, S1, a, acc.p + 2, s), "adjoint inlet");
-                c->launches++;
+        for (int t = t1 - 1; t >= t0; --t)
+            if ((rc = grad_unit(c, g, t, seg.p + state * (t - t0)))) return rc;
+    }
+    return grad_finish(c, g, T, J, dJ_duin, dJ_dtau, dJ_dx);
+}
+
+extern "C" int imb_drag_gradient_binomial(imb_ctx *c, int T, int snapshots, double *J, double *dJ_duin,
+                                          double *dJ_dtau, double *dJ_dx) {
+    if (!c || !J || !dJ_duin || !dJ_dtau || (c->np > 0 && !dJ_dx)) return IMB_E_INVALID_ARG;
+    if (T < 1 || snapshots < 0) return fail(c, IMB_E_INVALID_ARG, "T must be >= 1 and snapshots >= 0");
+    GradBufs g;
+    int rc = grad_prepare(c, T, g);
+    if (rc) return rc;
+    Sched sc;
+    binomial_schedule(T, snapshots, sc);
+    const size_t state = g.state, sb = g.sb;
+    DevTmp<float> snap;
+    CK(dalloc(&snap.p, state * sc.slot_t.size()), "snapshots");
+    std::vector<int> slot_t(sc.slot_t.size(), -1);
+    cudaStream_t s = c->stream;
+    int cur_t = 0, done = 0;   // time of the working state; steps whose drag is in J
+    for (size_t k = 0; k < sc.ops.size(); k += 2) {
+        const int kind = sc.ops[k], v = sc.ops[k + 1];
+        if (kind == IMB_CK_ADVANCE) {
+            for (int n = 0; n < v; ++n, ++cur_t) {
+                if (cur_t == done) {   // first pass over this step: its drag enters J
+                    if ((rc = grad_forward_step(c, g))) return rc;
+                    ++done;
+                } else if ((rc = lattice_step(c))) {
+                    return rc;
+                }
             }
-            CK(launch_adjoint_step(lam1, seg.p + state * (t - t0), lam0, a, Eb.p, gE.p, inv_T, acc.p + 1, s),
-               "adjoint step");
-            c->launches++;
-            std::swap(lam1, lam0);
+        } else if (kind == IMB_CK_STORE) {
+            CK(cudaMemcpyAsync(snap.p + state * v, c->fbuf[c->cur], sb, cudaMemcpyDeviceToDevice, s), "snapshot");
+            slot_t[v] = cur_t;
+        } else if (kind == IMB_CK_RESTORE) {
+            CK(cudaMemcpyAsync(c->fbuf[c->cur], snap.p + state * v, sb, cudaMemcpyDeviceToDevice, s), "restore");
+            cur_t = slot_t[v];
+        } else {   // IMB_CK_ADJOINT of step v from the working state
+            if (v != cur_t) return fail(c, IMB_E_CUDA, "internal: checkpoint schedule out of order");
+            if (v == T - 1) {   // the first adjoint: the last forward step completes J and the final state
+                if (done != T - 1) return fail(c, IMB_E_CUDA, "internal: checkpoint schedule skipped a step");
+                if ((rc = grad_forward_step(c, g))) return rc;
+                ++done;
+                if ((rc = grad_keep_final(c, g))) return rc;
+                c->cur ^= 1;   // the step wrote the other buffer: state T - 1 is still in this one
+            }
+            if ((rc = grad_unit(c, g, v, (const float *)c->fbuf[c->cur]))) return rc;
         }
     }
-    // the state and forces after the T forward steps
-    CK(cudaMemcpyAsync(c->fbuf[c->cur], fin.p, sb, cudaMemcpyDeviceToDevice, s), "restore final state");
-    if (np > 0) {
-        CK(cudaMemcpyAsync(c->F, Fsave.p, 16 * (size_t)np, cudaMemcpyDeviceToDevice, s), "forces");
-        CK(cudaMemcpyAsync(c->T, Fsave.p + 2 * (size_t)np, 8 * (size_t)np, cudaMemcpyDeviceToDevice, s), "torques");
-        CK(launch_position_grad(cnt.p, ids.p, gE.p, c->x, c->r, c->nx, c->ny, c->p.bc_x, c->p.bc_y, gx.p, s),
-           "position gradient");
-        c->launches++;
-    }
-    double h[4];
-    CK(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s), "accumulators");
-    if (np > 0) CK(cudaMemcpyAsync(dJ_dx, gx.p, 16 * (size_t)np, cudaMemcpyDeviceToHost, s), "gradient");
-    if ((rc = imb_sync(c))) return rc;
-    *J = h[0] / T;
-    *dJ_dtau = h[1];
-    *dJ_duin = h[2];
-    return IMB_OK;
+    return grad_finish(c, g, T, J, dJ_duin, dJ_dtau, dJ_dx);
 }

@@ -11,6 +11,9 @@ against central finite differences of the GPU's own forward steps.
   2e-2), and the checkpoint interval changes nothing (the recomputed states are the same; the
   order in which a tile's immersed nodes are summed into the forces is not fixed, which leaves
   differences of ~1e-10 in J and ~1e-12 in the gradient).
+* Binomial checkpointing (imb_drag_gradient_binomial) gives the gradient of the uniform scheme:
+  against the oracle's adjoint as above with 0, 2 and 5 snapshots, and on the 16-disk channel with
+  40 snapshots against the uniform scheme (the same tolerances as between checkpoint intervals).
 * The torch.autograd wrapper hands back the library's gradient.
 """
 import numpy as np
@@ -39,8 +42,11 @@ def _small(kind, u=0.02, tau=0.6):
                       u0=(0.02, 0.0), **common)
 
 
-@pytest.mark.parametrize("kind", ["channel", "periodic"])
-def test_drag_gradient_matches_oracle_adjoint(orc, imb, kind):
+@pytest.mark.parametrize("kind,scheme", [("channel", dict(checkpoint_every=16)),
+                                         ("periodic", dict(checkpoint_every=16)),
+                                         ("channel", dict(snapshots=0)), ("channel", dict(snapshots=2)),
+                                         ("periodic", dict(snapshots=5))])
+def test_drag_gradient_matches_oracle_adjoint(orc, imb, kind, scheme):
     w = _small(kind)
     o = orc.Sim(w)
     g = imb.Lattice.from_workload(w)
@@ -48,7 +54,7 @@ def test_drag_gradient_matches_oracle_adjoint(orc, imb, kind):
     g.step(20)
     T = 60
     Jo, _, gto, gxo = o.drag_adjoint(T)
-    Jg, _, gtg, gxg = g.drag_gradient(T, checkpoint_every=16)
+    Jg, _, gtg, gxg = g.drag_gradient(T, **scheme)
     assert Jg == pytest.approx(Jo, rel=1e-5)
     assert gtg == pytest.approx(gto, rel=2e-3)
     scale = np.abs(gxo).max()
@@ -96,6 +102,18 @@ def test_channel_16_disks_gradient(imb):
     assert J2 == pytest.approx(J, rel=1e-8) and g_u2 == pytest.approx(g_u, rel=1e-12)
     assert g_tau2 == pytest.approx(g_tau, rel=1e-12)
     assert np.abs(g_x2 - g_x).max() <= 1e-12 * np.abs(g_x).max()
+    # binomial checkpointing: 41 states held instead of 40 + 100
+    g4 = imb.Lattice.from_workload(w)
+    J4, g_u4, g_tau4, g_x4 = g4.drag_gradient(T, snapshots=40)
+    f4 = g4.populations()
+    g4.close()
+    assert J4 == pytest.approx(J, rel=1e-8) and g_u4 == pytest.approx(g_u, rel=1e-12)
+    assert g_tau4 == pytest.approx(g_tau, rel=1e-12)
+    assert np.abs(g_x4 - g_x).max() <= 1e-12 * np.abs(g_x).max()
+    g5 = imb.Lattice.from_workload(w)   # the lattice is left T steps on, as after the uniform scheme
+    g5.step(T)
+    assert np.abs(g5.populations() - f4).max() < 1e-6
+    g5.close()
 
     def J_of(**kw):
         g3 = imb.Lattice.from_workload(W.c4(**kw))
@@ -109,17 +127,18 @@ def test_channel_16_disks_gradient(imb):
     assert g_tau == pytest.approx(fd_t, rel=2e-2)
 
 
-def test_autograd_wrapper_returns_the_library_gradient(imb):
+@pytest.mark.parametrize("scheme", [dict(checkpoint_every=10), dict(snapshots=3)])
+def test_autograd_wrapper_returns_the_library_gradient(imb, scheme):
     torch = pytest.importorskip("torch")
     from paper_1809_07008_gb300.autodiff import drag_mean
     w = _small("channel")
     u = torch.tensor(0.02, dtype=torch.float64, requires_grad=True)
     tau = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
     x = torch.tensor(w.x, dtype=torch.float64, requires_grad=True)
-    J = drag_mean(u, tau, x, w, 50, checkpoint_every=10)
+    J = drag_mean(u, tau, x, w, 50, **scheme)
     J.backward()
     g = imb.Lattice.from_workload(w)
-    Jr, g_u, g_tau, g_x = g.drag_gradient(50, checkpoint_every=10)
+    Jr, g_u, g_tau, g_x = g.drag_gradient(50, **scheme)
     assert J.item() == pytest.approx(Jr, rel=1e-8)
     assert u.grad.item() == pytest.approx(g_u, rel=1e-12)
     assert tau.grad.item() == pytest.approx(g_tau, rel=1e-12)

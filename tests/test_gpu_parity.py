@@ -242,10 +242,11 @@ def test_shifted_low_precision_forces_suspension(orc, imb, storage, tol):
     assert np.abs(Fg - Fo).max() / np.abs(Fo).max() < tol
 
 
-@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-2), ("bf16", 2e-2)])
 def test_shifted_low_precision_drag_channel(orc, imb, storage, tol):
     # channel with one fixed disk at u_in = 0.01 for 2000 steps: the drag comes from the
-    # small residual velocity inside the disk, where 16-bit storage is weakest
+    # small residual velocity inside the disk, where 16-bit storage is weakest (measured on a
+    # GB300: FP16 0.7 %, BF16 0.8 %; FP16 must stay below 1 %)
     w = W.c1(steps=2000)
     o, g = _run_pair(orc, imb, w, w.steps, storage=storage)
     Fo, _ = o.forces()
