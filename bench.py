@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the batched-sweep line (256 periodic domains, FP16, 5000 steps)")
     ap.add_argument("--sweep-steps", type=int, default=5000)
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the solid-fraction-0.40 suspension, collapse-box and channel lines")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--nx", type=int, default=None, help="smaller lattice at the same disk density")
     ap.add_argument("--ny", type=int, default=None)
@@ -313,7 +315,48 @@ def time_oracle(target_s=12.0, max_steps=2000):
     dt = time.perf_counter() - t0
     mlups = w.cells * steps / dt / 1e6
     return mlups, {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{w.name}, {steps} steps in {dt:.1f} s, FP64, single host thread"}
+                   "sample": f"{w.name}, {steps} steps in {dt:.1f} s, FP64, single host thread",
+                   "cpu": f"{cpu_model()}, {os.cpu_count()} logical cores on the host"}
+
+
+def time_workload(imb, torch, ts, w, storage, steps, warmup):
+    """MLUPS of ``steps`` coupling cycles of workload ``w`` (CUDA events on stream ``ts``) and
+    the average stream-collide launch with its HBM roofline fraction."""
+    lv = imb.Lattice.from_workload(w, storage=storage)
+    lv.set_stream(ts.cuda_stream)
+    lv.step(warmup)
+    lv.enable_kernel_timing(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ts)
+    lv.step_async(steps)
+    e1.record(ts)
+    torch.cuda.synchronize()
+    lv.sync()
+    vms = e0.elapsed_time(e1)
+    km, kn = lv.kernel_time()
+    kavg = km / max(kn, 1) * 1e-3
+    gbs = lv.bytes_per_cell() * w.cells / kavg / 1e9
+    peak, _ = measured_hbm_peak()
+    out = {"mlups": round(w.cells * steps / (vms * 1e-3) / 1e6, 1), "ms_per_step": round(vms / steps, 4),
+           "steps": steps, "particles": w.n_particles, "kernel_ms_avg": round(kavg * 1e3, 4),
+           "kernel_gbs": round(gbs, 1), "kernel_frac": round(gbs / peak, 4), "bytes_per_cell": lv.bytes_per_cell()}
+    lv.close()
+    del lv
+    torch.cuda.synchronize()
+    return out
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------- runs
@@ -412,33 +455,22 @@ def run_gpu(args):
     e2e = {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 40 * n,
            "d2h_bytes_per_step": 24 * n + 40 * n, "steps": e2e_steps}
 
-    variants = {}
-    if not args.no_variants and args.storage == "fp32" and rank == 0:
+    variants, others = {}, {}
+    if rank == 0 and ((not args.no_variants and args.storage == "fp32") or not args.no_other):
         lat.close()
         del lat
         torch.cuda.synchronize()
+    if not args.no_variants and args.storage == "fp32" and rank == 0:
         for st in ("fp16", "bf16"):
-            lv = imb.Lattice.from_workload(w, storage=st)
-            lv.set_stream(ts.cuda_stream)
-            lv.step(max(args.warmup, 3))
-            lv.enable_kernel_timing(True)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(ts)
-            lv.step_async(args.steps)
-            e1.record(ts)
-            torch.cuda.synchronize()
-            lv.sync()
-            vms = e0.elapsed_time(e1)
-            km, kn = lv.kernel_time()
-            kavg = km / max(kn, 1) * 1e-3
-            variants[st] = {"mlups": round(cells * args.steps / (vms * 1e-3) / 1e6, 1),
-                            "kernel_ms_avg": round(kavg * 1e3, 4),
-                            "kernel_gbs": round(lv.bytes_per_cell() * cells / kavg / 1e9, 1),
-                            "bytes_per_cell": lv.bytes_per_cell()}
-            lv.close()
-            del lv
-            torch.cuda.synchronize()
+            variants[st] = time_workload(imb, torch, ts, w, st, args.steps, max(args.warmup, 3))
+    if not args.no_other and rank == 0:
+        # the 8192 x 4096 suspension at solid fraction 0.40 (42 722 disks), the collapse box
+        # and the one-disk channel (in L2: launch-bound)
+        w40 = W.c3(n=42722).with_(name="c3_suspension_8192x4096_42722disks_phi040")
+        for st in ("fp32", "fp16"):
+            others[f"{w40.name}:{st}"] = time_workload(imb, torch, ts, w40, st, 100, 3)
+        others["c2_collapse_2048x1024_1000disks:fp32"] = time_workload(imb, torch, ts, W.c2(), "fp32", 200, 3)
+        others["c1_channel_200x100_1disk:fp32"] = time_workload(imb, torch, ts, W.c1(), "fp32", 2000, 10)
 
     gradient = None
     if not args.no_gradient and rank == 0:
@@ -465,6 +497,8 @@ def run_gpu(args):
                 "clocks": clocks}
         if variants:
             line["storage_variants"] = variants
+        if others:
+            line["other_workloads"] = others
         if gradient:
             line["drag_gradient"] = gradient
         if sweep:
