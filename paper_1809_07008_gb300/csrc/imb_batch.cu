@@ -78,16 +78,20 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     }
     const float ec = fminf(e, 1.0f), tm = te - 0.5f;
     const float B = __fdividef(ec * tm, (1.0f - ec) + tm);   // Eq. 14 (0 in uncovered cells)
-    const float fl = 1.0f - B, sf = 1.0f - 0.5f * omega;
+    const float fl = 1.0f - B, flw = -fl * omega, fls = fl * (1.0f - 0.5f * omega), Bd = B * drho;
     const float g = -3.0f * (ux * D.Fx + uy * D.Fy);
+    // d*_q = (1 - B) d_q - (1 - B) omega n_q + B n_{-q} + w_q [(1 - B)(1 - omega/2) S_q + B drho]
+    // with S_q / w_q = cF (3 + 9 cu) - 3 u.F (cF = c_q.F)
+    const float k0 = w_of(0) * fls, k1 = w_of(1) * fls, k5 = w_of(5) * fls;
+    const float b0 = w_of(0) * Bd, b1 = w_of(1) * Bd, b5 = w_of(5) * Bd;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
         const float cF = (float)cx_of(q) * D.Fx + (float)cy_of(q) * D.Fy;
-        const float Sq = fmaf(9.0f * cu, cF, fmaf(3.0f, cF, g));
-        const float fluid = fmaf(sf * w_of(q), Sq, -omega * n[q]);
-        const float solid = fmaf(w_of(q), drho, n[opp_of(q)]) - d[q];
-        Store<S>::st(outp + (size_t)q * D.plane, fmaf(B, solid, fmaf(fl, fluid, d[q])));
+        const float Sq = fmaf(cF, fmaf(9.0f, cu, 3.0f), g);
+        const float kq = q == 0 ? k0 : (q < 5 ? k1 : k5), bq = q == 0 ? b0 : (q < 5 ? b1 : b5);
+        const float v = fmaf(fl, d[q], fmaf(flw, n[q], fmaf(B, n[opp_of(q)], fmaf(kq, Sq, bq))));
+        Store<S>::st(outp + (size_t)q * D.plane, v);
     }
     r.B = B;
     r.jx = jx;
