@@ -100,11 +100,18 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     return r;
 }
 
+// stored value as loaded (converted to FP32 where it is used)
+template <typename S> __device__ __forceinline__ S ld_raw(const S *p) { return __ldg(p); }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 // A work item is a segment of 32 CPL cells of one row (the last segment of a row may be
 // shorter); items are numbered domain by domain, row by row.  Each warp takes an equal run of
 // consecutive items, so the warps finish together whatever the domain sizes, the rows a warp
 // visits one after another share their neighbour rows in L1, and the drag of a domain is
-// summed in registers until the warp leaves the domain.
+// summed in registers until the warp leaves the domain.  With one cell per lane the loads of
+// the next item of the same domain are issued before the arithmetic of the current one.
 template <typename S, int CPL>
 __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin, S *__restrict__ fout, const BatchDomain *__restrict__ dom,
                              int ndom, int nitems, const float *__restrict__ E, double *drag, unsigned *err) {
@@ -129,6 +136,66 @@ __global__ void __launch_bounds__(256, 3) k_batch_step(const S *__restrict__ fin
     int sg = it - D.item0[CPL - 1] - y * nseg;
     bool unstable = false;
     float fx_acc = 0.0f, fy_acc = 0.0f;
+    if constexpr (CPL == 1) {
+        S r[9];
+        float e = 0.0f;
+        auto fetch = [&](const BatchDomain &Dc, int yc, int sgc) {   // pull (Eq. 1), periodic wrap
+            const int x = sgc * 32 + lane, nx = Dc.nx, ny = Dc.ny, plane = (int)Dc.plane;
+            if (x >= nx) return;
+            const S *src = fin + Dc.off;
+            const int rm = (yc == 0 ? ny - 1 : yc - 1) * nx, r0 = yc * nx, rp = (yc == ny - 1 ? 0 : yc + 1) * nx;
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int xs = cx_of(q) == 0 ? x : (cx_of(q) == 1 ? xm : xp);
+                const int ys = cy_of(q) == 0 ? r0 : (cy_of(q) == 1 ? rm : rp);
+                r[q] = ld_raw(src + (q * plane + ys + xs));
+            }
+            e = __ldg(E + Dc.e_off + (size_t)yc * nx + x);
+        };
+        fetch(D, y, sg);
+        for (;;) {
+            float d[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) d[q] = to_f32(r[q]);
+            const float ec = e;
+            const int x = sg * 32 + lane;
+            const bool act = x < D.nx;
+            S *dst = fout + D.off + (size_t)y * D.nx + x;
+            ++it;
+            if (++sg == nseg) {
+                sg = 0;
+                ++y;
+            }
+            const bool last = it == end, leave = last || y == D.ny;
+            if (!leave) fetch(D, y, sg);   // in flight during this item's arithmetic
+            if (act) {
+                const RestNode c = rest_node(d, ec, D, dst);
+                if (!c.ok) unstable = true;   // Mach guard, also catches NaN
+                fx_acc = fmaf(c.B, c.jx - D.Fx, fx_acc);   // Eq. 15 with u_s = 0
+                fy_acc = fmaf(c.B, c.jy - D.Fy, fy_acc);
+            }
+            if (leave) {   // leaving the domain: add its drag
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fx_acc += __shfl_xor_sync(0xffffffffu, fx_acc, o);
+                    fy_acc += __shfl_xor_sync(0xffffffffu, fy_acc, o);
+                }
+                if (lane == 0 && (fx_acc != 0.0f || fy_acc != 0.0f)) {
+                    atomicAdd(&drag[2 * dd], (double)fx_acc);
+                    atomicAdd(&drag[2 * dd + 1], (double)fy_acc);
+                }
+                fx_acc = fy_acc = 0.0f;
+                if (last) break;
+                D = dom[++dd];
+                nseg = (D.nx + SEG - 1) / SEG;
+                y = 0;
+                fetch(D, y, sg);
+            }
+        }
+        if (__any_sync(0xffffffffu, unstable) && lane == 0) set_err(err, ERR_UNSTABLE);
+        return;
+    }
     for (;;) {
         const int nx = D.nx, ny = D.ny, plane = (int)D.plane;
         const S *src = fin + D.off;
