@@ -210,6 +210,12 @@ int imb_batch_run(imb_batch *b, int steps);
 int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block, int *cells_per_lane,
                        double *best_ms_per_step);
 
+/* Set the launch shape by hand: `block` threads per block (128, 256 or 512) and
+ * `cells_per_lane` (1 or 2) cells per lane along a row.  The state is unchanged.
+ * IMB_E_INVALID_ARG for another value or a block the kernel cannot launch (its
+ * registers); the previous shape is then kept. */
+int imb_batch_set_launch(imb_batch *b, int block, int cells_per_lane);
+
 /* Mean drag of every domain over the steps run so far: Fx_mean[n_domains],
  * Fy_mean[n_domains] (the force on the domain's disks, summed over them). */
 int imb_batch_mean_drag(imb_batch *b, double *Fx_mean, double *Fy_mean);

@@ -33,7 +33,7 @@ EXPORTS = (
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
     "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
     "imb_drag_gradient_binomial", "imb_binomial_schedule",
-    "imb_batch_create", "imb_batch_run", "imb_batch_autotune", "imb_batch_mean_drag",
+    "imb_batch_create", "imb_batch_run", "imb_batch_autotune", "imb_batch_set_launch", "imb_batch_mean_drag",
     "imb_batch_get_populations", "imb_batch_cells", "imb_batch_last_error", "imb_batch_destroy",
 )
 
@@ -141,6 +141,7 @@ def load(build_if_missing: bool = True):
     L.imb_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _dp, _dp, C.c_int]
     L.imb_batch_run.argtypes = [_vp, C.c_int]
     L.imb_batch_autotune.argtypes = [_vp, C.c_int, _ip, _ip, _dp]
+    L.imb_batch_set_launch.argtypes = [_vp, C.c_int, C.c_int]
     L.imb_batch_mean_drag.argtypes = [_vp, _dp, _dp]
     L.imb_batch_get_populations.argtypes = [_vp, C.c_int, _dp]
     L.imb_batch_cells.argtypes = [_vp]
@@ -386,6 +387,10 @@ class Batch:
         self._check(self._L.imb_batch_autotune(self.h, int(steps_per_trial), C.byref(blk), C.byref(cpl),
                                                C.byref(ms)))
         return blk.value, cpl.value, ms.value
+
+    def set_launch(self, block, cells_per_lane):
+        """Pin the launch shape (imb_batch_set_launch)."""
+        self._check(self._L.imb_batch_set_launch(self.h, int(block), int(cells_per_lane)))
 
     def mean_drag(self):
         fx, fy = np.zeros(self.n), np.zeros(self.n)

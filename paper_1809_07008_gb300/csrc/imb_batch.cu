@@ -581,6 +581,26 @@ extern "C" int imb_batch_autotune(imb_batch *b, int steps_per_trial, int *block,
     return IMB_OK;
 }
 
+extern "C" int imb_batch_set_launch(imb_batch *b, int block, int cells_per_lane) {
+    if (!b) return IMB_E_INVALID_ARG;
+    if ((block != 128 && block != 256 && block != 512) || (cells_per_lane != 1 && cells_per_lane != 2))
+        return bfail(b, IMB_E_INVALID_ARG, "block must be 128, 256 or 512 and cells_per_lane 1 or 2");
+    BCK(cudaSetDevice(b->device), "cudaSetDevice");
+    const int old_block = b->block, old_cpl = b->cpl;
+    b->cpl = cells_per_lane;
+    if (max_block(b) < block) {
+        b->cpl = old_cpl;
+        return bfail(b, IMB_E_INVALID_ARG, "the kernel cannot launch blocks of this size");
+    }
+    if (block != old_block || cells_per_lane != old_cpl) {
+        BCK(cudaStreamSynchronize(b->stream), "batch stream");
+        b->block = block;
+        b->grid = 0;
+        drop_graphs(b);
+    }
+    return IMB_OK;
+}
+
 extern "C" int imb_batch_mean_drag(imb_batch *b, double *Fx_mean, double *Fy_mean) {
     if (!b || !Fx_mean || !Fy_mean) return IMB_E_INVALID_ARG;
     int rc = batch_wait(b);

@@ -1,11 +1,12 @@
 """Batched sweep of independent periodic domains (imb_batch_*) against the FP64 oracle run on
 each domain by itself.
 
-* Three domains of different sizes, disk diameters, solid fractions, relaxation times, body
-  forces and Smagorinsky constants (0 and 0.1), 300 steps from rest: populations of every domain (FP32 storage: 1e-6; FP16: 2e-4,
-  the rounding of the stored deviation f - w accumulated over the steps) and the per-domain
-  mean drag (FP32: 1e-4 of the drag scale; FP16: 1 %, the storage bar the single-lattice tests
-  use).
+* Four domains of different sizes (one 75 x 41: rows that end inside a warp's segment), disk
+  diameters, solid fractions, relaxation times, body forces and Smagorinsky constants (0 and
+  0.1), 300 steps from rest, with one and with two cells per lane: populations of every domain
+  (FP32 storage: 1e-6; FP16: 2e-4, the rounding of the stored deviation f - w accumulated over
+  the steps) and the per-domain mean drag (FP32: 1e-4 of the drag scale; FP16: 1 %, the storage
+  bar the single-lattice tests use).
 * Steps taken two at a time by the replayed graph or one at a time give the same populations
   (bit for bit), the launch-shape search leaves the state as it found it, and steps with the
   shape it chose agree to FP32 rounding.
@@ -28,23 +29,32 @@ def imb():
 def _domains():
     return [W.c5_domain(0, 96, 64, 12.0, 0.2, 0.7, 1.0, 11, C_smag=0.0),
             W.c5_domain(1, 128, 96, 16.0, 0.3, 0.52, 30.0, 12),
-            W.c5_domain(2, 64, 64, 10.0, 0.12, 1.0, 0.5, 13)]
+            W.c5_domain(2, 64, 64, 10.0, 0.12, 1.0, 0.5, 13),
+            W.c5_domain(3, 75, 41, 11.0, 0.25, 0.6, 5.0, 14)]
+
+
+_ORACLE = {}
 
 
 def _oracle(orc, w, steps):
-    o = orc.Sim(w)
-    s = 0.0
-    for _ in range(steps):
-        o.step(1)
-        s += o.forces()[0][:, 0].sum()
-    return o.f(), s / steps
+    key = (w.name, steps)
+    if key not in _ORACLE:
+        o = orc.Sim(w)
+        s = 0.0
+        for _ in range(steps):
+            o.step(1)
+            s += o.forces()[0][:, 0].sum()
+        _ORACLE[key] = (o.f(), s / steps)
+    return _ORACLE[key]
 
 
-@pytest.mark.parametrize("storage,tol_f,tol_drag", [("fp32", 1e-6, 1e-4), ("fp16", 2e-4, 1e-2)])
-def test_batch_matches_oracle_per_domain(orc, imb, storage, tol_f, tol_drag):
+@pytest.mark.parametrize("storage,tol_f,tol_drag,shape", [("fp32", 1e-6, 1e-4, (256, 1)), ("fp32", 1e-6, 1e-4, (128, 2)),
+                                                          ("fp16", 2e-4, 1e-2, (256, 1)), ("fp16", 2e-4, 1e-2, (256, 2))])
+def test_batch_matches_oracle_per_domain(orc, imb, storage, tol_f, tol_drag, shape):
     ds = _domains()
     steps = 300
     b = imb.Batch(ds, storage=storage)
+    b.set_launch(*shape)
     b.run(steps)
     fx, _ = b.mean_drag()
     for k, w in enumerate(ds):
@@ -75,3 +85,17 @@ def test_graph_steps_equal_single_steps_and_autotune_keeps_state(imb):
         assert np.abs(b1.populations(k) - b2.populations(k)).max() < 1e-6
     b1.close()
     b2.close()
+
+
+def test_set_launch_rejects_bad_shapes_and_keeps_state(imb):
+    ds = _domains()
+    b = imb.Batch(ds, storage="fp32")
+    b.run(5)
+    before = [b.populations(k) for k in range(len(ds))]
+    for blk, cpl in ((64, 1), (256, 3), (1024, 1)):
+        with pytest.raises(imb.ImbError):
+            b.set_launch(blk, cpl)
+    b.set_launch(128, 2)
+    for k in range(len(ds)):
+        assert np.array_equal(b.populations(k), before[k])
+    b.close()
