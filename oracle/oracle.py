@@ -1,4 +1,5 @@
-"""ctypes wrapper and build step for the FP64 CPU oracle (``imb_oracle.c``).
+"""ctypes wrapper and build step for the FP64 CPU oracle (``imb_oracle.c``, and the 3D
+D3Q19 lattice with spheres in ``imb_oracle3.c``).
 
 TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -18,6 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liborc.so")
 SRC = os.path.join(HERE, "imb_oracle.c")
 HDR = os.path.join(HERE, "imb_oracle.h")
+SRC3 = os.path.join(HERE, "imb_oracle3.c")
+HDR3 = os.path.join(HERE, "imb_oracle3.h")
 
 PERIODIC, WALL, INLET_OUTLET = 0, 1, 2
 EPS_EXACT, EPS_SUBCELL = 0, 1
@@ -27,12 +30,13 @@ MAX_SLOTS = 4
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library (plain gcc, no GPU code)."""
     os.makedirs(BUILD, exist_ok=True)
+    srcs = (SRC, HDR, SRC3, HDR3)
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(HDR))):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(x) for x in srcs)):
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           SRC, "-o", tmp, "-lm"]
+           SRC, SRC3, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -50,6 +54,13 @@ class Params(C.Structure):
                 ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double)]
+
+
+class Params3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("tau", C.c_double),
+                ("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
+                ("n_sub", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double), ("uy0", C.c_double),
+                ("uz0", C.c_double)]
 
 
 _lib = None
@@ -91,6 +102,20 @@ def lib():
         L.orc_wall_contact_xi.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_wall_contact_xi.restype = C.c_double
         L.orc_drag_adjoint.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc3_lattice.argtypes = [_ip, _dp]
+        L.orc3_feq.argtypes = [C.c_double] * 4 + [_dp]
+        L.orc3_omega_s.argtypes = [_dp] + [C.c_double] * 7 + [_dp]
+        L.orc3_subcell_count.argtypes = [C.c_int] * 3 + [C.c_double] * 4 + [C.c_int]
+        L.orc3_new.argtypes = [C.POINTER(Params3)]
+        L.orc3_new.restype = C.c_void_p
+        L.orc3_free.argtypes = [C.c_void_p]
+        L.orc3_set_spheres.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc3_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc3_get_f.argtypes = [C.c_void_p, _dp]
+        L.orc3_set_f.argtypes = [C.c_void_p, _dp]
+        L.orc3_get_macro.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc3_get_forces.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc3_cell_map.argtypes = [C.c_void_p, _ip, _ip]
         _lib = L
     return _lib
 
@@ -273,3 +298,91 @@ class Sim:
             self.step(1)
             s += self.forces()[0][:, 0].sum()
         return s / T
+
+
+# ------------------------------------------------------------------- 3D (D3Q19)
+def lattice3():
+    c = np.zeros((19, 3), dtype=np.int32)
+    w = np.zeros(19)
+    lib().orc3_lattice(_i(c), _d(w))
+    return c, w
+
+
+def feq3(rho, ux, uy, uz):
+    out = np.zeros(19)
+    lib().orc3_feq(rho, ux, uy, uz, _d(out))
+    return out
+
+
+def omega_s3(f19, rho, u, us):
+    f19 = np.ascontiguousarray(f19, dtype=np.float64)
+    out = np.zeros(19)
+    lib().orc3_omega_s(_d(f19), rho, u[0], u[1], u[2], us[0], us[1], us[2], _d(out))
+    return out
+
+
+def subcell_count3(off, frac, R, n):
+    return lib().orc3_subcell_count(int(off[0]), int(off[1]), int(off[2]), float(frac[0]), float(frac[1]),
+                                    float(frac[2]), float(R), int(n))
+
+
+class Sim3:
+    """One 3D oracle simulation (``workloads.Workload3``): D3Q19 with held spheres."""
+
+    def __init__(self, w):
+        self.w = w
+        p = Params3()
+        p.nx, p.ny, p.nz = w.nx, w.ny, w.nz
+        p.tau, p.wall_y = w.tau, int(w.wall_y)
+        p.Fx, p.Fy, p.Fz = w.force
+        p.n_sub = w.n_sub
+        p.rho0 = w.rho0
+        p.ux0, p.uy0, p.uz0 = w.u0
+        self.p = p
+        self.h = lib().orc3_new(C.byref(p))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+        self.np = len(w.R)
+        x = np.ascontiguousarray(w.x, dtype=np.float64).reshape(-1)
+        v = np.ascontiguousarray(w.v, dtype=np.float64).reshape(-1)
+        om = np.ascontiguousarray(w.omega, dtype=np.float64).reshape(-1)
+        R = np.ascontiguousarray(w.R, dtype=np.float64).reshape(-1)
+        rc = lib().orc3_set_spheres(self.h, self.np, _d(x), _d(v), _d(om), _d(R))
+        if rc:
+            raise ValueError(f"oracle rejected the spheres ({rc})")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc3_free(self.h)
+            self.h = None
+
+    def step(self, n=1):
+        lib().orc3_step(self.h, n)
+
+    def f(self):
+        out = np.zeros((19, self.w.nz, self.w.ny, self.w.nx))
+        lib().orc3_get_f(self.h, _d(out))
+        return out
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        lib().orc3_set_f(self.h, _d(f))
+
+    def macro(self):
+        shp = (self.w.nz, self.w.ny, self.w.nx)
+        rho, ux, uy, uz = (np.zeros(shp) for _ in range(4))
+        lib().orc3_get_macro(self.h, _d(rho), _d(ux), _d(uy), _d(uz))
+        return rho, ux, uy, uz
+
+    def forces(self):
+        F = np.zeros((max(self.np, 1), 3))
+        T = np.zeros((max(self.np, 1), 3))
+        lib().orc3_get_forces(self.h, _d(F), _d(T))
+        return F[:self.np], T[:self.np]
+
+    def cell_map(self):
+        shp = (self.w.nz, self.w.ny, self.w.nx, 4)
+        sph = np.zeros(shp, dtype=np.int32)
+        cnt = np.zeros(shp, dtype=np.int32)
+        lib().orc3_cell_map(self.h, _i(sph), _i(cnt))
+        return sph, cnt

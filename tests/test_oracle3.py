@@ -1,0 +1,182 @@
+"""Pins of the 3D (D3Q19) oracle against what the paper and the mathematics fix.
+
+* Lattice (Tab. 1): weights sum to one; isotropy of the second and fourth velocity moments
+  (sum w c_a c_b = 1/3 delta_ab, sum w c_a c_b c_c c_d = 1/9 (delta delta + ...)), the
+  opposite of each velocity; the equilibrium's moments in closed form (rho, rho u,
+  rho (u u + I/3)).
+* Eq. 12: the solid operator conserves mass and, at u_s = u, is the bounce-back of the
+  non-equilibrium part; its momentum is rho (u_s - u) summed with that bounce-back.
+* Sub-cell solid ratio (Sec. 2.3): hand-worked counts (n_sub = 1: cell centre; n_sub = 2:
+  a sphere between the sub-cell centres), cells wholly inside count n^3 and cells wholly
+  outside 0, and the summed solid ratio converges to the sphere's volume as n_sub grows.
+* Whole steps: mass conserved to 1e-12 with walls, a body force and spinning moving-surface
+  spheres; plane Poiseuille flow between halfway bounce-back walls is exact at
+  tau = 1/2 + sqrt(3)/4 (the BGK wall slip vanishes there); a sphere in the middle of a
+  symmetric channel feels no lift, no side force and no torque; in an all-periodic box the
+  steady drag equals the body force times sum_j (1 - B_j) (the momentum the fluid does not
+  keep), to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def O(orc):
+    return orc
+
+
+def test_lattice_moments_and_equilibrium(O):
+    c, w = O.lattice3()
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs((w[:, None] * c).sum(0)).max() < 1e-16
+    I = np.eye(3)
+    m2 = np.einsum("q,qa,qb->ab", w, c, c)
+    assert np.abs(m2 - I / 3.0).max() < 1e-15
+    m4 = np.einsum("q,qa,qb,qc,qd->abcd", w, c, c, c, c)
+    iso = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I) + np.einsum("ad,bc->abcd", I, I)) / 9.0
+    assert np.abs(m4 - iso).max() < 1e-15
+    for q in range(1, 19):
+        o = q + 1 if q % 2 else q - 1
+        assert np.array_equal(c[o], -c[q])
+    assert sorted(map(tuple, c.tolist())) == sorted(
+        [(0, 0, 0)] + [tuple(s * np.eye(3, dtype=int)[a]) for a in range(3) for s in (1, -1)] +
+        [(a, b, 0) for a in (1, -1) for b in (1, -1)] + [(a, 0, b) for a in (1, -1) for b in (1, -1)] +
+        [(0, a, b) for a in (1, -1) for b in (1, -1)])
+    rho, u = 1.07, np.array([0.03, -0.02, 0.011])
+    fe = O.feq3(rho, *u)
+    assert abs(fe.sum() - rho) < 1e-14
+    assert np.abs((fe[:, None] * c).sum(0) - rho * u).max() < 1e-15
+    P = np.einsum("q,qa,qb->ab", fe, c, c)
+    assert np.abs(P - rho * (np.outer(u, u) + I / 3.0)).max() < 1e-15
+
+
+def test_solid_operator_identities(O):
+    c, _ = O.lattice3()
+    rng = np.random.default_rng(5)
+    rho, u = 1.02, np.array([0.02, 0.01, -0.015])
+    f = O.feq3(rho, *u) + 1e-3 * rng.standard_normal(19)
+    # moments of f define rho and u
+    rho = f.sum()
+    u = (f[:, None] * c).sum(0) / rho
+    us = np.array([-0.01, 0.005, 0.02])
+    om = O.omega_s3(f, rho, u, us)
+    assert abs(om.sum()) < 1e-15
+    fe = O.feq3(rho, *u)
+    neq = f - fe
+    opp = [0] + [q + 1 if q % 2 else q - 1 for q in range(1, 19)]
+    om0 = O.omega_s3(f, rho, u, u)
+    assert np.abs(om0 - (neq[opp] - neq)).max() < 1e-16
+    # momentum: the non-equilibrium bounce-back's plus rho (u_s - u)
+    mom = (om[:, None] * c).sum(0)
+    assert np.abs(mom - ((neq[opp] - neq)[:, None] * c).sum(0) - rho * (us - u)).max() < 1e-15
+
+
+def test_subcell_counts_by_hand(O):
+    # n_sub = 1: the cell counts when its centre is in the sphere (a centre on the surface counts)
+    assert O.subcell_count3((0, 0, 0), (0.5, 0.5, 0.5), 0.01, 1) == 1
+    assert O.subcell_count3((1, 0, 0), (0.5, 0.5, 0.5), 0.99, 1) == 0
+    assert O.subcell_count3((1, 0, 0), (0.5, 0.5, 0.5), 1.0, 1) == 1
+    # n_sub = 2: sub-cell centres at distance sqrt(3)/4 = 0.4330 from the cell centre
+    assert O.subcell_count3((0, 0, 0), (0.5, 0.5, 0.5), 0.433, 2) == 0
+    assert O.subcell_count3((0, 0, 0), (0.5, 0.5, 0.5), 0.4331, 2) == 8
+    # a sphere centred on a cell corner reaches one sub-cell centre of each of the 8 cells
+    for off in [(a, b, cc) for a in (0, -1) for b in (0, -1) for cc in (0, -1)]:
+        assert O.subcell_count3(off, (0.0, 0.0, 0.0), 0.44, 2) == 1
+
+
+def test_subcell_whole_cells_and_volume(O):
+    R, frac = 4.3, (0.37, 0.61, 0.18)
+    span = int(math.ceil(R)) + 1
+    prev = None
+    for n in (2, 5, 10):
+        tot = 0
+        for di in range(-span, span + 1):
+            for dj in range(-span, span + 1):
+                for dk in range(-span, span + 1):
+                    k = O.subcell_count3((di, dj, dk), frac, R, n)
+                    lo = np.array([di, dj, dk]) - np.array(frac)
+                    hi = lo + 1.0
+                    far = np.maximum(np.abs(lo), np.abs(hi))
+                    near = np.where(lo > 0, lo, np.where(hi < 0, -hi, 0.0))
+                    if (far ** 2).sum() < R * R * (1 - 1e-12):
+                        assert k == n ** 3
+                    if (near ** 2).sum() > R * R * (1 + 1e-12):
+                        assert k == 0
+                    tot += k
+        vol = tot / n ** 3
+        err = abs(vol - 4.0 / 3.0 * math.pi * R ** 3) / (4.0 / 3.0 * math.pi * R ** 3)
+        if prev is not None:
+            assert err < prev or err < 2e-3
+        prev = err
+    assert prev < 3e-3
+
+
+def test_mass_conserved_with_walls_force_and_moving_surfaces(O):
+    w = W.spheres3(nx=20, ny=14, nz=18, n=2, r_lo=2.5, r_hi=3.5, seed=11, tau=0.62)
+    assert w.n_spheres == 2
+    s = O.Sim3(w)
+    m0 = s.macro()[0].sum()
+    s.step(150)
+    assert abs(s.macro()[0].sum() - m0) < 1e-12 * m0
+    F, T = s.forces()
+    assert np.abs(F).max() > 0 and np.abs(T).max() > 0
+
+
+def test_plane_poiseuille_exact_at_magic_tau(O):
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    H, g = 12, 1e-6
+    w = W.Workload3(name="poiseuille3", nx=3, ny=H, nz=3, tau=tau, wall_y=True, force=(g, 0.0, 0.0))
+    s = O.Sim3(w)
+    nu = (tau - 0.5) / 3.0
+    s.step(int(40 * H * H / nu / math.pi ** 2))
+    _, ux, uy, uz = s.macro()
+    y = np.arange(H) + 0.5
+    exact = g / (2 * nu) * y * (H - y)
+    prof = ux[:, :, :].mean(axis=(0, 2))
+    assert np.abs(ux - exact[None, :, None]).max() < 1e-10 * exact.max()
+    assert np.abs(prof - exact).max() / exact.max() < 1e-10
+    assert np.abs(uy).max() < 1e-14 and np.abs(uz).max() < 1e-14
+
+
+def test_symmetric_channel_sphere_has_drag_only(O):
+    # sphere centred on a cell corner in the middle of the channel: the lattice is symmetric
+    # under y -> H - y and z -> L - z through the centre, so only F_x survives
+    N, L, H = 4, 16, 12
+    w = W.Workload3(name="sym3", nx=L, ny=H, nz=L, tau=0.8, wall_y=True, force=(1e-5, 0.0, 0.0),
+                    x=np.array([[L / 2, H / 2, L / 2]]), v=np.zeros((1, 3)), omega=np.zeros((1, 3)),
+                    R=np.array([N / 2 + 0.3]))
+    s = O.Sim3(w)
+    s.step(300)
+    F, T = s.forces()
+    assert F[0, 0] > 0.0
+    assert abs(F[0, 1]) < 1e-12 * F[0, 0] and abs(F[0, 2]) < 1e-12 * F[0, 0]
+    assert np.abs(T).max() < 1e-12 * F[0, 0] * w.R[0]
+
+
+def test_drag_momentum_balance_periodic_box(O):
+    # all-periodic box: at steady state each cell gains (1 - B_j) g per step from the forcing
+    # and the sphere takes the rest, so F_x = g sum_j (1 - B_j); no lateral force, no torque
+    # (the sphere sits on a cell corner in the middle of the box)
+    L, tau, g, R = 12, 1.0, 1e-6, 2.6
+    w = W.Workload3(name="box3", nx=L, ny=L, nz=L, tau=tau, wall_y=False, force=(g, 0.0, 0.0),
+                    x=np.array([[L / 2, L / 2, L / 2]]), v=np.zeros((1, 3)), omega=np.zeros((1, 3)),
+                    R=np.array([R]))
+    s = O.Sim3(w)
+    prev = None
+    for _ in range(40):
+        s.step(100)
+        F, T = s.forces()
+        if prev is not None and abs(F[0, 0] - prev) < 1e-14 * abs(F[0, 0]):
+            break
+        prev = F[0, 0]
+    sph, cnt = s.cell_map()
+    eps = np.minimum(1.0, cnt.sum(axis=-1) / w.n_sub ** 3)
+    B = eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5))
+    expect = g * np.sum(1.0 - B)
+    assert abs(F[0, 0] - expect) / expect < 1e-10
+    assert abs(F[0, 1]) < 1e-9 * expect and abs(F[0, 2]) < 1e-9 * expect
+    assert np.abs(T).max() < 1e-9 * expect * R

@@ -21,6 +21,10 @@ Workloads (lattice units, dx = dt = 1, rho0 = 1):
             random sequential addition with a one-cell gap, random velocities of
             magnitude 0.005, tau = 0.51, Smagorinsky C = 0.1, DEM on, no gravity.
   * ``c3sub`` the 512 x 512 subdomain of ``c3`` at the same number density.
+  * ``happel``  3D (D3Q19): plane Poiseuille flow between walls y = 0 and y = 5N past one
+            held sphere of diameter N cells a quarter of the way across, periodic in x and z
+            with l_x = l_z = 20 N (the paper's Sec. 3.1 case in lattice units).
+  * ``spheres3`` small 3D boxes with seeded held spheres (parity cases).
 """
 from __future__ import annotations
 
@@ -320,3 +324,95 @@ def poiseuille(H=32, nx=4, tau=0.6, g=1.0e-6, steps=20000) -> Workload:
 
 
 WORKLOADS = {"c1": c1, "c2": c2, "c3": c3, "c3sub": c3sub, "c4": c4}
+
+
+# ------------------------------------------------------------------- 3D (D3Q19)
+@dataclass
+class Workload3:
+    """3D lattice with held spheres: x and z periodic, y walls (``wall_y``) or periodic."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    wall_y: bool = True
+    force: tuple = (0.0, 0.0, 0.0)
+    n_sub: int = 5
+    rho0: float = 1.0
+    u0: tuple = (0.0, 0.0, 0.0)
+    steps: int = 1000
+    x: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    v: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    omega: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    R: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def n_spheres(self) -> int:
+        return int(self.R.shape[0])
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def with_(self, **kw) -> "Workload3":
+        return replace(self, **kw)
+
+
+def happel(N=5, tau=1.0, n_sub=5, u_c=2.0e-4, steps=None) -> Workload3:
+    """Poiseuille flow past a held sphere (the paper's first benchmark) at N cells per
+    diameter: walls 5 N apart, sphere centre N 5/4 from the lower wall and half-way in x and z,
+    l_x = l_z = 20 N.  The body force g makes the undisturbed velocity at the centre height
+    u_c = 3 g H^2 / (32 nu) (plane Poiseuille flow u(y) = g y (H - y) / (2 nu))."""
+    H = 5 * N
+    L = 20 * N
+    nu = (tau - 0.5) / 3.0
+    g = u_c * 32.0 * nu / (3.0 * H * H)
+    if steps is None:   # about five viscous times of the wall gap
+        steps = int(5.0 * H * H / (nu * math.pi ** 2)) + 500
+    x = np.array([[L / 2.0, H / 4.0, L / 2.0]])
+    return Workload3(name=f"happel_N{N}_tau{tau:g}_nsub{n_sub}", nx=L, ny=H, nz=L, tau=tau, wall_y=True,
+                     force=(g, 0.0, 0.0), n_sub=n_sub, steps=steps, x=x, v=np.zeros((1, 3)),
+                     omega=np.zeros((1, 3)), R=np.array([N / 2.0]))
+
+
+def spheres3(nx=40, ny=24, nz=36, n=3, r_lo=2.5, r_hi=5.0, seed=3, tau=0.7, wall_y=True,
+             force=(2.0e-5, 0.0, 1.0e-5), speed=0.004, spin=0.001, n_sub=5, gap=2.0) -> Workload3:
+    """Up to ``n`` spheres by random sequential addition (surfaces at least ``gap`` cells
+    apart and from the walls), random velocities of magnitude ``speed`` and spins of
+    magnitude ``spin`` (they enter u_s only: the spheres are held)."""
+    rng = SplitMix64(seed)
+    pts, rad = [], []
+    for _ in range(200 * n):
+        if len(pts) == n:
+            break
+        r = rng.uniform_range(r_lo, r_hi)
+        c = np.array([rng.uniform_range(0.0, nx), rng.uniform_range(0.0, ny), rng.uniform_range(0.0, nz)])
+        if wall_y and (c[1] - r < gap or c[1] + r > ny - gap):
+            continue
+        ok = True
+        for p, rp in zip(pts, rad):
+            d = c - p
+            d[0] -= nx * round(d[0] / nx)
+            d[2] -= nz * round(d[2] / nz)
+            if not wall_y:
+                d[1] -= ny * round(d[1] / ny)
+            if float(np.sqrt((d * d).sum())) < r + rp + gap:
+                ok = False
+                break
+        if ok:
+            pts.append(c)
+            rad.append(r)
+    m = len(pts)
+    v = np.array([_unit3(rng) * speed for _ in range(m)]).reshape(-1, 3)
+    om = np.array([_unit3(rng) * spin for _ in range(m)]).reshape(-1, 3)
+    return Workload3(name=f"spheres3_{nx}x{ny}x{nz}_{m}", nx=nx, ny=ny, nz=nz, tau=tau, wall_y=wall_y,
+                     force=force, n_sub=n_sub, x=np.array(pts).reshape(-1, 3), v=v, omega=om,
+                     R=np.array(rad))
+
+
+def _unit3(rng):
+    while True:
+        a = np.array([rng.uniform_range(-1.0, 1.0) for _ in range(3)])
+        n2 = float((a * a).sum())
+        if 1e-6 < n2 <= 1.0:
+            return a / math.sqrt(n2)
