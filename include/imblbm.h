@@ -286,6 +286,67 @@ const char *imb_last_error(imb_ctx *ctx);
 /* Free the context and its device memory.  NULL is accepted. */
 void imb_destroy(imb_ctx *ctx);
 
+/* ---- the paper's own lattice: D3Q19 with held spheres (Sec. 2.1, Tab. 1) ----
+ * An nx x ny x nz lattice, x and z periodic, y periodic or bounded by halfway
+ * bounce-back walls at y = 0 and y = ny (cell (i, j, k) is [i, i+1) x [j, j+1) x
+ * [k, k+1), its node at the centre).  BGK collision with Guo forcing for the body
+ * force (weighted by 1 - B), the partially saturated collision of Eqs. 12-14 in
+ * cells a sphere covers, the solid ratio of a cell being the fraction of its
+ * n_sub^3 sub-cell centres inside the sphere (a centre on the surface counts,
+ * Sec. 2.3), and per-sphere force and torque (Eqs. 15-16, the force ON the sphere).
+ * Spheres are held in place; their velocity and spin enter u_s = v + w x r.  A cell
+ * may be covered by one sphere only.  Populations are stored as f_i - w_i, SoA
+ * [19][nz][ny][nx], x fastest.  Velocity order: 0 rest; 1-6 (+x, -x, +y, -y, +z,
+ * -z); 7-18 (+x+y, -x-y, +x-y, -x+y, +x+z, -x-z, +x-z, -x+z, +y+z, -y-z, +y-z, -y+z). */
+typedef struct imb3_ctx imb3_ctx;
+
+typedef struct imb3_params {
+    int wall_y;               /* 1: walls at y = 0 and y = ny; 0: periodic in y */
+    double Fx, Fy, Fz;        /* body force density on the fluid */
+    int n_sub;                /* sub-cells per axis for the solid ratio, 1..10 */
+    int storage;              /* IMB_STORE_* */
+    double rho0, ux0, uy0, uz0; /* initial state: f* = f^eq(rho0, u0) everywhere */
+    int timeout_ms;           /* bound of every host wait */
+} imb3_params;
+
+/* Defaults: walls in y, no force, n_sub = 5, FP32, rho0 = 1, at rest, 60 s. */
+void imb3_default_params(imb3_params *p);
+
+/* Create the lattice (p may be NULL for the defaults).  IMB_E_INVALID_ARG for a size
+ * below 3, tau <= 1/2, n_sub outside 1..10 or a bad storage code; IMB_E_NOMEM /
+ * IMB_E_CUDA on device failures (then *out may hold a context to destroy). */
+int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_params *p);
+
+/* Set n held spheres: centres x[3n] (inside the lattice), velocities v[3n], spins
+ * omega[3n], radii R[n] (host arrays, copied); builds the cell map on the GPU.
+ * IMB_E_INVALID_ARG for a radius outside (0, 1000], a centre outside, or a periodic
+ * extent below 2 (R + 2); IMB_E_OVERFLOW when two spheres cover one cell. */
+int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const double *v, const double *omega, const double *R);
+
+/* Advance n steps and wait (bounded).  IMB_E_UNSTABLE on NaN or |u| >= 0.3. */
+int imb3_step(imb3_ctx *c, int n);
+
+/* f(x, t) as FP64 [19][nz][ny][nx] (the pull of the stored post-collision field). */
+int imb3_get_populations(imb3_ctx *c, double *f);
+
+/* rho and u of f(x, t) (u with the half-force shift), each [nz][ny][nx]. */
+int imb3_get_macro(imb3_ctx *c, double *rho, double *ux, double *uy, double *uz);
+
+/* Force F[3n] and torque T[3n] on each sphere from the last step. */
+int imb3_get_forces(imb3_ctx *c, double *F, double *T);
+
+/* Per cell: the covering sphere (-1: none) and its sub-cell count, each [nz][ny][nx]. */
+int imb3_get_cell_map(imb3_ctx *c, int *sphere, int *count);
+
+/* CUDA-event timing of every stream-collide launch (as imb_enable_kernel_timing). */
+int imb3_enable_kernel_timing(imb3_ctx *c, int on);
+int imb3_kernel_time(imb3_ctx *c, double *ms, long long *launches);
+long long imb3_launch_count(imb3_ctx *c);
+/* Algorithmic bytes per cell update: 19 loads + 19 stores of the storage type. */
+double imb3_bytes_per_cell(imb3_ctx *c);
+const char *imb3_last_error(imb3_ctx *c);
+void imb3_destroy(imb3_ctx *c);
+
 #ifdef __cplusplus
 }
 #endif

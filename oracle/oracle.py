@@ -9,6 +9,7 @@ it.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -386,3 +387,26 @@ class Sim3:
         cnt = np.zeros(shp, dtype=np.int32)
         lib().orc3_cell_map(self.h, _i(sph), _i(cnt))
         return sph, cnt
+
+
+def happel_brenner(R, l, U, rho, nu):
+    """Eqs. 18-19: drag and torque on a held sphere of radius R whose centre is a distance l
+    from a plane wall, in a shear flow whose undisturbed velocity at the centre is U (density
+    rho, kinematic viscosity nu).  (The paper's printed values for its case follow with l the
+    centre's distance from the nearer wall and U the Poiseuille velocity at the centre.)"""
+    a = R / l
+    F = 6.0 * math.pi * rho * nu * R * U * (1.0 - a ** 2 / 9.0) / (1.0 - 0.6526 * a + 0.316 * a ** 3 - 0.242 * a ** 4)
+    T = 8.0 / 3.0 * math.pi * rho * nu * R ** 2 * U * a * (1.0 + 0.0758 * a + 0.049 * a ** 2)
+    return F, T
+
+
+def happel_table2():
+    """The paper's Table 2 rows (tests/golden/happel_table2.txt): (N, n_sub, tau, err_F %, err_T %)."""
+    path = os.path.join(os.path.dirname(HERE), "tests", "golden", "happel_table2.txt")
+    rows = []
+    for ln in open(path):
+        ln = ln.strip()
+        if ln and not ln.startswith("#"):
+            a = ln.split()
+            rows.append((int(a[0]), int(a[1]), float(a[2]), float(a[3]), float(a[4])))
+    return rows

@@ -33,6 +33,9 @@ EXPORTS = (
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
     "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
     "imb_drag_gradient_binomial", "imb_binomial_schedule",
+    "imb3_default_params", "imb3_init", "imb3_set_spheres", "imb3_step", "imb3_get_populations",
+    "imb3_get_macro", "imb3_get_forces", "imb3_get_cell_map", "imb3_enable_kernel_timing",
+    "imb3_kernel_time", "imb3_launch_count", "imb3_bytes_per_cell", "imb3_last_error", "imb3_destroy",
     "imb_batch_create", "imb_batch_run", "imb_batch_autotune", "imb_batch_set_launch", "imb_batch_mean_drag",
     "imb_batch_get_populations", "imb_batch_cells", "imb_batch_last_error", "imb_batch_destroy",
 )
@@ -69,6 +72,13 @@ class ImbError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class Params3(C.Structure):
+    """Mirror of imb3_params (include/imblbm.h)."""
+    _fields_ = [("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
+                ("n_sub", C.c_int), ("storage", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double),
+                ("uy0", C.c_double), ("uz0", C.c_double), ("timeout_ms", C.c_int)]
 
 
 class Params(C.Structure):
@@ -150,6 +160,25 @@ def load(build_if_missing: bool = True):
     L.imb_batch_last_error.restype = C.c_char_p
     L.imb_batch_destroy.argtypes = [_vp]
     L.imb_batch_destroy.restype = None
+    L.imb3_default_params.argtypes = [C.POINTER(Params3)]
+    L.imb3_default_params.restype = None
+    L.imb3_init.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(Params3)]
+    L.imb3_set_spheres.argtypes = [_vp, C.c_int, _dp, _dp, _dp, _dp]
+    L.imb3_step.argtypes = [_vp, C.c_int]
+    L.imb3_get_populations.argtypes = [_vp, _dp]
+    L.imb3_get_macro.argtypes = [_vp, _dp, _dp, _dp, _dp]
+    L.imb3_get_forces.argtypes = [_vp, _dp, _dp]
+    L.imb3_get_cell_map.argtypes = [_vp, _ip, _ip]
+    L.imb3_enable_kernel_timing.argtypes = [_vp, C.c_int]
+    L.imb3_kernel_time.argtypes = [_vp, _dp, C.POINTER(C.c_longlong)]
+    L.imb3_launch_count.argtypes = [_vp]
+    L.imb3_launch_count.restype = C.c_longlong
+    L.imb3_bytes_per_cell.argtypes = [_vp]
+    L.imb3_bytes_per_cell.restype = C.c_double
+    L.imb3_last_error.argtypes = [_vp]
+    L.imb3_last_error.restype = C.c_char_p
+    L.imb3_destroy.argtypes = [_vp]
+    L.imb3_destroy.restype = None
     _lib = L
     return L
 
@@ -410,6 +439,100 @@ class Batch:
         if getattr(self, "h", None):
             self._L.imb_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice3:
+    """A D3Q19 lattice with held spheres (imb3_*; the paper's own lattice)."""
+
+    def __init__(self, nx, ny, nz, tau, wall_y=True, force=(0.0, 0.0, 0.0), n_sub=5, storage="fp32",
+                 rho0=1.0, u0=(0.0, 0.0, 0.0)):
+        L = load()
+        p = Params3()
+        L.imb3_default_params(C.byref(p))
+        p.wall_y = int(bool(wall_y))
+        p.Fx, p.Fy, p.Fz = map(float, force)
+        p.n_sub = int(n_sub)
+        p.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+        p.rho0 = float(rho0)
+        p.ux0, p.uy0, p.uz0 = map(float, u0)
+        h = _vp()
+        rc = L.imb3_init(C.byref(h), int(nx), int(ny), int(nz), float(tau), C.byref(p))
+        if rc != IMB_OK:
+            msg = L.imb3_last_error(h if h.value else None).decode()
+            if h.value:
+                L.imb3_destroy(h)
+            raise ImbError(rc, msg)
+        self._L, self.h, self.params = L, h, p
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.np = 0
+
+    @classmethod
+    def from_workload(cls, w, storage="fp32"):
+        lat = cls(w.nx, w.ny, w.nz, w.tau, wall_y=w.wall_y, force=w.force, n_sub=w.n_sub, storage=storage,
+                  rho0=w.rho0, u0=w.u0)
+        if w.n_spheres:
+            lat.set_spheres(w.x, w.v, w.omega, w.R)
+        return lat
+
+    def _check(self, rc):
+        if rc != IMB_OK:
+            raise ImbError(rc, self._L.imb3_last_error(self.h).decode())
+
+    def set_spheres(self, x, v, omega, R):
+        n = int(np.asarray(R).reshape(-1).shape[0])
+        self._check(self._L.imb3_set_spheres(self.h, n, _d(_f64(x, 3 * n)), _d(_f64(v, 3 * n)),
+                                             _d(_f64(omega, 3 * n)), _d(_f64(R, n))))
+        self.np = n
+
+    def step(self, n=1):
+        self._check(self._L.imb3_step(self.h, int(n)))
+
+    def populations(self):
+        out = np.zeros((19, self.nz, self.ny, self.nx))
+        self._check(self._L.imb3_get_populations(self.h, _d(out)))
+        return out
+
+    def macro(self):
+        shp = (self.nz, self.ny, self.nx)
+        rho, ux, uy, uz = (np.zeros(shp) for _ in range(4))
+        self._check(self._L.imb3_get_macro(self.h, _d(rho), _d(ux), _d(uy), _d(uz)))
+        return rho, ux, uy, uz
+
+    def forces(self):
+        F, T = np.zeros((max(self.np, 1), 3)), np.zeros((max(self.np, 1), 3))
+        self._check(self._L.imb3_get_forces(self.h, _d(F), _d(T)))
+        return F[:self.np], T[:self.np]
+
+    def cell_map(self):
+        shp = (self.nz, self.ny, self.nx)
+        sph, cnt = np.zeros(shp, dtype=np.int32), np.zeros(shp, dtype=np.int32)
+        self._check(self._L.imb3_get_cell_map(self.h, sph.ctypes.data_as(_ip), cnt.ctypes.data_as(_ip)))
+        return sph, cnt
+
+    def enable_kernel_timing(self, on=True):
+        self._check(self._L.imb3_enable_kernel_timing(self.h, int(bool(on))))
+
+    def kernel_time(self):
+        ms, n = C.c_double(0.0), C.c_longlong(0)
+        self._check(self._L.imb3_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self):
+        return self._L.imb3_launch_count(self.h)
+
+    def bytes_per_cell(self):
+        return self._L.imb3_bytes_per_cell(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._L.imb3_destroy(self.h)
+        self.h = None
 
     def __del__(self):
         try:

@@ -29,6 +29,7 @@ UNITS = {
     "imb_noalloc.cu": [],
     "imb_adjoint.cu": [],
     "imb_batch.cu": [],
+    "imb_lbm3.cu": [],
 }
 
 

@@ -1,0 +1,622 @@
+// imb_lbm3.cu -- the paper's own lattice: D3Q19 stream-collide with held spheres.
+//
+// Sec. 2.1 (Tab. 1) lattice, BGK with Guo forcing (Eqs. 1-5), the partially saturated
+// collision of Eqs. 12-14 with the solid ratio of each cell counted on its n_sub^3 sub-cells
+// (Sec. 2.3), and per-sphere force and torque (Eqs. 15-16).  Spheres are held in place; their
+// velocity and spin enter u_s.  One thread per cell, warps along x rows: a pull of the 19
+// planes (x and z periodic, y periodic or halfway bounce-back walls), the collision in
+// registers, the store, and the sphere's force summed over the warp before one FP64
+// atomicAdd per component.  A cell is covered by at most one sphere (a per-cell map word
+// holds the sphere and its sub-cell count); spheres closer than that raise IMB_E_OVERFLOW.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/imblbm.h"
+#include "imb_device.cuh"
+
+namespace imb3 {
+
+using imb::Store;
+
+// D3Q19 (Tab. 1): 0 rest; 1-6 faces (+x, -x, +y, -y, +z, -z); 7-18 edges in opposite pairs
+__host__ __device__ constexpr int cx3(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+           : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy3(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+           : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz3(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+           : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp3(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr float w3(int q) { return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+
+constexpr unsigned ID_BITS = 22, ID_MASK = (1u << ID_BITS) - 1u;   // map word: sphere + 1 | count << 22
+constexpr unsigned ERR_UNSTABLE = imb::ERR_UNSTABLE, ERR_OVERLAP = imb::ERR_CELL_SLOTS;
+
+struct Args3 {
+    int nx, ny, nz, wall_y;
+    size_t plane;            // cells
+    float tau, omega, Fx, Fy, Fz;
+    float inv_nsub3;         // 1 / n_sub^3
+    int n_sub;
+};
+
+// sphere as the stream-collide kernel reads it: centre cell and FP32 offset in it, v, spin
+struct __align__(16) Sph3 {
+    int ci, cj, ck, pad;
+    float fx, fy, fz, pad2;
+    float vx, vy, vz, pad3;
+    float wx, wy, wz, pad4;
+};
+
+__device__ __forceinline__ int wrap(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
+__device__ __forceinline__ int min_image(int d, int L) {
+    const int h = L / 2;
+    return d >= h ? d - L : (d < -h ? d + L : d);
+}
+
+// Sec. 2.3: sub-cell centres of cell offset (di, dj, dk) inside the sphere; every FP64
+// operation rounded on its own, in the order of the plain definition
+__device__ int subcell_count(int di, int dj, int dk, double fx, double fy, double fz, double R, int n) {
+    const double R2 = __dmul_rn(R, R);
+    const double dn = (double)n;
+    int cnt = 0;
+    for (int c = 0; c < n; ++c) {
+        const double dz = __dsub_rn(__dadd_rn((double)dk, __ddiv_rn(__dadd_rn((double)c, 0.5), dn)), fz);
+        for (int b = 0; b < n; ++b) {
+            const double dy = __dsub_rn(__dadd_rn((double)dj, __ddiv_rn(__dadd_rn((double)b, 0.5), dn)), fy);
+            for (int a = 0; a < n; ++a) {
+                const double dx = __dsub_rn(__dadd_rn((double)di, __ddiv_rn(__dadd_rn((double)a, 0.5), dn)), fx);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                if (d2 <= R2) ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+// one thread per (sphere, cell of its bounding box of half-width `span`)
+__global__ void k3_map(const double *__restrict__ xyz, const double *__restrict__ R, int n, int span, Args3 a,
+                       unsigned *map, unsigned *err) {
+    const int w = 2 * span + 1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * w * w * w) return;
+    const int s = (int)(t / ((long long)w * w * w));
+    int c = (int)(t % ((long long)w * w * w));
+    const int di = c % w - span;
+    c /= w;
+    const int dj = c % w - span, dk = c / w - span;
+    const double cx = xyz[3 * s], cy = xyz[3 * s + 1], cz = xyz[3 * s + 2];
+    const double fi = floor(cx), fj = floor(cy), fk = floor(cz);
+    const int ci = (int)fi, cj = (int)fj, ck = (int)fk;
+    int i = ci + di, j = cj + dj, k = ck + dk;
+    i = ((i % a.nx) + a.nx) % a.nx;
+    k = ((k % a.nz) + a.nz) % a.nz;
+    if (a.wall_y) {
+        if (j < 0 || j >= a.ny) return;
+    } else {
+        j = ((j % a.ny) + a.ny) % a.ny;
+    }
+    const int cnt = subcell_count(di, dj, dk, cx - fi, cy - fj, cz - fk, R[s], a.n_sub);
+    if (cnt == 0) return;
+    const unsigned word = (unsigned)(s + 1) | ((unsigned)cnt << ID_BITS);
+    const size_t cell = ((size_t)k * a.ny + j) * a.nx + i;
+    if (atomicCAS(&map[cell], 0u, word) != 0u) atomicOr(err, ERR_OVERLAP);
+}
+
+template <typename S>
+__global__ void k3_init(S *f, size_t plane, float rho0, float ux, float uy, float uz) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= plane) return;
+    const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+        Store<S>::st(f + (size_t)q * plane + c, w3(q) * (rho0 * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu) - 1.0f));
+    }
+}
+
+// f(x, t) at one cell: the pull of the post-collision field with the boundary rules
+template <typename S>
+__device__ __forceinline__ void pull3(const S *__restrict__ fin, const Args3 &a, int x, int y, int z, float (&d)[19]) {
+    const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        int ys = y - cy3(q);
+        if (a.wall_y && (ys < 0 || ys >= a.ny)) {   // halfway bounce-back: the cell's own opposite
+            d[q] = Store<S>::ld(fin + (size_t)opp3(q) * a.plane + cell);
+            continue;
+        }
+        ys = wrap(ys, a.ny);
+        const int xs = wrap(x - cx3(q), a.nx), zs = wrap(z - cz3(q), a.nz);
+        d[q] = Store<S>::ld(fin + (size_t)q * a.plane + ((size_t)zs * a.ny + ys) * a.nx + xs);
+    }
+}
+
+// stream-collide; blocks of 32 x 8 cells of one z plane
+template <typename S>
+__global__ void __launch_bounds__(256) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
+                                                         const unsigned *__restrict__ map,
+                                                         const Sph3 *__restrict__ sph, double *FT, unsigned *err) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    const int lane = threadIdx.x;
+    const bool in = x < a.nx && y < a.ny;
+    int sid = -1;
+    float fo[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    bool unstable = false;
+    if (in) {
+        float d[19];
+        pull3(fin, a, x, y, z, d);
+        const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
+        // moments (Eqs. 3-4) with the Guo half-force shift
+        float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            drho += d[q];
+            if (cx3(q)) mx += cx3(q) * d[q];
+            if (cy3(q)) my += cy3(q) * d[q];
+            if (cz3(q)) mz += cz3(q) * d[q];
+        }
+        const float rho = 1.0f + drho;
+        const float jx = fmaf(0.5f, a.Fx, mx), jy = fmaf(0.5f, a.Fy, my), jz = fmaf(0.5f, a.Fz, mz);
+        const float inv = __fdividef(1.0f, rho);
+        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        if (!(uu < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+        const float t = fmaf(-1.5f * rho, uu, drho);
+        float n[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
+            const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+            n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+        }
+        const unsigned word = map[cell];
+        float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f, rx = 0.0f, ry = 0.0f, rz = 0.0f;
+        if (word) {   // Eq. 14 with the sub-cell solid ratio; u_s = v + w x r at the node
+            sid = (int)(word & ID_MASK) - 1;
+            const float eps = (float)(word >> ID_BITS) * a.inv_nsub3;
+            const float tm = a.tau - 0.5f;
+            B = __fdividef(eps * tm, (1.0f - eps) + tm);
+            const Sph3 P = sph[sid];
+            rx = (float)min_image(x - P.ci, a.nx) + 0.5f - P.fx;
+            ry = (float)(a.wall_y ? y - P.cj : min_image(y - P.cj, a.ny)) + 0.5f - P.fy;
+            rz = (float)min_image(z - P.ck, a.nz) + 0.5f - P.fz;
+            usx = P.vx + (P.wy * rz - P.wz * ry);
+            usy = P.vy + (P.wz * rx - P.wx * rz);
+            usz = P.vz + (P.wx * ry - P.wy * rx);
+        }
+        const float fl = 1.0f - B, sf = 1.0f - 0.5f * a.omega;
+        const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
+        const float uss = usx * usx + usy * usy + usz * usz;
+        const float ts = fmaf(-1.5f * rho, uss, drho);
+        const size_t base = cell;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+            const float cF = cx3(q) * a.Fx + cy3(q) * a.Fy + cz3(q) * a.Fz;
+            const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);   // Guo forcing / (1 - 1/(2 tau))
+            float v = fl * fmaf(-a.omega, n[q], sf * Sg);
+            if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q
+                const float cs = cx3(q) * usx + cy3(q) * usy + cz3(q) * usz;
+                const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
+                v = fmaf(B, n[opp3(q)] + eqs - d[q], v);
+            }
+            Store<S>::st(fout + (size_t)q * a.plane + base, d[q] + v);
+        }
+        if (word) {   // Eqs. 15-16: force on the sphere B (rho u - rho u_s - F), torque r x force
+            fo[0] = B * (jx - rho * usx - a.Fx);
+            fo[1] = B * (jy - rho * usy - a.Fy);
+            fo[2] = B * (jz - rho * usz - a.Fz);
+            fo[3] = ry * fo[2] - rz * fo[1];
+            fo[4] = rz * fo[0] - rx * fo[2];
+            fo[5] = rx * fo[1] - ry * fo[0];
+        }
+    }
+    // the warp's force: lanes of its first sphere summed by shuffles, any other sphere direct
+    const unsigned has = __ballot_sync(0xffffffffu, sid >= 0);
+    if (has) {
+        const int lead = __shfl_sync(0xffffffffu, sid, __ffs(has) - 1);
+        const bool mine = sid == lead;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float v = mine ? fo[c] : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(&FT[6 * lead + c], (double)v);
+            if (sid >= 0 && !mine) atomicAdd(&FT[6 * sid + c], (double)fo[c]);
+        }
+    }
+    if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(err, ERR_UNSTABLE);
+}
+
+// f(x, t) = w + pulled deviation, FP64, [19][cells]
+template <typename S>
+__global__ void k3_gather(const S *__restrict__ fin, const Args3 a, double *out) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.plane) return;
+    const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((size_t)a.nx * a.ny));
+    float d[19];
+    pull3(fin, a, x, y, z, d);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) out[(size_t)q * a.plane + c] = (double)w3(q) + (double)d[q];
+}
+
+// rho and u (with the half-force shift) of f(x, t)
+template <typename S>
+__global__ void k3_macro(const S *__restrict__ fin, const Args3 a, double *rho, double *ux, double *uy, double *uz) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.plane) return;
+    const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((size_t)a.nx * a.ny));
+    float d[19];
+    pull3(fin, a, x, y, z, d);
+    double r = 1.0, m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        r += d[q];
+        m[0] += cx3(q) * (double)d[q];
+        m[1] += cy3(q) * (double)d[q];
+        m[2] += cz3(q) * (double)d[q];
+    }
+    rho[c] = r;
+    ux[c] = (m[0] + 0.5 * a.Fx) / r;
+    uy[c] = (m[1] + 0.5 * a.Fy) / r;
+    uz[c] = (m[2] + 0.5 * a.Fz) / r;
+}
+
+}  // namespace imb3
+
+using namespace imb3;
+
+struct imb3_ctx {
+    int device = 0, nx = 0, ny = 0, nz = 0, np = 0, elem = 4, cur = 0;
+    double tau = 0.0;
+    imb3_params p{};
+    Args3 a{};
+    void *buf[2] = {nullptr, nullptr};
+    unsigned *map = nullptr, *err = nullptr, *h_err = nullptr;
+    Sph3 *sph = nullptr;
+    double *FT = nullptr;
+    cudaStream_t stream = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    long long launches = 0;
+    std::string msg;
+};
+
+namespace {
+
+std::string g3_err;
+
+int fail3(imb3_ctx *c, int code, const std::string &m) {
+    if (c) c->msg = m;
+    else g3_err = m;
+    return code;
+}
+
+#define CK3(call, what)                                                                            \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail3(c, e_ == cudaErrorMemoryAllocation ? IMB_E_NOMEM : IMB_E_CUDA,            \
+                         std::string(what) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+template <typename F>
+cudaError_t by_storage3(int storage, F &&fn) {
+    switch (storage) {
+    case IMB_STORE_FP32: return fn((float *)nullptr);
+    case IMB_STORE_FP16: return fn((__half *)nullptr);
+    case IMB_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// wait for the stream with a deadline, then read and clear the device error bits
+int wait3(imb3_ctx *c) {
+    cudaEvent_t ev;
+    CK3(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    CK3(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "error word");
+    CK3(cudaEventRecord(ev, c->stream), "event record");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t q;
+    while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > c->p.timeout_ms) {
+            cudaEventDestroy(ev);
+            return fail3(c, IMB_E_TIMEOUT, "stream did not finish within timeout_ms");
+        }
+        if (ms > 2.0) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+    CK3(q, "stream");
+    const unsigned bits = *c->h_err;
+    if (bits) {
+        CK3(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream), "clear");
+        CK3(cudaStreamSynchronize(c->stream), "clear");
+        if (bits & ERR_OVERLAP) return fail3(c, IMB_E_OVERFLOW, "two spheres cover one cell");
+        if (bits & ERR_UNSTABLE) return fail3(c, IMB_E_UNSTABLE, "NaN or |u| >= 0.3 (Mach guard)");
+    }
+    return IMB_OK;
+}
+
+}  // namespace
+
+extern "C" void imb3_default_params(imb3_params *p) {
+    if (!p) return;
+    p->wall_y = 1;
+    p->Fx = p->Fy = p->Fz = 0.0;
+    p->n_sub = 5;
+    p->storage = IMB_STORE_FP32;
+    p->rho0 = 1.0;
+    p->ux0 = p->uy0 = p->uz0 = 0.0;
+    p->timeout_ms = 60000;
+}
+
+extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_params *params) {
+    imb3_ctx *c = nullptr;
+    if (!out) return fail3(c, IMB_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    imb3_params p;
+    imb3_default_params(&p);
+    if (params) p = *params;
+    if (nx < 3 || ny < 3 || nz < 3 || !(tau > 0.5) || p.n_sub < 1 || p.n_sub > 10 || p.storage < 0 ||
+        p.storage > 2 || (double)nx * ny * nz > 2.0e9 || p.timeout_ms < 1)
+        return fail3(c, IMB_E_INVALID_ARG, "bad lattice size, tau <= 1/2, n_sub outside 1..10 or bad storage");
+    c = new imb3_ctx();
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->tau = tau;
+    c->p = p;
+    c->elem = p.storage == IMB_STORE_FP32 ? 4 : 2;
+    Args3 &a = c->a;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.wall_y = p.wall_y ? 1 : 0;
+    a.plane = (size_t)nx * ny * nz;
+    a.tau = (float)tau;
+    a.omega = (float)(1.0 / tau);
+    a.Fx = (float)p.Fx;
+    a.Fy = (float)p.Fy;
+    a.Fz = (float)p.Fz;
+    a.n_sub = p.n_sub;
+    a.inv_nsub3 = (float)(1.0 / ((double)p.n_sub * p.n_sub * p.n_sub));
+    *out = c;
+    CK3(cudaGetDevice(&c->device), "cudaGetDevice");
+    CK3(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+    CK3(cudaMalloc(&c->buf[0], 19 * a.plane * c->elem), "populations");
+    CK3(cudaMalloc(&c->buf[1], 19 * a.plane * c->elem), "populations");
+    CK3(cudaMalloc(&c->map, a.plane * sizeof(unsigned)), "cell map");
+    CK3(cudaMalloc(&c->err, sizeof(unsigned)), "error word");
+    CK3(cudaMallocHost(&c->h_err, sizeof(unsigned)), "error word");
+    CK3(cudaMemsetAsync(c->map, 0, a.plane * sizeof(unsigned), c->stream), "clear");
+    CK3(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream), "clear");
+    CK3(by_storage3(p.storage, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            k3_init<S><<<(unsigned)((a.plane + 255) / 256), 256, 0, c->stream>>>(
+                (S *)c->buf[0], a.plane, (float)p.rho0, (float)p.ux0, (float)p.uy0, (float)p.uz0);
+            return cudaGetLastError();
+        }),
+        "init");
+    c->launches++;
+    return wait3(c);
+}
+
+extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const double *v, const double *omega,
+                                const double *R) {
+    if (!c || n < 0 || (n > 0 && (!x || !v || !omega || !R)) || n >= (int)ID_MASK)
+        return fail3(c, IMB_E_INVALID_ARG, "bad sphere arrays");
+    const int L[3] = {c->nx, c->ny, c->nz};
+    const bool per[3] = {true, !c->p.wall_y, true};
+    double rmax = 0.0;
+    for (int s = 0; s < n; ++s) {
+        if (!(R[s] > 0.0) || R[s] > 1000.0) return fail3(c, IMB_E_INVALID_ARG, "radius must be in (0, 1000]");
+        for (int d = 0; d < 3; ++d) {
+            if (!(x[3 * s + d] >= 0.0 && x[3 * s + d] < L[d]))
+                return fail3(c, IMB_E_INVALID_ARG, "sphere centre outside the lattice");
+            if (per[d] && 2.0 * (R[s] + 2.0) > L[d])
+                return fail3(c, IMB_E_INVALID_ARG, "periodic extent below 2 (R + 2)");
+        }
+        rmax = std::max(rmax, R[s]);
+    }
+    CK3(cudaSetDevice(c->device), "cudaSetDevice");
+    CK3(cudaStreamSynchronize(c->stream), "stream");
+    if (c->sph) cudaFree(c->sph);
+    if (c->FT) cudaFree(c->FT);
+    c->sph = nullptr;
+    c->FT = nullptr;
+    c->np = n;
+    CK3(cudaMemsetAsync(c->map, 0, c->a.plane * sizeof(unsigned), c->stream), "clear map");
+    if (n == 0) return wait3(c);
+    std::vector<Sph3> hs(n);
+    for (int s = 0; s < n; ++s) {
+        Sph3 &P = hs[s];
+        const double fi = std::floor(x[3 * s]), fj = std::floor(x[3 * s + 1]), fk = std::floor(x[3 * s + 2]);
+        P.ci = (int)fi;
+        P.cj = (int)fj;
+        P.ck = (int)fk;
+        P.fx = (float)(x[3 * s] - fi);
+        P.fy = (float)(x[3 * s + 1] - fj);
+        P.fz = (float)(x[3 * s + 2] - fk);
+        P.vx = (float)v[3 * s];
+        P.vy = (float)v[3 * s + 1];
+        P.vz = (float)v[3 * s + 2];
+        P.wx = (float)omega[3 * s];
+        P.wy = (float)omega[3 * s + 1];
+        P.wz = (float)omega[3 * s + 2];
+    }
+    double *dx = nullptr, *dR = nullptr;
+    CK3(cudaMalloc(&c->sph, sizeof(Sph3) * n), "spheres");
+    CK3(cudaMalloc(&c->FT, sizeof(double) * 6 * n), "forces");
+    CK3(cudaMalloc(&dx, sizeof(double) * 3 * n), "spheres");
+    CK3(cudaMalloc(&dR, sizeof(double) * n), "spheres");
+    CK3(cudaMemcpyAsync(c->sph, hs.data(), sizeof(Sph3) * n, cudaMemcpyHostToDevice, c->stream), "spheres");
+    CK3(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream), "spheres");
+    CK3(cudaMemcpyAsync(dR, R, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "spheres");
+    CK3(cudaMemsetAsync(c->FT, 0, sizeof(double) * 6 * n, c->stream), "clear forces");
+    const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;
+    const long long nt = (long long)n * w * w * w;
+    k3_map<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(dx, dR, n, span, c->a, c->map, c->err);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    int rc = e == cudaSuccess ? wait3(c) : fail3(c, IMB_E_CUDA, std::string("cell map: ") + cudaGetErrorString(e));
+    cudaFree(dx);
+    cudaFree(dR);
+    return rc;
+}
+
+extern "C" int imb3_step(imb3_ctx *c, int nsteps) {
+    if (!c || nsteps < 0) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
+    CK3(cudaSetDevice(c->device), "cudaSetDevice");
+    const dim3 blk(32, 8, 1), grd((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
+    for (int t = 0; t < nsteps; ++t) {
+        if (c->np) CK3(cudaMemsetAsync(c->FT, 0, sizeof(double) * 6 * c->np, c->stream), "clear forces");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->timing) {
+            while (c->events.size() < c->ev_used + 2) {
+                cudaEvent_t e;
+                CK3(cudaEventCreate(&e), "event");
+                c->events.push_back(e);
+            }
+            e0 = c->events[c->ev_used];
+            e1 = c->events[c->ev_used + 1];
+            c->ev_used += 2;
+            CK3(cudaEventRecord(e0, c->stream), "event record");
+        }
+        CK3(by_storage3(c->p.storage, [&](auto tag) {
+                using S = std::remove_pointer_t<decltype(tag)>;
+                k3_stream_collide<S><<<grd, blk, 0, c->stream>>>((const S *)c->buf[c->cur], (S *)c->buf[c->cur ^ 1],
+                                                                 c->a, c->map, c->sph, c->FT, c->err);
+                return cudaGetLastError();
+            }),
+            "stream-collide");
+        if (c->timing) CK3(cudaEventRecord(e1, c->stream), "event record");
+        c->launches++;
+        c->cur ^= 1;
+    }
+    return wait3(c);
+}
+
+extern "C" int imb3_get_populations(imb3_ctx *c, double *f) {
+    if (!c || !f) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
+    CK3(cudaSetDevice(c->device), "cudaSetDevice");
+    double *d = nullptr;
+    CK3(cudaMalloc(&d, sizeof(double) * 19 * c->a.plane), "readback buffer");
+    cudaError_t e = by_storage3(c->p.storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        k3_gather<S><<<(unsigned)((c->a.plane + 255) / 256), 256, 0, c->stream>>>((const S *)c->buf[c->cur], c->a, d);
+        return cudaGetLastError();
+    });
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, d, sizeof(double) * 19 * c->a.plane, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    CK3(e, "populations");
+    c->launches++;
+    return wait3(c);
+}
+
+extern "C" int imb3_get_macro(imb3_ctx *c, double *rho, double *ux, double *uy, double *uz) {
+    if (!c || !rho || !ux || !uy || !uz) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
+    CK3(cudaSetDevice(c->device), "cudaSetDevice");
+    double *d = nullptr;
+    const size_t n = c->a.plane;
+    CK3(cudaMalloc(&d, sizeof(double) * 4 * n), "readback buffer");
+    cudaError_t e = by_storage3(c->p.storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        k3_macro<S><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const S *)c->buf[c->cur], c->a, d, d + n,
+                                                                        d + 2 * n, d + 3 * n);
+        return cudaGetLastError();
+    });
+    double *outs[4] = {rho, ux, uy, uz};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(outs[k], d + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    CK3(e, "macroscopic fields");
+    c->launches++;
+    return wait3(c);
+}
+
+extern "C" int imb3_get_forces(imb3_ctx *c, double *F, double *T) {
+    if (!c || (c->np && (!F || !T))) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
+    int rc = wait3(c);
+    if (rc || c->np == 0) return rc;
+    std::vector<double> h(6 * (size_t)c->np);
+    CK3(cudaMemcpy(h.data(), c->FT, sizeof(double) * h.size(), cudaMemcpyDeviceToHost), "forces");
+    for (int s = 0; s < c->np; ++s)
+        for (int d = 0; d < 3; ++d) {
+            F[3 * s + d] = h[6 * s + d];
+            T[3 * s + d] = h[6 * s + 3 + d];
+        }
+    return IMB_OK;
+}
+
+extern "C" int imb3_get_cell_map(imb3_ctx *c, int *sphere, int *count) {
+    if (!c || !sphere || !count) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
+    int rc = wait3(c);
+    if (rc) return rc;
+    std::vector<unsigned> h(c->a.plane);
+    CK3(cudaMemcpy(h.data(), c->map, sizeof(unsigned) * h.size(), cudaMemcpyDeviceToHost), "cell map");
+    for (size_t k = 0; k < h.size(); ++k) {
+        sphere[k] = (int)(h[k] & ID_MASK) - 1;
+        count[k] = (int)(h[k] >> ID_BITS);
+    }
+    return IMB_OK;
+}
+
+extern "C" int imb3_enable_kernel_timing(imb3_ctx *c, int on) {
+    if (!c) return IMB_E_INVALID_ARG;
+    c->timing = on != 0;
+    c->ev_used = 0;
+    return IMB_OK;
+}
+
+extern "C" int imb3_kernel_time(imb3_ctx *c, double *ms, long long *launches) {
+    if (!c || !ms || !launches) return IMB_E_INVALID_ARG;
+    int rc = wait3(c);
+    if (rc) return rc;
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float t = 0.0f;
+        CK3(cudaEventElapsedTime(&t, c->events[k], c->events[k + 1]), "event elapsed");
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (long long)(c->ev_used / 2);
+    c->ev_used = 0;
+    return IMB_OK;
+}
+
+extern "C" long long imb3_launch_count(imb3_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" double imb3_bytes_per_cell(imb3_ctx *c) { return c ? 38.0 * (double)c->elem : 0.0; }
+
+extern "C" const char *imb3_last_error(imb3_ctx *c) { return c ? c->msg.c_str() : g3_err.c_str(); }
+
+extern "C" void imb3_destroy(imb3_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void *b : c->buf)
+        if (b) cudaFree(b);
+    if (c->map) cudaFree(c->map);
+    if (c->err) cudaFree(c->err);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->sph) cudaFree(c->sph);
+    if (c->FT) cudaFree(c->FT);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}

@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "imblbm.h")
 def _declared():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(imb_\w+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(imb3?_\w+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol(lib):
     from paper_1809_07008_gb300 import binding
     out = subprocess.run(["nm", "-D", "--defined-only", binding.library_path()], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\b(imb_\w+)$", out, flags=re.M))
+    exported = set(re.findall(r"\b(imb3?_\w+)$", out, flags=re.M))
     missing = [n for n in _declared() if n not in exported]
     assert not missing, missing
     assert sorted(binding.EXPORTS) == _declared()
@@ -60,3 +60,17 @@ def test_params_struct_layout_matches_header(lib):
     for decl in re.findall(r"(int|double)\s+([^;]+);", body):
         fields += [f.strip() for f in decl[1].split(",")]
     assert [f[0] for f in binding.Params._fields_] == fields
+
+
+def test_params3_struct_layout_matches_header(lib):
+    from paper_1809_07008_gb300 import binding
+    txt = open(HEADER).read()
+    body = txt[txt.index("typedef struct imb3_params {"):txt.index("} imb3_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in re.findall(r"(int|double)\s+([^;]+);", body):
+        fields += [f.strip() for f in decl[1].split(",")]
+    assert [f[0] for f in binding.Params3._fields_] == fields
+    p = binding.Params3()
+    lib.imb3_default_params(ctypes.byref(p))
+    assert (p.wall_y, p.n_sub, p.storage, p.rho0, p.timeout_ms) == (1, 5, 0, 1.0, 60000)

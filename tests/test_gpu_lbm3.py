@@ -1,0 +1,127 @@
+"""GPU D3Q19 lattice with held spheres (imb3_*) against the FP64 3D oracle, and the paper's
+Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 2.
+
+* Cell map: the covering sphere and the sub-cell count of every cell bit-exact (FP64 counts
+  with every operation rounded on its own on both sides), for n_sub = 1, 2, 5 and 10.
+* Steps: seeded boxes with three spheres that move their surfaces (v, w in u_s), a body force,
+  walls in y or all periodic, 200 steps from rest: populations within 2e-6 (FP32 storage) and
+  velocity relative L2 within 1e-5, per-sphere force and torque within 1e-4 of their scale;
+  FP16 storage: forces within 1 %.
+* Errors: two spheres on one cell -> IMB_E_OVERFLOW; bad sizes and radii -> IMB_E_INVALID_ARG.
+* Benchmark: N = 5 and 10 cells per diameter, n_sub = 5, tau = 1, run to a steady drag: the
+  relative errors against Eqs. 18-19 fall with N and lie within 3 percentage points of the
+  paper's Table 2 (17.8 / 31.4 % at N = 5, 7.0 / 11.3 % at N = 10).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imb():
+    import paper_1809_07008_gb300 as imb
+    imb.load()
+    return imb
+
+
+@pytest.mark.parametrize("n_sub", [1, 2, 5, 10])
+def test_cell_map_bit_exact(orc, imb, n_sub):
+    w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=3, n_sub=n_sub)
+    assert w.n_spheres == 3
+    g = imb.Lattice3.from_workload(w)
+    gs, gc = g.cell_map()
+    os_, oc = orc.Sim3(w).cell_map()
+    assert (os_[..., 1] < 0).all()                   # one sphere per cell in this case
+    assert np.array_equal(gs, os_[..., 0])
+    assert np.array_equal(gc, oc[..., 0])
+    assert (gc > 0).sum() > 100
+    g.close()
+
+
+@pytest.mark.parametrize("wall_y", [True, False])
+def test_steps_match_oracle(orc, imb, wall_y):
+    w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=5 if wall_y else 6, wall_y=wall_y, tau=0.7)
+    assert w.n_spheres == 3
+    o = orc.Sim3(w)
+    g = imb.Lattice3.from_workload(w)
+    o.step(200)
+    g.step(200)
+    assert np.abs(g.populations() - o.f()).max() < 2e-6
+    _, oux, ouy, ouz = o.macro()
+    _, gux, guy, guz = g.macro()
+    uo = np.stack([oux, ouy, ouz])
+    ug = np.stack([gux, guy, guz])
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    sF = np.abs(Fo).max()
+    assert sF > 0 and np.abs(Fg - Fo).max() < 1e-4 * sF
+    sT = np.abs(To).max()
+    assert sT > 0 and np.abs(Tg - To).max() < 1e-4 * sT
+    g.close()
+
+
+def test_fp16_storage_forces(orc, imb):
+    w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=5, tau=0.7)
+    o = orc.Sim3(w)
+    g = imb.Lattice3.from_workload(w, storage="fp16")
+    o.step(300)
+    g.step(300)
+    Fo, _ = o.forces()
+    Fg, _ = g.forces()
+    assert np.abs(Fg - Fo).max() < 1e-2 * np.abs(Fo).max()
+    g.close()
+
+
+def test_errors(imb):
+    with pytest.raises(imb.ImbError):
+        imb.Lattice3(2, 10, 10, 0.8)
+    with pytest.raises(imb.ImbError):
+        imb.Lattice3(10, 10, 10, 0.5)
+    g = imb.Lattice3(24, 16, 24, 0.8)
+    z = np.zeros((2, 3))
+    with pytest.raises(imb.ImbError) as e:     # two spheres whose cells touch
+        g.set_spheres(np.array([[8.0, 8.0, 12.0], [13.5, 8.0, 12.0]]), z, z, np.array([3.0, 3.0]))
+    assert "OVERFLOW" in str(e.value)
+    with pytest.raises(imb.ImbError):
+        g.set_spheres(np.array([[8.0, 8.0, 12.0]]), z[:1], z[:1], np.array([-1.0]))
+    with pytest.raises(imb.ImbError):          # periodic extent below 2 (R + 2)
+        g.set_spheres(np.array([[8.0, 8.0, 12.0]]), z[:1], z[:1], np.array([11.0]))
+    g.set_spheres(np.array([[8.0, 8.0, 12.0]]), z[:1], z[:1], np.array([3.0]))
+    g.step(5)
+    g.close()
+
+
+def _happel_errors(orc, imb, N, tau=1.0, n_sub=5):
+    w = W.happel(N, tau=tau, n_sub=n_sub)
+    g = imb.Lattice3.from_workload(w)
+    H = w.ny
+    nu = (tau - 0.5) / 3.0
+    g_force = w.force[0]
+    yc = w.x[0, 1]
+    U = g_force / (2 * nu) * yc * (H - yc)
+    F_a, T_a = orc.happel_brenner(w.R[0], yc, U, 1.0, nu)
+    prev = None
+    for _ in range(60):
+        g.step(500)
+        F, T = g.forces()
+        if prev is not None and abs(F[0, 0] - prev) < 1e-5 * abs(F[0, 0]):
+            break
+        prev = F[0, 0]
+    g.close()
+    # Eq. 20; the torque about z is negative for a flow along +x above the wall-side sphere
+    return abs(F_a - F[0, 0]) / F_a * 100.0, abs(T_a - abs(T[0, 2])) / T_a * 100.0, F, T
+
+
+def test_happel_brenner_convergence_against_table2(orc, imb):
+    tab = {(r[0], r[1], r[2]): (r[3], r[4]) for r in orc.happel_table2()}
+    eF5, eT5, F5, T5 = _happel_errors(orc, imb, 5)
+    eF10, eT10, F10, T10 = _happel_errors(orc, imb, 10)
+    assert F5[0, 0] > 0 and F10[0, 0] > 0
+    assert abs(F10[0, 1]) < 0.2 * F10[0, 0] and abs(F10[0, 2]) < 1e-3 * F10[0, 0]
+    assert eF10 < eF5 and eT10 < eT5
+    assert abs(eF5 - tab[(5, 5, 1.0)][0]) < 3.0 and abs(eT5 - tab[(5, 5, 1.0)][1]) < 3.0
+    assert abs(eF10 - tab[(10, 5, 1.0)][0]) < 3.0 and abs(eT10 - tab[(10, 5, 1.0)][1]) < 3.0

@@ -180,3 +180,20 @@ def test_drag_momentum_balance_periodic_box(O):
     assert abs(F[0, 0] - expect) / expect < 1e-10
     assert abs(F[0, 1]) < 1e-9 * expect and abs(F[0, 2]) < 1e-9 * expect
     assert np.abs(T).max() < 1e-9 * expect * R
+
+
+def test_happel_brenner_reading_reproduces_printed_values(O):
+    # Sec. 3.1: R = 1 mm, walls 10 mm apart, centre 2.5 mm from the lower wall, pressure
+    # gradient 2.5e-5 Pa/m, rho = 1000 kg/m^3, mu = 1e-3 Pa s.  With l the centre-to-wall
+    # distance and U the Poiseuille velocity at the centre, Eqs. 18-19 give the printed
+    # 5.7628e-12 N and 8.1537e-16 N m (Table 2 caption).
+    G, mu, rho, H, yc, R = 2.5e-5, 1e-3, 1000.0, 0.01, 0.0025, 0.001
+    U = G / (2 * mu) * yc * (H - yc)
+    F, T = O.happel_brenner(R, yc, U, rho, mu / rho)
+    assert abs(F - 5.7628e-12) / 5.7628e-12 < 2e-5
+    assert abs(T - 8.1537e-16) / 8.1537e-16 < 2e-5
+    # the wall gap (10 mm) as l does not reproduce them
+    F2, _ = O.happel_brenner(R, H, U, rho, mu / rho)
+    assert abs(F2 - 5.7628e-12) / 5.7628e-12 > 0.1
+    rows = O.happel_table2()
+    assert len(rows) == 10 and rows[0] == (5, 5, 1.0, 17.791, 31.4374)
