@@ -48,6 +48,7 @@ struct Args3 {
     float tau, omega, Fx, Fy, Fz;
     float inv_nsub3;         // 1 / n_sub^3
     int n_sub;
+    long long off[19];       // element offset of the source of direction q: q plane - c_q (interior)
 };
 
 // sphere as the stream-collide kernel reads it: centre cell and FP32 offset in it, v, spin
@@ -144,7 +145,7 @@ __device__ __forceinline__ void pull3(const S *__restrict__ fin, const Args3 &a,
 
 // stream-collide; blocks of 32 x 8 cells of one z plane
 template <typename S>
-__global__ void __launch_bounds__(256) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
+__global__ void __launch_bounds__(256, 3) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
                                                          const unsigned *__restrict__ map,
                                                          const Sph3 *__restrict__ sph, double *FT, unsigned *err) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
@@ -155,8 +156,13 @@ __global__ void __launch_bounds__(256) k3_stream_collide(const S *__restrict__ f
     bool unstable = false;
     if (in) {
         float d[19];
-        pull3(fin, a, x, y, z, d);
         const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
+        if (x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+#pragma unroll
+            for (int q = 0; q < 19; ++q) d[q] = Store<S>::ld(fin + (cell + a.off[q]));   // no wrap, no wall
+        } else {
+            pull3(fin, a, x, y, z, d);
+        }
         // moments (Eqs. 3-4) with the Guo half-force shift
         float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
@@ -392,6 +398,9 @@ extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, con
     a.Fz = (float)p.Fz;
     a.n_sub = p.n_sub;
     a.inv_nsub3 = (float)(1.0 / ((double)p.n_sub * p.n_sub * p.n_sub));
+    for (int q = 0; q < 19; ++q)
+        a.off[q] = (long long)q * (long long)a.plane -
+                   ((long long)cz3(q) * ny * nx + (long long)cy3(q) * nx + (long long)cx3(q));
     *out = c;
     CK3(cudaGetDevice(&c->device), "cudaGetDevice");
     CK3(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
