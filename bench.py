@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import statistics
@@ -64,6 +65,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the batched-sweep line (256 periodic domains, FP16, 5000 steps)")
     ap.add_argument("--sweep-steps", type=int, default=5000)
+    ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 lines")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the solid-fraction-0.40 suspension, collapse-box and channel lines")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -296,6 +298,60 @@ def time_batched_sweep(imb, steps=5000, n_domains=256, storage="fp16"):
             "note": "host clock around imb_batch_run (graph replays, one sync at the end)"}
 
 
+def _happel_brenner(R, l, U, nu):
+    """Eqs. 18-19 (drag and torque on a held sphere a distance l from a wall, undisturbed
+    velocity U at its centre, rho = 1), for reporting the benchmark's errors."""
+    a = R / l
+    F = 6.0 * math.pi * nu * R * U * (1.0 - a * a / 9.0) / (1.0 - 0.6526 * a + 0.316 * a ** 3 - 0.242 * a ** 4)
+    T = 8.0 / 3.0 * math.pi * nu * R * R * U * a * (1.0 + 0.0758 * a + 0.049 * a * a)
+    return F, T
+
+
+def time_lattice3(imb, torch, ts, steps=100):
+    """The D3Q19 path: throughput on the 400 x 100 x 400 Poiseuille-flow-past-a-sphere box
+    (N = 20 cells per diameter, 16 M cells) in FP32 and FP16 storage, and the steady drag and
+    torque errors against Eqs. 18-19 at N = 5 and 10 (n_sub = 5, tau = 1)."""
+    out = {}
+    peak, kind = measured_hbm_peak()
+    w = W.happel(20)
+    for st in ("fp32", "fp16"):
+        g = imb.Lattice3.from_workload(w, storage=st)
+        g.step(5)
+        g.enable_kernel_timing(True)
+        t0 = time.perf_counter()
+        g.step(steps)
+        dt = time.perf_counter() - t0
+        ms, n = g.kernel_time()
+        kavg = ms / max(n, 1) * 1e-3
+        gbs = g.bytes_per_cell() * w.cells / kavg / 1e9
+        out[f"{w.name}:{st}"] = {"cells": w.cells, "steps": steps, "ms_per_step": round(dt / steps * 1e3, 4),
+                                 "mlups": round(w.cells / kavg / 1e6, 1), "kernel": "k3_stream_collide",
+                                 "kernel_ms_avg": round(kavg * 1e3, 4), "bytes_per_cell": g.bytes_per_cell(),
+                                 "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "peak_source": kind}
+        g.close()
+    for N in (5, 10):
+        wh = W.happel(N)
+        g = imb.Lattice3.from_workload(wh)
+        prev, n_steps = None, 0
+        for _ in range(60):
+            g.step(500)
+            n_steps += 500
+            F, T = g.forces()
+            if prev is not None and abs(F[0, 0] - prev) < 1e-5 * abs(F[0, 0]):
+                break
+            prev = F[0, 0]
+        g.close()
+        nu = (wh.tau - 0.5) / 3.0
+        yc = wh.x[0, 1]
+        U = wh.force[0] / (2 * nu) * yc * (wh.ny - yc)
+        Fa, Ta = _happel_brenner(wh.R[0], yc, U, nu)
+        out[f"happel_N{N}_error_pct"] = {"force": round(abs(Fa - F[0, 0]) / Fa * 100, 3),
+                                         "torque": round(abs(Ta - abs(T[0, 2])) / Ta * 100, 3),
+                                         "steps": n_steps, "paper_table2": {5: [17.791, 31.4374],
+                                                                            10: [6.9793, 11.256]}[N]}
+    return out
+
+
 def oracle_sample_workload():
     # bounded sample: the 512 x 512 subdomain of the suspension at the same disk density
     return W.c3sub(steps=0)
@@ -479,6 +535,10 @@ def run_gpu(args):
     if not args.no_sweep and rank == 0:
         sweep = time_batched_sweep(imb, args.sweep_steps)
 
+    lattice3 = None
+    if not args.no_3d and rank == 0:
+        lattice3 = time_lattice3(imb, torch, ts)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu = time_oracle()
@@ -499,6 +559,8 @@ def run_gpu(args):
             line["storage_variants"] = variants
         if others:
             line["other_workloads"] = others
+        if lattice3:
+            line["lattice_3d"] = lattice3
         if gradient:
             line["drag_gradient"] = gradient
         if sweep:
