@@ -6,7 +6,8 @@
 // velocity and spin enter u_s.  One thread per cell, warps along x rows: a pull of the 19
 // planes (x and z periodic, y periodic or halfway bounce-back walls), the collision in
 // registers, the store, and the sphere's force summed over the warp before one FP64
-// atomicAdd per component.  A cell is covered by at most one sphere (a per-cell map word
+// atomicAdd per component; each thread walks a short column of cells along z, the loads of
+// the next cell in flight during the arithmetic of the current one.  A cell is covered by at most one sphere (a per-cell map word
 // holds the sphere and its sub-cell count); spheres closer than that raise IMB_E_OVERFLOW.
 #include <algorithm>
 #include <chrono>
@@ -143,102 +144,144 @@ __device__ __forceinline__ void pull3(const S *__restrict__ fin, const Args3 &a,
     }
 }
 
-// stream-collide; blocks of 32 x 8 cells of one z plane
+template <typename S> __device__ __forceinline__ S ld_raw3(const S *p) { return __ldg(p); }
+__device__ __forceinline__ float f32_of(float v) { return v; }
+__device__ __forceinline__ float f32_of(__half v) { return __half2float(v); }
+__device__ __forceinline__ float f32_of(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// the 19 stored values a cell pulls (Eq. 1), as stored: interior cells by the per-direction
+// offsets, edge cells with the wrap and wall rules
 template <typename S>
-__global__ void __launch_bounds__(256, 3) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
+__device__ __forceinline__ void fetch3(const S *__restrict__ fin, const Args3 &a, int x, int y, int z, S (&r)[19]) {
+    const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
+    if (x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) r[q] = ld_raw3(fin + (cell + a.off[q]));
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        int ys = y - cy3(q);
+        if (a.wall_y && (ys < 0 || ys >= a.ny)) {   // halfway bounce-back: the cell's own opposite
+            r[q] = ld_raw3(fin + (size_t)opp3(q) * a.plane + cell);
+            continue;
+        }
+        ys = wrap(ys, a.ny);
+        const int xs = wrap(x - cx3(q), a.nx), zs = wrap(z - cz3(q), a.nz);
+        r[q] = ld_raw3(fin + (size_t)q * a.plane + ((size_t)zs * a.ny + ys) * a.nx + xs);
+    }
+}
+
+// collision of one cell from its pulled values d: moments (Eqs. 3-4, Guo half-force shift),
+// BGK with Guo forcing, Eqs. 12-14 where a sphere covers the cell, the 19 stores; returns the
+// covering sphere (-1: none) and its force and torque contribution (Eqs. 15-16)
+template <typename S>
+__device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, int x, int y, int z, size_t cell,
+                                        const unsigned *__restrict__ map, const Sph3 *__restrict__ sph,
+                                        S *__restrict__ fout, float (&fo)[6], bool &unstable) {
+    float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        drho += d[q];
+        if (cx3(q)) mx += cx3(q) * d[q];
+        if (cy3(q)) my += cy3(q) * d[q];
+        if (cz3(q)) mz += cz3(q) * d[q];
+    }
+    const float rho = 1.0f + drho;
+    const float jx = fmaf(0.5f, a.Fx, mx), jy = fmaf(0.5f, a.Fy, my), jz = fmaf(0.5f, a.Fz, mz);
+    const float inv = __fdividef(1.0f, rho);
+    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    if (!(uu < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+    const float t = fmaf(-1.5f * rho, uu, drho);
+    float n[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
+        const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+        n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+    }
+    const unsigned word = map[cell];
+    int sid = -1;
+    float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f, rx = 0.0f, ry = 0.0f, rz = 0.0f;
+    if (word) {   // Eq. 14 with the sub-cell solid ratio; u_s = v + w x r at the node
+        sid = (int)(word & ID_MASK) - 1;
+        const float eps = (float)(word >> ID_BITS) * a.inv_nsub3;
+        const float tm = a.tau - 0.5f;
+        B = __fdividef(eps * tm, (1.0f - eps) + tm);
+        const Sph3 P = sph[sid];
+        rx = (float)min_image(x - P.ci, a.nx) + 0.5f - P.fx;
+        ry = (float)(a.wall_y ? y - P.cj : min_image(y - P.cj, a.ny)) + 0.5f - P.fy;
+        rz = (float)min_image(z - P.ck, a.nz) + 0.5f - P.fz;
+        usx = P.vx + (P.wy * rz - P.wz * ry);
+        usy = P.vy + (P.wz * rx - P.wx * rz);
+        usz = P.vz + (P.wx * ry - P.wy * rx);
+    }
+    const float fl = 1.0f - B, sf = 1.0f - 0.5f * a.omega;
+    const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
+    const float uss = usx * usx + usy * usy + usz * usz;
+    const float ts = fmaf(-1.5f * rho, uss, drho);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+        const float cF = cx3(q) * a.Fx + cy3(q) * a.Fy + cz3(q) * a.Fz;
+        const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);   // Guo forcing / (1 - 1/(2 tau))
+        float v = fl * fmaf(-a.omega, n[q], sf * Sg);
+        if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q
+            const float cs = cx3(q) * usx + cy3(q) * usy + cz3(q) * usz;
+            const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
+            v = fmaf(B, n[opp3(q)] + eqs - d[q], v);
+        }
+        Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
+    }
+    if (word) {   // Eqs. 15-16: force on the sphere B (rho u - rho u_s - F), torque r x force
+        fo[0] = B * (jx - rho * usx - a.Fx);
+        fo[1] = B * (jy - rho * usy - a.Fy);
+        fo[2] = B * (jz - rho * usz - a.Fz);
+        fo[3] = ry * fo[2] - rz * fo[1];
+        fo[4] = rz * fo[0] - rx * fo[2];
+        fo[5] = rx * fo[1] - ry * fo[0];
+    }
+    return sid;
+}
+
+// stream-collide; blocks of 32 x 8 cells, each thread a column of ZC cells along z whose next
+// cell's loads are issued before the current cell's arithmetic
+constexpr int ZC = 8;
+
+template <typename S>
+__global__ void __launch_bounds__(256, 2) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
                                                          const unsigned *__restrict__ map,
                                                          const Sph3 *__restrict__ sph, double *FT, unsigned *err) {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, a.nz);
     const int lane = threadIdx.x;
     const bool in = x < a.nx && y < a.ny;
-    int sid = -1;
-    float fo[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     bool unstable = false;
-    if (in) {
-        float d[19];
-        const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
-        if (x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+    S r[19];
+    if (in) fetch3(fin, a, x, y, z0, r);
+    for (int z = z0; z < z1; ++z) {
+        int sid = -1;
+        float fo[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (in) {
+            float d[19];
 #pragma unroll
-            for (int q = 0; q < 19; ++q) d[q] = Store<S>::ld(fin + (cell + a.off[q]));   // no wrap, no wall
-        } else {
-            pull3(fin, a, x, y, z, d);
+            for (int q = 0; q < 19; ++q) d[q] = f32_of(r[q]);
+            if (z + 1 < z1) fetch3(fin, a, x, y, z + 1, r);   // in flight during this cell's arithmetic
+            sid = collide3(d, a, x, y, z, ((size_t)z * a.ny + y) * a.nx + x, map, sph, fout, fo, unstable);
         }
-        // moments (Eqs. 3-4) with the Guo half-force shift
-        float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+        // the warp's force: lanes of its first sphere summed by shuffles, any other sphere direct
+        const unsigned has = __ballot_sync(0xffffffffu, sid >= 0);
+        if (has) {
+            const int lead = __shfl_sync(0xffffffffu, sid, __ffs(has) - 1);
+            const bool mine = sid == lead;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            drho += d[q];
-            if (cx3(q)) mx += cx3(q) * d[q];
-            if (cy3(q)) my += cy3(q) * d[q];
-            if (cz3(q)) mz += cz3(q) * d[q];
-        }
-        const float rho = 1.0f + drho;
-        const float jx = fmaf(0.5f, a.Fx, mx), jy = fmaf(0.5f, a.Fy, my), jz = fmaf(0.5f, a.Fz, mz);
-        const float inv = __fdividef(1.0f, rho);
-        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-        const float uu = ux * ux + uy * uy + uz * uz;
-        if (!(uu < 0.09f)) unstable = true;   // Mach guard, also catches NaN
-        const float t = fmaf(-1.5f * rho, uu, drho);
-        float n[19];
+            for (int c = 0; c < 6; ++c) {
+                float v = mine ? fo[c] : 0.0f;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
-            const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
-            n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
-        }
-        const unsigned word = map[cell];
-        float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f, rx = 0.0f, ry = 0.0f, rz = 0.0f;
-        if (word) {   // Eq. 14 with the sub-cell solid ratio; u_s = v + w x r at the node
-            sid = (int)(word & ID_MASK) - 1;
-            const float eps = (float)(word >> ID_BITS) * a.inv_nsub3;
-            const float tm = a.tau - 0.5f;
-            B = __fdividef(eps * tm, (1.0f - eps) + tm);
-            const Sph3 P = sph[sid];
-            rx = (float)min_image(x - P.ci, a.nx) + 0.5f - P.fx;
-            ry = (float)(a.wall_y ? y - P.cj : min_image(y - P.cj, a.ny)) + 0.5f - P.fy;
-            rz = (float)min_image(z - P.ck, a.nz) + 0.5f - P.fz;
-            usx = P.vx + (P.wy * rz - P.wz * ry);
-            usy = P.vy + (P.wz * rx - P.wx * rz);
-            usz = P.vz + (P.wx * ry - P.wy * rx);
-        }
-        const float fl = 1.0f - B, sf = 1.0f - 0.5f * a.omega;
-        const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
-        const float uss = usx * usx + usy * usy + usz * usz;
-        const float ts = fmaf(-1.5f * rho, uss, drho);
-        const size_t base = cell;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
-            const float cF = cx3(q) * a.Fx + cy3(q) * a.Fy + cz3(q) * a.Fz;
-            const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);   // Guo forcing / (1 - 1/(2 tau))
-            float v = fl * fmaf(-a.omega, n[q], sf * Sg);
-            if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q
-                const float cs = cx3(q) * usx + cy3(q) * usy + cz3(q) * usz;
-                const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
-                v = fmaf(B, n[opp3(q)] + eqs - d[q], v);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) atomicAdd(&FT[6 * lead + c], (double)v);
+                if (sid >= 0 && !mine) atomicAdd(&FT[6 * sid + c], (double)fo[c]);
             }
-            Store<S>::st(fout + (size_t)q * a.plane + base, d[q] + v);
-        }
-        if (word) {   // Eqs. 15-16: force on the sphere B (rho u - rho u_s - F), torque r x force
-            fo[0] = B * (jx - rho * usx - a.Fx);
-            fo[1] = B * (jy - rho * usy - a.Fy);
-            fo[2] = B * (jz - rho * usz - a.Fz);
-            fo[3] = ry * fo[2] - rz * fo[1];
-            fo[4] = rz * fo[0] - rx * fo[2];
-            fo[5] = rx * fo[1] - ry * fo[0];
-        }
-    }
-    // the warp's force: lanes of its first sphere summed by shuffles, any other sphere direct
-    const unsigned has = __ballot_sync(0xffffffffu, sid >= 0);
-    if (has) {
-        const int lead = __shfl_sync(0xffffffffu, sid, __ffs(has) - 1);
-        const bool mine = sid == lead;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            float v = mine ? fo[c] : 0.0f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) atomicAdd(&FT[6 * lead + c], (double)v);
-            if (sid >= 0 && !mine) atomicAdd(&FT[6 * sid + c], (double)fo[c]);
         }
     }
     if (__any_sync(0xffffffffu, unstable) && lane == 0) atomicOr(err, ERR_UNSTABLE);
@@ -488,7 +531,7 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
 extern "C" int imb3_step(imb3_ctx *c, int nsteps) {
     if (!c || nsteps < 0) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
     CK3(cudaSetDevice(c->device), "cudaSetDevice");
-    const dim3 blk(32, 8, 1), grd((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
+    const dim3 blk(32, 8, 1), grd((c->nx + 31) / 32, (c->ny + 7) / 8, (c->nz + ZC - 1) / ZC);
     for (int t = 0; t < nsteps; ++t) {
         if (c->np) CK3(cudaMemsetAsync(c->FT, 0, sizeof(double) * 6 * c->np, c->stream), "clear forces");
         cudaEvent_t e0 = nullptr, e1 = nullptr;
