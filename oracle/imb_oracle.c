@@ -231,8 +231,11 @@ static void stream(orc_sim *s)
                 if (yn < 0 || yn >= ny) {
                     if (s->p.bc_y == ORC_PERIODIC) {
                         yn = (yn + ny) % ny;
-                    } else { /* halfway bounce-back at y = 0 and y = ny */
-                        s->f[IDX(s, OPP[q], k, i)] = v;
+                    } else { /* halfway bounce-back at y = 0 and y = ny; a wall moving along x
+                              * returns the population with the momentum term
+                              * -2 w_q rho_w (c_q . u_w) / c_s^2, rho_w = 1 */
+                        const double uw = yn < 0 ? s->p.wall_u_bot : s->p.wall_u_top;
+                        s->f[IDX(s, OPP[q], k, i)] = v - 6.0 * W[q] * CX[q] * uw;
                         continue;
                     }
                 }

@@ -38,6 +38,7 @@ typedef struct {
     int eps_mode, n_sub;
     int dem_on, N_sub;
     double kn, kt, e_rest, ct_ratio, mu, rho_s, gx, gy;
+    double wall_u_bot, wall_u_top;   /* x velocity of the walls y = 0 and y = ny (fluid rule only) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

@@ -100,8 +100,11 @@ static void stream(orc3_sim *s, const double *src, double *dst) {
                 const size_t c = cidx(s, i, j, k);
                 for (int q = 0; q < Q3; ++q) {
                     const int jj = j + C3[q][1];
-                    if (s->p.wall_y && (jj < 0 || jj >= ny)) {   /* halfway bounce-back */
-                        dst[(size_t)opp3(q) * nc + c] = src[(size_t)q * nc + c];
+                    if (s->p.wall_y && (jj < 0 || jj >= ny)) {
+                        /* halfway bounce-back; a wall moving along x adds the momentum term
+                         * -2 w_q rho_w (c_q . u_w) / c_s^2 with rho_w = 1 */
+                        const double uw = jj < 0 ? s->p.wall_ux_bot : s->p.wall_ux_top;
+                        dst[(size_t)opp3(q) * nc + c] = src[(size_t)q * nc + c] - 6.0 * w3(q) * C3[q][0] * uw;
                         continue;
                     }
                     const int ii = wrapi(i + C3[q][0], nx), kk = wrapi(k + C3[q][2], nz);

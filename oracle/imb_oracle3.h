@@ -21,6 +21,7 @@ typedef struct {
     double Fx, Fy, Fz;        /* body force density */
     int n_sub;                /* sub-cells per axis for the solid ratio */
     double rho0, ux0, uy0, uz0;
+    double wall_ux_bot, wall_ux_top;   /* x velocity of the walls y = 0 and y = ny */
 } orc3_params;
 
 typedef struct orc3_sim orc3_sim;

@@ -54,14 +54,15 @@ class Params(C.Structure):
                 ("dem_on", C.c_int), ("N_sub", C.c_int),
                 ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
-                ("gx", C.c_double), ("gy", C.c_double)]
+                ("gx", C.c_double), ("gy", C.c_double),
+                ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double)]
 
 
 class Params3(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("tau", C.c_double),
                 ("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
                 ("n_sub", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double), ("uy0", C.c_double),
-                ("uz0", C.c_double)]
+                ("uz0", C.c_double), ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double)]
 
 
 _lib = None
@@ -177,6 +178,7 @@ def params_from_workload(w) -> Params:
     p.kn, p.kt, p.e_rest, p.ct_ratio = w.kn, w.kt, w.e_rest, w.ct_ratio
     p.mu, p.rho_s = w.mu, w.rho_s
     p.gx, p.gy = w.gravity
+    p.wall_u_bot, p.wall_u_top = w.wall_u
     return p
 
 
@@ -339,6 +341,7 @@ class Sim3:
         p.n_sub = w.n_sub
         p.rho0 = w.rho0
         p.ux0, p.uy0, p.uz0 = w.u0
+        p.wall_ux_bot, p.wall_ux_top = w.wall_u
         self.p = p
         self.h = lib().orc3_new(C.byref(p))
         if not self.h:

@@ -197,3 +197,17 @@ def test_happel_brenner_reading_reproduces_printed_values(O):
     assert abs(F2 - 5.7628e-12) / 5.7628e-12 > 0.1
     rows = O.happel_table2()
     assert len(rows) == 10 and rows[0] == (5, 5, 1.0, 17.791, 31.4374)
+
+
+def test_plane_couette_exact_with_moving_walls(O):
+    H, tau, uw = 16, 0.8, 0.01
+    w = W.Workload3(name="couette3", nx=3, ny=H, nz=3, tau=tau, wall_y=True, wall_u=(-uw, uw))
+    s = O.Sim3(w)
+    m0 = s.macro()[0].sum()
+    nu = (tau - 0.5) / 3.0
+    s.step(int(30 * H * H / (nu * math.pi ** 2)))
+    rho, ux, uy, uz = s.macro()
+    y = np.arange(H) + 0.5
+    assert np.abs(ux - (-uw + 2 * uw * y / H)[None, :, None]).max() < 1e-13
+    assert np.abs(uy).max() < 1e-13 and np.abs(uz).max() < 1e-13
+    assert abs(rho.sum() - m0) < 1e-12 * m0

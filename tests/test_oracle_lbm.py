@@ -139,3 +139,20 @@ def test_drag_converges_with_resolution(orc):
     d2 = abs(K[20] - K[10])
     assert d2 < 0.6 * d1                         # differences shrink with resolution
     assert abs(K[20] - K[10]) / K[20] < 0.05     # N = 20 within 5 % of N = 10 (paper: < 4.5 %)
+
+
+def test_plane_couette_exact_with_moving_walls(orc):
+    # walls y = 0 and y = H moving along x at -u_w and +u_w (the paper's Couette case,
+    # Sec. 3.4): halfway bounce-back with the moving-wall momentum term gives the linear
+    # profile u(y) = -u_w + 2 u_w y / H exactly at the nodes (y = j + 1/2), v = 0, mass kept
+    H, tau, uw = 16, 0.8, 0.01
+    w = W.Workload(name="couette", nx=4, ny=H, tau=tau, bc_x=W.BC_PERIODIC, bc_y=W.BC_WALL, wall_u=(-uw, uw))
+    s = orc.Sim(w)
+    m0 = s.macro()[0].sum()
+    nu = (tau - 0.5) / 3.0
+    s.step(int(30 * H * H / (nu * np.pi ** 2)))
+    rho, ux, uy = s.macro()
+    y = np.arange(H) + 0.5
+    assert np.abs(ux - (-uw + 2 * uw * y / H)[:, None]).max() < 1e-13
+    assert np.abs(uy).max() < 1e-13
+    assert abs(rho.sum() - m0) < 1e-12 * m0

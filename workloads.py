@@ -93,6 +93,7 @@ class Workload:
     mu: float = 0.5
     rho_s: float = 2.65
     gravity: tuple = (0.0, 0.0)
+    wall_u: tuple = (0.0, 0.0)         # x velocity of the walls y = 0 and y = ny
     steps: int = 1000
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
     v: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
@@ -340,6 +341,7 @@ class Workload3:
     n_sub: int = 5
     rho0: float = 1.0
     u0: tuple = (0.0, 0.0, 0.0)
+    wall_u: tuple = (0.0, 0.0)         # x velocity of the walls y = 0 and y = ny
     steps: int = 1000
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     v: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
