@@ -73,6 +73,10 @@ typedef struct imb_params {
     double gx, gy;       /* gravity; particles feel (1 - 1/rho_s) g (buoyancy-reduced)         */
     double skin;         /* DEM neighbour-list skin in cells (default 1)                       */
     int timeout_ms;      /* bound on every host wait (default 60000)                           */
+    double wall_u_bot, wall_u_top; /* x velocity of the walls y = 0 and y = ny (bc_y = WALL):
+                            halfway bounce-back with the moving-wall momentum term (wall
+                            density 1); the fluid sees it, DEM wall contacts see walls at
+                            rest (default 0, 0)                                                */
 } imb_params;
 
 typedef struct imb_ctx imb_ctx;
@@ -307,9 +311,11 @@ typedef struct imb3_params {
     int storage;              /* IMB_STORE_* */
     double rho0, ux0, uy0, uz0; /* initial state: f* = f^eq(rho0, u0) everywhere */
     int timeout_ms;           /* bound of every host wait */
+    double wall_ux_bot, wall_ux_top; /* x velocity of the walls y = 0 and y = ny (moving-wall
+                                 bounce-back, wall density 1; default 0, 0) */
 } imb3_params;
 
-/* Defaults: walls in y, no force, n_sub = 5, FP32, rho0 = 1, at rest, 60 s. */
+/* Defaults: walls in y at rest, no force, n_sub = 5, FP32, rho0 = 1, at rest, 60 s. */
 void imb3_default_params(imb3_params *p);
 
 /* Create the lattice (p may be NULL for the defaults).  IMB_E_INVALID_ARG for a size

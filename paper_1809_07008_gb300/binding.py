@@ -78,7 +78,8 @@ class Params3(C.Structure):
     """Mirror of imb3_params (include/imblbm.h)."""
     _fields_ = [("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
                 ("n_sub", C.c_int), ("storage", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double),
-                ("uy0", C.c_double), ("uz0", C.c_double), ("timeout_ms", C.c_int)]
+                ("uy0", C.c_double), ("uz0", C.c_double), ("timeout_ms", C.c_int),
+                ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double)]
 
 
 class Params(C.Structure):
@@ -91,7 +92,7 @@ class Params(C.Structure):
                 ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double), ("skin", C.c_double),
-                ("timeout_ms", C.c_int)]
+                ("timeout_ms", C.c_int), ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double)]
 
 
 _lib = None
@@ -234,6 +235,7 @@ class Lattice:
         p.kn, p.kt, p.e_rest, p.ct_ratio = w.kn, w.kt, w.e_rest, w.ct_ratio
         p.mu, p.rho_s = w.mu, w.rho_s
         p.gx, p.gy = w.gravity
+        p.wall_u_bot, p.wall_u_top = w.wall_u
         for k, v in kw.items():
             setattr(p, k, v)
         lat = cls(w.nx, w.ny, w.tau, w.C_smag, params=p)
@@ -451,7 +453,7 @@ class Lattice3:
     """A D3Q19 lattice with held spheres (imb3_*; the paper's own lattice)."""
 
     def __init__(self, nx, ny, nz, tau, wall_y=True, force=(0.0, 0.0, 0.0), n_sub=5, storage="fp32",
-                 rho0=1.0, u0=(0.0, 0.0, 0.0)):
+                 rho0=1.0, u0=(0.0, 0.0, 0.0), wall_u=(0.0, 0.0)):
         L = load()
         p = Params3()
         L.imb3_default_params(C.byref(p))
@@ -461,6 +463,7 @@ class Lattice3:
         p.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
         p.rho0 = float(rho0)
         p.ux0, p.uy0, p.uz0 = map(float, u0)
+        p.wall_ux_bot, p.wall_ux_top = map(float, wall_u)
         h = _vp()
         rc = L.imb3_init(C.byref(h), int(nx), int(ny), int(nz), float(tau), C.byref(p))
         if rc != IMB_OK:
@@ -475,7 +478,7 @@ class Lattice3:
     @classmethod
     def from_workload(cls, w, storage="fp32"):
         lat = cls(w.nx, w.ny, w.nz, w.tau, wall_y=w.wall_y, force=w.force, n_sub=w.n_sub, storage=storage,
-                  rho0=w.rho0, u0=w.u0)
+                  rho0=w.rho0, u0=w.u0, wall_u=w.wall_u)
         if w.n_spheres:
             lat.set_spheres(w.x, w.v, w.omega, w.R)
         return lat

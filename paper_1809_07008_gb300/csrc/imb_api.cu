@@ -135,6 +135,8 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.Fy = (float)c->p.Fy;
     a.u_in_x = (float)c->p.u_in_x;
     a.u_in_y = (float)c->p.u_in_y;
+    a.uw_bot = (float)c->p.wall_u_bot;
+    a.uw_top = (float)c->p.wall_u_top;
     a.eps_mode = c->p.eps_mode;
     a.n_sub = c->p.n_sub;
     a.nbx = c->nbx;
@@ -790,9 +792,9 @@ struct GradBufs {
 
 int grad_prepare(imb_ctx *c, int T, GradBufs &g) {
     if (c->p.dem_on || c->C_smag != 0.0 || c->p.Fx != 0.0 || c->p.Fy != 0.0 || c->p.eps_mode != IMB_EPS_EXACT ||
-        c->p.storage != IMB_STORE_FP32)
-        return fail(c, IMB_E_INVALID_ARG,
-                    "drag gradient needs DEM off, C_smag = 0, no body force, exact solid ratio, FP32 storage");
+        c->p.storage != IMB_STORE_FP32 || c->p.wall_u_bot != 0.0 || c->p.wall_u_top != 0.0)
+        return fail(c, IMB_E_INVALID_ARG, "drag gradient needs DEM off, C_smag = 0, no body force, exact solid "
+                                          "ratio, FP32 storage and walls at rest");
     int rc = imb_sync(c);
     if (rc) return rc;
     CK(cudaSetDevice(c->device), "cudaSetDevice");

@@ -20,6 +20,7 @@ struct LatticeArgs {
     float smag_coef;           // 18 sqrt(2) C^2 (0 switches the Smagorinsky model off)
     float Fx, Fy;              // body force density (0, 0 = no forcing)
     float u_in_x, u_in_y;
+    float uw_bot, uw_top;      // x velocity of the walls y = 0 and y = ny
     int eps_mode, n_sub;
     int nbx, nby;              // bins of 32 x 32 cells
     int np;

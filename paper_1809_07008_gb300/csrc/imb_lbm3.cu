@@ -49,6 +49,7 @@ struct Args3 {
     float tau, omega, Fx, Fy, Fz;
     float inv_nsub3;         // 1 / n_sub^3
     int n_sub;
+    float uw_bot, uw_top;    // x velocity of the walls y = 0 and y = ny
     long long off[19];       // element offset of the source of direction q: q plane - c_q (interior)
 };
 
@@ -136,6 +137,7 @@ __device__ __forceinline__ void pull3(const S *__restrict__ fin, const Args3 &a,
         int ys = y - cy3(q);
         if (a.wall_y && (ys < 0 || ys >= a.ny)) {   // halfway bounce-back: the cell's own opposite
             d[q] = Store<S>::ld(fin + (size_t)opp3(q) * a.plane + cell);
+            if (cx3(q) != 0) d[q] += 6.0f * w3(q) * (float)cx3(q) * (ys < 0 ? a.uw_bot : a.uw_top);
             continue;
         }
         ys = wrap(ys, a.ny);
@@ -266,6 +268,12 @@ __global__ void __launch_bounds__(256, 2) k3_stream_collide(const S *__restrict_
             float d[19];
 #pragma unroll
             for (int q = 0; q < 19; ++q) d[q] = f32_of(r[q]);
+            if (a.wall_y && (y == 0 || y == a.ny - 1)) {   // moving-wall term of the bounced values
+#pragma unroll
+                for (int q = 0; q < 19; ++q)
+                    if (cx3(q) != 0 && ((y == 0 && cy3(q) == 1) || (y == a.ny - 1 && cy3(q) == -1)))
+                        d[q] += 6.0f * w3(q) * (float)cx3(q) * (y == 0 ? a.uw_bot : a.uw_top);
+            }
             if (z + 1 < z1) fetch3(fin, a, x, y, z + 1, r);   // in flight during this cell's arithmetic
             sid = collide3(d, a, x, y, z, ((size_t)z * a.ny + y) * a.nx + x, map, sph, fout, fo, unstable);
         }
@@ -409,6 +417,7 @@ extern "C" void imb3_default_params(imb3_params *p) {
     p->rho0 = 1.0;
     p->ux0 = p->uy0 = p->uz0 = 0.0;
     p->timeout_ms = 60000;
+    p->wall_ux_bot = p->wall_ux_top = 0.0;
 }
 
 extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_params *params) {
@@ -441,6 +450,8 @@ extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, con
     a.Fz = (float)p.Fz;
     a.n_sub = p.n_sub;
     a.inv_nsub3 = (float)(1.0 / ((double)p.n_sub * p.n_sub * p.n_sub));
+    a.uw_bot = (float)p.wall_ux_bot;
+    a.uw_top = (float)p.wall_ux_top;
     for (int q = 0; q < 19; ++q)
         a.off[q] = (long long)q * (long long)a.plane -
                    ((long long)cz3(q) * ny * nx + (long long)cy3(q) * nx + (long long)cx3(q));

@@ -1,6 +1,6 @@
 // imb_pull.cuh -- the pull half of the stream step (Eq. 1 LHS) with the boundary rules:
-// periodic wrap, halfway bounce-back walls, velocity inlet / zero-gradient outlet.  Shared by
-// the stream-collide kernel and its adjoint.
+// periodic wrap, halfway bounce-back walls (those at y = 0 and y = ny may move along x),
+// velocity inlet / zero-gradient outlet.  Shared by the stream-collide kernel and its adjoint.
 #pragma once
 #include "imb_device.cuh"
 #include "imb_kernels.h"
@@ -18,8 +18,10 @@ __device__ __forceinline__ void pull_generic(const S *__restrict__ fin, const La
         if (ys < 0 || ys >= a.ny) {
             if (a.bc_y == BC_PERIODIC) {
                 ys = ys < 0 ? ys + a.ny : ys - a.ny;
-            } else {  // halfway bounce-back: what left (x,y) towards the wall comes back
+            } else {  // halfway bounce-back: what left (x,y) towards the wall comes back, with
+                      // the moving wall's momentum term 2 w_q rho_w (c_q . u_w) / c_s^2, rho_w = 1
                 d[q] = Store<S>::ld(fin + self_opp);
+                if (cx_of(q) != 0) d[q] += 6.0f * w_of(q) * (float)cx_of(q) * (ys < 0 ? a.uw_bot : a.uw_top);
                 continue;
             }
         }

@@ -309,3 +309,35 @@ def test_host_wait_is_bounded(imb):
         except imb.ImbError:
             time.sleep(0.05)
     lat.sync()
+
+
+def test_couette_moving_walls(orc, imb):
+    # walls y = 0 and y = H moving along x at -u_w and +u_w (Sec. 3.4): the fluid-only
+    # steady profile is the exact line in FP32, and a suspension between the moving walls
+    # (DEM on, the 8192 x 4096 case's density) matches the oracle after 200 steps
+    H, tau, uw = 16, 0.8, 0.01
+    w = W.Workload(name="couette", nx=64, ny=H, tau=tau, bc_x=W.BC_PERIODIC, bc_y=W.BC_WALL, wall_u=(-uw, uw))
+    g = imb.Lattice.from_workload(w)
+    nu = (tau - 0.5) / 3.0
+    g.step(int(30 * H * H / (nu * math.pi ** 2)))
+    _, ux, uy = g.macro()
+    y = np.arange(H) + 0.5
+    assert np.abs(ux - (-uw + 2 * uw * y / H)[:, None]).max() < 2e-6 * uw / 0.01
+    assert np.abs(uy).max() < 1e-7
+    g.close()
+    ws = W.c3sub(steps=0, nx=128, ny=96).with_(wall_u=(-uw, uw))
+    o, g = _run_pair(orc, imb, ws, 200)
+    assert _u_rel_l2(g.macro(), o.macro(), _fluid_mask(o)) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    errF, errT = _force_ok(Fg, Tg, Fo, To, ws.r)
+    assert errF < 1e-4 and errT < 1e-4
+    g.close()
+
+
+def test_drag_gradient_refuses_moving_walls(imb):
+    w = W.c4(steps=0, nx=96, ny=48, n_side=1).with_(wall_u=(0.0, 0.01))
+    g = imb.Lattice.from_workload(w)
+    with pytest.raises(imb.ImbError):
+        g.drag_gradient(10)
+    g.close()
