@@ -53,6 +53,7 @@ struct orc_sim {
     double *eps;                   /* per cell and slot: solid ratio of that particle */
     double zeta;                   /* damping ratio from the restitution coefficient */
     double gx_eff, gy_eff;         /* buoyancy-reduced gravity */
+    double hm_kn0, hm_sn0, hm_kt0, hm_c0; /* Hertz-Mindlin: 4/3 E*, 2 E*, 8 G*, 2 sqrt(5/6) |beta| */
 };
 
 #define IDX(s, q, k, i) (((size_t)(q) * (s)->p.ny + (size_t)(k)) * (s)->p.nx + (size_t)(i))
@@ -272,6 +273,9 @@ orc_sim *orc_new(const orc_params *p)
 {
     if (p->nx < 3 || p->ny < 3 || !(p->tau > 0.5) || p->C_smag < 0.0)
         return NULL;
+    if (p->contact_model < 0 || p->contact_model > 1 ||
+        (p->contact_model == 1 && !(p->E_young > 0.0 && p->nu_poisson >= 0.0 && p->nu_poisson < 0.5)))
+        return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
     size_t n = (size_t)9 * p->nx * p->ny;
@@ -282,6 +286,16 @@ orc_sim *orc_new(const orc_params *p)
     s->eps = (double *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS, sizeof(double));
     double le = log(p->e_rest > 0.0 ? p->e_rest : 1.0);
     s->zeta = -le / sqrt(M_PI * M_PI + le * le);
+    {   /* Hertz-Mindlin constants, identical materials: E* = E / (2 (1 - nu^2)),
+         * G* = E / (4 (2 - nu)(1 + nu)) */
+        const double E = p->E_young, nu = p->nu_poisson;
+        const double Es = E / (2.0 * (1.0 - nu * nu));
+        const double Gs = E / (4.0 * (2.0 - nu) * (1.0 + nu));
+        s->hm_kn0 = 4.0 / 3.0 * Es;
+        s->hm_sn0 = 2.0 * Es;
+        s->hm_kt0 = 8.0 * Gs;
+        s->hm_c0 = 2.0 * sqrt(5.0 / 6.0) * s->zeta;
+    }
     s->gx_eff = (1.0 - 1.0 / p->rho_s) * p->gx;
     s->gy_eff = (1.0 - 1.0 / p->rho_s) * p->gy;
     /* initial condition: the post-collision field is f^eq(rho0, u0); streaming
@@ -339,27 +353,42 @@ int orc_set_particles(orc_sim *s, int n, const double *x, const double *v, const
 }
 
 /* ---------------------------------------------------------------- DEM */
-/* Linear spring-dashpot contact between particle a and a partner seen from a
- * (Eqs. 7-9).  n points from a to the partner, t = z x n.  dvx,dvy is the
- * partner's translational velocity minus a's; rot = w_a r_a + w_b r_b.
- * Returns the force on a (fx, fy) and the tangential force magnitude Ft (the
- * torque on each side is its own radius times Ft). */
+/* Spring-dashpot contact between particle a and a partner seen from a (Eqs. 7-9).
+ * n points from a to the partner, t = z x n.  dvx,dvy is the partner's
+ * translational velocity minus a's; rot = w_a r_a + w_b r_b; R* and m* the pair's
+ * reduced radius and mass.  Linear law: constant k_n, k_t, c_n = 2 zeta sqrt(m* k_n),
+ * c_t = ct_ratio c_n.  Simplified Hertz-Mindlin (the paper's law, Sec. 2.2, after di
+ * Renzo and di Maio): with s = sqrt(R* delta), k_n = 4/3 E* s, k_t = 8 G* s and the
+ * dashpots 2 sqrt(5/6) |beta| sqrt(S m*) for S_n = 2 E* s and S_t = 8 G* s, where
+ * |beta| = zeta.  Returns the force on a (fx, fy) and the tangential force magnitude Ft
+ * (the torque on each side is its own radius times Ft). */
 static void contact_law(const orc_sim *s, double nxv, double nyv, double delta, double dvx,
-                        double dvy, double rot, double mstar, double dt, double *xi, double *fx,
-                        double *fy, double *Ft_out)
+                        double dvy, double rot, double Rstar, double mstar, double dt, double *xi,
+                        double *fx, double *fy, double *Ft_out)
 {
     double tx = -nyv, ty = nxv;
     double vn = dvx * nxv + dvy * nyv;
     double vt = (dvx * tx + dvy * ty) - rot;
-    double cn = 2.0 * s->zeta * sqrt(mstar * s->p.kn);
-    double ct = s->p.ct_ratio * cn;
+    double kn, kt, cn, ct;
+    if (s->p.contact_model == 1) {
+        double sq = sqrt(Rstar * delta);
+        kn = s->hm_kn0 * sq;
+        kt = s->hm_kt0 * sq;
+        cn = s->hm_c0 * sqrt(s->hm_sn0 * sq * mstar);
+        ct = s->hm_c0 * sqrt(s->hm_kt0 * sq * mstar);
+    } else {
+        kn = s->p.kn;
+        kt = s->p.kt;
+        cn = 2.0 * s->zeta * sqrt(mstar * s->p.kn);
+        ct = s->p.ct_ratio * cn;
+    }
     *xi = *xi + vt * dt;                      /* incremental spring of Eq. 9 */
-    double Fn = s->p.kn * delta - cn * vn;    /* Eq. 8, repulsive when positive */
-    double Ft = s->p.kt * *xi + ct * vt;      /* Eq. 9 */
+    double Fn = kn * delta - cn * vn;         /* Eq. 8, repulsive when positive */
+    double Ft = kt * *xi + ct * vt;           /* Eq. 9 */
     double lim = s->p.mu * fabs(Fn);          /* Coulomb cap */
     if (fabs(Ft) > lim) {
         Ft = copysign(lim, Ft);
-        *xi = copysign(lim / s->p.kt, *xi);
+        *xi = copysign(lim / kt, *xi);
     }
     *fx = -Fn * nxv + Ft * tx;
     *fy = -Fn * nyv + Ft * ty;
@@ -396,9 +425,10 @@ static void dem_substep(orc_sim *s, double dt, double *Fcx, double *Fcy, double 
             double nxv = dx / d, nyv = dy / d;
             double delta = R - d;
             double mstar = s->m[a] * s->m[b] / (s->m[a] + s->m[b]);
+            double Rstar = s->r[a] * s->r[b] / (s->r[a] + s->r[b]);
             double rot = s->w[a] * s->r[a] + s->w[b] * s->r[b];
             double fx, fy, Ft;
-            contact_law(s, nxv, nyv, delta, s->vx[b] - s->vx[a], s->vy[b] - s->vy[a], rot, mstar,
+            contact_law(s, nxv, nyv, delta, s->vx[b] - s->vx[a], s->vy[b] - s->vy[a], rot, Rstar, mstar,
                         dt, xi, &fx, &fy, &Ft);
             Fcx[a] += fx; Fcy[a] += fy; Tc[a] += s->r[a] * Ft;
             Fcx[b] -= fx; Fcy[b] -= fy; Tc[b] += s->r[b] * Ft;
@@ -423,7 +453,7 @@ static void dem_substep(orc_sim *s, double dt, double *Fcx, double *Fcy, double 
             }
             double delta = s->r[p] - dist;
             double fx, fy, Ft;
-            contact_law(s, nxv, nyv, delta, -s->vx[p], -s->vy[p], s->w[p] * s->r[p], s->m[p], dt,
+            contact_law(s, nxv, nyv, delta, -s->vx[p], -s->vy[p], s->w[p] * s->r[p], s->r[p], s->m[p], dt,
                         xi, &fx, &fy, &Ft);
             Fcx[p] += fx; Fcy[p] += fy; Tc[p] += s->r[p] * Ft;
         }

@@ -39,6 +39,8 @@ typedef struct {
     int dem_on, N_sub;
     double kn, kt, e_rest, ct_ratio, mu, rho_s, gx, gy;
     double wall_u_bot, wall_u_top;   /* x velocity of the walls y = 0 and y = ny (fluid rule only) */
+    int contact_model;               /* 0: linear spring-dashpot, 1: simplified Hertz-Mindlin */
+    double E_young, nu_poisson;      /* Hertz-Mindlin material (same for particles and walls) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

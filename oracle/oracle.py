@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double),
-                ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double)]
+                ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double),
+                ("contact_model", C.c_int), ("E_young", C.c_double), ("nu_poisson", C.c_double)]
 
 
 class Params3(C.Structure):
@@ -179,6 +180,7 @@ def params_from_workload(w) -> Params:
     p.mu, p.rho_s = w.mu, w.rho_s
     p.gx, p.gy = w.gravity
     p.wall_u_bot, p.wall_u_top = w.wall_u
+    p.contact_model, p.E_young, p.nu_poisson = w.contact_model, w.E_young, w.nu_poisson
     return p
 
 

@@ -2,6 +2,9 @@
 
 * two-disk head-on collision against the damped linear oscillator: contact time
   pi / omega_d and restitution e (the damping is set from e);
+* the simplified Hertz-Mindlin law (the paper's, Sec. 2.2): an undamped head-on impact against
+  the closed-form Hertz peak overlap, contact time and rebound speed; with damping the
+  restitution falls as e falls and lies near e;
 * free flight under buoyancy-reduced gravity against the closed-form sum of the
   leapfrog recurrence;
 * a disk sliding on a wall decelerates at mu g until it rolls at 2/3 of its
@@ -143,3 +146,43 @@ def test_spinning_disk_torque_opposes_rotation(orc):
     F, T = sim.forces()
     assert T[0] < 0
     assert np.max(np.abs(F)) < 1e-12 * abs(T[0])
+
+
+def _hertz_collision(orc, E, nu, e, v0=0.01, R=10.0, N_sub=4000, steps=None):
+    w = _dem_only(x=[(100.0, 100.0), (120.002, 100.0)], v=[(v0, 0.0), (-v0, 0.0)], r=[R, R], e=e,
+                  N_sub=N_sub).with_(contact_model=1, E_young=E, nu_poisson=nu)
+    sim = orc.Sim(w)
+    in_contact, dmax = 0, 0.0
+    for _ in range(steps or N_sub):
+        sim.dem_substeps(1)
+        x, v, om = sim.particles()
+        if len(sim.contacts()):
+            in_contact += 1
+            dmax = max(dmax, 2 * R - (x[1, 0] - x[0, 0]))
+        assert abs(v[0, 0] + v[1, 0]) < 1e-17
+    x, v, _ = sim.particles()
+    return w, in_contact / N_sub, dmax, (v[1, 0] - v[0, 0]) / (2 * v0)
+
+
+def test_hertz_mindlin_head_on_collision_matches_closed_form(orc):
+    # undamped (e = 1) Hertz impact of two disks: m* delta'' = -K delta^(3/2) with
+    # K = 4/3 E* sqrt(R*), E* = E / (2 (1 - nu^2)): peak overlap (5 m* v^2 / (4 K))^(2/5) for the
+    # approach speed v, duration 2 (delta_max / v) (2/5) B(2/5, 1/2), rebound at the approach speed
+    R, v0, E, nu = 10.0, 0.01, 2.0e5, 0.3
+    w, tc_meas, dmax, e_meas = _hertz_collision(orc, E, nu, 1.0, v0=v0, R=R)
+    m = w.rho_s * math.pi * R * R
+    mstar, Rstar = m / 2, R / 2
+    K = 4.0 / 3.0 * E / (2 * (1 - nu * nu)) * math.sqrt(Rstar)
+    v = 2 * v0
+    delta_max = (5 * mstar * v * v / (4 * K)) ** 0.4
+    beta = math.gamma(0.4) * math.gamma(0.5) / math.gamma(0.9)
+    tc = 2 * delta_max / v * 0.4 * beta
+    assert abs(tc_meas - tc) <= 2.0 / w.N_sub + 1e-3 * tc
+    assert abs(dmax - delta_max) < 1e-3 * delta_max
+    assert abs(e_meas - 1.0) < 1e-4
+
+
+def test_hertz_mindlin_damping_orders_restitution(orc):
+    es = [_hertz_collision(orc, 2.0e5, 0.3, e)[3] for e in (0.9, 0.5, 0.2)]
+    assert 1.0 > es[0] > es[1] > es[2] > 0.0
+    assert abs(es[1] - 0.5) < 0.15      # the dashpot is set from e (di Renzo and di Maio)

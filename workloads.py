@@ -94,6 +94,9 @@ class Workload:
     rho_s: float = 2.65
     gravity: tuple = (0.0, 0.0)
     wall_u: tuple = (0.0, 0.0)         # x velocity of the walls y = 0 and y = ny
+    contact_model: int = 0             # 0 linear spring-dashpot, 1 simplified Hertz-Mindlin
+    E_young: float = 0.0               # Hertz-Mindlin material
+    nu_poisson: float = 0.3
     steps: int = 1000
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
     v: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
