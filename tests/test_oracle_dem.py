@@ -182,7 +182,8 @@ def test_hertz_mindlin_head_on_collision_matches_closed_form(orc):
     assert abs(e_meas - 1.0) < 1e-4
 
 
-def test_hertz_mindlin_damping_orders_restitution(orc):
-    es = [_hertz_collision(orc, 2.0e5, 0.3, e)[3] for e in (0.9, 0.5, 0.2)]
-    assert 1.0 > es[0] > es[1] > es[2] > 0.0
-    assert abs(es[1] - 0.5) < 0.15      # the dashpot is set from e (di Renzo and di Maio)
+def test_hertz_mindlin_damping_gives_the_restitution(orc):
+    # the dashpot 2 sqrt(5/6) |beta| sqrt(S_n m*) with beta from e returns the rebound speed
+    # e times the approach speed (to the sub-step's first-order error)
+    for e in (0.9, 0.5, 0.2):
+        assert abs(_hertz_collision(orc, 2.0e5, 0.3, e)[3] - e) < 2e-3
