@@ -51,6 +51,7 @@ extern "C" {
 enum { IMB_BC_PERIODIC = 0, IMB_BC_WALL = 1, IMB_BC_INLET_OUTLET = 2 };
 enum { IMB_STORE_FP32 = 0, IMB_STORE_FP16 = 1, IMB_STORE_BF16 = 2 };
 enum { IMB_EPS_EXACT = 0, IMB_EPS_SUBCELL = 1 };
+enum { IMB_CONTACT_LINEAR = 0, IMB_CONTACT_HERTZ_MINDLIN = 1 };
 
 /* Parameters of a lattice.  imb_default_params() fills every field. */
 typedef struct imb_params {
@@ -77,6 +78,13 @@ typedef struct imb_params {
                             halfway bounce-back with the moving-wall momentum term (wall
                             density 1); the fluid sees it, DEM wall contacts see walls at
                             rest (default 0, 0)                                                */
+    int contact_model;   /* IMB_CONTACT_LINEAR (kn, kt, e_rest, ct_ratio) or
+                            IMB_CONTACT_HERTZ_MINDLIN: the simplified Hertz-Mindlin law the paper
+                            adopts (Sec. 2.2): with s = sqrt(R* delta), k_n = 4/3 E* s, k_t = 8 G* s,
+                            dashpots 2 sqrt(5/6) |beta| sqrt(S m*) (S_n = 2 E* s, S_t = 8 G* s, beta
+                            from e_rest); E* = E / (2 (1 - nu^2)), G* = E / (4 (2 - nu)(1 + nu)),
+                            walls of the same material; mu caps the tangential force           */
+    double E_young, nu_poisson; /* Hertz-Mindlin material (E > 0, 0 <= nu < 1/2)               */
 } imb_params;
 
 typedef struct imb_ctx imb_ctx;

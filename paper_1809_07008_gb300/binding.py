@@ -92,7 +92,8 @@ class Params(C.Structure):
                 ("kn", C.c_double), ("kt", C.c_double), ("e_rest", C.c_double),
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double), ("skin", C.c_double),
-                ("timeout_ms", C.c_int), ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double)]
+                ("timeout_ms", C.c_int), ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double),
+                ("contact_model", C.c_int), ("E_young", C.c_double), ("nu_poisson", C.c_double)]
 
 
 _lib = None
@@ -236,6 +237,7 @@ class Lattice:
         p.mu, p.rho_s = w.mu, w.rho_s
         p.gx, p.gy = w.gravity
         p.wall_u_bot, p.wall_u_top = w.wall_u
+        p.contact_model, p.E_young, p.nu_poisson = w.contact_model, w.E_young, w.nu_poisson
         for k, v in kw.items():
             setattr(p, k, v)
         lat = cls(w.nx, w.ny, w.tau, w.C_smag, params=p)

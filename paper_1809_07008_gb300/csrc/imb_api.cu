@@ -61,6 +61,7 @@ struct imb_ctx {
     CUtensorMap tmap[2][2];         // TMA descriptors [buffer][narrow, wide] of the populations
     // parameters derived on the host
     double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
+    double hm_kn0 = 0.0, hm_sn0 = 0.0, hm_kt0 = 0.0, hm_c0 = 0.0;   // Hertz-Mindlin constants
     // timing / accounting
     bool timing = false;
     std::vector<cudaEvent_t> events;
@@ -168,6 +169,11 @@ static DemArgs dem_args(imb_ctx *c) {
     d.kn = c->p.kn;
     d.kt = c->p.kt;
     d.zeta = c->zeta;
+    d.model = c->p.contact_model;
+    d.hm_kn0 = c->hm_kn0;
+    d.hm_sn0 = c->hm_sn0;
+    d.hm_kt0 = c->hm_kt0;
+    d.hm_c0 = c->hm_c0;
     d.ct_ratio = c->p.ct_ratio;
     d.mu = c->p.mu;
     d.gx_eff = c->gx_eff;
@@ -299,6 +305,10 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     if (p.N_sub < 1 || !(p.kn > 0.0) || !(p.kt > 0.0) || !(p.e_rest > 0.0) || !(p.e_rest <= 1.0) ||
         !(p.rho_s > 0.0) || !(p.mu >= 0.0) || !(p.skin > 0.0))
         return fail(nullptr, IMB_E_INVALID_ARG, "bad DEM parameters");
+    if (p.contact_model < 0 || p.contact_model > 1 ||
+        (p.contact_model == IMB_CONTACT_HERTZ_MINDLIN &&
+         !(p.E_young > 0.0 && p.nu_poisson >= 0.0 && p.nu_poisson < 0.5)))
+        return fail(nullptr, IMB_E_INVALID_ARG, "bad contact model or Hertz-Mindlin material");
     if (p.timeout_ms <= 0) p.timeout_ms = 60000;
     if ((long long)nx * ny > (1ll << 31) / 16) return fail(nullptr, IMB_E_INVALID_ARG, "lattice too large");
 
@@ -317,6 +327,15 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     c->nbins = c->nbx * c->nby;
     const double le = std::log(p.e_rest);
     c->zeta = -le / std::sqrt(M_PI * M_PI + le * le);
+    {   // identical materials: E* = E / (2 (1 - nu^2)), G* = E / (4 (2 - nu)(1 + nu))
+        const double E = p.E_young, nu = p.nu_poisson;
+        const double Es = E / (2.0 * (1.0 - nu * nu));
+        const double Gs = E / (4.0 * (2.0 - nu) * (1.0 + nu));
+        c->hm_kn0 = 4.0 / 3.0 * Es;
+        c->hm_sn0 = 2.0 * Es;
+        c->hm_kt0 = 8.0 * Gs;
+        c->hm_c0 = 2.0 * std::sqrt(5.0 / 6.0) * c->zeta;
+    }
     c->gx_eff = (1.0 - 1.0 / p.rho_s) * p.gx;
     c->gy_eff = (1.0 - 1.0 / p.rho_s) * p.gy;
     auto bail = [&](cudaError_t e, const char *what) {

@@ -39,6 +39,8 @@ struct LatticeArgs {
 struct DemArgs {
     int np, nx, ny, bc_x, bc_y, N_sub;
     double dt, kn, kt, zeta, ct_ratio, mu, gx_eff, gy_eff, skin;
+    int model;                  // 0 linear spring-dashpot, 1 simplified Hertz-Mindlin
+    double hm_kn0, hm_sn0, hm_kt0, hm_c0;   // 4/3 E*, 2 E*, 8 G*, 2 sqrt(5/6) |beta|
     double *x, *v, *w;          // primary state [2np], [2np], [np]
     double *x1, *v1, *w1;       // second buffer of the coupled sub-cycle loop
     double *x_start;            // positions at the start of the coupling cycle

@@ -158,8 +158,10 @@ __global__ void k_bin_fill(const int *__restrict__ pbin, int np, int *fill, cons
 }
 
 // ----------------------------------------------------------------- DEM
-// Linear spring-dashpot contact seen from particle a (Eqs. 7-9): n from a to the
-// partner, t = z x n, (dvx, dvy) partner minus a, rot = w_a r_a + w_b r_b.
+// Spring-dashpot contact seen from particle a (Eqs. 7-9): n from a to the partner,
+// t = z x n, (dvx, dvy) partner minus a, rot = w_a r_a + w_b r_b, R* and m* the pair's
+// reduced radius and mass.  Linear law (cn of the pair precomputed) or the simplified
+// Hertz-Mindlin law of Sec. 2.2 (stiffness and dashpots from s = sqrt(R* delta)).
 // Returns the force on a and the tangential force magnitude.
 // Normal damping of a pair of reduced mass m* (set from the restitution coefficient).
 __device__ __forceinline__ double damping_cn(const DemArgs &d, double mstar) {
@@ -167,19 +169,32 @@ __device__ __forceinline__ double damping_cn(const DemArgs &d, double mstar) {
 }
 
 __device__ __forceinline__ void contact_law_cn(const DemArgs &d, double nxv, double nyv, double delta,
-                                               double dvx, double dvy, double rot, double cn,
-                                               double &xi, double &fx, double &fy, double &Ft) {
+                                               double dvx, double dvy, double rot, double cn_lin,
+                                               double Rstar, double mstar, double &xi, double &fx,
+                                               double &fy, double &Ft) {
     const double tx = -nyv, ty = nxv;
     const double vn = dvx * nxv + dvy * nyv;
     const double vt = (dvx * tx + dvy * ty) - rot;
-    const double ct = d.ct_ratio * cn;
+    double kn, kt, cn, ct;
+    if (d.model == 1) {
+        const double sq = sqrt(Rstar * delta);
+        kn = d.hm_kn0 * sq;
+        kt = d.hm_kt0 * sq;
+        cn = d.hm_c0 * sqrt(d.hm_sn0 * sq * mstar);
+        ct = d.hm_c0 * sqrt(d.hm_kt0 * sq * mstar);
+    } else {
+        kn = d.kn;
+        kt = d.kt;
+        cn = cn_lin;
+        ct = d.ct_ratio * cn;
+    }
     xi = xi + vt * d.dt;                     // incremental tangential spring (Eq. 9)
-    const double Fn = d.kn * delta - cn * vn; // Eq. 8, repulsive when positive
-    double F_t = d.kt * xi + ct * vt;        // Eq. 9
+    const double Fn = kn * delta - cn * vn;  // Eq. 8, repulsive when positive
+    double F_t = kt * xi + ct * vt;          // Eq. 9
     const double lim = d.mu * fabs(Fn);      // Coulomb cap
     if (fabs(F_t) > lim) {
         F_t = copysign(lim, F_t);
-        xi = copysign(lim / d.kt, xi);
+        xi = copysign(lim / kt, xi);
     }
     fx = -Fn * nxv + F_t * tx;
     fy = -Fn * nyv + F_t * ty;
@@ -187,9 +202,10 @@ __device__ __forceinline__ void contact_law_cn(const DemArgs &d, double nxv, dou
 }
 
 __device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double nyv, double delta,
-                                            double dvx, double dvy, double rot, double mstar,
+                                            double dvx, double dvy, double rot, double Rstar, double mstar,
                                             double &xi, double &fx, double &fy, double &Ft) {
-    contact_law_cn(d, nxv, nyv, delta, dvx, dvy, rot, damping_cn(d, mstar), xi, fx, fy, Ft);
+    contact_law_cn(d, nxv, nyv, delta, dvx, dvy, rot, d.model == 1 ? 0.0 : damping_cn(d, mstar), Rstar, mstar,
+                   xi, fx, fy, Ft);
 }
 
 // Force of candidate slot j on particle p (seen from p), the pair's damping constant
@@ -214,7 +230,13 @@ __device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const 
     const double dist = sqrt(d2);
     const double nxv = dx / dist, nyv = dy / dist;
     const double rot = w * rp + qw * d.r[q];
-    contact_law_cn(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, d.nbr_cn[p * MAX_NBR + j], xi, fx, fy, Ft);
+    double Rstar = 0.0, mstar = 0.0;
+    if (d.model == 1) {
+        Rstar = rp * d.r[q] / (rp + d.r[q]);
+        mstar = d.m[p] * d.m[q] / (d.m[p] + d.m[q]);
+    }
+    contact_law_cn(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, d.nbr_cn[p * MAX_NBR + j], Rstar, mstar, xi,
+                   fx, fy, Ft);
     return true;
 }
 
@@ -236,7 +258,7 @@ __device__ __forceinline__ void wall_contacts(const DemArgs &d, int p, double px
             continue;
         }
         double fx, fy, Ft;
-        contact_law(d, nxv, nyv, rp - dist, -vx, -vy, w * rp, mp, xiw[wl], fx, fy, Ft);
+        contact_law(d, nxv, nyv, rp - dist, -vx, -vy, w * rp, rp, mp, xiw[wl], fx, fy, Ft);
         Fcx += fx;
         Fcy += fy;
         Tc += rp * Ft;

@@ -169,6 +169,29 @@ def test_dem_only_trajectories_bit_exact(orc, imb):
     assert len(o.contacts()) > 10
 
 
+def test_dem_only_hertz_mindlin_bit_exact(orc, imb):
+    # the paper's contact law (simplified Hertz-Mindlin, Sec. 2.2) on the same pile: the GPU
+    # sub-cycles reproduce the oracle bit for bit
+    w = _pile().with_(contact_model=1, E_young=2.0e6, nu_poisson=0.3)
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    cycles = 40
+    o.dem_substeps(cycles * w.N_sub)
+    g.dem_step(cycles)
+    xo, vo, wo = o.particles()
+    xg, vg, wg = g.particles()
+    assert np.array_equal(xo, xg) and np.array_equal(vo, vg) and np.array_equal(wo, wg)
+    assert np.array_equal(o.contacts(), g.contacts())
+    assert len(o.contacts()) > 10
+    # the pile settles differently under the two laws
+    lin = orc.Sim(_pile())
+    lin.dem_substeps(cycles * w.N_sub)
+    assert not np.array_equal(lin.particles()[0], xo)
+    g.close()
+    with pytest.raises(imb.ImbError):       # Hertz-Mindlin needs a material
+        imb.Lattice.from_workload(_pile().with_(contact_model=1, E_young=0.0))
+
+
 def test_dem_only_with_frozen_fluid_force_bit_exact(orc, imb):
     w = _pile(rows=4, cols=10, seed=9)
     rng = np.random.default_rng(9)
