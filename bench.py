@@ -269,8 +269,9 @@ def time_drag_gradient(imb, T=4000, checkpoint_every=100, nx=512, ny=256, snapsh
             "of the whole gradient (forward, recomputation and adjoint)", "J": J, "dJ_duin": g_u,
             "dJ_dtau": g_tau, "dJ_dx_max": float(np.abs(g_x).max()),
             "binomial": {"snapshots": snapshots, "seconds": round(dtb, 4), "forward_steps": fwd_b + 1,
-                         "states_held": snapshots + 1, "J_rel_diff": abs(Jb - J) / abs(J),
-                         "dJ_dtau_rel_diff": abs(g_taub - g_tau) / abs(g_tau)}}
+                         "states_held": snapshots + 1,
+                         "J_rel_diff": abs(Jb - J) / abs(J) if J != 0.0 else abs(Jb - J),
+                         "dJ_dtau_rel_diff": abs(g_taub - g_tau) / abs(g_tau) if g_tau != 0.0 else abs(g_taub - g_tau)}}
 
 
 def time_batched_sweep(imb, steps=5000, n_domains=256, storage="fp16"):

@@ -139,16 +139,16 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const float *__restrict__ 
         }
         float drho = 0.0f, jx = 0.0f, jy = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 0; q < 9; ++q) {   // products with a zero velocity component left out
             drho += d[q];
-            jx += (float)cx_of(q) * d[q];
-            jy += (float)cy_of(q) * d[q];
+            if (cx_of(q) != 0) jx += cx_of(q) > 0 ? d[q] : -d[q];
+            if (cy_of(q) != 0) jy += cy_of(q) > 0 ? d[q] : -d[q];
         }
         const float rho = 1.0f + drho, ux = jx / rho, uy = jy / rho, usq = ux * ux + uy * uy;
         float n[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+            const float cu = cdot(q, ux, uy);
             n[q] = d[q] - w_of(q) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
         }
         const size_t c = (size_t)y * a.nx + x;
@@ -164,17 +164,21 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const float *__restrict__ 
         float lr = nu, ljx = 0.0f, ljy = 0.0f;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q), cu = cxq * ux + cyq * uy;
+            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q), cu = cdot(q, ux, uy);
             lr += mu[q] * w_of(q) * (1.0f - 4.5f * cu * cu + 1.5f * usq);
-            ljx += mu[q] * w_of(q) * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux);
-            ljy += mu[q] * w_of(q) * (3.0f * cyq + 9.0f * cu * cyq - 3.0f * uy);
+            ljx += mu[q] * w_of(q) * (cx_of(q) != 0 ? 3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux : -3.0f * ux);
+            ljy += mu[q] * w_of(q) * (cy_of(q) != 0 ? 3.0f * cyq + 9.0f * cu * cyq - 3.0f * uy : -3.0f * uy);
         }
         float gtf = 0.0f;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-            lam0[(size_t)q * a.plane + (size_t)y * a.pitch + x] =
-                L[q] * (1.0f - af - B) + B * L[opp_of(q)] + inv_T * B * cxq + lr + cxq * ljx + cyq * ljy;
+            float v = L[q] * (1.0f - af - B) + B * L[opp_of(q)];
+            if (cx_of(q) != 0) v += inv_T * B * cxq;
+            v += lr;
+            if (cx_of(q) != 0) v += cxq * ljx;
+            if (cy_of(q) != 0) v += cyq * ljy;
+            lam0[(size_t)q * a.plane + (size_t)y * a.pitch + x] = v;
             gtf += L[q] * (1.0f - B) * n[q] / (tau * tau);
         }
         gt = gtf;

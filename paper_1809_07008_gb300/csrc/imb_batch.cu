@@ -62,7 +62,7 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     float n[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {   // non-equilibrium parts (Eq. 2)
-        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        const float cu = cdot(q, ux, uy);
         n[q] = d[q] - w_of(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
     }
     float omega = D.omega0, te = D.tau;
@@ -86,8 +86,8 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     const float b0 = w_of(0) * Bd, b1 = w_of(1) * Bd, b5 = w_of(5) * Bd;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
-        const float cF = (float)cx_of(q) * D.Fx + (float)cy_of(q) * D.Fy;
+        const float cu = cdot(q, ux, uy);
+        const float cF = cdot(q, D.Fx, D.Fy);
         const float Sq = fmaf(cF, fmaf(9.0f, cu, 3.0f), g);
         const float kq = q == 0 ? k0 : (q < 5 ? k1 : k5), bq = q == 0 ? b0 : (q < 5 ? b1 : b5);
         const float v = fmaf(fl, d[q], fmaf(flw, n[q], fmaf(B, n[opp_of(q)], fmaf(kq, Sq, bq))));

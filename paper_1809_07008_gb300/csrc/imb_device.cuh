@@ -26,6 +26,22 @@ __host__ __device__ constexpr float w_of(int q) {
     return q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
 }
 
+// c_q . (a, b) with the zero components of c_q left out (under IEEE rules the compiler may not
+// drop a product with 0)
+__device__ __forceinline__ float cdot(int q, float a, float b) {
+    const int x = cx_of(q), y = cy_of(q);
+    const float ta = x > 0 ? a : -a, tb = y > 0 ? b : -b;
+    return x == 0 ? (y == 0 ? 0.0f : tb) : (y == 0 ? ta : ta + tb);
+}
+// c_q c_q : (A xx, A yy, A xy) likewise
+__device__ __forceinline__ float ccdot(int q, float axx, float ayy, float axy) {
+    const int x = cx_of(q), y = cy_of(q);
+    if (x == 0 && y == 0) return 0.0f;
+    if (y == 0) return axx;
+    if (x == 0) return ayy;
+    return (x == y ? axx + 2.0f * axy : axx - 2.0f * axy) + ayy;
+}
+
 enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET_OUTLET = 2 };
 enum : int { EPS_EXACT = 0, EPS_SUBCELL = 1 };
 

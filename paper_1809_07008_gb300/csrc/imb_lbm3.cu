@@ -38,6 +38,20 @@ __host__ __device__ constexpr int cz3(int q) {
            : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
 }
 __host__ __device__ constexpr int opp3(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+
+// c_q . (a, b, c) with the zero components of c_q left out (under IEEE rules the compiler may
+// not drop a product with 0, and these dot products run for every direction of every node)
+__device__ __forceinline__ float cdot3(int q, float a, float b, float c) {
+    const int x = cx3(q), y = cy3(q), z = cz3(q);
+    const float ta = x > 0 ? a : -a, tb = y > 0 ? b : -b, tc = z > 0 ? c : -c;
+    if (x == 0 && y == 0 && z == 0) return 0.0f;
+    if (y == 0 && z == 0) return ta;
+    if (x == 0 && z == 0) return tb;
+    if (x == 0 && y == 0) return tc;
+    if (z == 0) return ta + tb;
+    if (y == 0) return ta + tc;
+    return tb + tc;
+}
 __host__ __device__ constexpr float w3(int q) { return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
 
 constexpr unsigned ID_BITS = 22, ID_MASK = (1u << ID_BITS) - 1u;   // map word: sphere + 1 | count << 22
@@ -199,7 +213,7 @@ __device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, in
     float n[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
-        const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
+        const float cu = cdot3(q, ux, uy, uz);
         n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
     }
     const unsigned word = map[cell];
@@ -224,12 +238,12 @@ __device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, in
     const float ts = fmaf(-1.5f * rho, uss, drho);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-        const float cu = cx3(q) * ux + cy3(q) * uy + cz3(q) * uz;
-        const float cF = cx3(q) * a.Fx + cy3(q) * a.Fy + cz3(q) * a.Fz;
+        const float cu = cdot3(q, ux, uy, uz);
+        const float cF = cdot3(q, a.Fx, a.Fy, a.Fz);
         const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);   // Guo forcing / (1 - 1/(2 tau))
         float v = fl * fmaf(-a.omega, n[q], sf * Sg);
         if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q
-            const float cs = cx3(q) * usx + cy3(q) * usy + cz3(q) * usz;
+            const float cs = cdot3(q, usx, usy, usz);
             const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
             v = fmaf(B, n[opp3(q)] + eqs - d[q], v);
         }

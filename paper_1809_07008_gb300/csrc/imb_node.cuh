@@ -32,7 +32,7 @@ __device__ __forceinline__ void node_state(const float (&d)[9], const LatticeArg
     // ---- non-equilibrium parts (Eq. 2)
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const float cu = (float)cx_of(q) * c.ux + (float)cy_of(q) * c.uy;
+        const float cu = cdot(q, c.ux, c.uy);
         c.n[q] = d[q] - w_of(q) * (c.drho + c.rho * (cu * (3.0f + 4.5f * cu) - 1.5f * c.usq));
     }
     // ---- Smagorinsky effective relaxation time (Hou et al. 1996 closure)
@@ -75,15 +75,15 @@ __device__ __forceinline__ void node_collide_store(const float (&d)[9], const No
         const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
         float upd = -c.omega * c.n[q];
         if (forced) {  // Guo forcing term
-            const float cu = cxq * c.ux + cyq * c.uy;
+            const float cu = cdot(q, c.ux, c.uy);
             const float S_q = w_of(q) * (3.0f * ((cxq - c.ux) * a.Fx + (cyq - c.uy) * a.Fy) +
-                                         9.0f * cu * (cxq * a.Fx + cyq * a.Fy));
+                                         9.0f * cu * cdot(q, a.Fx, a.Fy));
             upd = fmaf(sf, S_q, upd);
         }
         upd *= fl;
         if (B > 0.0f) {
-            const float ca1 = cxq * a1x + cyq * a1y;
-            const float ca2c = cxq * cxq * a2xx + 2.0f * cxq * cyq * a2xy + cyq * cyq * a2yy;
+            const float ca1 = cdot(q, a1x, a1y);
+            const float ca2c = ccdot(q, a2xx, a2yy, a2xy);
             upd += B * (c.n[opp_of(q)] - c.n[q]) + c.rho * w_of(q) * (3.0f * ca1 + 4.5f * ca2c - 1.5f * tra2);
         }
         Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);

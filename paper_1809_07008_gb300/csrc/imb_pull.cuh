@@ -46,7 +46,7 @@ __device__ __forceinline__ void equilibrium_shifted(float drho, float rho, float
     const float usq = ux * ux + uy * uy;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const float cu = (float)cx_of(q) * ux + (float)cy_of(q) * uy;
+        const float cu = cdot(q, ux, uy);
         d[q] = w_of(q) * (drho + rho * (cu * (3.0f + 4.5f * cu) - 1.5f * usq));
     }
 }
