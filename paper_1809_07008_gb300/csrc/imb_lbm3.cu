@@ -234,20 +234,26 @@ __device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, in
     }
     const float fl = 1.0f - B, sf = 1.0f - 0.5f * a.omega;
     const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
-    const float uss = usx * usx + usy * usy + usz * usz;
-    const float ts = fmaf(-1.5f * rho, uss, drho);
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
+    // BGK with Guo forcing (its source divided by 1 - 1/(2 tau)), weighted by 1 - B
+    auto fluid = [&](int q) {
         const float cu = cdot3(q, ux, uy, uz);
         const float cF = cdot3(q, a.Fx, a.Fy, a.Fz);
-        const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);   // Guo forcing / (1 - 1/(2 tau))
-        float v = fl * fmaf(-a.omega, n[q], sf * Sg);
-        if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q
+        const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        return fmaf(-a.omega, n[q], sf * Sg);
+    };
+    if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q, weighted by B
+        const float uss = usx * usx + usy * usy + usz * usz;
+        const float ts = fmaf(-1.5f * rho, uss, drho);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
             const float cs = cdot3(q, usx, usy, usz);
             const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
-            v = fmaf(B, n[opp3(q)] + eqs - d[q], v);
+            const float v = fmaf(B, n[opp3(q)] + eqs - d[q], fl * fluid(q));
+            Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
         }
-        Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
+    } else {      // no sphere: the fluid operator alone
+#pragma unroll
+        for (int q = 0; q < 19; ++q) Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + fluid(q));
     }
     if (word) {   // Eqs. 15-16: force on the sphere B (rho u - rho u_s - F), torque r x force
         fo[0] = B * (jx - rho * usx - a.Fx);
