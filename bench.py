@@ -499,18 +499,16 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(e2e_steps):   # one imb_step_io per cycle: upload, cycle, read back, one wait
         if n:
-            lat.set_kinematics(hx, hv, hw)
-        lat.step(1)
-        if n:
-            lat.forces(F, T)
-            lat.particles(hx, hv, hw)
+            lat.step_io(1, (hx, hv, hw), F, T, hx, hv, hw)
+        else:
+            lat.step(1)
     t1 = time.perf_counter()
     e2e_s = max_over_ranks(t1 - t0, world)
     e2e_mlups = sum_over_ranks(float(cells) * e2e_steps, world) / e2e_s / 1e6
     e2e = {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 40 * n,
-           "d2h_bytes_per_step": 24 * n + 40 * n, "steps": e2e_steps}
+           "d2h_bytes_per_step": 24 * n + 40 * n, "steps": e2e_steps, "call": "imb_step_io"}
 
     variants, others = {}, {}
     if rank == 0 and ((not args.no_variants and args.storage == "fp32") or not args.no_other):

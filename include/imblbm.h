@@ -117,6 +117,16 @@ int imb_set_kinematics(imb_ctx *ctx, const double *x, const double *v, const dou
  * the call waits (bounded by timeout_ms) for them and checks the device error flags. */
 int imb_step(imb_ctx *ctx, int n);
 
+/* One host-coupled round trip: when x_in, v_in and omega_in are given (host arrays of
+ * 2n, 2n and n values, as imb_set_kinematics; all three or none) they are uploaded first,
+ * then n coupling cycles run, then the force F_out[2n] and torque T_out[n] of the last
+ * cycle and the particle state x_out[2n], v_out[2n], omega_out[n] are read back (each
+ * output may be NULL).  Everything is queued on the context stream and the call waits
+ * once; for pinned host arrays the copies are asynchronous.  Errors as imb_step and
+ * imb_set_kinematics. */
+int imb_step_io(imb_ctx *ctx, int n, const double *x_in, const double *v_in, const double *omega_in,
+                double *F_out, double *T_out, double *x_out, double *v_out, double *omega_out);
+
 /* Queue n coupling cycles without waiting and without reading the error flags
  * (imb_sync() does both).  Used for timing. */
 int imb_step_async(imb_ctx *ctx, int n);

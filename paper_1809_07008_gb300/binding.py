@@ -31,7 +31,7 @@ EXPORTS = (
     "imb_get_macro", "imb_get_forces", "imb_set_forces", "imb_get_particles",
     "imb_get_cell_map", "imb_get_contacts", "imb_get_bins", "imb_set_stream", "imb_get_stream",
     "imb_enable_kernel_timing", "imb_kernel_time", "imb_launch_count", "imb_bytes_per_cell",
-    "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient",
+    "imb_last_error", "imb_destroy", "imb_bin_particles_noalloc", "imb_drag_gradient", "imb_step_io",
     "imb_drag_gradient_binomial", "imb_binomial_schedule",
     "imb3_default_params", "imb3_init", "imb3_set_spheres", "imb3_step", "imb3_get_populations",
     "imb3_get_macro", "imb3_get_forces", "imb3_get_cell_map", "imb3_enable_kernel_timing",
@@ -125,6 +125,7 @@ def load(build_if_missing: bool = True):
     for name in ("imb_step", "imb_step_async", "imb_dem_step"):
         getattr(L, name).argtypes = [_vp, C.c_int]
     L.imb_sync.argtypes = [_vp]
+    L.imb_step_io.argtypes = [_vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.imb_get_populations.argtypes = [_vp, _dp]
     L.imb_get_macro.argtypes = [_vp, _dp, _dp, _dp]
     L.imb_get_forces.argtypes = [_vp, _dp, _dp]
@@ -275,6 +276,21 @@ class Lattice:
 
     def step(self, n=1):
         self._check(self._L.imb_step(self.h, int(n)))
+
+    def step_io(self, n=1, kin_in=None, F=None, T=None, x=None, v=None, w=None):
+        """imb_step_io: optional upload of (x, v, omega), n cycles, read-back into the given
+        host arrays (any may be None), one wait."""
+        n_p = self.np
+        xi = vi = wi = None
+        if kin_in is not None:
+            xi, vi, wi = kin_in
+            xi, vi, wi = _d(_f64(xi, 2 * n_p)), _d(_f64(vi, 2 * n_p)), _d(_f64(wi, n_p))
+        outs = []
+        for a, k in ((F, 2), (T, 1), (x, 2), (v, 2), (w, 1)):
+            if a is not None and (a.size != k * n_p or a.dtype != np.float64 or not a.flags.c_contiguous):
+                raise ValueError(f"outputs must be contiguous float64 arrays of {k} x {n_p} values")
+            outs.append(None if a is None else _d(a))
+        self._check(self._L.imb_step_io(self.h, int(n), xi, vi, wi, *outs))
 
     def step_async(self, n=1):
         self._check(self._L.imb_step_async(self.h, int(n)))

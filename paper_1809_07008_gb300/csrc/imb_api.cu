@@ -608,6 +608,25 @@ extern "C" int imb_step(imb_ctx *c, int n) {
     return imb_sync(c);
 }
 
+extern "C" int imb_step_io(imb_ctx *c, int n, const double *x_in, const double *v_in, const double *omega_in,
+                           double *F_out, double *T_out, double *x_out, double *v_out, double *omega_out) {
+    if (!c) return IMB_E_INVALID_ARG;
+    const bool in = x_in || v_in || omega_in;
+    if (in && !(x_in && v_in && omega_in)) return fail(c, IMB_E_INVALID_ARG, "give x_in, v_in and omega_in together");
+    int rc;
+    if (in && (rc = imb_set_kinematics(c, x_in, v_in, omega_in))) return rc;
+    if ((rc = queue_steps(c, n))) return rc;
+    const size_t np = (size_t)c->np;
+    if (np) {
+        if (F_out) CK(cudaMemcpyAsync(F_out, c->F, 16 * np, cudaMemcpyDeviceToHost, c->stream), "copy F");
+        if (T_out) CK(cudaMemcpyAsync(T_out, c->T, 8 * np, cudaMemcpyDeviceToHost, c->stream), "copy T");
+        if (x_out) CK(cudaMemcpyAsync(x_out, c->x, 16 * np, cudaMemcpyDeviceToHost, c->stream), "copy x");
+        if (v_out) CK(cudaMemcpyAsync(v_out, c->v, 16 * np, cudaMemcpyDeviceToHost, c->stream), "copy v");
+        if (omega_out) CK(cudaMemcpyAsync(omega_out, c->w, 8 * np, cudaMemcpyDeviceToHost, c->stream), "copy w");
+    }
+    return imb_sync(c);
+}
+
 extern "C" int imb_dem_step(imb_ctx *c, int n) {
     if (!c) return IMB_E_INVALID_ARG;
     if (n < 0) return fail(c, IMB_E_INVALID_ARG, "n must be >= 0");
