@@ -7,6 +7,7 @@ each domain by itself.
   (FP32 storage: 1e-6; FP16: 2e-4, the rounding of the stored deviation f - w accumulated over
   the steps) and the per-domain mean drag (FP32: 1e-4 of the drag scale; FP16: 1 %, the storage
   bar the single-lattice tests use).
+* A domain without disks (zero drag) beside one with disks, and a batch of a single domain.
 * Steps taken two at a time by the replayed graph or one at a time give the same populations
   (bit for bit), the launch-shape search leaves the state as it found it, and steps with the
   shape it chose agree to FP32 rounding.
@@ -99,3 +100,22 @@ def test_set_launch_rejects_bad_shapes_and_keeps_state(imb):
     for k in range(len(ds)):
         assert np.array_equal(b.populations(k), before[k])
     b.close()
+
+
+def test_domain_without_disks_and_single_domain(orc, imb):
+    # a domain with no disks (plain forced periodic flow, zero drag) beside one with disks,
+    # and a batch of one domain
+    plain = W.c5_domain(0, 64, 48, 12.0, 0.2, 0.7, 1.0, 31).with_(x=np.zeros((0, 2)), v=np.zeros((0, 2)),
+                                                               omega=np.zeros(0), r=np.zeros(0))
+    ds = [plain, W.c5_domain(1, 96, 64, 12.0, 0.2, 0.7, 1.0, 32)]
+    for batch in (ds, ds[1:]):
+        b = imb.Batch(batch, storage="fp32")
+        b.run(100)
+        fx, fy = b.mean_drag()
+        for k, w in enumerate(batch):
+            o = orc.Sim(w)
+            o.step(100)
+            assert np.abs(b.populations(k) - o.f()).max() < 1e-6
+        if batch is ds:
+            assert fx[0] == 0.0 and fy[0] == 0.0 and fx[1] != 0.0
+        b.close()

@@ -10,6 +10,9 @@ Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 
 * Errors: two spheres on one cell -> IMB_E_OVERFLOW; bad sizes and radii -> IMB_E_INVALID_ARG.
 * Walls moving along x (Couette, Sec. 3.4): the fluid-only profile is the exact line within
   FP32 rounding, and a box with three spheres matches the oracle after 200 steps.
+* Full size: the bench's 16 M-cell box, one step checked on a window around the sphere that the
+  oracle steps from the GPU's own f(x, t) (interior populations 2e-6, force 1e-4, torque 1e-4
+  of R x the force scale).
 * Benchmark: N = 5 and 10 cells per diameter, n_sub = 5, tau = 1, run to a steady drag: the
   relative errors against Eqs. 18-19 fall with N and lie within 3 percentage points of the
   paper's Table 2 (17.8 / 31.4 % at N = 5, 7.0 / 11.3 % at N = 10).
@@ -152,3 +155,33 @@ def test_couette_moving_walls(orc, imb):
     assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
     assert np.abs(Tg - To).max() < 1e-4 * np.abs(To).max()
     g.close()
+
+
+def test_full_size_box_on_a_window(orc, imb):
+    # the bench's 400 x 100 x 400 box (N = 20, 16 M cells): 40 steps on the GPU, then one step
+    # of the oracle on a 48 x 100 x 48 window around the sphere started from the GPU's f(x, t);
+    # the window's x and z edges are not the lattice's, so only cells at least 2 from them
+    # are compared, and the sphere (radius 10) lies inside that interior
+    w = W.happel(20)
+    g = imb.Lattice3.from_workload(w)
+    g.step(40)
+    f_t = g.populations()
+    g.step(1)
+    F, T = g.forces()
+    f_t1 = g.populations()
+    g.close()
+    cx, cz, S = int(w.x[0, 0]), int(w.x[0, 2]), 48
+    x0, z0 = cx - S // 2, cz - S // 2
+    ww = W.Workload3(name="window3", nx=S, ny=w.ny, nz=S, tau=w.tau, wall_y=True, force=w.force,
+                     n_sub=w.n_sub, x=w.x - np.array([x0, 0.0, z0]), v=w.v, omega=w.omega, R=w.R)
+    o = orc.Sim3(ww)
+    o.set_f(np.ascontiguousarray(f_t[:, z0:z0 + S, :, x0:x0 + S]))
+    o.step(1)
+    m = 2
+    diff = np.abs(o.f()[:, m:S - m, :, m:S - m] - f_t1[:, z0 + m:z0 + S - m, :, x0 + m:x0 + S - m])
+    assert diff.max() < 2e-6
+    Fo, To = o.forces()
+    # torque bar on the scale R x the force scale, as in the 2D tests: early in the flow the
+    # net torque is a near-cancelling sum of the cells' FP32 terms
+    assert np.abs(F - Fo).max() < 1e-4 * np.abs(Fo).max()
+    assert np.abs(T - To).max() < 1e-4 * np.abs(Fo).max() * w.R[0]
