@@ -24,8 +24,9 @@
  *   4. Stream (Eq. 1 LHS) with periodic, halfway bounce-back and
  *      inlet/outlet boundaries.
  *
- * Readings of points the paper leaves open are listed in the design doc; the ones
- * that change arithmetic are repeated at the code that applies them.
+ * Where the paper leaves a point open (lattice order, force sign, which tau enters
+ * B, forcing scheme, wall placement, contact constants), the reading taken is
+ * stated at the code that applies it.
  */
 #include "imb_oracle.h"
 
