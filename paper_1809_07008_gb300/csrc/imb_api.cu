@@ -26,6 +26,8 @@ struct imb_ctx {
     imb_params p{};
     int device = 0;
     cudaStream_t own_stream = nullptr, stream = nullptr;
+    cudaStream_t side = nullptr;                  // solid-ratio tables beside the bins and tile lists
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *fbuf[2] = {nullptr, nullptr};
     int cur = 0;               // buffer holding the latest post-collision populations
     size_t plane = 0, elem = 4;
@@ -257,6 +259,10 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->tiles);
     dfree(c->eps_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -347,6 +353,10 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "cudaStreamCreate");
     c->stream = c->own_stream;
+    if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(e, "side stream");
     for (int b = 0; b < 2; ++b)
         if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess)
             return bail(e, "population buffers");
@@ -393,10 +403,17 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
                              0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
                              c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
        "particle table");
+    // the solid-ratio tables need only the particle records: they run on the side stream
+    // while the bins and the tile lists are built, and the stream waits for them at the end
+    CK(cudaEventRecord(c->ev_fork, c->stream), "fork");
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+    CK(launch_particle_eps(lattice_args(c), c->side), "solid-ratio tables");
+    CK(cudaEventRecord(c->ev_join, c->side), "join");
     CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->bin_bsum, c->counters, c->stream),
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
     CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
     c->launches += 6;   // table, scan (two passes), fill, tile lists, solid-ratio map
     return IMB_OK;
 }

@@ -74,6 +74,7 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
                                   const TileCand *tiles, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
+cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s);
 int tma_box_width(int storage, int wide);
 int tma_box_rows(int storage);
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,

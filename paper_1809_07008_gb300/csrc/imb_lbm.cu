@@ -803,8 +803,11 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s) {
     const int ntiles = a.nbx * a.nby;
     k_tile_lists<<<(ntiles + WARPS - 1) / WARPS, BLOCK, 0, s>>>(a, tiles, ntiles);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.np == 0) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s) {
+    if (a.np == 0) return cudaSuccess;
     k_particle_eps<<<(a.np + EPS_WARPS - 1) / EPS_WARPS, 32 * EPS_WARPS, 0, s>>>(
         a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h, a.tab_stride);
     return cudaGetLastError();
