@@ -1,0 +1,87 @@
+"""The seeded inputs shared by the oracle and the GPU path.
+
+* splitmix64 reproduces its published outputs (Steele, Lea and Flood; the reference
+  implementation's first values for seeds 0 and 1234567), and the doubles drawn from it use
+  the top 53 bits;
+* random sequential addition keeps every pair of disks (minimum image) and every disk and wall
+  at least the stated gap apart, in the suspension, the periodic sweep domains and the sphere
+  boxes;
+* the batched sweep's 256 domains have the stated sizes, fractions, relaxation times and a
+  mean speed capped at 0.02; the Poiseuille-flow-past-a-sphere box has the paper's proportions
+  (walls 5 N apart, l_x = l_z = 20 N, radius N / 2, centre N 5/4 above the lower wall) and the body
+  force that gives the stated centre-height velocity.
+"""
+import math
+
+import numpy as np
+
+import workloads as W
+
+
+def test_splitmix64_published_outputs():
+    r = W.SplitMix64(0)
+    assert [r.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert W.SplitMix64(1234567).next_u64() == 6457827717110365317
+    r1, r2 = W.SplitMix64(99), W.SplitMix64(99)
+    u = r1.uniform()
+    assert u == (r2.next_u64() >> 11) / 2.0 ** 53 and 0.0 <= u < 1.0
+
+
+def _min_pair_gap(x, r, Lx, Ly, per_x, per_y):
+    d = x[:, None, :] - x[None, :, :]
+    if per_x:
+        d[..., 0] -= Lx * np.round(d[..., 0] / Lx)
+    if per_y:
+        d[..., 1] -= Ly * np.round(d[..., 1] / Ly)
+    dist = np.sqrt((d ** 2).sum(-1))
+    gap = dist - (r[:, None] + r[None, :])
+    np.fill_diagonal(gap, np.inf)
+    return gap.min()
+
+
+def test_suspension_disks_keep_their_gap():
+    w = W.c3sub(steps=0, nx=512, ny=512)
+    assert w.n_particles == round(20000 * 512 * 512 / (8192 * 4096))
+    assert _min_pair_gap(w.x, w.r, w.nx, w.ny, True, False) >= 1.0 - 1e-12
+    assert (w.x[:, 1] - w.r >= 1.0 - 1e-12).all() and (w.x[:, 1] + w.r <= w.ny - 1.0 + 1e-12).all()
+    assert np.allclose(np.linalg.norm(w.v, axis=1), 0.005)
+
+
+def test_sweep_domains():
+    ds = W.c5(256)
+    assert len(ds) == 256
+    for w in ds:
+        assert 128 <= w.nx <= 512 and w.nx % 32 == 0 and 128 <= w.ny <= 256 and w.ny % 32 == 0
+        assert 0.51 <= w.tau < 1.0 and w.C_smag == 0.1 and w.force[0] > 0.0 and w.force[1] == 0.0
+        d = 2 * w.r[0]
+        assert 10.0 <= d < 30.0 and np.all(w.r == w.r[0])
+        if w.n_particles > 1:
+            assert _min_pair_gap(w.x, w.r, w.nx, w.ny, True, True) >= 1.0 - 1e-12
+        phi = w.n_particles * math.pi * w.r[0] ** 2 / (w.nx * w.ny)
+        assert 0.0 < phi < 0.5 + 1e-9
+        nu = (w.tau - 0.5) / 3.0
+        k = d * d * (1 - phi) ** 3 / (9 * phi * phi)
+        U = w.force[0] * k / nu
+        assert U <= 0.02 + 1e-12
+    # reproducible from the seed
+    again = W.c5(3)
+    assert all(np.array_equal(a.x, b.x) and a.tau == b.tau for a, b in zip(again, ds[:3]))
+
+
+def test_sphere_boxes_and_happel_geometry():
+    w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=3)
+    assert w.n_spheres == 3
+    for i in range(3):
+        for j in range(i + 1, 3):
+            d = w.x[i] - w.x[j]
+            d[0] -= w.nx * round(d[0] / w.nx)
+            d[2] -= w.nz * round(d[2] / w.nz)
+            assert np.linalg.norm(d) >= w.R[i] + w.R[j] + 2.0
+        assert w.x[i, 1] - w.R[i] >= 2.0 and w.x[i, 1] + w.R[i] <= w.ny - 2.0
+    for N in (5, 10, 20):
+        h = W.happel(N)
+        assert (h.nx, h.ny, h.nz) == (20 * N, 5 * N, 20 * N) and h.R[0] == N / 2
+        assert tuple(h.x[0]) == (10 * N, 1.25 * N, 10 * N) and h.wall_y
+        nu = (h.tau - 0.5) / 3.0
+        yc, H = h.x[0, 1], h.ny
+        assert abs(h.force[0] / (2 * nu) * yc * (H - yc) - 2.0e-4) < 1e-15
