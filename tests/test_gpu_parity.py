@@ -392,3 +392,12 @@ def test_step_io_equals_separate_calls(imb):
         a.step_io(1, None, np.zeros(3))
     a.close()
     b.close()
+
+
+def test_lid_driven_cavity_parity(orc, imb):
+    # moving top wall meeting the fixed side walls at the corners: GPU against the oracle
+    w = W.Workload(name="cavity", nx=96, ny=64, tau=0.7, bc_x=W.BC_WALL, bc_y=W.BC_WALL, wall_u=(0.0, 0.05))
+    o, g = _run_pair(orc, imb, w, 500)
+    assert np.abs(g.populations() - o.f()).max() < 1e-6
+    assert _u_rel_l2(g.macro(), o.macro(), np.ones((w.ny, w.nx), bool)) < 1e-5
+    g.close()

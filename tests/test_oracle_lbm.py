@@ -156,3 +156,17 @@ def test_plane_couette_exact_with_moving_walls(orc):
     assert np.abs(ux - (-uw + 2 * uw * y / H)[:, None]).max() < 1e-13
     assert np.abs(uy).max() < 1e-13
     assert abs(rho.sum() - m0) < 1e-12 * m0
+
+
+def test_lid_driven_cavity_conserves_mass(orc):
+    # closed box, top wall moving along x: the moving-wall terms of the directions leaving a
+    # wall cell cancel (w (c_x u_w) summed over them is zero), corners included, so the mass
+    # stays; the lid drags the fluid along +x under it and the return flow runs below
+    H, uw = 32, 0.05
+    w = W.Workload(name="cavity", nx=H, ny=H, tau=0.7, bc_x=W.BC_WALL, bc_y=W.BC_WALL, wall_u=(0.0, uw))
+    s = orc.Sim(w)
+    m0 = s.macro()[0].sum()
+    s.step(2000)
+    rho, ux, uy = s.macro()
+    assert abs(rho.sum() - m0) < 1e-12 * m0
+    assert ux[H - 1, H // 2] > 0.3 * uw and ux[H // 4, H // 2] < 0.0
