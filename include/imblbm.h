@@ -344,7 +344,8 @@ int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_par
 /* Set n held spheres: centres x[3n] (inside the lattice), velocities v[3n], spins
  * omega[3n], radii R[n] (host arrays, copied); builds the cell map on the GPU.
  * IMB_E_INVALID_ARG for a radius outside (0, 1000], a centre outside, or a periodic
- * extent below 2 (R + 2); IMB_E_OVERFLOW when two spheres cover one cell. */
+ * extent below 2 (R + 2); IMB_E_OVERFLOW when two spheres cover one cell (the lattice is
+ * then left without spheres). */
 int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const double *v, const double *omega, const double *R);
 
 /* Advance n steps and wait (bounded).  IMB_E_UNSTABLE on NaN or |u| >= 0.3. */

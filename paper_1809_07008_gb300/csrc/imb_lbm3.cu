@@ -556,6 +556,15 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
     int rc = e == cudaSuccess ? wait3(c) : fail3(c, IMB_E_CUDA, std::string("cell map: ") + cudaGetErrorString(e));
     cudaFree(dx);
     cudaFree(dR);
+    if (rc != IMB_OK) {   // a refused set leaves the lattice without spheres, not half mapped
+        cudaMemsetAsync(c->map, 0, c->a.plane * sizeof(unsigned), c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->sph);
+        cudaFree(c->FT);
+        c->sph = nullptr;
+        c->FT = nullptr;
+        c->np = 0;
+    }
     return rc;
 }
 

@@ -91,6 +91,9 @@ def test_errors(imb):
     with pytest.raises(imb.ImbError) as e:     # two spheres whose cells touch
         g.set_spheres(np.array([[8.0, 8.0, 12.0], [13.5, 8.0, 12.0]]), z, z, np.array([3.0, 3.0]))
     assert "OVERFLOW" in str(e.value)
+    sph, cnt = g.cell_map()                    # left without spheres, not half mapped
+    assert (sph < 0).all() and (cnt == 0).all()
+    g.step(2)
     with pytest.raises(imb.ImbError):
         g.set_spheres(np.array([[8.0, 8.0, 12.0]]), z[:1], z[:1], np.array([-1.0]))
     with pytest.raises(imb.ImbError):          # periodic extent below 2 (R + 2)
