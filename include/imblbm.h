@@ -363,13 +363,20 @@ int imb3_get_forces(imb3_ctx *c, double *F, double *T);
 /* Per cell: the covering sphere (-1: none) and its sub-cell count, each [nz][ny][nx]. */
 int imb3_get_cell_map(imb3_ctx *c, int *sphere, int *count);
 
-/* CUDA-event timing of every stream-collide launch (as imb_enable_kernel_timing). */
+/* CUDA-event timing of every stream-collide launch (as imb_enable_kernel_timing):
+ * on = 1 records a pair of events around each launch from now on. */
 int imb3_enable_kernel_timing(imb3_ctx *c, int on);
+/* Waits (bounded), then returns the summed time *ms of the timed launches and their
+ * number *launches, and restarts the count.  IMB_E_INVALID_ARG for NULL outputs. */
 int imb3_kernel_time(imb3_ctx *c, double *ms, long long *launches);
+/* Kernel launches this context has made so far (0 for NULL). */
 long long imb3_launch_count(imb3_ctx *c);
 /* Algorithmic bytes per cell update: 19 loads + 19 stores of the storage type. */
 double imb3_bytes_per_cell(imb3_ctx *c);
+/* Message of the last failed call on c (of the last failed imb3_init for NULL); the string
+ * belongs to the library and stays valid until the next call on c. */
 const char *imb3_last_error(imb3_ctx *c);
+/* Waits for the context's work and frees everything it holds; NULL is ignored. */
 void imb3_destroy(imb3_ctx *c);
 
 #ifdef __cplusplus
