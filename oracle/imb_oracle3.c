@@ -46,6 +46,26 @@ void orc3_omega_s(const double *f, double rho, double ux, double uy, double uz, 
     for (int q = 0; q < Q3; ++q) om[q] = f[opp3(q)] - fe[opp3(q)] + fs[q] - f[q];
 }
 
+double orc3_tau_eff(const double *f, double Fx, double Fy, double Fz, double tau, double C_smag) {
+    if (C_smag <= 0.0) return tau;
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < Q3; ++q) {
+        rho += f[q];
+        for (int d = 0; d < 3; ++d) m[d] += C3[q][d] * f[q];
+    }
+    const double Fb[3] = {Fx, Fy, Fz};
+    double u[3], fe[Q3], P[3][3] = {{0.0}};
+    for (int d = 0; d < 3; ++d) u[d] = (m[d] + 0.5 * Fb[d]) / rho;
+    orc3_feq(rho, u[0], u[1], u[2], fe);
+    for (int q = 0; q < Q3; ++q)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) P[a][b] += C3[q][a] * C3[q][b] * (f[q] - fe[q]);
+    double Q = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Q += P[a][b] * P[a][b];
+    return 0.5 * (tau + sqrt(tau * tau + 18.0 * sqrt(2.0) * C_smag * C_smag * sqrt(Q) / rho));
+}
+
 /* Sec. 2.3: the cell is cut into n x n x n sub-cells; those whose centre lies in the sphere
  * (distance <= R) count.  Offsets are formed from the integer cell offset and the centre's
  * fractional part, every operation rounded separately. */
@@ -114,7 +134,7 @@ static void stream(orc3_sim *s, const double *src, double *dst) {
 }
 
 orc3_sim *orc3_new(const orc3_params *p) {
-    if (p->nx < 3 || p->ny < 3 || p->nz < 3 || !(p->tau > 0.5) || p->n_sub < 1) return NULL;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 3 || !(p->tau > 0.5) || p->n_sub < 1 || !(p->C_smag >= 0.0)) return NULL;
     orc3_sim *s = (orc3_sim *)calloc(1, sizeof(orc3_sim));
     s->p = *p;
     s->ncell = (size_t)p->nx * p->ny * p->nz;
@@ -234,18 +254,20 @@ int orc3_step(orc3_sim *s, int nsteps) {
                     double u[3];
                     for (int d = 0; d < 3; ++d) u[d] = (m[d] + 0.5 * Fb[d]) / rho;
                     orc3_feq(rho, u[0], u[1], u[2], fe);
+                    /* the Smagorinsky relaxation time enters the BGK term, the forcing and B */
+                    const double te = orc3_tau_eff(f, Fb[0], Fb[1], Fb[2], tau, s->p.C_smag);
                     /* solid ratio and B (Eq. 14) */
                     double esum = 0.0;
                     for (int k2 = 0; k2 < SLOTS3; ++k2)
                         if (s->msph[c * SLOTS3 + k2] >= 0) esum += s->mcnt[c * SLOTS3 + k2] / nsub3;
                     const double eps = esum < 1.0 ? esum : 1.0;
-                    const double B = esum > 0.0 ? eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5)) : 0.0;
+                    const double B = esum > 0.0 ? eps * (te - 0.5) / ((1.0 - eps) + (te - 0.5)) : 0.0;
                     const double uF = u[0] * Fb[0] + u[1] * Fb[1] + u[2] * Fb[2];
                     for (int q = 0; q < Q3; ++q) {
                         const double cu = C3[q][0] * u[0] + C3[q][1] * u[1] + C3[q][2] * u[2];
                         const double cF = C3[q][0] * Fb[0] + C3[q][1] * Fb[1] + C3[q][2] * Fb[2];
-                        const double S = (1.0 - 0.5 / tau) * w3(q) * (3.0 * (cF - uF) + 9.0 * cu * cF);
-                        out[q] = f[q] + (1.0 - B) * (-(f[q] - fe[q]) / tau + S);
+                        const double S = (1.0 - 0.5 / te) * w3(q) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+                        out[q] = f[q] + (1.0 - B) * (-(f[q] - fe[q]) / te + S);
                     }
                     if (B > 0.0) {
                         const double node[3] = {i + 0.5, j + 0.5, k + 0.5};

@@ -9,7 +9,10 @@
  * Spheres are held in place (they may carry a velocity and a spin that enter u_s).
  * Geometry: cell (i, j, k) is [i, i+1) x [j, j+1) x [k, k+1) with its node at the centre;
  * x and z periodic; y periodic or bounded by halfway bounce-back walls on the domain edges.
- * The body force enters by Guo forcing weighted by 1 - B.  Populations are [19][nz][ny][nx].
+ * The body force enters by Guo forcing weighted by 1 - B.  With C_smag > 0 the relaxation time
+ * of each node is the Smagorinsky one (tau_eff in the BGK term, the forcing and B).  A cell may
+ * hold up to four spheres; B is shared between them by their solid ratios.
+ * Populations are [19][nz][ny][nx].
  */
 #ifndef IMB_ORACLE3_H
 #define IMB_ORACLE3_H
@@ -22,6 +25,7 @@ typedef struct {
     int n_sub;                /* sub-cells per axis for the solid ratio */
     double rho0, ux0, uy0, uz0;
     double wall_ux_bot, wall_ux_top;   /* x velocity of the walls y = 0 and y = ny */
+    double C_smag;                     /* Smagorinsky constant (0: plain BGK) */
 } orc3_params;
 
 typedef struct orc3_sim orc3_sim;
@@ -32,6 +36,10 @@ void orc3_feq(double rho, double ux, double uy, double uz, double *feq19);
 /* Eq. 12 for one particle: Omega^s_q = f_{-q} - feq_{-q}(rho, u) + feq_q(rho, u_s) - f_q */
 void orc3_omega_s(const double *f19, double rho, double ux, double uy, double uz, double usx, double usy,
                   double usz, double *om19);
+/* Smagorinsky relaxation time of one node (the closure of the 2D path in three dimensions):
+ * Pi = sum_q c_q c_q (f_q - f^eq_q), Q = Pi : Pi, tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2
+ * sqrt(Q) / rho)) / 2, with u from the moments and the half-force shift */
+double orc3_tau_eff(const double *f19, double Fx, double Fy, double Fz, double tau, double C_smag);
 /* sub-cell centres of cell offset (di, dj, dk) from the sphere's centre cell that lie in the
  * sphere (fractional centre offset (fx, fy, fz) in [0, 1)); a centre on the surface counts */
 int orc3_subcell_count(int di, int dj, int dk, double fx, double fy, double fz, double R, int n);

@@ -63,7 +63,8 @@ class Params3(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("tau", C.c_double),
                 ("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
                 ("n_sub", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double), ("uy0", C.c_double),
-                ("uz0", C.c_double), ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double)]
+                ("uz0", C.c_double), ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double),
+                ("C_smag", C.c_double)]
 
 
 _lib = None
@@ -109,6 +110,8 @@ def lib():
         L.orc3_feq.argtypes = [C.c_double] * 4 + [_dp]
         L.orc3_omega_s.argtypes = [_dp] + [C.c_double] * 7 + [_dp]
         L.orc3_subcell_count.argtypes = [C.c_int] * 3 + [C.c_double] * 4 + [C.c_int]
+        L.orc3_tau_eff.argtypes = [_dp] + [C.c_double] * 5
+        L.orc3_tau_eff.restype = C.c_double
         L.orc3_new.argtypes = [C.POINTER(Params3)]
         L.orc3_new.restype = C.c_void_p
         L.orc3_free.argtypes = [C.c_void_p]
@@ -326,6 +329,11 @@ def omega_s3(f19, rho, u, us):
     return out
 
 
+def tau_eff3(f19, tau, C_smag, force=(0.0, 0.0, 0.0)):
+    f19 = np.ascontiguousarray(f19, dtype=np.float64)
+    return lib().orc3_tau_eff(_d(f19), force[0], force[1], force[2], tau, C_smag)
+
+
 def subcell_count3(off, frac, R, n):
     return lib().orc3_subcell_count(int(off[0]), int(off[1]), int(off[2]), float(frac[0]), float(frac[1]),
                                     float(frac[2]), float(R), int(n))
@@ -344,6 +352,7 @@ class Sim3:
         p.rho0 = w.rho0
         p.ux0, p.uy0, p.uz0 = w.u0
         p.wall_ux_bot, p.wall_ux_top = w.wall_u
+        p.C_smag = w.C_smag
         self.p = p
         self.h = lib().orc3_new(C.byref(p))
         if not self.h:

@@ -14,7 +14,11 @@
   tau = 1/2 + sqrt(3)/4 (the BGK wall slip vanishes there); a sphere in the middle of a
   symmetric channel feels no lift, no side force and no torque; in an all-periodic box the
   steady drag equals the body force times sum_j (1 - B_j) (the momentum the fluid does not
-  keep), to 1e-10.
+  keep), to 1e-10, and so does the summed drag of two spheres pressed into each other that
+  share the cells around their contact (1e-11 after the transient has died out).
+* Smagorinsky closure: C = 0 or an unstrained equilibrium give tau; otherwise the closed form
+  solves tau_eff = tau + 3 C^2 sqrt(2 S:S) with the strain read from the non-equilibrium
+  stress, S = -Pi / (2 rho cs^2 tau_eff).
 """
 import math
 
@@ -211,3 +215,45 @@ def test_plane_couette_exact_with_moving_walls(O):
     assert np.abs(ux - (-uw + 2 * uw * y / H)[None, :, None]).max() < 1e-13
     assert np.abs(uy).max() < 1e-13 and np.abs(uz).max() < 1e-13
     assert abs(rho.sum() - m0) < 1e-12 * m0
+
+
+def test_smagorinsky_closure_3d(O):
+    # C = 0 and an unstrained equilibrium give tau; otherwise tau_eff = tau + 3 nu_t with
+    # nu_t = C^2 sqrt(2 S:S) and the lattice strain S = -Pi / (2 rho cs^2 tau_eff)
+    c, _ = O.lattice3()
+    rng = np.random.default_rng(9)
+    fe = O.feq3(1.01, 0.02, -0.01, 0.015)
+    assert O.tau_eff3(fe, 0.51, 0.0) == 0.51 and abs(O.tau_eff3(fe, 0.51, 0.1) - 0.51) < 1e-15
+    for C in (0.1, 0.3):
+        for _ in range(10):
+            f = O.feq3(1.0, 0.01, 0.02, -0.01) + 5e-3 * rng.standard_normal(19) / 19
+            rho = f.sum()
+            u = (f[:, None] * c).sum(0) / rho
+            ne = f - O.feq3(rho, *u)
+            Pi = np.einsum("q,qa,qb->ab", ne, c, c)
+            te = O.tau_eff3(f, 0.51, C)
+            S = -Pi / (2 * rho * (1 / 3) * te)
+            assert abs(te - (0.51 + 3 * C * C * math.sqrt(2 * (S * S).sum()))) < 1e-13 and te > 0.51
+
+
+def test_two_spheres_sharing_cells_momentum_balance(O):
+    # two held spheres pressed slightly into each other share the cells around the contact: B is split between
+    # them by their solid ratios (B_p = B eps_p / sum eps); at steady state in an all-periodic
+    # box their summed drag is g sum_j (1 - B_j), and the mass stays
+    L, tau, g, R = 16, 1.0, 1e-6, 2.6
+    x = np.array([[L / 2 - R + 0.25, L / 2 + 0.3, L / 2], [L / 2 + R - 0.25, L / 2 - 0.2, L / 2 + 0.1]])
+    w = W.Workload3(name="pair3", nx=L, ny=L, nz=L, tau=tau, wall_y=False, force=(g, 0.0, 0.0),
+                    x=x, v=np.zeros((2, 3)), omega=np.zeros((2, 3)), R=np.array([R, R]))
+    s = O.Sim3(w)
+    sph, cnt = s.cell_map()
+    assert (sph[..., 1] >= 0).sum() > 0                     # some cells hold both spheres
+    m0 = s.macro()[0].sum()
+    eps = np.minimum(1.0, cnt.sum(axis=-1) / w.n_sub ** 3)
+    B = eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5))
+    expect = g * np.sum(1.0 - B)
+    # the transient decays by about 5x per 1000 steps once the flow has formed (it crosses zero
+    # near 5000 steps): 12 000 steps leave it below 1e-12 of the drag
+    s.step(12000)
+    F, T = s.forces()
+    assert abs(F[:, 0].sum() - expect) / expect < 1e-11
+    assert abs(s.macro()[0].sum() - m0) < 1e-12 * m0

@@ -345,6 +345,7 @@ class Workload3:
     rho0: float = 1.0
     u0: tuple = (0.0, 0.0, 0.0)
     wall_u: tuple = (0.0, 0.0)         # x velocity of the walls y = 0 and y = ny
+    C_smag: float = 0.0                # Smagorinsky constant
     steps: int = 1000
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     v: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
