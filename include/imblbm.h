@@ -317,7 +317,12 @@ void imb_destroy(imb_ctx *ctx);
  * n_sub^3 sub-cell centres inside the sphere (a centre on the surface counts,
  * Sec. 2.3), and per-sphere force and torque (Eqs. 15-16, the force ON the sphere).
  * Spheres are held in place; their velocity and spin enter u_s = v + w x r.  A cell
- * may be covered by one sphere only.  Populations are stored as f_i - w_i, SoA
+ * may be covered by two spheres (touching spheres of a packed bed): B of Eq. 14 then
+ * comes from their summed solid ratio (at most 1) and is shared between them in
+ * proportion to their own ratios, B_p = B eps_p / (eps_1 + eps_2), each sphere's
+ * Omega^s weighted by its B_p.  With C_smag > 0 each cell relaxes with the
+ * Smagorinsky time tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 |Pi| / rho)) / 2, Pi
+ * the non-equilibrium momentum flux, in the BGK term, the forcing and B.  Populations are stored as f_i - w_i, SoA
  * [19][nz][ny][nx], x fastest.  Velocity order: 0 rest; 1-6 (+x, -x, +y, -y, +z,
  * -z); 7-18 (+x+y, -x-y, +x-y, -x+y, +x+z, -x-z, +x-z, -x+z, +y+z, -y-z, +y-z, -y+z). */
 typedef struct imb3_ctx imb3_ctx;
@@ -331,21 +336,23 @@ typedef struct imb3_params {
     int timeout_ms;           /* bound of every host wait */
     double wall_ux_bot, wall_ux_top; /* x velocity of the walls y = 0 and y = ny (moving-wall
                                  bounce-back, wall density 1; default 0, 0) */
+    double C_smag;            /* Smagorinsky constant, >= 0 (default 0: plain BGK) */
 } imb3_params;
 
-/* Defaults: walls in y at rest, no force, n_sub = 5, FP32, rho0 = 1, at rest, 60 s. */
+/* Defaults: walls in y at rest, no force, n_sub = 5, FP32, rho0 = 1, at rest, 60 s,
+ * C_smag = 0. */
 void imb3_default_params(imb3_params *p);
 
 /* Create the lattice (p may be NULL for the defaults).  IMB_E_INVALID_ARG for a size
- * below 3, tau <= 1/2, n_sub outside 1..10 or a bad storage code; IMB_E_NOMEM /
+ * below 3, tau <= 1/2, n_sub outside 1..10, a bad storage code or C_smag < 0; IMB_E_NOMEM /
  * IMB_E_CUDA on device failures (then *out may hold a context to destroy). */
 int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_params *p);
 
 /* Set n held spheres: centres x[3n] (inside the lattice), velocities v[3n], spins
  * omega[3n], radii R[n] (host arrays, copied); builds the cell map on the GPU.
  * IMB_E_INVALID_ARG for a radius outside (0, 1000], a centre outside, or a periodic
- * extent below 2 (R + 2); IMB_E_OVERFLOW when two spheres cover one cell (the lattice is
- * then left without spheres). */
+ * extent below 2 (R + 2); IMB_E_OVERFLOW when three spheres cover one cell (the lattice
+ * is then left without spheres). */
 int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const double *v, const double *omega, const double *R);
 
 /* Advance n steps and wait (bounded).  IMB_E_UNSTABLE on NaN or |u| >= 0.3. */
@@ -360,7 +367,8 @@ int imb3_get_macro(imb3_ctx *c, double *rho, double *ux, double *uy, double *uz)
 /* Force F[3n] and torque T[3n] on each sphere from the last step. */
 int imb3_get_forces(imb3_ctx *c, double *F, double *T);
 
-/* Per cell: the covering sphere (-1: none) and its sub-cell count, each [nz][ny][nx]. */
+/* Per cell, two slots: the covering spheres (lower index first, -1: none) and their
+ * sub-cell counts, each [nz][ny][nx][2]. */
 int imb3_get_cell_map(imb3_ctx *c, int *sphere, int *count);
 
 /* CUDA-event timing of every stream-collide launch (as imb_enable_kernel_timing):

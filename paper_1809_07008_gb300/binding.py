@@ -79,7 +79,7 @@ class Params3(C.Structure):
     _fields_ = [("wall_y", C.c_int), ("Fx", C.c_double), ("Fy", C.c_double), ("Fz", C.c_double),
                 ("n_sub", C.c_int), ("storage", C.c_int), ("rho0", C.c_double), ("ux0", C.c_double),
                 ("uy0", C.c_double), ("uz0", C.c_double), ("timeout_ms", C.c_int),
-                ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double)]
+                ("wall_ux_bot", C.c_double), ("wall_ux_top", C.c_double), ("C_smag", C.c_double)]
 
 
 class Params(C.Structure):
@@ -471,7 +471,7 @@ class Lattice3:
     """A D3Q19 lattice with held spheres (imb3_*; the paper's own lattice)."""
 
     def __init__(self, nx, ny, nz, tau, wall_y=True, force=(0.0, 0.0, 0.0), n_sub=5, storage="fp32",
-                 rho0=1.0, u0=(0.0, 0.0, 0.0), wall_u=(0.0, 0.0)):
+                 rho0=1.0, u0=(0.0, 0.0, 0.0), wall_u=(0.0, 0.0), C_smag=0.0):
         L = load()
         p = Params3()
         L.imb3_default_params(C.byref(p))
@@ -482,6 +482,7 @@ class Lattice3:
         p.rho0 = float(rho0)
         p.ux0, p.uy0, p.uz0 = map(float, u0)
         p.wall_ux_bot, p.wall_ux_top = map(float, wall_u)
+        p.C_smag = float(C_smag)
         h = _vp()
         rc = L.imb3_init(C.byref(h), int(nx), int(ny), int(nz), float(tau), C.byref(p))
         if rc != IMB_OK:
@@ -496,7 +497,7 @@ class Lattice3:
     @classmethod
     def from_workload(cls, w, storage="fp32"):
         lat = cls(w.nx, w.ny, w.nz, w.tau, wall_y=w.wall_y, force=w.force, n_sub=w.n_sub, storage=storage,
-                  rho0=w.rho0, u0=w.u0, wall_u=w.wall_u)
+                  rho0=w.rho0, u0=w.u0, wall_u=w.wall_u, C_smag=w.C_smag)
         if w.n_spheres:
             lat.set_spheres(w.x, w.v, w.omega, w.R)
         return lat
@@ -531,7 +532,9 @@ class Lattice3:
         return F[:self.np], T[:self.np]
 
     def cell_map(self):
-        shp = (self.nz, self.ny, self.nx)
+        """Two slots per cell: covering spheres (lower index first, -1 none) and sub-cell counts,
+        each [nz][ny][nx][2]."""
+        shp = (self.nz, self.ny, self.nx, 2)
         sph, cnt = np.zeros(shp, dtype=np.int32), np.zeros(shp, dtype=np.int32)
         self._check(self._L.imb3_get_cell_map(self.h, sph.ctypes.data_as(_ip), cnt.ctypes.data_as(_ip)))
         return sph, cnt

@@ -7,8 +7,11 @@
 // planes (x and z periodic, y periodic or halfway bounce-back walls), the collision in
 // registers, the store, and the sphere's force summed over the warp before one FP64
 // atomicAdd per component; each thread walks a short column of cells along z, the loads of
-// the next cell in flight during the arithmetic of the current one.  A cell is covered by at most one sphere (a per-cell map word
-// holds the sphere and its sub-cell count); spheres closer than that raise IMB_E_OVERFLOW.
+// the next cell in flight during the arithmetic of the current one.  A cell may be covered by
+// two spheres (packed beds whose spheres touch): two per-cell map words hold the spheres and
+// their sub-cell counts, and B is shared between them by their solid ratios; a third sphere on
+// one cell raises IMB_E_OVERFLOW.  With C_smag > 0 every cell relaxes with its Smagorinsky
+// relaxation time, in the BGK term, the forcing and B.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -64,6 +67,8 @@ struct Args3 {
     float inv_nsub3;         // 1 / n_sub^3
     int n_sub;
     float uw_bot, uw_top;    // x velocity of the walls y = 0 and y = ny
+    float smag_coef;         // 18 sqrt(2) C^2 (0: plain BGK)
+    int two_slots;           // 1 once some cell holds a second sphere
     long long off[19];       // element offset of the source of direction q: q plane - c_q (interior)
 };
 
@@ -101,9 +106,11 @@ __device__ int subcell_count(int di, int dj, int dk, double fx, double fy, doubl
     return cnt;
 }
 
-// one thread per (sphere, cell of its bounding box of half-width `span`)
+// one thread per (sphere, cell of its bounding box of half-width `span`); the first sphere on a
+// cell takes map, the second map2 (and sets shared), a third raises the overlap bit.  Slots
+// are filled in whatever order the threads arrive: readers order them by sphere
 __global__ void k3_map(const double *__restrict__ xyz, const double *__restrict__ R, int n, int span, Args3 a,
-                       unsigned *map, unsigned *err) {
+                       unsigned *map, unsigned *map2, unsigned *shared, unsigned *err) {
     const int w = 2 * span + 1;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * w * w * w) return;
@@ -127,7 +134,9 @@ __global__ void k3_map(const double *__restrict__ xyz, const double *__restrict_
     if (cnt == 0) return;
     const unsigned word = (unsigned)(s + 1) | ((unsigned)cnt << ID_BITS);
     const size_t cell = ((size_t)k * a.ny + j) * a.nx + i;
-    if (atomicCAS(&map[cell], 0u, word) != 0u) atomicOr(err, ERR_OVERLAP);
+    if (atomicCAS(&map[cell], 0u, word) == 0u) return;
+    if (atomicCAS(&map2[cell], 0u, word) == 0u) atomicOr(shared, 1u);
+    else atomicOr(err, ERR_OVERLAP);
 }
 
 template <typename S>
@@ -188,11 +197,32 @@ __device__ __forceinline__ void fetch3(const S *__restrict__ fin, const Args3 &a
     }
 }
 
-// collision of one cell from its pulled values d: moments (Eqs. 3-4, Guo half-force shift),
-// BGK with Guo forcing, Eqs. 12-14 where a sphere covers the cell, the 19 stores; returns the
-// covering sphere (-1: none) and its force and torque contribution (Eqs. 15-16)
+// u_s = v + w x r at the node of cell (x, y, z), r from the sphere's centre (minimum image)
+__device__ __forceinline__ void surface_velocity(const Sph3 &P, const Args3 &a, int x, int y, int z, float (&r)[3],
+                                                 float (&us)[3]) {
+    r[0] = (float)min_image(x - P.ci, a.nx) + 0.5f - P.fx;
+    r[1] = (float)(a.wall_y ? y - P.cj : min_image(y - P.cj, a.ny)) + 0.5f - P.fy;
+    r[2] = (float)min_image(z - P.ck, a.nz) + 0.5f - P.fz;
+    us[0] = P.vx + (P.wy * r[2] - P.wz * r[1]);
+    us[1] = P.vy + (P.wz * r[0] - P.wx * r[2]);
+    us[2] = P.vz + (P.wx * r[1] - P.wy * r[0]);
+}
+
+// Eqs. 15-16 for one sphere: force B_p (rho u - rho u_s - F), torque r x force
+__device__ __forceinline__ void sphere_force(float Bp, float rho, float jx, float jy, float jz, const float (&us)[3],
+                                             const float (&r)[3], const Args3 &a, float (&fo)[6]) {
+    fo[0] = Bp * (jx - rho * us[0] - a.Fx);
+    fo[1] = Bp * (jy - rho * us[1] - a.Fy);
+    fo[2] = Bp * (jz - rho * us[2] - a.Fz);
+    fo[3] = r[1] * fo[2] - r[2] * fo[1];
+    fo[4] = r[2] * fo[0] - r[0] * fo[2];
+    fo[5] = r[0] * fo[1] - r[1] * fo[0];
+}
+
+// the plain variant of collide3_gen below (one sphere per cell, tau fixed), written out on its
+// own: folding the general function down to this case compiled to a 3 % slower FP32 kernel
 template <typename S>
-__device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, int x, int y, int z, size_t cell,
+__device__ __forceinline__ int collide3_plain(const float (&d)[19], const Args3 &a, int x, int y, int z, size_t cell,
                                         const unsigned *__restrict__ map, const Sph3 *__restrict__ sph,
                                         S *__restrict__ fout, float (&fo)[6], bool &unstable) {
     float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
@@ -266,13 +296,136 @@ __device__ __forceinline__ int collide3(const float (&d)[19], const Args3 &a, in
     return sid;
 }
 
+// collision of one cell from its pulled values d, general variant: moments (Eqs. 3-4, Guo
+// half-force shift), the Smagorinsky relaxation time (when smag_coef > 0), BGK with Guo
+// forcing, Eqs. 12-14 where one or two spheres cover the cell, the 19 stores; returns the
+// covering sphere of lower index (-1: none) with its force and torque contribution in fo
+// (Eqs. 15-16); a second covering sphere's share goes to FT directly.  The kernel runs it
+// only when some cell holds two spheres or C_smag > 0: its code in every cell's schedule
+// slowed the plain case by 9-13 %
+template <typename S>
+__device__ __forceinline__ int collide3_gen(const float (&d)[19], const Args3 &a, int x, int y, int z, size_t cell,
+                                        const unsigned *__restrict__ map, const unsigned *__restrict__ map2,
+                                        const Sph3 *__restrict__ sph, S *__restrict__ fout, double *FT,
+                                        float (&fo)[6], bool &unstable) {
+    float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        drho += d[q];
+        if (cx3(q)) mx += cx3(q) * d[q];
+        if (cy3(q)) my += cy3(q) * d[q];
+        if (cz3(q)) mz += cz3(q) * d[q];
+    }
+    const float rho = 1.0f + drho;
+    const float jx = fmaf(0.5f, a.Fx, mx), jy = fmaf(0.5f, a.Fy, my), jz = fmaf(0.5f, a.Fz, mz);
+    const float inv = __fdividef(1.0f, rho);
+    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    if (!(uu < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+    const float t = fmaf(-1.5f * rho, uu, drho);
+    float n[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
+        const float cu = cdot3(q, ux, uy, uz);
+        n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+    }
+    float te = a.tau, omega = a.omega;
+    if (a.smag_coef > 0.0f) {   // tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 sqrt(Pi : Pi) / rho)) / 2
+        float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+#pragma unroll
+        for (int q = 1; q < 19; ++q) {   // Pi = sum_q c_q c_q n_q
+            if (cx3(q)) pxx += n[q];
+            if (cy3(q)) pyy += n[q];
+            if (cz3(q)) pzz += n[q];
+            if (cx3(q) && cy3(q)) pxy += cx3(q) * cy3(q) > 0 ? n[q] : -n[q];
+            if (cx3(q) && cz3(q)) pxz += cx3(q) * cz3(q) > 0 ? n[q] : -n[q];
+            if (cy3(q) && cz3(q)) pyz += cy3(q) * cz3(q) > 0 ? n[q] : -n[q];
+        }
+        const float Q = fmaf(pxx, pxx, fmaf(pyy, pyy, pzz * pzz)) + 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz));
+        const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;   // sqrt(Q)
+        const float disc = fmaf(a.smag_coef * sq, inv, a.tau * a.tau);
+        te = 0.5f * (a.tau + disc * rsqrtf(disc));
+        omega = __fdividef(1.0f, te);
+    }
+    unsigned w1 = map[cell], w2 = 0u;
+    if (w1 && a.two_slots) {
+        w2 = map2[cell];
+        if (w2 && (w2 & ID_MASK) < (w1 & ID_MASK)) {   // the sphere of lower index first
+            const unsigned tw = w1;
+            w1 = w2;
+            w2 = tw;
+        }
+    }
+    int sid = -1;
+    float B = 0.0f, B1 = 0.0f, B2 = 0.0f;
+    float r1[3] = {0.0f, 0.0f, 0.0f}, u1[3] = {0.0f, 0.0f, 0.0f}, r2[3] = {0.0f, 0.0f, 0.0f}, u2[3] = {0.0f, 0.0f, 0.0f};
+    if (w1) {   // Eq. 14 with the summed sub-cell solid ratio, shared by the spheres' own ratios
+        sid = (int)(w1 & ID_MASK) - 1;
+        const unsigned c1 = w1 >> ID_BITS, c2 = w2 >> ID_BITS;
+        const float eps = fminf(1.0f, (float)(c1 + c2) * a.inv_nsub3);   // two spheres may overlap
+        const float tm = te - 0.5f;
+        B = __fdividef(eps * tm, (1.0f - eps) + tm);
+        B1 = B;
+        surface_velocity(sph[sid], a, x, y, z, r1, u1);
+        if (w2) {
+            const float inv_c = __fdividef(1.0f, (float)(c1 + c2));
+            B1 = B * ((float)c1 * inv_c);
+            B2 = B * ((float)c2 * inv_c);
+            surface_velocity(sph[(w2 & ID_MASK) - 1], a, x, y, z, r2, u2);
+        }
+    }
+    const float fl = 1.0f - B, sf = 1.0f - 0.5f * omega;
+    const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
+    // BGK with Guo forcing (its source divided by 1 - 1/(2 tau)), weighted by 1 - B
+    auto fluid = [&](int q) {
+        const float cu = cdot3(q, ux, uy, uz);
+        const float cF = cdot3(q, a.Fx, a.Fy, a.Fz);
+        const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        return fmaf(-omega, n[q], sf * Sg);
+    };
+    // f^eq_q(rho, u_s) - w_q
+    auto eq_solid = [&](int q, const float (&us)[3], float ts) {
+        const float cs = cdot3(q, us[0], us[1], us[2]);
+        return w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
+    };
+    if (w2) {     // Eq. 12 summed over both spheres: B (n_{-q} - d_q) + sum_p B_p (f^eq_q(u_s,p) - w_q)
+        const float ts1 = fmaf(-1.5f * rho, u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], drho);
+        const float ts2 = fmaf(-1.5f * rho, u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2], drho);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float v = fmaf(B, n[opp3(q)] - d[q], fl * fluid(q)) + fmaf(B1, eq_solid(q, u1, ts1), B2 * eq_solid(q, u2, ts2));
+            Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
+        }
+    } else if (w1) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q, weighted by B
+        const float ts = fmaf(-1.5f * rho, u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], drho);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float v = fmaf(B, n[opp3(q)] + eq_solid(q, u1, ts) - d[q], fl * fluid(q));
+            Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
+        }
+    } else {      // no sphere: the fluid operator alone
+#pragma unroll
+        for (int q = 0; q < 19; ++q) Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + fluid(q));
+    }
+    if (w1) sphere_force(B1, rho, jx, jy, jz, u1, r1, a, fo);
+    if (w2) {     // the second sphere's share, summed straight into its totals
+        float f2[6];
+        sphere_force(B2, rho, jx, jy, jz, u2, r2, a, f2);
+        const int s2 = (int)(w2 & ID_MASK) - 1;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) atomicAdd(&FT[6 * s2 + c], (double)f2[c]);
+    }
+    return sid;
+}
+
 // stream-collide; blocks of 32 x 8 cells, each thread a column of ZC cells along z whose next
 // cell's loads are issued before the current cell's arithmetic
 constexpr int ZC = 8;
 
-template <typename S>
+template <bool GEN, typename S>
 __global__ void __launch_bounds__(256, 2) k3_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, const Args3 a,
                                                          const unsigned *__restrict__ map,
+                                                         const unsigned *__restrict__ map2,
                                                          const Sph3 *__restrict__ sph, double *FT, unsigned *err) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, a.nz);
@@ -295,7 +448,11 @@ __global__ void __launch_bounds__(256, 2) k3_stream_collide(const S *__restrict_
                         d[q] += 6.0f * w3(q) * (float)cx3(q) * (y == 0 ? a.uw_bot : a.uw_top);
             }
             if (z + 1 < z1) fetch3(fin, a, x, y, z + 1, r);   // in flight during this cell's arithmetic
-            sid = collide3(d, a, x, y, z, ((size_t)z * a.ny + y) * a.nx + x, map, sph, fout, fo, unstable);
+            const size_t cell = ((size_t)z * a.ny + y) * a.nx + x;
+            if constexpr (GEN)
+                sid = collide3_gen(d, a, x, y, z, cell, map, map2, sph, fout, FT, fo, unstable);
+            else
+                sid = collide3_plain(d, a, x, y, z, cell, map, sph, fout, fo, unstable);
         }
         // the warp's force: lanes of its first sphere summed by shuffles, any other sphere direct
         const unsigned has = __ballot_sync(0xffffffffu, sid >= 0);
@@ -359,7 +516,8 @@ struct imb3_ctx {
     imb3_params p{};
     Args3 a{};
     void *buf[2] = {nullptr, nullptr};
-    unsigned *map = nullptr, *err = nullptr, *h_err = nullptr;
+    unsigned *map = nullptr, *map2 = nullptr, *h_err = nullptr;
+    unsigned *err = nullptr;   // [0] error bits, [1] set by the cell map when a cell holds two spheres
     Sph3 *sph = nullptr;
     double *FT = nullptr;
     cudaStream_t stream = nullptr;
@@ -420,7 +578,7 @@ int wait3(imb3_ctx *c) {
     if (bits) {
         CK3(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream), "clear");
         CK3(cudaStreamSynchronize(c->stream), "clear");
-        if (bits & ERR_OVERLAP) return fail3(c, IMB_E_OVERFLOW, "two spheres cover one cell");
+        if (bits & ERR_OVERLAP) return fail3(c, IMB_E_OVERFLOW, "three spheres cover one cell");
         if (bits & ERR_UNSTABLE) return fail3(c, IMB_E_UNSTABLE, "NaN or |u| >= 0.3 (Mach guard)");
     }
     return IMB_OK;
@@ -438,6 +596,7 @@ extern "C" void imb3_default_params(imb3_params *p) {
     p->ux0 = p->uy0 = p->uz0 = 0.0;
     p->timeout_ms = 60000;
     p->wall_ux_bot = p->wall_ux_top = 0.0;
+    p->C_smag = 0.0;
 }
 
 extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_params *params) {
@@ -448,8 +607,9 @@ extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, con
     imb3_default_params(&p);
     if (params) p = *params;
     if (nx < 3 || ny < 3 || nz < 3 || !(tau > 0.5) || p.n_sub < 1 || p.n_sub > 10 || p.storage < 0 ||
-        p.storage > 2 || (double)nx * ny * nz > 2.0e9 || p.timeout_ms < 1)
-        return fail3(c, IMB_E_INVALID_ARG, "bad lattice size, tau <= 1/2, n_sub outside 1..10 or bad storage");
+        p.storage > 2 || (double)nx * ny * nz > 2.0e9 || p.timeout_ms < 1 || !(p.C_smag >= 0.0))
+        return fail3(c, IMB_E_INVALID_ARG,
+                     "bad lattice size, tau <= 1/2, n_sub outside 1..10, bad storage or C_smag < 0");
     c = new imb3_ctx();
     c->nx = nx;
     c->ny = ny;
@@ -472,6 +632,8 @@ extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, con
     a.inv_nsub3 = (float)(1.0 / ((double)p.n_sub * p.n_sub * p.n_sub));
     a.uw_bot = (float)p.wall_ux_bot;
     a.uw_top = (float)p.wall_ux_top;
+    a.smag_coef = (float)(18.0 * std::sqrt(2.0) * p.C_smag * p.C_smag);
+    a.two_slots = 0;
     for (int q = 0; q < 19; ++q)
         a.off[q] = (long long)q * (long long)a.plane -
                    ((long long)cz3(q) * ny * nx + (long long)cy3(q) * nx + (long long)cx3(q));
@@ -481,10 +643,12 @@ extern "C" int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, con
     CK3(cudaMalloc(&c->buf[0], 19 * a.plane * c->elem), "populations");
     CK3(cudaMalloc(&c->buf[1], 19 * a.plane * c->elem), "populations");
     CK3(cudaMalloc(&c->map, a.plane * sizeof(unsigned)), "cell map");
-    CK3(cudaMalloc(&c->err, sizeof(unsigned)), "error word");
+    CK3(cudaMalloc(&c->map2, a.plane * sizeof(unsigned)), "cell map");
+    CK3(cudaMalloc(&c->err, 2 * sizeof(unsigned)), "error word");
     CK3(cudaMallocHost(&c->h_err, sizeof(unsigned)), "error word");
     CK3(cudaMemsetAsync(c->map, 0, a.plane * sizeof(unsigned), c->stream), "clear");
-    CK3(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream), "clear");
+    CK3(cudaMemsetAsync(c->map2, 0, a.plane * sizeof(unsigned), c->stream), "clear");
+    CK3(cudaMemsetAsync(c->err, 0, 2 * sizeof(unsigned), c->stream), "clear");
     CK3(by_storage3(p.storage, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             k3_init<S><<<(unsigned)((a.plane + 255) / 256), 256, 0, c->stream>>>(
@@ -520,7 +684,10 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
     c->sph = nullptr;
     c->FT = nullptr;
     c->np = n;
+    c->a.two_slots = 0;
     CK3(cudaMemsetAsync(c->map, 0, c->a.plane * sizeof(unsigned), c->stream), "clear map");
+    CK3(cudaMemsetAsync(c->map2, 0, c->a.plane * sizeof(unsigned), c->stream), "clear map");
+    CK3(cudaMemsetAsync(c->err + 1, 0, sizeof(unsigned), c->stream), "clear map");
     if (n == 0) return wait3(c);
     std::vector<Sph3> hs(n);
     for (int s = 0; s < n; ++s) {
@@ -550,14 +717,23 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
     CK3(cudaMemsetAsync(c->FT, 0, sizeof(double) * 6 * n, c->stream), "clear forces");
     const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;
     const long long nt = (long long)n * w * w * w;
-    k3_map<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(dx, dR, n, span, c->a, c->map, c->err);
+    k3_map<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(dx, dR, n, span, c->a, c->map, c->map2, c->err + 1,
+                                                                 c->err);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     int rc = e == cudaSuccess ? wait3(c) : fail3(c, IMB_E_CUDA, std::string("cell map: ") + cudaGetErrorString(e));
     cudaFree(dx);
     cudaFree(dR);
+    if (rc == IMB_OK) {   // the kernel reads the second slot only once some cell holds two spheres
+        unsigned shared = 0;
+        e = cudaMemcpy(&shared, c->err + 1, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = fail3(c, IMB_E_CUDA, std::string("cell map: ") + cudaGetErrorString(e));
+        c->a.two_slots = shared ? 1 : 0;
+    }
     if (rc != IMB_OK) {   // a refused set leaves the lattice without spheres, not half mapped
+        c->a.two_slots = 0;
         cudaMemsetAsync(c->map, 0, c->a.plane * sizeof(unsigned), c->stream);
+        cudaMemsetAsync(c->map2, 0, c->a.plane * sizeof(unsigned), c->stream);
         cudaStreamSynchronize(c->stream);
         cudaFree(c->sph);
         cudaFree(c->FT);
@@ -588,8 +764,14 @@ extern "C" int imb3_step(imb3_ctx *c, int nsteps) {
         }
         CK3(by_storage3(c->p.storage, [&](auto tag) {
                 using S = std::remove_pointer_t<decltype(tag)>;
-                k3_stream_collide<S><<<grd, blk, 0, c->stream>>>((const S *)c->buf[c->cur], (S *)c->buf[c->cur ^ 1],
-                                                                 c->a, c->map, c->sph, c->FT, c->err);
+                const S *fin = (const S *)c->buf[c->cur];
+                S *fout = (S *)c->buf[c->cur ^ 1];
+                if (c->a.smag_coef > 0.0f || c->a.two_slots)
+                    k3_stream_collide<true, S><<<grd, blk, 0, c->stream>>>(fin, fout, c->a, c->map, c->map2, c->sph,
+                                                                           c->FT, c->err);
+                else
+                    k3_stream_collide<false, S><<<grd, blk, 0, c->stream>>>(fin, fout, c->a, c->map, c->map2, c->sph,
+                                                                            c->FT, c->err);
                 return cudaGetLastError();
             }),
             "stream-collide");
@@ -659,11 +841,16 @@ extern "C" int imb3_get_cell_map(imb3_ctx *c, int *sphere, int *count) {
     if (!c || !sphere || !count) return fail3(c, IMB_E_INVALID_ARG, "bad arguments");
     int rc = wait3(c);
     if (rc) return rc;
-    std::vector<unsigned> h(c->a.plane);
+    std::vector<unsigned> h(c->a.plane), h2(c->a.plane);
     CK3(cudaMemcpy(h.data(), c->map, sizeof(unsigned) * h.size(), cudaMemcpyDeviceToHost), "cell map");
+    CK3(cudaMemcpy(h2.data(), c->map2, sizeof(unsigned) * h2.size(), cudaMemcpyDeviceToHost), "cell map");
     for (size_t k = 0; k < h.size(); ++k) {
-        sphere[k] = (int)(h[k] & ID_MASK) - 1;
-        count[k] = (int)(h[k] >> ID_BITS);
+        unsigned a = h[k], b = h2[k];
+        if (b && (b & ID_MASK) < (a & ID_MASK)) std::swap(a, b);   // the sphere of lower index first
+        sphere[2 * k] = (int)(a & ID_MASK) - 1;
+        count[2 * k] = (int)(a >> ID_BITS);
+        sphere[2 * k + 1] = (int)(b & ID_MASK) - 1;
+        count[2 * k + 1] = (int)(b >> ID_BITS);
     }
     return IMB_OK;
 }
@@ -704,6 +891,7 @@ extern "C" void imb3_destroy(imb3_ctx *c) {
     for (void *b : c->buf)
         if (b) cudaFree(b);
     if (c->map) cudaFree(c->map);
+    if (c->map2) cudaFree(c->map2);
     if (c->err) cudaFree(c->err);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->sph) cudaFree(c->sph);

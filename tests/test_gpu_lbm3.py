@@ -7,7 +7,13 @@ Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 
   walls in y or all periodic, 200 steps from rest: populations within 2e-6 (FP32 storage) and
   velocity relative L2 within 1e-5, per-sphere force and torque within 1e-4 of their scale;
   FP16 storage: forces within 1 %.
-* Errors: two spheres on one cell -> IMB_E_OVERFLOW; bad sizes and radii -> IMB_E_INVALID_ARG.
+* Packed bed: eight spheres whose surfaces reach up to 0.8 cells into each other, so that
+  some cells hold two: both map slots bit-exact, 200 steps within the same bars, and two
+  spheres pressed together in an all-periodic box.
+* Smagorinsky closure (C = 0.2 at tau = 0.51 and 0.55): 200 steps within the same bars, which
+  lie at least 20 times below the closure's own effect on the forces.
+* Errors: three spheres on one cell -> IMB_E_OVERFLOW; bad sizes, radii and C < 0 ->
+  IMB_E_INVALID_ARG.
 * Walls moving along x (Couette, Sec. 3.4): the fluid-only profile is the exact line within
   FP32 rounding, and a box with three spheres matches the oracle after 200 steps.
 * Full size: the bench's 16 M-cell box, one step checked on a window around the sphere that the
@@ -40,9 +46,9 @@ def test_cell_map_bit_exact(orc, imb, n_sub):
     gs, gc = g.cell_map()
     os_, oc = orc.Sim3(w).cell_map()
     assert (os_[..., 1] < 0).all()                   # one sphere per cell in this case
-    assert np.array_equal(gs, os_[..., 0])
-    assert np.array_equal(gc, oc[..., 0])
-    assert (gc > 0).sum() > 100
+    assert np.array_equal(gs, os_[..., :2])
+    assert np.array_equal(gc, oc[..., :2])
+    assert (gc[..., 0] > 0).sum() > 100
     g.close()
 
 
@@ -69,6 +75,61 @@ def test_steps_match_oracle(orc, imb, wall_y):
     g.close()
 
 
+def _parity(o, g, steps=200):
+    o.step(steps)
+    g.step(steps)
+    assert np.abs(g.populations() - o.f()).max() < 2e-6
+    _, oux, ouy, ouz = o.macro()
+    _, gux, guy, guz = g.macro()
+    uo = np.stack([oux, ouy, ouz])
+    assert np.linalg.norm(np.stack([gux, guy, guz]) - uo) / np.linalg.norm(uo) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    sF = np.abs(Fo).max()
+    assert sF > 0 and np.abs(Fg - Fo).max() < 1e-4 * sF
+    assert np.abs(Tg - To).max() < 1e-4 * sF * 5.0      # torque on the scale R x force, R <= 5
+    return Fo
+
+
+def test_packed_bed_two_spheres_per_cell(orc, imb):
+    w = W.spheres3(nx=40, ny=24, nz=36, n=8, seed=4, tau=0.7, gap=-0.8, r_lo=3.0, r_hi=5.0)
+    o = orc.Sim3(w)
+    os_, oc = o.cell_map()
+    assert (os_[..., 1] >= 0).sum() > 20 and (os_[..., 2] < 0).all()
+    g = imb.Lattice3.from_workload(w)
+    gs, gc = g.cell_map()
+    assert np.array_equal(gs, os_[..., :2]) and np.array_equal(gc, oc[..., :2])
+    _parity(o, g)
+    g.close()
+
+
+def test_pair_pressed_together_all_periodic(orc, imb):
+    L, R = 16, 2.6
+    x = np.array([[L / 2 - R + 0.25, L / 2 + 0.3, L / 2], [L / 2 + R - 0.25, L / 2 - 0.2, L / 2 + 0.1]])
+    w = W.Workload3(name="pair3", nx=L, ny=L, nz=L, tau=0.8, wall_y=False, force=(1e-5, 2e-6, 0.0),
+                    x=x, v=np.array([[0.002, 0.0, 0.001], [-0.001, 0.001, 0.0]]),
+                    omega=np.array([[0.0, 0.0, 0.001], [0.001, 0.0, 0.0]]), R=np.array([R, R]))
+    o = orc.Sim3(w)
+    g = imb.Lattice3.from_workload(w)
+    gs, _ = g.cell_map()
+    assert (gs[..., 1] >= 0).sum() > 0
+    _parity(o, g, 300)
+    g.close()
+
+
+@pytest.mark.parametrize("tau", [0.51, 0.55])
+def test_smagorinsky_matches_oracle(orc, imb, tau):
+    w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=5, tau=tau).with_(C_smag=0.2)
+    o = orc.Sim3(w)
+    g = imb.Lattice3.from_workload(w)
+    Fo = _parity(o, g)
+    g.close()
+    o0 = orc.Sim3(w.with_(C_smag=0.0))       # the closure's own effect is far above the bar
+    o0.step(200)
+    F0, _ = o0.forces()
+    assert np.abs(F0 - Fo).max() > 20 * 1e-4 * np.abs(Fo).max()
+
+
 def test_fp16_storage_forces(orc, imb):
     w = W.spheres3(nx=40, ny=24, nz=36, n=3, seed=5, tau=0.7)
     o = orc.Sim3(w)
@@ -87,9 +148,15 @@ def test_errors(imb):
     with pytest.raises(imb.ImbError):
         imb.Lattice3(10, 10, 10, 0.5)
     g = imb.Lattice3(24, 16, 24, 0.8)
-    z = np.zeros((2, 3))
-    with pytest.raises(imb.ImbError) as e:     # two spheres whose cells touch
-        g.set_spheres(np.array([[8.0, 8.0, 12.0], [13.5, 8.0, 12.0]]), z, z, np.array([3.0, 3.0]))
+    with pytest.raises(imb.ImbError):
+        imb.Lattice3(10, 10, 10, 0.8, C_smag=-0.1)
+    z = np.zeros((3, 3))
+    g.set_spheres(np.array([[8.0, 8.0, 12.0], [13.5, 8.0, 12.0]]), z[:2], z[:2], np.array([3.0, 3.0]))
+    sph, _ = g.cell_map()                      # two spheres whose cells touch share them
+    assert (sph[..., 1] >= 0).any()
+    with pytest.raises(imb.ImbError) as e:     # three spheres on one cell
+        g.set_spheres(np.array([[8.0, 8.0, 12.0], [13.5, 8.0, 12.0], [10.75, 12.0, 12.0]]), z, z,
+                      np.array([3.0, 3.0, 3.0]))
     assert "OVERFLOW" in str(e.value)
     sph, cnt = g.cell_map()                    # left without spheres, not half mapped
     assert (sph < 0).all() and (cnt == 0).all()
