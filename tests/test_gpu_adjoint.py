@@ -8,9 +8,12 @@ against central finite differences of the GPU's own forward steps.
   post-collision field with the inlet rule), so it is checked against differences instead.
 * The 512 x 256 channel with 16 fixed disks (the drag-gradient case): d J / d u_in and
   d J / d tau against central differences with h = 1e-4 of J from rest (FP32 forward:
-  2e-2), and the checkpoint interval changes nothing (the recomputed states are the same; the
-  order in which a tile's immersed nodes are summed into the forces is not fixed, which leaves
-  differences of ~1e-10 in J and ~1e-12 in the gradient).
+  2e-2), and the checkpoint interval changes nothing: the recomputed states are the same, and
+  only the order in which a tile's immersed nodes are summed into the FP32 force partials is not
+  fixed (warps queue those nodes through a shared-memory counter).  J is the mean of those
+  forces, so two runs agree on it to the FP32 rounding of the partials, ~1e-7 per step: the bar
+  is 1e-6 (16 FP32 ulps), whatever the number of steps that average it.  The gradient comes
+  from the states alone (FP64 sums): 1e-12.
 * Binomial checkpointing (imb_drag_gradient_binomial) gives the gradient of the uniform scheme:
   against the oracle's adjoint as above with 0, 2 and 5 snapshots, and on the 16-disk channel with
   40 snapshots against the uniform scheme (the same tolerances as between checkpoint intervals).
@@ -99,7 +102,7 @@ def test_channel_16_disks_gradient(imb):
     g2 = imb.Lattice.from_workload(w)
     J2, g_u2, g_tau2, g_x2 = g2.drag_gradient(T, checkpoint_every=37)
     g2.close()
-    assert J2 == pytest.approx(J, rel=1e-8) and g_u2 == pytest.approx(g_u, rel=1e-12)
+    assert J2 == pytest.approx(J, rel=1e-6) and g_u2 == pytest.approx(g_u, rel=1e-12)
     assert g_tau2 == pytest.approx(g_tau, rel=1e-12)
     assert np.abs(g_x2 - g_x).max() <= 1e-12 * np.abs(g_x).max()
     # binomial checkpointing: 41 states held instead of 40 + 100
@@ -107,7 +110,7 @@ def test_channel_16_disks_gradient(imb):
     J4, g_u4, g_tau4, g_x4 = g4.drag_gradient(T, snapshots=40)
     f4 = g4.populations()
     g4.close()
-    assert J4 == pytest.approx(J, rel=1e-8) and g_u4 == pytest.approx(g_u, rel=1e-12)
+    assert J4 == pytest.approx(J, rel=1e-6) and g_u4 == pytest.approx(g_u, rel=1e-12)
     assert g_tau4 == pytest.approx(g_tau, rel=1e-12)
     assert np.abs(g_x4 - g_x).max() <= 1e-12 * np.abs(g_x).max()
     g5 = imb.Lattice.from_workload(w)   # the lattice is left T steps on, as after the uniform scheme
@@ -139,7 +142,7 @@ def test_autograd_wrapper_returns_the_library_gradient(imb, scheme):
     J.backward()
     g = imb.Lattice.from_workload(w)
     Jr, g_u, g_tau, g_x = g.drag_gradient(50, **scheme)
-    assert J.item() == pytest.approx(Jr, rel=1e-8)
+    assert J.item() == pytest.approx(Jr, rel=1e-6)   # FP32 force partials summed in no fixed order
     assert u.grad.item() == pytest.approx(g_u, rel=1e-12)
     assert tau.grad.item() == pytest.approx(g_tau, rel=1e-12)
     assert np.abs(x.grad.numpy() - g_x).max() <= 1e-12 * np.abs(g_x).max()
