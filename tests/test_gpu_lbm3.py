@@ -9,7 +9,8 @@ Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 
   FP16 storage: forces within 1 %.
 * Packed bed: eight spheres whose surfaces reach up to 0.8 cells into each other, so that
   some cells hold two: both map slots bit-exact, 200 steps within the same bars, and two
-  spheres pressed together in an all-periodic box.
+  spheres pressed together in an all-periodic box; the bed with the Smagorinsky closure as
+  well, and stored in FP16 (forces within 1 %).
 * Smagorinsky closure (C = 0.2 at tau = 0.51 and 0.55): 200 steps within the same bars, which
   lie at least 20 times below the closure's own effect on the forces.
 * Errors: three spheres on one cell -> IMB_E_OVERFLOW; bad sizes, radii and C < 0 ->
@@ -100,6 +101,29 @@ def test_packed_bed_two_spheres_per_cell(orc, imb):
     gs, gc = g.cell_map()
     assert np.array_equal(gs, os_[..., :2]) and np.array_equal(gc, oc[..., :2])
     _parity(o, g)
+    g.close()
+
+
+def test_packed_bed_with_smagorinsky_and_fp16(orc, imb):
+    # both general-kernel features at once (C = 0.2 at tau = 0.51 moves the forces 12 times the
+    # bar), then the same bed stored in FP16: forces within 1 %
+    w = W.spheres3(nx=40, ny=24, nz=36, n=8, seed=4, tau=0.51, gap=-0.8, r_lo=3.0, r_hi=5.0).with_(C_smag=0.2)
+    o = orc.Sim3(w)
+    g = imb.Lattice3.from_workload(w)
+    Fo = _parity(o, g)
+    g.close()
+    o0 = orc.Sim3(w.with_(C_smag=0.0))
+    o0.step(200)
+    F0, _ = o0.forces()
+    assert np.abs(F0 - Fo).max() > 5 * 1e-4 * np.abs(Fo).max()
+    w16 = w.with_(tau=0.7, C_smag=0.0)
+    o = orc.Sim3(w16)
+    g = imb.Lattice3.from_workload(w16, storage="fp16")
+    o.step(300)
+    g.step(300)
+    Fo, _ = o.forces()
+    Fg, _ = g.forces()
+    assert np.abs(Fg - Fo).max() < 1e-2 * np.abs(Fo).max()
     g.close()
 
 
