@@ -18,7 +18,11 @@
   share the cells around their contact (1e-11 after the transient has died out).
 * Smagorinsky closure: C = 0 or an unstrained equilibrium give tau; otherwise the closed form
   solves tau_eff = tau + 3 C^2 sqrt(2 S:S) with the strain read from the non-equilibrium
-  stress, S = -Pi / (2 rho cs^2 tau_eff).
+  stress, S = -Pi / (2 rho cs^2 tau_eff), the equilibrium taken at the half-force shifted
+  velocity when a body force acts (the unshifted one fails the relation).  With C = 0.1 the
+  two-sphere balance holds with each cell's B from its own steady tau_eff (and misses with tau),
+  and mass is conserved in a packed bed of eight spheres with walls, moving surfaces, a body
+  force and C = 0.2 at tau = 0.51.
 """
 import math
 
@@ -234,26 +238,63 @@ def test_smagorinsky_closure_3d(O):
             te = O.tau_eff3(f, 0.51, C)
             S = -Pi / (2 * rho * (1 / 3) * te)
             assert abs(te - (0.51 + 3 * C * C * math.sqrt(2 * (S * S).sum()))) < 1e-13 and te > 0.51
+    # with a body force the equilibrium is taken at the half-force shifted velocity (Eq. 4 with
+    # Guo forcing); the unshifted velocity gives a different tau_eff
+    F = np.array([2e-3, -1e-3, 5e-4])
+    for _ in range(5):
+        f = O.feq3(1.0, 0.01, 0.02, -0.01) + 5e-3 * rng.standard_normal(19) / 19
+        rho = f.sum()
+        m = (f[:, None] * c).sum(0)
+        te = O.tau_eff3(f, 0.51, 0.2, tuple(F))
+        for u, hit in (((m + 0.5 * F) / rho, True), (m / rho, False)):
+            Pi = np.einsum("q,qa,qb->ab", f - O.feq3(rho, *u), c, c)
+            S = -Pi / (2 * rho * (1 / 3) * te)
+            ok = abs(te - (0.51 + 3 * 0.04 * math.sqrt(2 * (S * S).sum()))) < 1e-13
+            assert ok == hit
 
 
-def test_two_spheres_sharing_cells_momentum_balance(O):
+@pytest.mark.parametrize("C", [0.0, 0.1])
+def test_two_spheres_sharing_cells_momentum_balance(O, C):
     # two held spheres pressed slightly into each other share the cells around the contact: B is split between
     # them by their solid ratios (B_p = B eps_p / sum eps); at steady state in an all-periodic
-    # box their summed drag is g sum_j (1 - B_j), and the mass stays
+    # box their summed drag is g sum_j (1 - B_j), and the mass stays.  With the Smagorinsky
+    # closure each cell's B comes from its own tau_eff (Eq. 14 with tau_eff), taken from the
+    # steady state; tau in its place would miss by ~1e-8 here
     L, tau, g, R = 16, 1.0, 1e-6, 2.6
     x = np.array([[L / 2 - R + 0.25, L / 2 + 0.3, L / 2], [L / 2 + R - 0.25, L / 2 - 0.2, L / 2 + 0.1]])
-    w = W.Workload3(name="pair3", nx=L, ny=L, nz=L, tau=tau, wall_y=False, force=(g, 0.0, 0.0),
+    w = W.Workload3(name="pair3", nx=L, ny=L, nz=L, tau=tau, wall_y=False, force=(g, 0.0, 0.0), C_smag=C,
                     x=x, v=np.zeros((2, 3)), omega=np.zeros((2, 3)), R=np.array([R, R]))
     s = O.Sim3(w)
     sph, cnt = s.cell_map()
     assert (sph[..., 1] >= 0).sum() > 0                     # some cells hold both spheres
     m0 = s.macro()[0].sum()
     eps = np.minimum(1.0, cnt.sum(axis=-1) / w.n_sub ** 3)
-    B = eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5))
-    expect = g * np.sum(1.0 - B)
     # the transient decays by about 5x per 1000 steps once the flow has formed (it crosses zero
     # near 5000 steps): 12 000 steps leave it below 1e-12 of the drag
     s.step(12000)
+    te = np.full(eps.shape, tau)
+    if C > 0.0:
+        f = s.f()
+        for k, j, i in zip(*np.nonzero(eps)):
+            te[k, j, i] = O.tau_eff3(f[:, k, j, i], tau, C, w.force)
+        assert (te[eps > 0] - tau).max() > 1e-8
+    B = eps * (te - 0.5) / ((1.0 - eps) + (te - 0.5))
+    expect = g * np.sum(1.0 - B)
     F, T = s.forces()
     assert abs(F[:, 0].sum() - expect) / expect < 1e-11
+    assert abs(s.macro()[0].sum() - m0) < 1e-12 * m0
+    if C > 0.0:
+        B_tau = eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5))
+        assert abs(F[:, 0].sum() - g * np.sum(1.0 - B_tau)) / expect > 1e-9
+
+
+def test_mass_conserved_packed_bed_with_closure(O):
+    # spheres sharing cells, moving surfaces, walls, a body force and the Smagorinsky closure at
+    # tau = 0.51: each sphere's share B_p of Eq. 12 conserves mass on its own, so the total stays
+    w = W.spheres3(nx=40, ny=24, nz=36, n=8, seed=4, tau=0.51, gap=-0.8, r_lo=3.0, r_hi=5.0).with_(C_smag=0.2)
+    s = O.Sim3(w)
+    sph, _ = s.cell_map()
+    assert (sph[..., 1] >= 0).sum() > 20
+    m0 = s.macro()[0].sum()
+    s.step(100)
     assert abs(s.macro()[0].sum() - m0) < 1e-12 * m0
