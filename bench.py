@@ -308,28 +308,60 @@ def _happel_brenner(R, l, U, nu):
     return F, T
 
 
+def _ergun_friction(Re):
+    """Eq. 22: the Ergun packed bed friction factor 150 / Re*_p + 1.75."""
+    return 150.0 / Re + 1.75
+
+
 def time_lattice3(imb, torch, ts, steps=100):
     """The D3Q19 path: throughput on the 400 x 100 x 400 Poiseuille-flow-past-a-sphere box
-    (N = 20 cells per diameter, 16 M cells) in FP32 and FP16 storage, and the steady drag and
-    torque errors against Eqs. 18-19 at N = 5 and 10 (n_sub = 5, tau = 1)."""
+    (N = 20 cells per diameter, 16 M cells) and on the paper's packed bed (Sec. 3.3, N = 20,
+    240 x 100 x 100 cells, its Delta P = 1600 Pa run: tau = 0.501, C = 0.3, touching spheres
+    sharing cells), in FP32 and FP16 storage; the steady drag and torque errors against
+    Eqs. 18-19 at N = 5 and 10 (n_sub = 5, tau = 1); and the packed bed's friction factor at
+    its lowest pressure difference (1 Pa, tau = 0.58) against Ergun's (Eqs. 21-23)."""
     out = {}
     peak, kind = measured_hbm_peak()
-    w = W.happel(20)
-    for st in ("fp32", "fp16"):
-        g = imb.Lattice3.from_workload(w, storage=st)
-        g.step(5)
-        g.enable_kernel_timing(True)
-        t0 = time.perf_counter()
-        g.step(steps)
-        dt = time.perf_counter() - t0
-        ms, n = g.kernel_time()
-        kavg = ms / max(n, 1) * 1e-3
-        gbs = g.bytes_per_cell() * w.cells / kavg / 1e9
-        out[f"{w.name}:{st}"] = {"cells": w.cells, "steps": steps, "ms_per_step": round(dt / steps * 1e3, 4),
-                                 "mlups": round(w.cells / kavg / 1e6, 1), "kernel": "k3_stream_collide",
-                                 "kernel_ms_avg": round(kavg * 1e3, 4), "bytes_per_cell": g.bytes_per_cell(),
-                                 "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "peak_source": kind}
-        g.close()
+    for w, kern in ((W.happel(20), "k3_stream_collide (one sphere per cell, BGK)"),
+                    (W.packed_bed(20, run=9), "k3_stream_collide (two slots, Smagorinsky)")):
+        for st in ("fp32", "fp16"):
+            g = imb.Lattice3.from_workload(w, storage=st)
+            g.step(5)
+            g.enable_kernel_timing(True)
+            t0 = time.perf_counter()
+            g.step(steps)
+            dt = time.perf_counter() - t0
+            ms, n = g.kernel_time()
+            kavg = ms / max(n, 1) * 1e-3
+            gbs = g.bytes_per_cell() * w.cells / kavg / 1e9
+            out[f"{w.name}:{st}"] = {"cells": w.cells, "spheres": w.n_spheres, "steps": steps,
+                                     "ms_per_step": round(dt / steps * 1e3, 4),
+                                     "mlups": round(w.cells / kavg / 1e6, 1), "kernel": kern,
+                                     "kernel_ms_avg": round(kavg * 1e3, 4), "bytes_per_cell": g.bytes_per_cell(),
+                                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "peak_source": kind}
+            g.close()
+    # the packed bed at 1 Pa: the drag on the spheres per unit cross-section is the pressure drop
+    # a pressure-driven medium would need, and U the flow rate through the plane in the middle of
+    # the free fluid.  The drag settles within tens of steps (the momentum balance), the flow in
+    # the pores on the viscous time (d_p / 2)^2 / nu, about 3700 steps: 15 000 steps are four
+    N = 20
+    wb = W.packed_bed(N, run=0, C_smag=0.0)
+    g = imb.Lattice3.from_workload(wb)
+    n_steps = 15000
+    g.step(n_steps)
+    F, _ = g.forces()
+    D = float(F[:, 0].sum())
+    _, ux, _, _ = g.macro()
+    g.close()
+    n = 1.0 - math.pi / 6.0
+    nu = (wb.tau - 0.5) / 3.0
+    U = float(ux[:, :, 0].mean())
+    dPdL = D / (wb.ny * wb.nz * 10 * N)
+    Re = U * N / (nu * (1.0 - n))
+    f = dPdL * N * n ** 3 / (U * U * (1.0 - n))
+    out[f"{wb.name}_ergun"] = {"steps": n_steps, "Re_p": round(Re, 5), "f_star": round(f, 3),
+                               "f_star_ergun": round(_ergun_friction(Re), 3),
+                               "rel_diff": round(f / _ergun_friction(Re) - 1.0, 4)}
     for N in (5, 10):
         wh = W.happel(N)
         g = imb.Lattice3.from_workload(wh)

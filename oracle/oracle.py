@@ -414,6 +414,28 @@ def happel_brenner(R, l, U, rho, nu):
     return F, T
 
 
+def ergun_gradient(U, d_p, n, rho, mu):
+    """Eq. 21 (Ergun): pressure gradient Delta P / L across a packed bed of particle diameter d_p
+    and porosity n at superficial velocity U, a viscous loss linear in U plus an inertial one
+    quadratic in U."""
+    return 150.0 * mu / d_p ** 2 * (1.0 - n) ** 2 / n ** 3 * U + 1.75 * rho / d_p * (1.0 - n) / n ** 3 * U ** 2
+
+
+def packed_bed_reynolds(U, d_p, n, rho, mu):
+    """Eq. 23: the modified particle Reynolds number rho d_p U / (mu (1 - n))."""
+    return rho * d_p * U / (mu * (1.0 - n))
+
+
+def packed_bed_friction(dPdL, U, d_p, n, rho):
+    """Eq. 22, left: the packed bed friction factor (Delta P / L) d_p n^3 / (rho U^2 (1 - n))."""
+    return dPdL * d_p * n ** 3 / (rho * U ** 2 * (1.0 - n))
+
+
+def ergun_friction(Re):
+    """Eq. 22, right: the Ergun friction factor 150 / Re*_p + 1.75."""
+    return 150.0 / Re + 1.75
+
+
 def happel_table2():
     """The paper's Table 2 rows (tests/golden/happel_table2.txt): (N, n_sub, tau, err_F %, err_T %)."""
     path = os.path.join(os.path.dirname(HERE), "tests", "golden", "happel_table2.txt")

@@ -10,7 +10,8 @@ Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 
 * Packed bed: eight spheres whose surfaces reach up to 0.8 cells into each other, so that
   some cells hold two: both map slots bit-exact, 200 steps within the same bars, and two
   spheres pressed together in an all-periodic box; the bed with the Smagorinsky closure as
-  well, and stored in FP16 (forces within 1 %).
+  well, and stored in FP16 (forces within 1 %); the paper's simple cubic packed bed (Sec. 3.3,
+  N = 10, C = 0.3) with its touching spheres sharing 15 225 cells: maps bit-exact, 20 steps.
 * Smagorinsky closure (C = 0.2 at tau = 0.51 and 0.55): 200 steps within the same bars, which
   lie at least 20 times below the closure's own effect on the forces.
 * Errors: three spheres on one cell -> IMB_E_OVERFLOW; bad sizes, radii and C < 0 ->
@@ -124,6 +125,21 @@ def test_packed_bed_with_smagorinsky_and_fp16(orc, imb):
     Fo, _ = o.forces()
     Fg, _ = g.forces()
     assert np.abs(Fg - Fo).max() < 1e-2 * np.abs(Fo).max()
+    g.close()
+
+
+def test_packed_bed_paper_geometry(orc, imb):
+    # the paper's simple cubic packing (Sec. 3.3) at N = 10 with its run at Delta P = 50 Pa
+    # (tau = 0.51) and C = 0.3, the lattice half a cell off the packing: 15 225 cells shared by
+    # two touching spheres; both map slots bit-exact, then 20 steps within the parity bars
+    w = W.packed_bed(10, run=4)
+    o = orc.Sim3(w)
+    os_, oc = o.cell_map()
+    g = imb.Lattice3.from_workload(w)
+    gs, gc = g.cell_map()
+    assert (os_[..., 1] >= 0).sum() > 10000 and (os_[..., 2] < 0).all()
+    assert np.array_equal(gs, os_[..., :2]) and np.array_equal(gc, oc[..., :2])
+    _parity(o, g, 20)
     g.close()
 
 

@@ -298,3 +298,29 @@ def test_mass_conserved_packed_bed_with_closure(O):
     m0 = s.macro()[0].sum()
     s.step(100)
     assert abs(s.macro()[0].sum() - m0) < 1e-12 * m0
+
+
+def test_ergun_forms_agree(orc):
+    # Eq. 22 is Eq. 21 divided through: the friction factor of the Ergun gradient at any U is
+    # 150 / Re*_p + 1.75 with Re*_p of Eq. 23
+    n, rho, mu, d_p = 0.4764, 1000.0, 1.0e-3, 1.0e-3
+    for U in (1e-6, 1e-4, 3e-3, 0.1, 2.0):
+        G = orc.ergun_gradient(U, d_p, n, rho, mu)
+        f = orc.packed_bed_friction(G, U, d_p, n, rho)
+        assert abs(f - orc.ergun_friction(orc.packed_bed_reynolds(U, d_p, n, rho, mu))) < 1e-12 * f
+
+
+@pytest.mark.parametrize("offset", [0.5, 0.0])
+def test_packed_bed_cell_map(O, offset):
+    # the paper's simple cubic packing at N = 10: the sub-cell solid ratios sum to the spheres'
+    # volume fraction pi / 6 of the medium (n_sub = 5: within 1 %); touching spheres share the
+    # cells around their contacts when the lattice sits half a cell off the packing and none
+    # when the contacts lie on cell faces; no cell ever holds three
+    N = 10
+    w = W.packed_bed(N, run=4, offset=offset)
+    sph, cnt = O.Sim3(w).cell_map()
+    vol = cnt.sum() / w.n_sub ** 3
+    assert abs(vol / (250 * math.pi / 6.0 * N ** 3) - 1.0) < 1e-2
+    shared = (sph[..., 1] >= 0).sum()
+    assert (shared > 1000) if offset else (shared == 0)
+    assert (sph[..., 2] < 0).all()

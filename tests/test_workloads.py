@@ -85,3 +85,46 @@ def test_sphere_boxes_and_happel_geometry():
         nu = (h.tau - 0.5) / 3.0
         yc, H = h.x[0, 1], h.ny
         assert abs(h.force[0] / (2 * nu) * yc * (H - yc) - 2.0e-4) < 1e-15
+
+
+def test_packed_bed_geometry_and_units(orc):
+    # the paper's packing (Sec. 3.3): 10 x 5 x 5 touching spheres in a simple cubic arrangement,
+    # one d_p of free fluid at each end, N cells per diameter; its porosity 1 - pi / 6 is the
+    # printed n = 0.4764
+    N = 20
+    w = W.packed_bed(N, run=9)
+    assert (w.nx, w.ny, w.nz) == (12 * N, 5 * N, 5 * N) and w.n_spheres == 250 and (w.R == N / 2).all()
+    assert not w.wall_y and w.C_smag == 0.3 and w.tau == 0.501
+    assert (w.x >= 0).all() and (w.x < np.array([w.nx, w.ny, w.nz])).all()
+    d = w.x[:, None, :] - w.x[None, :, :]
+    for a, L in enumerate((w.nx, w.ny, w.nz)):
+        d[..., a] -= L * np.round(d[..., a] / L)
+    dist = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(dist, np.inf)
+    assert abs(dist.min() - N) < 1e-12                       # neighbours touch
+    assert ((np.abs(dist - N) < 1e-12).sum(1) >= 5).all()    # x neighbours at the ends: 5, else 6
+    assert w.x[:, 0].min() - w.R[0] == N + 0.5 and w.nx - (w.x[:, 0].max() + w.R[0]) == N - 0.5
+    assert round(1.0 - math.pi / 6.0, 4) == 0.4764
+    # units: nu_lattice dx^2 / dt is the fluid's viscosity, and Ergun (Eq. 21) solved in lattice
+    # units with the body force as the gradient gives the physical velocity times dt / dx
+    n, rho, mu, d_p = 1.0 - math.pi / 6.0, 1000.0, 1.0e-3, 1.0e-3
+    for run, (dP, tau) in enumerate(W.PACKED_BED_RUNS):
+        wr = W.packed_bed(N, run=run)
+        dx, dt = W.packed_bed_units(N, tau)
+        nu = (tau - 0.5) / 3.0
+        assert abs(nu * dx * dx / dt - mu / rho) < 1e-18
+        U = _bisect(lambda u: orc.ergun_gradient(u, d_p, n, rho, mu) - dP / (10 * d_p), 0.0, 10.0)
+        Ul = _bisect(lambda u: orc.ergun_gradient(u, N, n, 1.0, nu) - wr.force[0], 0.0, 1.0)
+        assert abs(Ul - U * dt / dx) < 1e-9 * Ul
+        assert abs(orc.packed_bed_reynolds(Ul, N, n, 1.0, nu) - orc.packed_bed_reynolds(U, d_p, n, rho, mu)) < 1e-8
+
+
+def _bisect(f, lo, hi):
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0.0:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+

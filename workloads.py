@@ -381,6 +381,40 @@ def happel(N=5, tau=1.0, n_sub=5, u_c=2.0e-4, steps=None) -> Workload3:
                      omega=np.zeros((1, 3)), R=np.array([N / 2.0]))
 
 
+# (Delta P [Pa] across the 10 d_p medium, tau) of the paper's ten packed-bed runs (Sec. 3.3)
+PACKED_BED_RUNS = ((1.0, 0.58), (5.0, 0.53), (10.0, 0.524), (20.0, 0.516), (50.0, 0.51), (100.0, 0.508),
+                   (200.0, 0.505), (400.0, 0.503), (800.0, 0.502), (1600.0, 0.501))
+
+
+def packed_bed_units(N, tau, d_p=1.0e-3, rho_f=1000.0, mu_f=1.0e-3):
+    """Lattice spacing and time step of the packed bed: dx = d_p / N, and dt from the fluid's
+    viscosity, nu_f = (tau - 1/2) / 3 dx^2 / dt."""
+    dx = d_p / N
+    dt = (tau - 0.5) / 3.0 * dx * dx / (mu_f / rho_f)
+    return dx, dt
+
+
+def packed_bed(N=20, run=9, C_smag=0.3, n_sub=5, offset=0.5, d_p=1.0e-3, rho_f=1000.0, mu_f=1.0e-3,
+               steps=1000) -> Workload3:
+    """The paper's flow through densely packed particles (Sec. 3.3): 10 x 5 x 5 spheres of
+    diameter d_p in a simple cubic arrangement with N cells per diameter, one d_p of free fluid
+    before and after the packing in x, periodic in every direction.  Run ``run`` of the ten
+    takes its pressure difference Delta P across the 10 d_p medium and its tau; the pressure
+    gradient Delta P / (10 d_p) drives the fluid as the body force g = (Delta P / L) dt^2 /
+    (rho_f dx) in lattice units.  The lattice sits ``offset`` cells off the packing in every
+    direction: at 0 (N even) every contact point lies on a cell face and no cell holds two
+    spheres; at 1/2 the contacts fall inside cells, which the two touching spheres share."""
+    dP, tau = PACKED_BED_RUNS[run]
+    dx, dt = packed_bed_units(N, tau, d_p, rho_f, mu_f)
+    g = dP / (10.0 * d_p) * dt * dt / (rho_f * dx)
+    x = np.array([[(1.5 + i) * N + offset, (0.5 + j) * N + offset, (0.5 + k) * N + offset]
+                  for i in range(10) for j in range(5) for k in range(5)])
+    n = x.shape[0]
+    return Workload3(name=f"packed_bed_N{N}_dP{dP:g}_tau{tau:g}_C{C_smag:g}", nx=12 * N, ny=5 * N, nz=5 * N,
+                     tau=tau, wall_y=False, force=(g, 0.0, 0.0), n_sub=n_sub, C_smag=C_smag, steps=steps, x=x,
+                     v=np.zeros((n, 3)), omega=np.zeros((n, 3)), R=np.full(n, N / 2.0))
+
+
 def spheres3(nx=40, ny=24, nz=36, n=3, r_lo=2.5, r_hi=5.0, seed=3, tau=0.7, wall_y=True,
              force=(2.0e-5, 0.0, 1.0e-5), speed=0.004, spin=0.001, n_sub=5, gap=2.0) -> Workload3:
     """Up to ``n`` spheres by random sequential addition (surfaces at least ``gap`` cells
