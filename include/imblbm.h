@@ -214,7 +214,8 @@ int imb_binomial_schedule(int T, int snapshots, int *ops, int max_ops, int *n_op
  * each cell, u_s = 0) and adds each domain's drag (Eq. 15, summed over its disks)
  * to an accumulator.  The library owns the batch; host arrays are copied.
  * Returns IMB_E_INVALID_ARG for a bad size, tau <= 0.5, C_smag < 0, a disk outside its domain
- * or wider than it minus four cells; IMB_E_NOMEM / IMB_E_CUDA on device failures
+ * or wider than it minus four cells, or disks x (2 ceil(r_max) + 3)^2 beyond one launch of
+ * 128-thread blocks (2^31 - 1 blocks); IMB_E_NOMEM / IMB_E_CUDA on device failures
  * (then *out holds a batch to destroy, with the message in imb_batch_last_error). */
 typedef struct imb_batch imb_batch;
 int imb_batch_create(imb_batch **out, int n_domains, const int *nx, const int *ny, const double *tau,
@@ -350,9 +351,10 @@ int imb3_init(imb3_ctx **out, int nx, int ny, int nz, double tau, const imb3_par
 
 /* Set n held spheres: centres x[3n] (inside the lattice), velocities v[3n], spins
  * omega[3n], radii R[n] (host arrays, copied); builds the cell map on the GPU.
- * IMB_E_INVALID_ARG for a radius outside (0, 1000], a centre outside, or a periodic
- * extent below 2 (R + 2); IMB_E_OVERFLOW when three spheres cover one cell (the lattice
- * is then left without spheres). */
+ * IMB_E_INVALID_ARG for a radius outside (0, 1000], a centre outside, a periodic
+ * extent below 2 (R + 2), or n x (2 ceil(R_max) + 3)^3 beyond one launch of 128-thread
+ * blocks (2^31 - 1 blocks; the lattice keeps its spheres); IMB_E_OVERFLOW when three
+ * spheres cover one cell (the lattice is then left without spheres). */
 int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const double *v, const double *omega, const double *R);
 
 /* Advance n steps and wait (bounded).  IMB_E_UNSTABLE on NaN or |u| >= 0.3. */

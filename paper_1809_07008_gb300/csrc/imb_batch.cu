@@ -441,7 +441,8 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
             }
             rmax = std::max(rmax, r);
         }
-    if (items > 2147483647LL) {
+    const long long wd = 2LL * ((long long)std::ceil(rmax) + 1) + 1;   // the solid-ratio launch's box
+    if (items > 2147483647LL || ((long long)ndisk * wd * wd + 127) / 128 > 2147483647LL) {
         delete b;
         return IMB_E_INVALID_ARG;
     }
@@ -471,23 +472,27 @@ extern "C" int imb_batch_create(imb_batch **out, int n_domains, const int *nx, c
     BCK(cudaMemcpyAsync(b->dom, b->hdom.data(), sizeof(BatchDomain) * n_domains, cudaMemcpyHostToDevice, b->stream),
         "domains");
     if (ndisk > 0) {
-        int *d_dd = nullptr;
-        double *d_xy = nullptr, *d_r = nullptr;
-        BCK(cudaMalloc(&d_dd, sizeof(int) * ndisk), "disks");
-        BCK(cudaMalloc(&d_xy, sizeof(double) * 2 * ndisk), "disks");
-        BCK(cudaMalloc(&d_r, sizeof(double) * ndisk), "disks");
-        BCK(cudaMemcpyAsync(d_dd, ddom.data(), sizeof(int) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
-        BCK(cudaMemcpyAsync(d_xy, disk_xy, sizeof(double) * 2 * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
-        BCK(cudaMemcpyAsync(d_r, disk_r, sizeof(double) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        struct DiskArrays {   // freed on every return (cudaFree waits for the launch)
+            int *dd = nullptr;
+            double *xy = nullptr, *r = nullptr;
+            ~DiskArrays() {
+                if (dd) cudaFree(dd);
+                if (xy) cudaFree(xy);
+                if (r) cudaFree(r);
+            }
+        } t;
+        BCK(cudaMalloc(&t.dd, sizeof(int) * ndisk), "disks");
+        BCK(cudaMalloc(&t.xy, sizeof(double) * 2 * ndisk), "disks");
+        BCK(cudaMalloc(&t.r, sizeof(double) * ndisk), "disks");
+        BCK(cudaMemcpyAsync(t.dd, ddom.data(), sizeof(int) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        BCK(cudaMemcpyAsync(t.xy, disk_xy, sizeof(double) * 2 * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
+        BCK(cudaMemcpyAsync(t.r, disk_r, sizeof(double) * ndisk, cudaMemcpyHostToDevice, b->stream), "disks");
         const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;
-        const long long nthreads = (long long)ndisk * w * w;
-        k_batch_solid<<<(unsigned)((nthreads + 127) / 128), 128, 0, b->stream>>>(b->dom, d_dd, d_xy, d_r, ndisk,
+        const long long nthreads = (long long)ndisk * w * w;   // grid size checked at validation
+        k_batch_solid<<<(unsigned)((nthreads + 127) / 128), 128, 0, b->stream>>>(b->dom, t.dd, t.xy, t.r, ndisk,
                                                                                span, b->E);
         BCK(cudaGetLastError(), "solid ratio");
         BCK(cudaStreamSynchronize(b->stream), "solid ratio");
-        cudaFree(d_dd);
-        cudaFree(d_xy);
-        cudaFree(d_r);
     }
     return batch_wait(b);
 }

@@ -677,6 +677,10 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
         }
         rmax = std::max(rmax, R[s]);
     }
+    const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;   // the cell map's box per sphere
+    const long long nt = (long long)n * w * w * w;
+    if ((nt + 127) / 128 > 2147483647LL)
+        return fail3(c, IMB_E_INVALID_ARG, "spheres x bounding box exceed one cell-map launch");
     CK3(cudaSetDevice(c->device), "cudaSetDevice");
     CK3(cudaStreamSynchronize(c->stream), "stream");
     if (c->sph) cudaFree(c->sph);
@@ -715,8 +719,6 @@ extern "C" int imb3_set_spheres(imb3_ctx *c, int n, const double *x, const doubl
     CK3(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream), "spheres");
     CK3(cudaMemcpyAsync(dR, R, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "spheres");
     CK3(cudaMemsetAsync(c->FT, 0, sizeof(double) * 6 * n, c->stream), "clear forces");
-    const int span = (int)std::ceil(rmax) + 1, w = 2 * span + 1;
-    const long long nt = (long long)n * w * w * w;
     k3_map<<<(unsigned)((nt + 127) / 128), 128, 0, c->stream>>>(dx, dR, n, span, c->a, c->map, c->map2, c->err + 1,
                                                                  c->err);
     c->launches++;
