@@ -313,6 +313,18 @@ def _ergun_friction(Re):
     return 150.0 / Re + 1.75
 
 
+def packed_bed_friction(D, U, N, tau, area, length):
+    """The packed bed's modified Reynolds number (Eq. 23) and friction factor (Eq. 22, left) in
+    lattice units (rho = 1, d_p = N cells, nu = (tau - 1/2) / 3, porosity 1 - pi / 6), with the
+    drag D on the spheres per cross-section ``area`` standing for Delta P across the medium of
+    ``length`` cells and U the superficial velocity; returns (Re*_p, f*, Ergun's f*)."""
+    n = 1.0 - math.pi / 6.0
+    nu = (tau - 0.5) / 3.0
+    Re = U * N / (nu * (1.0 - n))
+    f = D / (area * length) * N * n ** 3 / (U * U * (1.0 - n))
+    return Re, f, _ergun_friction(Re)
+
+
 def time_lattice3(imb, torch, ts, steps=100):
     """The D3Q19 path: throughput on the 400 x 100 x 400 Poiseuille-flow-past-a-sphere box
     (N = 20 cells per diameter, 16 M cells) and on the paper's packed bed (Sec. 3.3, N = 20,
@@ -353,15 +365,10 @@ def time_lattice3(imb, torch, ts, steps=100):
     D = float(F[:, 0].sum())
     _, ux, _, _ = g.macro()
     g.close()
-    n = 1.0 - math.pi / 6.0
-    nu = (wb.tau - 0.5) / 3.0
     U = float(ux[:, :, 0].mean())
-    dPdL = D / (wb.ny * wb.nz * 10 * N)
-    Re = U * N / (nu * (1.0 - n))
-    f = dPdL * N * n ** 3 / (U * U * (1.0 - n))
+    Re, f, fe = packed_bed_friction(D, U, N, wb.tau, wb.ny * wb.nz, 10 * N)
     out[f"{wb.name}_ergun"] = {"steps": n_steps, "Re_p": round(Re, 5), "f_star": round(f, 3),
-                               "f_star_ergun": round(_ergun_friction(Re), 3),
-                               "rel_diff": round(f / _ergun_friction(Re) - 1.0, 4)}
+                               "f_star_ergun": round(fe, 3), "rel_diff": round(f / fe - 1.0, 4)}
     for N in (5, 10):
         wh = W.happel(N)
         g = imb.Lattice3.from_workload(wh)

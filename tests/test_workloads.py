@@ -128,3 +128,21 @@ def _bisect(f, lo, hi):
             lo = mid
     return 0.5 * (lo + hi)
 
+
+
+def test_bench_packed_bed_friction_follows_eqs_22_23(orc):
+    # the bench's report of the packed bed: with D = (Delta P / L) x area x length (the drag a
+    # pressure-driven medium takes) its Re*_p and f* are Eqs. 23 and 22 in lattice units, and at
+    # the Ergun gradient of a velocity the two friction factors coincide
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = 1.0 - math.pi / 6.0
+    N, tau, area, length = 20, 0.58, 100 * 100, 200
+    nu = (tau - 0.5) / 3.0
+    for U in (1e-5, 3.5e-4, 0.01):
+        G = orc.ergun_gradient(U, N, n, 1.0, nu)
+        Re, f, fe = bench.packed_bed_friction(G * area * length, U, N, tau, area, length)
+        assert abs(Re - orc.packed_bed_reynolds(U, N, n, 1.0, nu)) < 1e-12 * Re
+        assert abs(f - orc.packed_bed_friction(G, U, N, n, 1.0)) < 1e-12 * f
+        assert abs(fe - orc.ergun_friction(Re)) < 1e-12 * fe and abs(f - fe) < 1e-10 * fe
