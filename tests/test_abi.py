@@ -1,5 +1,7 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-``include/imblbm.h`` declares.  No compute call is made (no GPU needed)."""
+``include/imblbm.h`` declares; the parameter structs mirror the header; and the host-side
+argument checks (which run before any CUDA call) refuse bad sizes, relaxation times,
+Smagorinsky constants, disks and oversized launches.  No compute call is made (no GPU needed)."""
 import ctypes
 import os
 import re
@@ -74,3 +76,47 @@ def test_params3_struct_layout_matches_header(lib):
     p = binding.Params3()
     lib.imb3_default_params(ctypes.byref(p))
     assert (p.wall_y, p.n_sub, p.storage, p.rho0, p.timeout_ms) == (1, 5, 0, 1.0, 60000)
+
+
+def test_host_validation_refuses_before_any_device_call(lib):
+    # the argument checks of imb3_init, imb_init_lattice and imb_batch_create run on the host
+    # before the first CUDA call, so their refusals answer here without a GPU
+    import numpy as np
+    from paper_1809_07008_gb300 import binding as B
+    C = ctypes
+    BAD = -1   # IMB_E_INVALID_ARG
+    h = C.c_void_p()
+    p3 = B.Params3()
+    lib.imb3_default_params(C.byref(p3))
+    assert p3.C_smag == 0.0 and p3.n_sub == 5
+    assert lib.imb3_init(C.byref(h), 2, 10, 10, 0.8, C.byref(p3)) == BAD and not h.value
+    assert lib.imb3_init(C.byref(h), 10, 10, 10, 0.5, C.byref(p3)) == BAD
+    p3.C_smag = -0.1
+    assert lib.imb3_init(C.byref(h), 10, 10, 10, 0.8, C.byref(p3)) == BAD and not h.value
+    assert b"C_smag" in lib.imb3_last_error(None)
+    p3.C_smag, p3.n_sub = 0.0, 11
+    assert lib.imb3_init(C.byref(h), 10, 10, 10, 0.8, C.byref(p3)) == BAD
+    p = B.default_params()
+    assert lib.imb_init_lattice(C.byref(h), 64, 32, 0.6, -0.1, C.byref(p)) == BAD and not h.value
+    assert lib.imb_init_lattice(C.byref(h), 64, 32, 0.5, 0.0, C.byref(p)) == BAD
+
+    def batch(nx, ny, tau, xy, r):
+        n = len(r)
+        ints = lambda v: np.array([v], dtype=np.int32)
+        dbl = lambda v: np.array([v], dtype=np.float64)
+        hb = C.c_void_p()
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        rc = lib.imb_batch_create(C.byref(hb), 1, ints(nx).ctypes.data_as(B._ip), ints(ny).ctypes.data_as(B._ip),
+                                  B._d(dbl(tau)), B._d(dbl(0.0)), B._d(dbl(1e-6)), B._d(dbl(0.0)),
+                                  ints(n).ctypes.data_as(B._ip), B._d(xy), B._d(r), 0)
+        assert not hb.value
+        return rc
+
+    assert batch(128, 128, 0.5, [[64.0, 64.0]], [5.0]) == BAD              # tau <= 1/2
+    assert batch(128, 128, 0.6, [[130.0, 64.0]], [5.0]) == BAD             # centre outside
+    assert batch(128, 128, 0.6, [[64.0, 64.0]], [62.5]) == BAD             # wider than the domain - 4
+    # 20 000 disks of radius 2046 in one 4096^2 domain pass every per-disk check, but their
+    # solid-ratio launch would need 20 000 x 4095^2 / 128 > 2^31 - 1 blocks
+    n = 20000
+    assert batch(4096, 4096, 0.6, np.full((n, 2), 2048.0), np.full(n, 2046.0)) == BAD
