@@ -468,7 +468,8 @@ class Batch:
 
 
 class Lattice3:
-    """A D3Q19 lattice with held spheres (imb3_*; the paper's own lattice)."""
+    """A D3Q19 lattice with held spheres (imb3_*; the paper's own lattice): up to two spheres per
+    cell, the Smagorinsky closure when ``C_smag`` > 0, walls in y fixed or moving along x."""
 
     def __init__(self, nx, ny, nz, tau, wall_y=True, force=(0.0, 0.0, 0.0), n_sub=5, storage="fp32",
                  rho0=1.0, u0=(0.0, 0.0, 0.0), wall_u=(0.0, 0.0), C_smag=0.0):
