@@ -23,7 +23,9 @@ Poiseuille-flow-past-a-sphere benchmark (Sec. 3.1) against Eqs. 18-19 and Table 
   of R x the force scale).
 * Benchmark: N = 5 and 10 cells per diameter, n_sub = 5, tau = 1, run to a steady drag: the
   relative errors against Eqs. 18-19 fall with N and lie within 3 percentage points of the
-  paper's Table 2 (17.8 / 31.4 % at N = 5, 7.0 / 11.3 % at N = 10).
+  paper's Table 2 (17.8 / 31.4 % at N = 5, 7.0 / 11.3 % at N = 10); the table's other eight
+  rows (N = 20 and 25, n_sub 2-10, tau 0.53-1) within one point, opt-in (IMB_LONG=1: minutes of
+  GPU time each).
 """
 import numpy as np
 import pytest
@@ -240,6 +242,33 @@ def test_happel_brenner_convergence_against_table2(orc, imb):
     assert eF10 < eF5 and eT10 < eT5
     assert abs(eF5 - tab[(5, 5, 1.0)][0]) < 3.0 and abs(eT5 - tab[(5, 5, 1.0)][1]) < 3.0
     assert abs(eF10 - tab[(10, 5, 1.0)][0]) < 3.0 and abs(eT10 - tab[(10, 5, 1.0)][1]) < 3.0
+
+
+@pytest.mark.skipif(__import__("os").environ.get("IMB_LONG") != "1",
+                    reason="minutes of GPU time per row; set IMB_LONG=1 to run")
+@pytest.mark.parametrize("N,n_sub,tau", [(20, 5, 1.0), (25, 5, 1.0), (20, 2, 1.0), (20, 4, 1.0), (20, 10, 1.0),
+                                         (20, 5, 0.8), (20, 5, 0.62), (20, 5, 0.53)])
+def test_happel_brenner_table2_fine_rows(orc, imb, N, n_sub, tau):
+    # the rest of Table 2 (N = 20 and 25, its n_sub and tau sweeps), each run to a steady drag:
+    # within one percentage point of the printed errors
+    tab = {(r[0], r[1], r[2]): (r[3], r[4]) for r in orc.happel_table2()}
+    w = W.happel(N, tau=tau, n_sub=n_sub)
+    g = imb.Lattice3.from_workload(w)
+    nu = (tau - 0.5) / 3.0
+    yc = w.x[0, 1]
+    U = w.force[0] / (2 * nu) * yc * (w.ny - yc)
+    F_a, T_a = orc.happel_brenner(w.R[0], yc, U, 1.0, nu)
+    prev = None
+    for _ in range(4000):
+        g.step(1000)
+        F, T = g.forces()
+        if prev is not None and abs(F[0, 0] - prev) < 1e-6 * abs(F[0, 0]):
+            break
+        prev = F[0, 0]
+    g.close()
+    eF, eT = abs(F_a - F[0, 0]) / F_a * 100.0, abs(T_a - abs(T[0, 2])) / T_a * 100.0
+    pF, pT = tab[(N, n_sub, tau)]
+    assert abs(eF - pF) < 1.0 and abs(eT - pT) < 1.0, (eF, eT, pF, pT)
 
 
 def test_couette_moving_walls(orc, imb):
