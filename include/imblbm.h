@@ -55,7 +55,10 @@ enum { IMB_CONTACT_LINEAR = 0, IMB_CONTACT_HERTZ_MINDLIN = 1 };
 
 /* Parameters of a lattice.  imb_default_params() fills every field. */
 typedef struct imb_params {
-    int bc_x;            /* PERIODIC, WALL, or INLET_OUTLET (inlet x = 0, outlet x = nx-1) */
+    int bc_x;            /* PERIODIC, WALL, or INLET_OUTLET: inlet column x = 0 set after each
+                            stream to f^eq(rho of column 1, u_in); outlet column x = nx-1 to
+                            f^eq(1, u of column nx-2) (reference pressure, zero velocity
+                            gradient); the walls y = 0, ny take the corners first        */
     int bc_y;            /* PERIODIC or WALL                                                  */
     double u_in_x, u_in_y; /* inlet velocity for INLET_OUTLET                                  */
     double Fx, Fy;       /* body force density on the fluid (Guo forcing); 0 = none            */

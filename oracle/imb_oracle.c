@@ -255,16 +255,25 @@ static void stream(orc_sim *s)
             }
     if (s->p.bc_x == ORC_INLET_OUTLET) {
         /* inlet column x = 0: equilibrium at the prescribed velocity with the
-         * density of the first interior column; outlet column x = nx-1: copy of
-         * column nx-2 (zero gradient) */
+         * density of the first interior column; outlet column x = nx-1:
+         * equilibrium at the reference density 1 with the velocity of column nx-2
+         * (zero velocity gradient).  The outlet holds the pressure level: with a
+         * velocity inlet, copying every population of column nx-2 leaves the
+         * density free and the channel's mass drifts without bound. */
         for (int k = 0; k < ny; ++k) {
-            double rho1 = 0.0, fe[9];
-            for (int q = 0; q < 9; ++q)
+            double rho1 = 0.0, fe[9], fo[9], ro = 0.0, jox = 0.0, joy = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                const double g = s->f[IDX(s, q, k, nx - 2)];
                 rho1 += s->f[IDX(s, q, k, 1)];
+                ro += g;
+                jox += CX[q] * g;
+                joy += CY[q] * g;
+            }
             orc_feq(rho1, s->p.u_in_x, s->p.u_in_y, fe);
+            orc_feq(1.0, jox / ro, joy / ro, fo);
             for (int q = 0; q < 9; ++q) {
                 s->f[IDX(s, q, k, 0)] = fe[q];
-                s->f[IDX(s, q, k, nx - 1)] = s->f[IDX(s, q, k, nx - 2)];
+                s->f[IDX(s, q, k, nx - 1)] = fo[q];
             }
         }
     }
@@ -768,11 +777,25 @@ static void stream_adjoint(const orc_sim *s, double *lam, const double *fn, doub
     if (s->p.bc_x == ORC_INLET_OUTLET) {
         const double ux = s->p.u_in_x, uy = s->p.u_in_y, usq = ux * ux + uy * uy;
         for (int k = 0; k < ny; ++k) {
-            /* outlet: f(nx-1) = f(nx-2) */
+            /* outlet: f(nx-1) = f^eq(1, u) with u = j / rho of f(nx-2); d f^eq_q / d u =
+             * w_q (3 c_q + 9 (c_q . u) c_q - 3 u) and d u / d f_p(nx-2) = (c_p - u) / rho */
+            double ro = 0.0, jox = 0.0, joy = 0.0;
             for (int q = 0; q < 9; ++q) {
-                lam[IDX(s, q, k, nx - 2)] += lam[IDX(s, q, k, nx - 1)];
+                const double g = fn[IDX(s, q, k, nx - 2)];
+                ro += g;
+                jox += CX[q] * g;
+                joy += CY[q] * g;
+            }
+            const double uox = jox / ro, uoy = joy / ro;
+            double gx = 0.0, gy = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                const double cu = CX[q] * uox + CY[q] * uoy, l = lam[IDX(s, q, k, nx - 1)];
+                gx += l * W[q] * (3.0 * CX[q] + 9.0 * cu * CX[q] - 3.0 * uox);
+                gy += l * W[q] * (3.0 * CY[q] + 9.0 * cu * CY[q] - 3.0 * uoy);
                 lam[IDX(s, q, k, nx - 1)] = 0.0;
             }
+            for (int q = 0; q < 9; ++q)
+                lam[IDX(s, q, k, nx - 2)] += (gx * (CX[q] - uox) + gy * (CY[q] - uoy)) / ro;
             /* inlet: f(0) = f^eq(rho1, u_in), rho1 = sum_q f(1) */
             double rho1 = 0.0;
             for (int q = 0; q < 9; ++q) rho1 += fn[IDX(s, q, k, 1)];

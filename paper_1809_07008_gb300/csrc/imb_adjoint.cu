@@ -12,7 +12,7 @@
 //     (plus the drag's own dependence on f),
 //   * adds d J / d tau and d J / d E of the cell.
 // The inlet rows of the transposed pull (f(0) = f^eq(rho of column 1, u_in), f(nx-1) =
-// f(nx-2)) run as a separate small kernel, which also adds d J / d u_in.  d E / d (disk
+// f^eq(1, u of column nx-2)) run as a separate small kernel, which also adds d J / d u_in.  d E / d (disk
 // centre) is the difference of the chord lengths on opposite cell edges.
 #include "imb_device.cuh"
 #include "imb_kernels.h"
@@ -55,40 +55,50 @@ __global__ void k_adjoint_inlet(float *__restrict__ lam, const float *__restrict
     const bool on = q < 9;
     const size_t row = (size_t)y * a.pitch;
     float *l = lam + (size_t)(on ? q : 0) * a.plane + row;
-    // outlet: f(nx-1) = f(nx-2)
-    if (on) {
-        l[a.nx - 2] += l[a.nx - 1];
-        l[a.nx - 1] = 0.0f;
-    }
-    // inlet: f(0) = f^eq(rho1, u_in), rho1 = 1 + the pulled shifted populations of column 1
-    float dq = 0.0f;
-    if (on) {
+    // population q of f(t+1) at column col (an interior column), pulled from S1
+    auto pulled = [&](int col) -> float {
+        if (!on) return 0.0f;
         int ys = y - cy_of(q);
         size_t src;
         if (ys < 0 || ys >= a.ny) {
             if (a.bc_y == BC_PERIODIC) {
                 ys = ys < 0 ? ys + a.ny : ys - a.ny;
-                src = (size_t)q * a.plane + (size_t)ys * a.pitch + (1 - cx_of(q));
+                src = (size_t)q * a.plane + (size_t)ys * a.pitch + (col - cx_of(q));
             } else {
-                src = (size_t)opp_of(q) * a.plane + row + 1;   // halfway bounce-back
+                src = (size_t)opp_of(q) * a.plane + row + col;   // halfway bounce-back
             }
         } else {
-            src = (size_t)q * a.plane + (size_t)ys * a.pitch + (1 - cx_of(q));
+            src = (size_t)q * a.plane + (size_t)ys * a.pitch + (col - cx_of(q));
         }
-        dq = S1[src];
-    }
-    const float ux = a.u_in_x, uy = a.u_in_y, usq = ux * ux + uy * uy;
-    const float cxq = on ? (float)cx_of(q) : 0.0f, cyq = on ? (float)cy_of(q) : 0.0f;
-    const float wq = on ? w_of(q) : 0.0f, cu = cxq * ux + cyq * uy;
-    const float l0 = on ? l[0] : 0.0f;
-    float lr = l0 * wq * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
-    float gq = l0 * wq * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux);
+        return S1[src];
+    };
+    auto wsum = [](float v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        dq += __shfl_xor_sync(0xffffffffu, dq, o);
-        lr += __shfl_xor_sync(0xffffffffu, lr, o);
-        gq += __shfl_xor_sync(0xffffffffu, gq, o);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    const float cxq = on ? (float)cx_of(q) : 0.0f, cyq = on ? (float)cy_of(q) : 0.0f;
+    const float wq = on ? w_of(q) : 0.0f;
+    // outlet: f(nx-1) = f^eq(1, u), u = j / rho of f(nx-2); d f^eq_q / d u = w_q (3 c_q +
+    // 9 (c_q . u) c_q - 3 u), d u / d f_p(nx-2) = (c_p - u) / rho
+    {
+        const float dq = pulled(a.nx - 2);
+        const float rho = 1.0f + wsum(dq), ux = wsum(cxq * dq) / rho, uy = wsum(cyq * dq) / rho;
+        const float lo = on ? l[a.nx - 1] : 0.0f, cu = cxq * ux + cyq * uy;
+        const float gx = wsum(lo * wq * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux));
+        const float gy = wsum(lo * wq * (3.0f * cyq + 9.0f * cu * cyq - 3.0f * uy));
+        if (on) {
+            l[a.nx - 1] = 0.0f;
+            l[a.nx - 2] += (gx * (cxq - ux) + gy * (cyq - uy)) / rho;
+        }
     }
+    // inlet: f(0) = f^eq(rho1, u_in), rho1 = 1 + the pulled shifted populations of column 1
+    const float dq = wsum(pulled(1));
+    const float ux = a.u_in_x, uy = a.u_in_y, usq = ux * ux + uy * uy;
+    const float cu = cxq * ux + cyq * uy;
+    const float l0 = on ? l[0] : 0.0f;
+    const float lr = wsum(l0 * wq * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+    const float gq = wsum(l0 * wq * (3.0f * cxq + 9.0f * cu * cxq - 3.0f * ux));
     if (on) {
         l[0] = 0.0f;
         l[1] += lr;

@@ -1,6 +1,6 @@
 // imb_pull.cuh -- the pull half of the stream step (Eq. 1 LHS) with the boundary rules:
 // periodic wrap, halfway bounce-back walls (those at y = 0 and y = ny may move along x),
-// velocity inlet / zero-gradient outlet.  Shared by the stream-collide kernel and its adjoint.
+// velocity inlet / pressure outlet with zero velocity gradient.  Shared by the stream-collide kernel and its adjoint.
 #pragma once
 #include "imb_device.cuh"
 #include "imb_kernels.h"
@@ -55,13 +55,19 @@ template <typename S>
 __device__ __forceinline__ void pull_cell(const S *__restrict__ fin, const LatticeArgs &a, int x,
                                           int y, float (&d)[9]) {
     if (a.bc_x == BC_INLET_OUTLET && (x == 0 || x == a.nx - 1)) {
-        // inlet: f^eq(rho of column 1, u_in); outlet: copy of column nx-2 (zero gradient)
+        // inlet: f^eq(rho of column 1, u_in); outlet: f^eq(1, u of column nx-2), the reference
+        // pressure with zero velocity gradient
         pull_generic(fin, a, x == 0 ? 1 : a.nx - 2, y, d);
-        if (x == 0) {
-            float drho = 0.0f;
+        float drho = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) drho += d[q];
+        for (int q = 0; q < 9; ++q) drho += d[q];
+        if (x == 0) {
             equilibrium_shifted(drho, 1.0f + drho, a.u_in_x, a.u_in_y, d);
+        } else {
+            const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+            const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+            const float inv = 1.0f / (1.0f + drho);
+            equilibrium_shifted(0.0f, 1.0f, jx * inv, jy * inv, d);
         }
         return;
     }
