@@ -47,6 +47,7 @@ struct imb_ctx {
     int *loud = nullptr, *iloud = nullptr;
     double *exc = nullptr;
     int *pbin = nullptr;
+    int *pslot = nullptr;      // [np][9] each particle's slot in the candidate lists of its 3 x 3 tiles
     PRec *prec = nullptr;
     // bins
     int nbx = 0, nby = 0, nbins = 0;
@@ -57,6 +58,7 @@ struct imb_ctx {
     unsigned *tile_ctr = nullptr;
     unsigned *h_err = nullptr;   // pinned host copy of the error word
     TileCand *tiles = nullptr;      // per 32 x 32 tile: particles that can reach it
+    double *tile_force = nullptr;   // per tile and candidate: partial force and torque sums
     float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
     size_t eps_tab_cap = 0;
     int tab_w = 0, tab_h = 0;
@@ -156,6 +158,8 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.T = c->T;
     a.err = c->err;
     a.tile_ctr = c->tile_ctr;
+    a.pbin = c->pbin;
+    a.pslot = c->pslot;
     return a;
 }
 
@@ -232,7 +236,7 @@ static void free_particles(imb_ctx *c) {
                      &c->nbr_cn[0], &c->nbr_cn[1], &c->exc};
     for (double **q : dp) { dfree(*q); *q = nullptr; }
     int **ip[] = {&c->nbr_cnt[0], &c->nbr_cnt[1], &c->nbr_id[0], &c->nbr_id[1], &c->free_ids,
-                  &c->coupled_ids, &c->pbin, &c->bin_ids, &c->parent, &c->label, &c->isz, &c->ifill,
+                  &c->coupled_ids, &c->pbin, &c->pslot, &c->bin_ids, &c->parent, &c->label, &c->isz, &c->ifill,
                   &c->istart, &c->members, &c->roots, &c->big_ids, &c->loud, &c->iloud};
     for (int **q : ip) { dfree(*q); *q = nullptr; }
     dfree(c->prec);
@@ -257,6 +261,7 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->tile_ctr);
     if (c->h_err) cudaFreeHost(c->h_err);
     dfree(c->tiles);
+    dfree(c->tile_force);
     dfree(c->eps_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->side) cudaStreamSynchronize(c->side);
@@ -366,6 +371,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
         (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess ||
+        (e = dalloc(&c->tile_force, (size_t)c->nbins * TILE_CAND * 3)) != cudaSuccess ||
         (e = cudaMallocHost((void **)&c->h_err, sizeof(unsigned))) != cudaSuccess ||
         (e = dalloc(&c->bin_bsum, c->nbins / 1024 + 1)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
@@ -412,6 +418,7 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
     CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->bin_bsum, c->counters, c->stream),
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
+    CK(cudaMemsetAsync(c->pslot, 0xff, 9 * sizeof(int) * (size_t)c->np, c->stream), "clear tile slots");
     CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
     c->launches += 6;   // table, scan (two passes), fill, tile lists, solid-ratio map
@@ -457,6 +464,7 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
         if (e == cudaSuccess) e = dalloc(&c->free_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->coupled_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->pbin, N);
+        if (e == cudaSuccess) e = dalloc(&c->pslot, 9 * N);
         if (e == cudaSuccess) e = dalloc(&c->bin_ids, N);
         if (e == cudaSuccess) e = dalloc(&c->prec, N);
         const size_t Np = (N + 31) / 32 * 32;
@@ -560,9 +568,13 @@ static int lattice_step(imb_ctx *c) {
         CK(cudaEventRecord(e0, c->stream), "event record");
     }
     CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur][0],
-                             &c->tmap[c->cur][1], c->tiles, c->stream),
+                             &c->tmap[c->cur][1], c->tiles, c->tile_force, c->stream),
        "stream-collide");
     c->launches++;
+    if (c->np > 0) {
+        CK(launch_force_gather(a, c->tile_force, c->stream), "force gather");
+        c->launches++;
+    }
     if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");
     c->cur ^= 1;
     return IMB_OK;

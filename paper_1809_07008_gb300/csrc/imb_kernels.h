@@ -33,6 +33,9 @@ struct LatticeArgs {
     double *T;                 // [np]   hydrodynamic torque accumulators
     unsigned *err;
     unsigned *tile_ctr;        // [2] tiles handed out and blocks finished (zero between launches)
+    const int *pbin;           // [np] bin of each particle
+    int *pslot;                // [np][9] tile * TILE_CAND + slot of the particle in the candidate lists of the
+                               // 3 x 3 tiles around its bin (row by row), -1 where it is not a candidate
 };
 
 // DEM state and parameters (FP64).
@@ -70,9 +73,12 @@ struct DemArgs {
 // lattice kernels (imb_lbm.cu)
 cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, float rho0, float ux0,
                                     float uy0, cudaStream_t s);
+// tile_force: [ntiles][TILE_CAND][3] FP64 partial force / torque sums of each tile's candidates
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
-                                  const TileCand *tiles, cudaStream_t s);
+                                  const TileCand *tiles, double *tile_force, cudaStream_t s);
+// a.F, a.T of every particle = its tiles' partial sums, in a fixed order
+cudaError_t launch_force_gather(const LatticeArgs &a, const double *tile_force, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
 cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s);
 int tma_box_width(int storage, int wide);

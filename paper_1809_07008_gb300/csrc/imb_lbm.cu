@@ -192,15 +192,15 @@ __device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const f
     return __ldg(tab + (dk + th) * tw + (di + th));
 }
 
-// Immersed moving boundary at one node (Sec. 2.3), all within the lane.  Bit s of
-// `cm` is set when tile candidate s reaches into the node; e0 is the solid ratio of its
-// first candidate s0 (fetched by the caller ahead of the node's moments).  Total solid
-// ratio -> B (Eq. 14) -> per-particle weights B_p = B eps_p / sum eps -> solid-velocity
-// moments; the per-particle force and torque (Eqs. 15-16) of the first PSLOTS
-// candidates go to the lane's own column of the warp's partials part[s][c][lane] (no
-// other thread touches it), those of later candidates straight to the particle.
-constexpr int PSLOTS = 4;
-
+// Immersed moving boundary on one row of a warp (Sec. 2.3).  Bit s of `cm` is set when
+// tile candidate s reaches into the lane's node, `rowc` is the union of cm over the warp
+// (non-zero: the caller tests it), e0 the solid ratio of the lane's first candidate
+// (fetched by the caller ahead of the row).  Total solid ratio -> B (Eq. 14) -> per-particle
+// weights B_p = B eps_p / sum eps -> solid-velocity moments.  The per-particle force and
+// torque terms of the node (Eqs. 15-16) go to the lane's register sums fa / fb when the
+// candidate is ka / kb (the first two candidates of the warp's rows in the unit); those of
+// any further candidate are summed over the warp's lanes at once (fixed shuffle tree) and
+// added to the warp's column of the tile's partials acc_w[(3 s + c) * WARPS].
 __device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
                                                int s, int xl, int yy, const LatticeArgs &a) {
     const PRec &P = cand[s];
@@ -208,60 +208,121 @@ __device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, co
                     a.eps_mode == EPS_EXACT);
 }
 
-__device__ __forceinline__ void node_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
-                                         const int s0, const float e0, const PRec *__restrict__ cand,
-                                         const int *__restrict__ cid, float *__restrict__ part,
-                                         const LatticeArgs &a, SolidMoments &sm) {
-    const int lane = threadIdx.x & 31;
+// force and torque terms of one node and particle (Eq. 15 per cell: -Bp sum_i Omega^s_i c_i =
+// Bp (rho u - rho u_s - F); Eq. 16, z component), with the particle's solid-velocity moments
+template <bool FORCED>
+__device__ __forceinline__ void node_particle(const NodeState &c, const PRec &P, const int di, const int dk,
+                                              const float Bp, const LatticeArgs &a, SolidMoments &sm,
+                                              float &vx, float &vy, float &vt) {
+    const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
+    const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
+    const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
+    sm.m1x += Bp * usx;
+    sm.m1y += Bp * usy;
+    sm.m2xx += Bp * usx * usx;
+    sm.m2xy += Bp * usx * usy;
+    sm.m2yy += Bp * usy * usy;
+    vx = Bp * (c.jx - c.rho * usx - (FORCED ? a.Fx : 0.0f));
+    vy = Bp * (c.jy - c.rho * usy - (FORCED ? a.Fy : 0.0f));
+    vt = rx * vy - ry * vx;
+}
+
+// add one row's force terms of candidate s: to the lane's register sums when s is ka or kb,
+// else summed over the warp's lanes at once (fixed shuffle tree) into the warp's column of
+// the tile's partials
+__device__ __forceinline__ void add_terms(const int s, float vx, float vy, float vt, const int ka, const int kb,
+                                          float (&fa)[3], float (&fb)[3], float *__restrict__ acc_w) {
+    if (s == ka) {
+        fa[0] += vx;
+        fa[1] += vy;
+        fa[2] += vt;
+    } else if (s == kb) {
+        fb[0] += vx;
+        fb[1] += vy;
+        fb[2] += vt;
+    } else {   // a third candidate in the warp's rows of the unit
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the same sums
+            vx += __shfl_xor_sync(FULL, vx, o);
+            vy += __shfl_xor_sync(FULL, vy, o);
+            vt += __shfl_xor_sync(FULL, vt, o);
+        }
+        const int lane = threadIdx.x & 31;
+        if (lane < 3) acc_w[(3 * s + lane) * WARPS] += lane == 0 ? vx : (lane == 1 ? vy : vt);
+    }
+}
+
+template <bool FORCED>
+__device__ __forceinline__ void row_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
+                                        const unsigned rowc, const float e0, const PRec *__restrict__ cand,
+                                        const int *__restrict__ cid, const int ka, const int kb,
+                                        float (&fa)[3], float (&fb)[3], float *__restrict__ acc_w,
+                                        const LatticeArgs &a, SolidMoments &sm) {
     sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
+    const float tm = c.te - 0.5f;
+    if (!(rowc & (rowc - 1u))) {
+        // one candidate s in the row: a lane's node is covered by s alone or not at all (e0 = 0,
+        // hence B = B_p = 0 and no terms)
+        const int s = __ffs(rowc) - 1;
+        const float eps = fminf(e0, 1.0f);
+        sm.B = e0 > 0.0f ? __fdividef(eps * tm, (1.0f - eps) + tm) : 0.0f;   // Eq. 14
+        const float Bp = e0 > 0.0f ? __fdividef(sm.B, e0) * e0 : 0.0f;
+        const PRec &P = cand[s];
+        float vx, vy, vt;
+        node_particle<FORCED>(c, P, xl - P.ci, yy - P.cj, Bp, a, sm, vx, vy, vt);
+        add_terms(s, vx, vy, vt, ka, kb, fa, fb, acc_w);
+        return;
+    }
     if (__popc(cm) > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
+    const int s0 = cm ? __ffs(cm) - 1 : 0;
     float esum = e0;   // summed in slot order
     for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += cand_slot_eps(cand, cid, __ffs(m) - 1, xl, yy, a);
     if (esum > 0.0f) {
         const float eps = fminf(esum, 1.0f);
-        const float tm = c.te - 0.5f;
         sm.B = __fdividef(eps * tm, (1.0f - eps) + tm);       // Eq. 14
     }
-    if (!(sm.B > 0.0f)) return;
-    const float Bs = __fdividef(sm.B, esum);
-    for (unsigned m = cm; m; m &= m - 1u) {
+    const float Bs = sm.B > 0.0f ? __fdividef(sm.B, esum) : 0.0f;
+    for (unsigned m = rowc; m; m &= m - 1u) {   // warp-uniform: the row's candidates, ascending
         const int s = __ffs(m) - 1;
-        const PRec &P = cand[s];
-        const int di = xl - P.ci, dk = yy - P.cj;
-        const float Bp = Bs * (s == s0 ? e0 : cand_slot_eps(cand, cid, s, xl, yy, a));
-        const float rx = __fsub_rn((float)di, P.fx) + 0.5f;   // node minus centre
-        const float ry = __fsub_rn((float)dk, P.fy) + 0.5f;
-        const float usx = P.vx - P.w * ry, usy = P.vy + P.w * rx; // u_s = v + w z x r
-        sm.m1x += Bp * usx;
-        sm.m1y += Bp * usy;
-        sm.m2xx += Bp * usx * usx;
-        sm.m2xy += Bp * usx * usy;
-        sm.m2yy += Bp * usy * usy;
-        if (Bp > 0.0f) {
-            // Eq. 15 per cell: -Bp sum_i Omega^s_i c_i = Bp (rho u - rho u_s - F); Eq. 16 (z)
-            const float vx = Bp * (c.jx - c.rho * usx - a.Fx);
-            const float vy = Bp * (c.jy - c.rho * usy - a.Fy);
-            const float vt = rx * vy - ry * vx;
-            if (s < PSLOTS) {
-                float *pp = part + s * 96 + lane;
-                pp[0] += vx;
-                pp[32] += vy;
-                pp[64] += vt;
-            } else {   // a crowded tile: later candidates add straight to the particle
-                atomicAdd(&a.F[2 * cid[s]], (double)vx);
-                atomicAdd(&a.F[2 * cid[s] + 1], (double)vy);
-                atomicAdd(&a.T[cid[s]], (double)vt);
-            }
+        float vx = 0.0f, vy = 0.0f, vt = 0.0f;
+        if (((cm >> s) & 1u) && Bs > 0.0f) {
+            const PRec &P = cand[s];
+            const float Bp = Bs * (s == s0 ? e0 : cand_slot_eps(cand, cid, s, xl, yy, a));
+            node_particle<FORCED>(c, P, xl - P.ci, yy - P.cj, Bp, a, sm, vx, vy, vt);
         }
+        add_terms(s, vx, vy, vt, ka, kb, fa, fb, acc_w);
     }
+}
+
+// Sum of six per-lane values over the warp with 9 shuffles (each level halves the values a
+// lane carries): afterwards lane l holds the warp sum of value 4 b4 + 2 b3 + b2 (bits of l).
+__device__ __forceinline__ float warp_sum6(const float (&fa)[3], const float (&fb)[3]) {
+    const int lane = threadIdx.x & 31;
+    float v[8] = {fa[0], fa[1], fa[2], fb[0], fb[1], fb[2], 0.0f, 0.0f};
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float w4[4], w2[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float keep = h4 ? v[j + 4] : v[j], send = h4 ? v[j] : v[j + 4];
+        w4[j] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float keep = h3 ? w4[j + 2] : w4[j], send = h3 ? w4[j] : w4[j + 2];
+        w2[j] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    float r = (h2 ? w2[1] : w2[0]) + __shfl_xor_sync(FULL, h2 ? w2[0] : w2[1], 4);
+    r += __shfl_xor_sync(FULL, r, 2);
+    r += __shfl_xor_sync(FULL, r, 1);
+    return r;
 }
 
 // Row mask: bit s set when candidate s can cover a cell of tile row yy (dy_near^2 <
 // r^2, the same rounding as covers(), hence a necessary condition).  Lane-parallel.
-__device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int nc, int yy, bool row_ok) {
+__device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int nc, int yy) {
     const int lane = threadIdx.x & 31;
     bool rel = false;
-    if (lane < nc && row_ok) {
+    if (lane < nc) {
         const PRec &P = cand[lane];
         const float loy = __fsub_rn((float)(yy - P.cj), P.fy);
         const float hiy = __fadd_rn(loy, 1.0f);
@@ -271,18 +332,17 @@ __device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int 
     return __ballot_sync(FULL, rel);
 }
 
-// Work unit of the persistent kernel: HROWS rows of a 32 x 32 tile; NST units are in
-// flight per block, so that NST - 1 of them are loading while one is computed.  TMA
-// boxes: the x start must be 16-byte aligned, so the six planes pulled from x - 1 or
-// x + 1 (c_x = +-1) take a box HALO cells wider than the tile (starting HALO cells left
-// of the tile for c_x = +1), the three with c_x = 0 exactly the tile width.
+// Work unit of the persistent kernel: HROWS rows of a 32 x 32 tile; NST units are staged
+// per block, so that while the warps work on one, the others are loading.  TMA boxes: the
+// x start must be 16-byte aligned, so the six planes pulled from x - 1 or x + 1 (c_x = +-1)
+// take a box HALO cells wider than the tile (starting HALO cells left of the tile for
+// c_x = +1), the three with c_x = 0 exactly the tile width.
 template <typename S> struct Box {
     static constexpr int HROWS = sizeof(S) == 4 ? 16 : 32;  // rows per work unit
     static constexpr int UPT = TILE / HROWS;                 // work units per tile
     static constexpr int RPW = HROWS / WARPS;                // rows per warp per unit
-    static constexpr int QCAP = HROWS * 32;                  // immersed-node queue of a unit
     static constexpr int HALO = 16 / (int)sizeof(S);
-    static constexpr int NST = 2;                            // units in flight per block
+    static constexpr int NST = sizeof(S) == 4 ? 3 : 2;       // stages per block
     static constexpr int BLOCKS_PER_SM = 3;
     static constexpr int WN = TILE, WW = TILE + HALO;
     __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
@@ -297,10 +357,12 @@ template <typename S> struct Box {
     }
     static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
-    static constexpr int PART_FLOATS = WARPS * PSLOTS * 3 * 32;
-    // force partials (per warp, candidate, component and lane), queue (cover masks, node
-    // offsets), two queue counters, the tile of each stage (index, column, row, spare)
-    static constexpr int EXTRA_BYTES = PART_FLOATS * 4 + QCAP * 4 + QCAP * 2 + 16 + NST * 16;
+    // force partials of the block's last NACC tiles: [tile slot][candidate][component][warp]
+    static constexpr int NACC = 3;
+    static constexpr int ACC_FLOATS = NACC * TILE_CAND * 3 * WARPS;
+    // partials, the tile of each stage (index, column, row, unit), warps done per stage,
+    // the producer's state (units issued, tile of the unit group, next tile, end reached)
+    static constexpr int EXTRA_BYTES = ACC_FLOATS * 4 + NST * 16 + (NST + 4 + 3) / 4 * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
 static_assert((Box<float>::WN * Box<float>::HROWS * 4) % 128 == 0 &&
@@ -318,39 +380,41 @@ __device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
     return bx >= 1 && by >= 1 && (bx + 1) * TILE <= nx - 1 && (by + 1) * TILE <= ny - 1;
 }
 
-// Persistent fused stream-collide.  Tiles are handed out dynamically (a counter in
-// global memory), so that blocks finish together whatever their mix of interior and
-// boundary tiles.  Thread 0 keeps NST tiles in flight: for interior tiles nine TMA boxes
-// (one per population plane, rows shifted by -c_y) plus the tile's candidate block;
-// boundary tiles take the candidate block only and pull their populations with the
-// boundary rules.  Pass A collides the fluid nodes and queues, block-wide, the nodes a
-// disk reaches into with their candidate mask; pass B spreads the queue over the warps.
-// A stage is handed back, and the forces of its tile flushed, once every warp has
-// passed the top of the next tile.
-template <typename S>
+// Persistent fused stream-collide.  Tiles are handed out dynamically (a counter in global
+// memory), so that blocks finish together whatever their mix of interior and boundary
+// tiles.  NST units are staged per block: for interior tiles nine TMA boxes (one per
+// population plane, rows shifted by -c_y) plus the tile's candidate block; boundary tiles
+// take the candidate block only and pull their populations with the boundary rules.  Each
+// warp takes its rows of a unit, collides every node and, where a disk reaches into the
+// row, the immersed nodes of the row with it.  There is no block-wide barrier: the last
+// warp to finish with a stage sums the unit's force partials over the warps (FP64, fixed
+// order) into the tile's partial sums, hands the stage back to the copy engine and starts
+// the next unit's copies, so warps run up to NST - 1 units apart.
+template <typename S, bool FORCED>
 __global__ void __launch_bounds__(BLOCK, Box<S>::BLOCKS_PER_SM)
 k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_constant__ CUtensorMap tmap_w,
                  const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
-                 const TileCand *__restrict__ tiles, const int ntiles) {
+                 const TileCand *__restrict__ tiles, const int ntiles, double *__restrict__ tile_force) {
     using G = Box<S>;
-    constexpr int NST = G::NST, HROWS = G::HROWS, UPT = G::UPT, RPW = G::RPW, QCAP = G::QCAP;
+    constexpr int NST = G::NST, HROWS = G::HROWS, UPT = G::UPT, RPW = G::RPW;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
-    float *part = reinterpret_cast<float *>(extra);
-    unsigned *q_cm = reinterpret_cast<unsigned *>(extra + G::PART_FLOATS * 4);
-    unsigned short *q_node = reinterpret_cast<unsigned short *>(q_cm + QCAP);
-    int *q_count = reinterpret_cast<int *>(q_node + QCAP);
-    int4 *stage_tile = reinterpret_cast<int4 *>(q_count + 4);
+    float *acc = reinterpret_cast<float *>(extra);
+    int4 *stage_tile = reinterpret_cast<int4 *>(extra + G::ACC_FLOATS * 4);
+    int *done = reinterpret_cast<int *>(stage_tile + NST);
+    int *prod = done + NST;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(extra + G::EXTRA_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
     const bool smag = a.smag_coef > 0.0f;
 
-    for (int i = threadIdx.x; i < G::PART_FLOATS; i += BLOCK) part[i] = 0.0f;
-    if (threadIdx.x < 2) q_count[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < G::ACC_FLOATS; i += BLOCK) acc[i] = 0.0f;
+    if (threadIdx.x < NST) done[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
+        prod[0] = 0;
+        prod[3] = 0;
+        prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // tiles are taken one ahead
     }
     __syncthreads();
 
@@ -358,22 +422,17 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     auto stage_cand = [&](int st) {
         return reinterpret_cast<TileCand *>(smem + st * G::STAGE_BYTES + G::POP_BYTES);
     };
-    // producer (thread 0): takes the next tile and starts its copies into the next stage;
-    // after the first tile past the end it hands out nothing more
-    int pk = 0, cur_t = 0;
-    bool pdone = false;
-    int next_t = threadIdx.x == 0 ? (int)atomicAdd(&a.tile_ctr[0], 1u) : 0;   // taken one tile ahead
+    // Start the copies of the next unit into its stage (one thread; the units are issued in
+    // order, by whichever warp released the stage).  Past the last tile a stage gets the end
+    // marker, and nothing more is issued.
     auto issue_next = [&]() {
-        if (pdone) return;
-        const int st = pk % NST, h = pk % UPT;
-        ++pk;
-        if (h == 0) {
-            cur_t = next_t;
-            if (cur_t < ntiles) next_t = (int)atomicAdd(&a.tile_ctr[0], 1u);
-        }
-        const int t = cur_t;
+        if (prod[3]) return;
+        const int u = prod[0], st = u % NST, h = u % UPT;
+        prod[0] = u + 1;
+        if (h == 0) prod[1] = prod[2];
+        const int t = prod[1];
         if (t >= ntiles) {
-            pdone = true;
+            prod[3] = 1;
             stage_tile[st] = make_int4(-1, 0, 0, 0);
             mbar_arrive_expect_tx(&mbar[st], 0u);
             return;
@@ -390,156 +449,170 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
                             cx_of(q) == 1 ? x0 - G::HALO : x0, yb - cy_of(q), q, &mbar[st]);
         }
+        if (h == 0) prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // after the copies are on their way
     };
     if (threadIdx.x == 0)
         for (int k = 0; k < NST; ++k) issue_next();
+
     bool unstable = false;
-    int fid = -1;   // particle whose force component this thread flushes for the previous tile
     for (int k = 0;; ++k) {
         const int st = k % NST;
-        const int qc = k & 1;
-        const bool ok = mbar_wait(&mbar[st], (uint32_t)((k / NST) & 1));
-        const int4 ti = stage_tile[st];
-        const int bad = __syncthreads_or(!ok);
-        // every warp is past the previous tile: its stage goes back to the copy engine
-        // and its forces are flushed
-        if (k > 0) {
-            if (threadIdx.x == 0 && !bad) {
-                fence_proxy_async_smem();
-                issue_next();
-            }
-            if (fid >= 0) {   // thread 3 s + c sums component c of candidate s over the warps
-                float *pb = part + threadIdx.x * 32;
-                float acc = 0.0f;
-#pragma unroll
-                for (int w = 0; w < WARPS; ++w) {
-                    acc += pb[w * PSLOTS * 96];
-                    pb[w * PSLOTS * 96] = 0.0f;
-                }
-                if (acc != 0.0f) {
-                    const int c = threadIdx.x % 3;
-                    if (c < 2) atomicAdd(&a.F[2 * fid + c], (double)acc);
-                    else atomicAdd(&a.T[fid], (double)acc);
-                }
-            }
-        }
-        if (bad) {
-            if (threadIdx.x == 0) set_err(a.err, ERR_TMA);
+        if (!mbar_wait(&mbar[st], (uint32_t)((k / NST) & 1))) {
+            if (lane == 0) set_err(a.err, ERR_TMA);
             break;
         }
-        if (ti.x < 0) break;   // past the last tile (the same value in every thread)
-        const int h = ti.w;   // half of the tile, for units of 16 rows
+        const int4 ti = stage_tile[st];
+        if (ti.x < 0) break;   // past the last tile (the same value in every warp)
+        const int h = ti.w;
         const int x0 = ti.y * TILE, y0 = ti.z * TILE;
         const bool in = tma_tile(ti.y, ti.z, a.nx, a.ny);
         const TileCand *tc = stage_cand(st);
         const int nc = min(tc->n, TILE_CAND);
         const S *pop = stage_pop(st);
-        auto load_node = [&](int xl, int yy, float (&d)[9]) {
-            if (in) {
-                const int r = yy - h * HROWS;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) d[q] = Store<S>::lds(pop + G::offset(q) + r * G::width(q) + G::col(q, xl));
-            } else if (x0 + xl < a.nx) {
-                pull_cell(fin, a, x0 + xl, y0 + yy, d);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 9; ++q) d[q] = 0.0f;
-            }
-        };
-        // pass A: the warp's rows; fluid nodes collide and store here, nodes that a disk
-        // reaches into are queued with the mask of the candidates that reach them
+        float *acc_t = acc + ((k / UPT) % G::NACC) * (TILE_CAND * 3 * WARPS);
         const int x = x0 + lane;
         const bool xin = x < a.nx;
-#pragma unroll 2
+        // the candidates that reach into the nodes of the warp's rows, and the solid ratio of
+        // each node's first candidate (its table reads start here, ahead of the rows)
+        unsigned cmr[RPW], rowcr[RPW];
+        float e0r[RPW];
+        unsigned uni = 0u;
+#pragma unroll
+        for (int rr = 0; rr < RPW; ++rr) {
+            const int yy = h * HROWS + warp + WARPS * rr;
+            unsigned cm = 0u;
+            if (nc && y0 + yy < a.ny) {
+                for (unsigned m = row_mask(tc->p, nc, yy); m; m &= m - 1u) {
+                    const int s = __ffs(m) - 1;
+                    const PRec &P = tc->p[s];
+                    if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
+                        cm |= 1u << s;
+                }
+                if (!xin) cm = 0u;
+            }
+            cmr[rr] = cm;
+            e0r[rr] = cm ? cand_slot_eps(tc->p, tc->id, __ffs(cm) - 1, lane, yy, a) : 0.0f;
+            rowcr[rr] = __reduce_or_sync(FULL, cm);
+            uni |= rowcr[rr];
+        }
+        // register sums of the force terms of the first two candidates of these rows
+        const int ka = uni ? __ffs(uni) - 1 : -1;
+        const int kb = (uni & (uni - 1u)) ? __ffs(uni & (uni - 1u)) - 1 : -1;
+        float fa[3] = {0.0f, 0.0f, 0.0f}, fb[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
         for (int rr = 0; rr < RPW; ++rr) {
             const int yy = h * HROWS + warp + WARPS * rr;
             const int y = y0 + yy;
             if (y >= a.ny) continue;
-            float d[9];
-            load_node(lane, yy, d);
-            const unsigned mask = nc ? row_mask(tc->p, nc, yy, true) : 0u;
-            unsigned cm = 0u;
-            for (unsigned m = mask; m; m &= m - 1u) {
-                const int s = __ffs(m) - 1;
-                const PRec &P = tc->p[s];
-                if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
-                    cm |= 1u << s;
-            }
-            if (!xin) cm = 0u;
-            const unsigned ib = __ballot_sync(FULL, cm != 0u);
-            if (ib) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&q_count[qc], __popc(ib));
-                base = __shfl_sync(FULL, base, 0);
-                if (cm) {
-                    const int i = base + __popc(ib & ((1u << lane) - 1u));
-                    q_cm[i] = cm;
-                    q_node[i] = (unsigned short)((yy - h * HROWS) * 32 + lane);
+            unsigned cm = cmr[0], rowc = rowcr[0];
+            float e0 = e0r[0];
+#pragma unroll
+            for (int j = 1; j < RPW; ++j)
+                if (rr == j) {
+                    cm = cmr[j];
+                    rowc = rowcr[j];
+                    e0 = e0r[j];
                 }
-            }
-            if (ib != FULL) {
-                NodeState c;
-                node_state(d, a, forced, smag, c);
-                if (xin && !(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
-                if (xin && !cm) {
-                    const SolidMoments none = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                    node_collide_store(d, c, none, fout + (size_t)y * a.pitch + x, a, forced);
-                }
-            }
-        }
-        __syncthreads();   // the unit's queue is complete
-        const int nq = min(q_count[qc], QCAP);
-        if (threadIdx.x == 0) q_count[qc ^ 1] = 0;   // the next unit's counter, last read a unit ago
-        // pass B: the queued immersed-boundary nodes, 32 per warp at a time
-        float *part_w = part + warp * PSLOTS * 96;
-        unsigned used = 0u;   // candidates this lane's nodes gave force to
-#pragma unroll 1
-        for (int base = warp * 32; base < nq; base += WARPS * 32) {
-            const bool act = base + lane < nq;
-            const int i = act ? base + lane : base;
-            const unsigned cm = act ? q_cm[i] : 0u;
-            const int e = q_node[i];
-            const int yy = h * HROWS + (e >> 5), xl = e & 31;
-            // the first candidate's solid ratio is fetched before the moments so that the
-            // table read overlaps them
-            const int s0 = cm ? __ffs(cm) - 1 : 0;
-            const float e0 = cm ? cand_slot_eps(tc->p, tc->id, s0, xl, yy, a) : 0.0f;
-            used |= cm;
             float d[9];
-            load_node(xl, yy, d);
+            if (in) {
+                const int r = yy - h * HROWS;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) d[q] = Store<S>::lds(pop + G::offset(q) + r * G::width(q) + G::col(q, lane));
+            } else if (xin) {
+                pull_cell(fin, a, x, y, d);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) d[q] = 0.0f;
+            }
             NodeState c;
-            node_state(d, a, forced, smag, c);
-            SolidMoments sm;
-            node_imb(c, xl, yy, cm, s0, e0, tc->p, tc->id, part_w, a, sm);
-            if (act)
-                node_collide_store(d, c, sm, fout + (size_t)(y0 + yy) * a.pitch + (x0 + xl), a, forced);
-        }
-        // the warp's partials: sum over the lanes into lane 0's column
-        for (unsigned m = __reduce_or_sync(FULL, used) & ((1u << PSLOTS) - 1u); m; m &= m - 1u) {
-            float *pp = part_w + (__ffs(m) - 1) * 96 + lane;
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                float v = pp[32 * cc];
-                pp[32 * cc] = 0.0f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                if (lane == 0) pp[32 * cc] = v;
+            node_state(d, a, FORCED, smag, c);
+            if (xin && !(c.usq < 0.09f)) unstable = true;   // Mach guard, also catches NaN
+            if (!rowc) {
+                if (xin) {
+                    const SolidMoments none = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                    node_collide_store<S, false, FORCED>(d, c, none, fout + (size_t)y * a.pitch + x, a);
+                }
+            } else {
+                SolidMoments sm;
+                row_imb<FORCED>(c, lane, yy, cm, rowc, e0, tc->p, tc->id, ka, kb, fa, fb, acc_t + warp, a, sm);
+                if (xin) node_collide_store<S, true, FORCED>(d, c, sm, fout + (size_t)y * a.pitch + x, a);
             }
         }
-        // the threads that flush this tile's forces take their particle id now, while the
-        // stage still holds the tile's candidate block
-        fid = threadIdx.x < min(nc, PSLOTS) * 3 ? tc->id[threadIdx.x / 3] : -1;
+        if (uni) {   // the unit's sums of ka and kb into the warp's columns of the tile partials
+            const float v = warp_sum6(fa, fb);
+            const int j = lane >> 2;   // value j: candidate ka (j < 3) or kb, component j % 3
+            if ((lane & 3) == 0 && j < 6) {
+                const int s = j < 3 ? ka : kb;
+                if (s >= 0) acc_t[(3 * s + j % 3) * WARPS + warp] += v;
+            }
+        }
+        // hand the stage back: the last warp to finish with it starts the copies of the unit
+        // NST ahead into it and, after the last unit of a tile, sums the tile's partials over
+        // the warps (FP64, fixed order) into the tile's force sums
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&done[st], 1) == WARPS - 1;
+        }
+        if (__shfl_sync(FULL, last, 0)) {
+            __threadfence_block();
+            if (lane == 0) {
+                done[st] = 0;
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            if (h == UPT - 1) {
+                double *tf = tile_force + (size_t)ti.x * (TILE_CAND * 3);
+                for (int i = lane; i < nc * 3; i += 32) {
+                    float *pa = acc_t + i * WARPS;
+                    double v = 0.0;
+#pragma unroll
+                    for (int w = 0; w < WARPS; ++w) {
+                        v += (double)pa[w];
+                        pa[w] = 0.0f;
+                    }
+                    tf[i] = v;
+                }
+            }
+            __syncwarp();
+        }
     }
     if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
-    // the last block to finish leaves the tile counter at zero for the next launch
     __syncthreads();
     if (threadIdx.x == 0) {
+        // after a failed wait: let every copy that was started land before the block leaves
+        for (int u = max(0, prod[0] - NST); u < prod[0]; ++u) mbar_wait(&mbar[u % NST], (uint32_t)((u / NST) & 1));
+        // the last block to finish leaves the tile counter at zero for the next launch
         __threadfence();
         if (atomicAdd(&a.tile_ctr[1], 1u) == gridDim.x - 1) {
             atomicExch(&a.tile_ctr[0], 0u);
             atomicExch(&a.tile_ctr[1], 0u);
         }
     }
+}
+
+// Force and torque of each particle: the sum of its partial sums over the tiles whose
+// candidate lists hold it, in a fixed order (the 3 x 3 tiles around its bin, row by row), so
+// that the result does not depend on the order in which the tiles were worked.
+__global__ void __launch_bounds__(256) k_force_gather(const LatticeArgs a, const double *__restrict__ tile_force) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    int e[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) e[j] = a.pslot[9 * p + j];
+    double fx = 0.0, fy = 0.0, tz = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j)
+        if (e[j] >= 0) {
+            const double *tf = tile_force + (size_t)e[j] * 3;
+            fx += tf[0];
+            fy += tf[1];
+            tz += tf[2];
+        }
+    a.F[2 * p] = fx;
+    a.F[2 * p + 1] = fy;
+    a.T[p] = tz;
 }
 
 // Per-tile candidate lists: one warp per tile gathers the particles of the 3 x 3
@@ -560,8 +633,14 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
         const int xc = bx * TILE + TILE / 2, yc = by * TILE + TILE / 2;
         P.ci = TILE / 2 - wrap_rel(xc - P.ci, a.nx, a.bc_x == BC_PERIODIC);
         P.cj = TILE / 2 - wrap_rel(yc - P.cj, a.ny, a.bc_y == BC_PERIODIC);
-        out->id[lane] = sh[warp].id[lane];
+        const int pid = sh[warp].id[lane];
+        out->id[lane] = pid;
         out->p[lane] = P;
+        // the particle's entry for this tile: its place among the 3 x 3 tiles around its bin
+        const int b = a.pbin[pid], pbx = b % a.nbx, pby = b / a.nbx;
+        const int dx = wrap_rel(bx - pbx, a.nbx, a.bc_x == BC_PERIODIC);
+        const int dy = wrap_rel(by - pby, a.nby, a.bc_y == BC_PERIODIC);
+        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) a.pslot[9 * pid + 3 * (dy + 1) + dx + 1] = t * TILE_CAND + lane;
     }
 }
 
@@ -772,13 +851,14 @@ cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, 
     });
 }
 
-template <typename S>
+template <typename S, bool FORCED>
 static int stream_collide_grid(int ntiles) {
     static int per_sm = -1, sms = 0;
     if (per_sm < 0) {
-        cudaFuncSetAttribute(k_stream_collide<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_stream_collide<S, FORCED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Box<S>::SMEM_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<S>, BLOCK, Box<S>::SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<S, FORCED>, BLOCK,
+                                                      Box<S>::SMEM_BYTES);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -789,15 +869,27 @@ static int stream_collide_grid(int ntiles) {
 
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
-                                  const TileCand *tiles, cudaStream_t s) {
+                                  const TileCand *tiles, double *tile_force, cudaStream_t s) {
     const int ntiles = a.nbx * a.nby;
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        const int grid = stream_collide_grid<S>(ntiles);
-        k_stream_collide<S><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(*tmap_narrow, *tmap_wide, (const S *)fin,
-                                                                   (S *)fout, a, tiles, ntiles);
+        if (a.Fx != 0.0f || a.Fy != 0.0f) {
+            const int grid = stream_collide_grid<S, true>(ntiles);
+            k_stream_collide<S, true><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(
+                *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
+        } else {
+            const int grid = stream_collide_grid<S, false>(ntiles);
+            k_stream_collide<S, false><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(
+                *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
+        }
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_force_gather(const LatticeArgs &a, const double *tile_force, cudaStream_t s) {
+    if (a.np == 0) return cudaSuccess;
+    k_force_gather<<<(a.np + 255) / 256, 256, 0, s>>>(a, tile_force);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s) {

@@ -56,37 +56,54 @@ struct SolidMoments {
 };
 
 // Collision (Eq. 13) -- fluid part weighted 1 - B, solid part (Eq. 12 summed over the
-// covering particles) by B -- and store of the post-collision populations.
-template <typename S>
+// covering particles) by B -- and store of the post-collision populations.  IMB = false
+// compiles the fluid node alone (B = 0); FORCED adds the Guo forcing term.  The solid part
+// is written without branches (B = 0 leaves the fluid update unchanged) and takes each
+// direction together with its opposite, whose terms differ only in sign.
+template <typename S, bool IMB, bool FORCED>
 __device__ __forceinline__ void node_collide_store(const float (&d)[9], const NodeState &c,
                                                    const SolidMoments &sm, S *__restrict__ outp,
-                                                   const LatticeArgs &a, const bool forced) {
-    const float B = sm.B;
-    const float fl = 1.0f - B;
-    const float sf = 1.0f - 0.5f * c.omega;
-    // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u)), with
-    // sum_p B_p f^eq_q(u_s,p) - B f^eq_q(u) = rho w_q (3 c.A1 + 4.5 c.A2.c - 1.5 tr A2)
-    const float a1x = sm.m1x - B * c.ux, a1y = sm.m1y - B * c.uy;
-    const float a2xx = sm.m2xx - B * c.ux * c.ux, a2yy = sm.m2yy - B * c.uy * c.uy;
-    const float a2xy = sm.m2xy - B * c.ux * c.uy;
-    const float tra2 = a2xx + a2yy;
+                                                   const LatticeArgs &a) {
+    float upd[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-        float upd = -c.omega * c.n[q];
-        if (forced) {  // Guo forcing term
+    for (int q = 0; q < 9; ++q) upd[q] = -c.omega * c.n[q];
+    if (FORCED) {  // Guo forcing term
+        const float sf = 1.0f - 0.5f * c.omega;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
             const float cu = cdot(q, c.ux, c.uy);
             const float S_q = w_of(q) * (3.0f * ((cxq - c.ux) * a.Fx + (cyq - c.uy) * a.Fy) +
                                          9.0f * cu * cdot(q, a.Fx, a.Fy));
-            upd = fmaf(sf, S_q, upd);
+            upd[q] = fmaf(sf, S_q, upd[q]);
         }
-        upd *= fl;
-        if (B > 0.0f) {
-            const float ca1 = cdot(q, a1x, a1y);
-            const float ca2c = ccdot(q, a2xx, a2yy, a2xy);
-            upd += B * (c.n[opp_of(q)] - c.n[q]) + c.rho * w_of(q) * (3.0f * ca1 + 4.5f * ca2c - 1.5f * tra2);
+    }
+    if (IMB) {
+        const float B = sm.B;
+        const float fl = 1.0f - B;
+        // sum_p B_p Omega^s_p = B (n_{-q} - n_q) + sum_p B_p (f^eq_q(u_s,p) - f^eq_q(u)), with
+        // sum_p B_p f^eq_q(u_s,p) - B f^eq_q(u) = rho w_q (3 c.A1 + 4.5 c.A2.c - 1.5 tr A2)
+        const float a1x = sm.m1x - B * c.ux, a1y = sm.m1y - B * c.uy;
+        const float a2xx = sm.m2xx - B * c.ux * c.ux, a2yy = sm.m2yy - B * c.uy * c.uy;
+        const float a2xy = sm.m2xy - B * c.ux * c.uy;
+        const float tra2 = a2xx + a2yy;
+        upd[0] = fmaf(fl, upd[0], c.rho * w_of(0) * (-1.5f * tra2));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int q = k < 2 ? k + 1 : k + 3, o = opp_of(q);   // q = 1, 2, 5, 6
+            const float rw = c.rho * w_of(q);
+            const float t1 = 3.0f * cdot(q, a1x, a1y);
+            const float t2 = 4.5f * ccdot(q, a2xx, a2yy, a2xy) - 1.5f * tra2;
+            const float bd = B * (c.n[o] - c.n[q]);
+            upd[q] = fmaf(fl, upd[q], bd) + rw * (t2 + t1);
+            upd[o] = fmaf(fl, upd[o], -bd) + rw * (t2 - t1);
         }
-        Store<S>::st(outp + (size_t)q * a.plane, d[q] + upd);
+    }
+    S *p = outp;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        Store<S>::st(p, d[q] + upd[q]);
+        p += a.plane;
     }
 }
 
