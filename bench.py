@@ -66,6 +66,8 @@ def parse():
                     help="skip the batched-sweep line (256 periodic domains, FP16, 5000 steps)")
     ap.add_argument("--sweep-steps", type=int, default=5000)
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 lines")
+    ap.add_argument("--ergun", action="store_true",
+                    help="add the packed bed's friction factor against Ergun's (15 000 D3Q19 steps)")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the solid-fraction-0.40 suspension, collapse-box and channel lines")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -325,13 +327,14 @@ def packed_bed_friction(D, U, N, tau, area, length):
     return Re, f, _ergun_friction(Re)
 
 
-def time_lattice3(imb, torch, ts, steps=100):
+def time_lattice3(imb, torch, ts, steps=100, ergun=False):
     """The D3Q19 path: throughput on the 400 x 100 x 400 Poiseuille-flow-past-a-sphere box
     (N = 20 cells per diameter, 16 M cells) and on the paper's packed bed (Sec. 3.3, N = 20,
     240 x 100 x 100 cells, its Delta P = 1600 Pa run: tau = 0.501, C = 0.3, touching spheres
     sharing cells), in FP32 and FP16 storage; the steady drag and torque errors against
-    Eqs. 18-19 at N = 5 and 10 (n_sub = 5, tau = 1); and the packed bed's friction factor at
-    its lowest pressure difference (1 Pa, tau = 0.58) against Ergun's (Eqs. 21-23)."""
+    Eqs. 18-19 at N = 5, 10 and 20 (n_sub = 5, tau = 1: Table 2's rows); with ``ergun``, the
+    packed bed's friction factor at its lowest pressure difference (1 Pa, tau = 0.58) against
+    Ergun's (Eqs. 21-23)."""
     out = {}
     peak, kind = measured_hbm_peak()
     for w, kern in ((W.happel(20), "k3_stream_collide (one sphere per cell, BGK)"),
@@ -356,26 +359,27 @@ def time_lattice3(imb, torch, ts, steps=100):
     # a pressure-driven medium would need, and U the flow rate through the plane in the middle of
     # the free fluid.  The drag settles within tens of steps (the momentum balance), the flow in
     # the pores on the viscous time (d_p / 2)^2 / nu, about 3700 steps: 15 000 steps are four
-    N = 20
-    wb = W.packed_bed(N, run=0, C_smag=0.0)
-    g = imb.Lattice3.from_workload(wb)
-    n_steps = 15000
-    g.step(n_steps)
-    F, _ = g.forces()
-    D = float(F[:, 0].sum())
-    _, ux, _, _ = g.macro()
-    g.close()
-    U = float(ux[:, :, 0].mean())
-    Re, f, fe = packed_bed_friction(D, U, N, wb.tau, wb.ny * wb.nz, 10 * N)
-    out[f"{wb.name}_ergun"] = {"steps": n_steps, "Re_p": round(Re, 5), "f_star": round(f, 3),
-                               "f_star_ergun": round(fe, 3), "rel_diff": round(f / fe - 1.0, 4)}
-    for N in (5, 10):
+    if ergun:
+        N = 20
+        wb = W.packed_bed(N, run=0, C_smag=0.0)
+        g = imb.Lattice3.from_workload(wb)
+        n_steps = 15000
+        g.step(n_steps)
+        F, _ = g.forces()
+        D = float(F[:, 0].sum())
+        _, ux, _, _ = g.macro()
+        g.close()
+        U = float(ux[:, :, 0].mean())
+        Re, f, fe = packed_bed_friction(D, U, N, wb.tau, wb.ny * wb.nz, 10 * N)
+        out[f"{wb.name}_ergun"] = {"steps": n_steps, "Re_p": round(Re, 5), "f_star": round(f, 3),
+                                   "f_star_ergun": round(fe, 3), "rel_diff": round(f / fe - 1.0, 4)}
+    for N in (5, 10, 20):
         wh = W.happel(N)
         g = imb.Lattice3.from_workload(wh)
-        prev, n_steps = None, 0
+        prev, n_steps, chunk = None, 0, 500 if N < 20 else 1000
         for _ in range(60):
-            g.step(500)
-            n_steps += 500
+            g.step(chunk)
+            n_steps += chunk
             F, T = g.forces()
             if prev is not None and abs(F[0, 0] - prev) < 1e-5 * abs(F[0, 0]):
                 break
@@ -388,7 +392,8 @@ def time_lattice3(imb, torch, ts, steps=100):
         out[f"happel_N{N}_error_pct"] = {"force": round(abs(Fa - F[0, 0]) / Fa * 100, 3),
                                          "torque": round(abs(Ta - abs(T[0, 2])) / Ta * 100, 3),
                                          "steps": n_steps, "paper_table2": {5: [17.791, 31.4374],
-                                                                            10: [6.9793, 11.256]}[N]}
+                                                                            10: [6.9793, 11.256],
+                                                                            20: [3.7595, 4.426]}[N]}
     return out
 
 
@@ -397,11 +402,8 @@ def oracle_sample_workload():
     return W.c3sub(steps=0)
 
 
-def time_oracle(target_s=12.0, max_steps=2000):
-    """FP64 oracle (as it stands, one host thread) on the bounded sample; MLUPS."""
-    from oracle import oracle as O
-    O.build()
-    w = oracle_sample_workload()
+def _oracle_mlups(O, w, threads, target_s, max_steps):
+    prev = O.set_threads(threads)
     sim = O.Sim(w)
     sim.step(2)
     steps, t0 = 0, time.perf_counter()
@@ -409,10 +411,32 @@ def time_oracle(target_s=12.0, max_steps=2000):
         sim.step(5)
         steps += 5
     dt = time.perf_counter() - t0
-    mlups = w.cells * steps / dt / 1e6
-    return mlups, {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{w.name}, {steps} steps in {dt:.1f} s, FP64, single host thread",
-                   "cpu": f"{cpu_model()}, {os.cpu_count()} logical cores on the host"}
+    O.set_threads(prev)
+    return w.cells * steps / dt / 1e6, steps, dt
+
+
+def time_oracle(target_s=12.0, max_steps=2000):
+    """The FP64 oracle (as it stands: its collide and stream loops spread over the host's
+    cores, the rest on one thread; results identical whatever the thread count) on bounded
+    samples: the 512 x 512 subdomain of the suspension at the same disk density on all cores
+    (the line's value) and on one core, and the one-disk 200 x 100 channel on one core and on
+    all cores; MLUPS."""
+    from oracle import oracle as O
+    O.build()
+    ncores = os.cpu_count() or 1
+    w = oracle_sample_workload()
+    mlups, steps, dt = _oracle_mlups(O, w, ncores, target_s, max_steps)
+    m1, s1, d1 = _oracle_mlups(O, w, 1, 0.5 * target_s, max_steps)
+    wc = W.c1(steps=0)
+    c1a, _, _ = _oracle_mlups(O, wc, ncores, 0.25 * target_s, 2000)
+    c11, _, _ = _oracle_mlups(O, wc, 1, 0.25 * target_s, 2000)
+    return mlups, {"value": round(mlups, 3), "unit": "MLUPS", "cores": ncores, "kind": "oracle",
+                   "sample": f"{w.name}, {steps} steps in {dt:.1f} s, FP64, {ncores} host threads",
+                   "single_thread": {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
+                                     "sample": f"{w.name}, {s1} steps in {d1:.1f} s"},
+                   "config1_channel": {"workload": wc.name, "all_cores_mlups": round(c1a, 3),
+                                       "single_thread_mlups": round(c11, 3)},
+                   "cpu": f"{cpu_model()}, {ncores} logical cores on the host"}
 
 
 def time_workload(imb, torch, ts, w, storage, steps, warmup):
@@ -575,7 +599,7 @@ def run_gpu(args):
 
     lattice3 = None
     if not args.no_3d and rank == 0:
-        lattice3 = time_lattice3(imb, torch, ts)
+        lattice3 = time_lattice3(imb, torch, ts, ergun=args.ergun)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -126,7 +126,9 @@ int imb_step(imb_ctx *ctx, int n);
  * cycle and the particle state x_out[2n], v_out[2n], omega_out[n] are read back (each
  * output may be NULL).  Everything is queued on the context stream and the call waits
  * once; for pinned host arrays the copies are asynchronous.  Errors as imb_step and
- * imb_set_kinematics. */
+ * imb_set_kinematics.  After IMB_E_TIMEOUT the copies into the output arrays may still be
+ * queued: the caller must keep those arrays alive and unused until imb_sync returns
+ * IMB_OK or the context is destroyed. */
 int imb_step_io(imb_ctx *ctx, int n, const double *x_in, const double *v_in, const double *omega_in,
                 double *F_out, double *T_out, double *x_out, double *v_out, double *omega_out);
 
@@ -292,13 +294,16 @@ double imb_bytes_per_cell(imb_ctx *ctx);
  * d_bin_start: DEVICE pointer to nbins + 1 ints, nbins = ceil(nx/32) * ceil(ny/32);
  * d_bin_ids: DEVICE pointer to n ints, the particle ids grouped by bin (bin = by * nbx
  * + bx, bx = floor(x/32) clamped to the lattice), ascending within each bin -- the same
- * result as imb_get_bins for the same centres.  stream: a cudaStream_t or NULL; the
- * call only queues work on it.
+ * result as imb_get_bins for the same centres.  stream: a cudaStream_t of the current
+ * device, or NULL; the call only queues work on it (a stream of another device returns
+ * IMB_E_INVALID_ARG).
  * Scratch (per-bin counts and fill cursors) lives in one fixed device array of
  * 2 * IMB_NOALLOC_MAX_BINS ints inside the library, held by every GPU that loads it
  * until process exit; nbins > IMB_NOALLOC_MAX_BINS returns IMB_E_INVALID_ARG.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress, with that
- * device current), so make that first call before any stream capture.  Every call
+ * device current), so make that first call before any stream capture; the address is
+ * kept for the life of the process, so a cudaDeviceReset of that device makes it stale
+ * (do not call this function on a device after resetting it).  Every call
  * shares the array and clears the part it uses; calls that overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller. */
 #define IMB_NOALLOC_MAX_BINS 65536

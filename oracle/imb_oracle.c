@@ -41,6 +41,16 @@ static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
+/* Host threads of the collide and stream loops (1 unless orc_set_threads says otherwise).
+ * Every cell is computed by the same arithmetic whatever the count, and the particles'
+ * forces are summed in the same order, so the results do not depend on it. */
+static int g_threads = 1;
+
+void orc_set_threads(int n)
+{
+    g_threads = n > 0 ? n : 1;
+}
+
 struct orc_sim {
     orc_params p;
     double *f;    /* f(x,t): post-stream, pre-collision  [9][ny][nx] */
@@ -52,6 +62,8 @@ struct orc_sim {
     double *xiw;                   /* tangential spring per particle-wall, [np][4] */
     int *cnt, *ids;                /* per cell: covering particles (ascending id) */
     double *eps;                   /* per cell and slot: solid ratio of that particle */
+    double *fterm;                 /* per cell and slot: force x, y and torque terms (Eqs. 15-16) */
+    int *fns;                      /* per cell: slots whose terms were computed */
     double zeta;                   /* damping ratio from the restitution coefficient */
     double gx_eff, gy_eff;         /* buoyancy-reduced gravity */
     double hm_kn0, hm_sn0, hm_kt0, hm_c0; /* Hertz-Mindlin: 4/3 E*, 2 E*, 8 G*, 2 sqrt(5/6) |beta| */
@@ -225,6 +237,8 @@ void orc_omega_s(const double *f9, double rho, double ux, double uy, double usx,
 static void stream(orc_sim *s)
 {
     const int nx = s->p.nx, ny = s->p.ny;
+    /* every (direction, destination) is written by one source cell, so rows run in parallel */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int k = 0; k < ny; ++k)
         for (int i = 0; i < nx; ++i)
             for (int q = 0; q < 9; ++q) {
@@ -294,6 +308,8 @@ orc_sim *orc_new(const orc_params *p)
     s->cnt = (int *)calloc((size_t)p->nx * p->ny, sizeof(int));
     s->ids = (int *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS, sizeof(int));
     s->eps = (double *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS, sizeof(double));
+    s->fterm = (double *)calloc((size_t)p->nx * p->ny * ORC_MAX_SLOTS * 3, sizeof(double));
+    s->fns = (int *)calloc((size_t)p->nx * p->ny, sizeof(int));
     double le = log(p->e_rest > 0.0 ? p->e_rest : 1.0);
     s->zeta = -le / sqrt(M_PI * M_PI + le * le);
     {   /* Hertz-Mindlin constants, identical materials: E* = E / (2 (1 - nu^2)),
@@ -332,7 +348,7 @@ void orc_free(orc_sim *s)
 {
     if (!s) return;
     free_particles(s);
-    free(s->f); free(s->fs); free(s->cnt); free(s->ids); free(s->eps);
+    free(s->f); free(s->fs); free(s->cnt); free(s->ids); free(s->eps); free(s->fterm); free(s->fns);
     free(s);
 }
 
@@ -571,7 +587,7 @@ static void collide(orc_sim *s)
     const int nx = s->p.nx, ny = s->p.ny;
     const int perx = s->p.bc_x == ORC_PERIODIC, pery = s->p.bc_y == ORC_PERIODIC;
     const double Fx = s->p.Fx, Fy = s->p.Fy;
-    for (int p = 0; p < s->np; ++p) s->Ffx[p] = s->Ffy[p] = s->Tf[p] = 0.0;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int k = 0; k < ny; ++k)
         for (int i = 0; i < nx; ++i) {
             double f[9], fe[9], fo[9];
@@ -596,6 +612,7 @@ static void collide(orc_sim *s)
                            (3.0 * (cmu_x * Fx + cmu_y * Fy) + 9.0 * cu * (CX[q] * Fx + CY[q] * Fy));
                 fo[q] = f[q] + (1.0 - B) * (omf + S);       /* Eq. 13, fluid part */
             }
+            s->fns[c] = B > 0.0 ? nc : 0;
             for (int t = 0; t < nc && B > 0.0; ++t) {
                 int p = s->ids[c * ORC_MAX_SLOTS + t];
                 double Bp = B * s->eps[c * ORC_MAX_SLOTS + t] / esum;
@@ -615,11 +632,22 @@ static void collide(orc_sim *s)
                 /* Eq. 15: B sum_i Omega^s_i c_i is the momentum the fluid gains
                  * in this cell; the particle receives the opposite */
                 double fpx = -Bp * mx, fpy = -Bp * my;
-                s->Ffx[p] += fpx;
-                s->Ffy[p] += fpy;
-                s->Tf[p] += dx * fpy - dy * fpx;            /* Eq. 16 */
+                double *ft = s->fterm + (c * ORC_MAX_SLOTS + t) * 3;
+                ft[0] = fpx;
+                ft[1] = fpy;
+                ft[2] = dx * fpy - dy * fpx;                /* Eq. 16 */
             }
             for (int q = 0; q < 9; ++q) s->fs[IDX(s, q, k, i)] = fo[q];
+        }
+    /* each particle's force and torque: its cells' terms summed in row-major order */
+    for (int p = 0; p < s->np; ++p) s->Ffx[p] = s->Ffy[p] = s->Tf[p] = 0.0;
+    for (size_t c = 0; c < (size_t)nx * ny; ++c)
+        for (int t = 0; t < s->fns[c]; ++t) {
+            const int p = s->ids[c * ORC_MAX_SLOTS + t];
+            const double *ft = s->fterm + (c * ORC_MAX_SLOTS + t) * 3;
+            s->Ffx[p] += ft[0];
+            s->Ffy[p] += ft[1];
+            s->Tf[p] += ft[2];
         }
 }
 

@@ -56,6 +56,8 @@ void   orc_omega_s(const double *f9, double rho, double ux, double uy, double us
                    double *om9);
 
 /* simulation */
+/* host threads of the collide and stream loops (default 1); results do not depend on it */
+void     orc_set_threads(int n);
 orc_sim *orc_new(const orc_params *p);
 void     orc_free(orc_sim *s);
 int      orc_set_particles(orc_sim *s, int n, const double *x, const double *v, const double *w,

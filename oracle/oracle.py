@@ -38,7 +38,10 @@ def build(force: bool = False) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            SRC, SRC3, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP only spreads the collide and stream loops over host threads (orc_set_threads,
+    # default one); without it the same code builds single-threaded
+    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
 
@@ -88,6 +91,7 @@ def lib():
         L.orc_covers.argtypes = [C.c_float, C.c_float, C.c_float]
         L.orc_covers.restype = C.c_int
         L.orc_omega_s.argtypes = [_dp] + [C.c_double] * 5 + [_dp]
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_new.argtypes = [C.POINTER(Params)]
         L.orc_new.restype = C.c_void_p
         L.orc_free.argtypes = [C.c_void_p]
@@ -124,6 +128,19 @@ def lib():
         L.orc3_cell_map.argtypes = [C.c_void_p, _ip, _ip]
         _lib = L
     return _lib
+
+
+_threads = 1
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's collide and stream loops (default 1); returns the previous
+    count.  The results do not depend on it: each cell's arithmetic is the same and the
+    particles' forces are summed in the same order."""
+    global _threads
+    prev, _threads = _threads, max(1, int(n))
+    lib().orc_set_threads(_threads)
+    return prev
 
 
 def _d(a):

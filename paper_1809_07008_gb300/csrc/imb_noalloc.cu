@@ -109,6 +109,11 @@ extern "C" int imb_bin_particles_noalloc(const double *d_x, int n, int nx, int n
     const int nbins = nbx * nby;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return IMB_E_CUDA;
+    if (stream) {   // the scratch address below is the current device's
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) return IMB_E_CUDA;
+        if (sdev != dev) return IMB_E_INVALID_ARG;
+    }
     int *scratch;
     {
         // first call on this device: the host-side name of the array is not a device

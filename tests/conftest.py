@@ -17,4 +17,6 @@ def pytest_configure(config):
 def orc():
     from oracle import oracle
     oracle.build()
+    # the oracle's results do not depend on its thread count (pinned in test_oracle_lbm.py)
+    oracle.set_threads(min(16, os.cpu_count() or 1))
     return oracle

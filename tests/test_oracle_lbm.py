@@ -175,3 +175,21 @@ def test_lid_driven_cavity_conserves_mass(orc):
     rho, ux, uy = s.macro()
     assert abs(rho.sum() - m0) < 1e-12 * m0
     assert ux[H - 1, H // 2] > 0.3 * uw and ux[H // 4, H // 2] < 0.0
+
+
+def test_oracle_threads_do_not_change_results(orc):
+    # the collide and stream loops may run on several host threads (the bench's CPU baseline):
+    # each cell's arithmetic is the same and the particles' forces are summed in row-major cell
+    # order whatever the count, so populations, forces and torques are bit-identical
+    w = W.c3sub(steps=0, nx=128, ny=96)
+    out = []
+    for th in (1, 4):
+        prev = orc.set_threads(th)
+        try:
+            s = orc.Sim(w)
+            s.step(15)
+            out.append((s.f(), *s.forces(), *s.particles()))
+        finally:
+            orc.set_threads(prev)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)

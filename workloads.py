@@ -246,9 +246,33 @@ def c3sub(steps=1000, nx=512, ny=512, seed=7008) -> Workload:
     return w.with_(name=f"c3sub_suspension_{nx}x{ny}_{n}disks")
 
 
+def c2_stack(steps=1000, n=30, nx=256, ny=192, ncols=4, gap=0.2, seed=1809) -> Workload:
+    """The collapse case's physics (closed box, d ~ U[16, 24], tau = 0.52, C = 0.1, buoyant
+    gravity, DEM on) on a small box: ``n`` disks stacked in ``ncols`` columns, each disk
+    ``gap`` cells above the one below it (the lowest ``gap`` above the wall), so that wall and
+    pair contacts form within the first coupling cycles."""
+    rng = SplitMix64(seed)
+    d = [rng.uniform_range(16.0, 24.0) for _ in range(n)]
+    pitch = 24.0 + gap
+    xs, top = [], [0.0] * ncols
+    for k in range(n):
+        c = k % ncols
+        r = d[k] / 2.0
+        y = top[c] + gap + r
+        top[c] = y + r
+        xs.append(((c + 0.5) * pitch + gap, y))
+    if max(top) + gap > ny or ncols * pitch + 2 * gap > nx:
+        raise ValueError("the stack does not fit the box")
+    x, v, om, r = _particles(xs, np.zeros((n, 2)), np.zeros(n), [di / 2.0 for di in d])
+    return Workload(name=f"c2_stack_{nx}x{ny}_{n}disks", nx=nx, ny=ny, tau=0.52, C_smag=0.1,
+                    bc_x=BC_WALL, bc_y=BC_WALL, dem_on=1, gravity=(0.0, -1.0e-5),
+                    steps=steps, x=x, v=v, omega=om, r=r)
+
+
 def c4(steps=4000, nx=512, ny=256, n_side=4, d=20.0, seed=1809, u_in=0.02, tau=0.6) -> Workload:
-    """Channel with n_side x n_side fixed disks on a jittered grid (velocity inlet, zero-gradient
-    outlet, walls), the case of the drag-gradient computation."""
+    """Channel with n_side x n_side fixed disks on a jittered grid (velocity inlet, outlet at the
+    reference pressure with zero velocity gradient, walls), the case of the drag-gradient
+    computation."""
     rng = SplitMix64(seed)
     sx, sy = nx / (n_side + 1), ny / (n_side + 1)
     xs = []
