@@ -70,13 +70,21 @@ struct __align__(16) PRec {
     float r, vx, vy, w;
 };
 
+constexpr int IVL_CAND = 4;     // candidates whose per-row cell intervals a tile block carries
+
 // Particles that can reach one 32 x 32 tile, ascending id (built by k_tile_lists,
-// bulk-copied into shared memory by the stream-collide kernel).
+// bulk-copied into shared memory by the stream-collide kernel).  For each tile row, the
+// candidates that can reach into it, and for the first IVL_CAND candidates the columns
+// (tile-relative) of the row's cells the disk reaches into, [x, y], and covers whole, [z, w]
+// (empty when the lower end exceeds the upper): the same decisions as covers() and
+// fully_covered() on each cell.
 struct __align__(16) TileCand {
     int n;
     int pad[3];
     int id[TILE_CAND];
     PRec p[TILE_CAND];
+    unsigned rowmask[TILE];
+    char4 ivl[IVL_CAND][TILE];
 };
 static_assert(sizeof(TileCand) % 16 == 0, "bulk copies move multiples of 16 bytes");
 

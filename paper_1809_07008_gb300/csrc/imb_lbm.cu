@@ -201,6 +201,14 @@ __device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const f
 // candidate is ka / kb (the first two candidates of the warp's rows in the unit); those of
 // any further candidate are summed over the warp's lanes at once (fixed shuffle tree) and
 // added to the warp's column of the tile's partials acc_w[(3 s + c) * WARPS].
+// solid ratio of tile candidate s at node (xl, yy) from the particle's table (a cell the disk
+// covers in part, or any covered cell in the cell-decomposition mode)
+__device__ __forceinline__ float cand_table_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
+                                                int s, int xl, int yy, const LatticeArgs &a) {
+    const PRec &P = cand[s];
+    return __ldg(a.eps_tab + (size_t)cid[s] * a.tab_stride + (yy - P.cj + a.tab_h) * a.tab_w + (xl - P.ci + a.tab_h));
+}
+
 __device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
                                                int s, int xl, int yy, const LatticeArgs &a) {
     const PRec &P = cand[s];
@@ -315,21 +323,6 @@ __device__ __forceinline__ float warp_sum6(const float (&fa)[3], const float (&f
     r += __shfl_xor_sync(FULL, r, 2);
     r += __shfl_xor_sync(FULL, r, 1);
     return r;
-}
-
-// Row mask: bit s set when candidate s can cover a cell of tile row yy (dy_near^2 <
-// r^2, the same rounding as covers(), hence a necessary condition).  Lane-parallel.
-__device__ __forceinline__ unsigned row_mask(const PRec *__restrict__ cand, int nc, int yy) {
-    const int lane = threadIdx.x & 31;
-    bool rel = false;
-    if (lane < nc) {
-        const PRec &P = cand[lane];
-        const float loy = __fsub_rn((float)(yy - P.cj), P.fy);
-        const float hiy = __fadd_rn(loy, 1.0f);
-        const float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
-        rel = __fmul_rn(dy, dy) < __fmul_rn(P.r, P.r);
-    }
-    return __ballot_sync(FULL, rel);
 }
 
 // Work unit of the persistent kernel: HROWS rows of a 32 x 32 tile; NST units are staged
@@ -480,18 +473,29 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
 #pragma unroll
         for (int rr = 0; rr < RPW; ++rr) {
             const int yy = h * HROWS + warp + WARPS * rr;
-            unsigned cm = 0u;
+            unsigned cm = 0u, fm = 0u;   // candidates that reach into / cover the node whole
             if (nc && y0 + yy < a.ny) {
-                for (unsigned m = row_mask(tc->p, nc, yy); m; m &= m - 1u) {
+                for (unsigned m = tc->rowmask[yy]; m; m &= m - 1u) {
                     const int s = __ffs(m) - 1;
-                    const PRec &P = tc->p[s];
-                    if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
-                        cm |= 1u << s;
+                    if (s < IVL_CAND) {   // the row's intervals, decided by k_tile_lists
+                        const char4 iv = tc->ivl[s][yy];
+                        cm |= (unsigned)(lane >= iv.x && lane <= iv.y) << s;
+                        fm |= (unsigned)(lane >= iv.z && lane <= iv.w) << s;
+                    } else {
+                        const PRec &P = tc->p[s];
+                        if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
+                            cm |= 1u << s;
+                    }
                 }
                 if (!xin) cm = 0u;
             }
             cmr[rr] = cm;
-            e0r[rr] = cm ? cand_slot_eps(tc->p, tc->id, __ffs(cm) - 1, lane, yy, a) : 0.0f;
+            const int s0 = cm ? __ffs(cm) - 1 : 0;
+            e0r[rr] = !cm ? 0.0f
+                          : s0 >= IVL_CAND ? cand_slot_eps(tc->p, tc->id, s0, lane, yy, a)
+                                           : (a.eps_mode == EPS_EXACT && ((fm >> s0) & 1u))
+                                                 ? 1.0f
+                                                 : cand_table_eps(tc->p, tc->id, s0, lane, yy, a);
             rowcr[rr] = __reduce_or_sync(FULL, cm);
             uni |= rowcr[rr];
         }
@@ -615,8 +619,12 @@ __global__ void __launch_bounds__(256) k_force_gather(const LatticeArgs a, const
     a.T[p] = tz;
 }
 
+__device__ __forceinline__ void row_reach(float fx, float loy, float r, int &L, int &H);
+__device__ __forceinline__ void row_full(float fx, float loy, float r, int &L, int &H);
+
 // Per-tile candidate lists: one warp per tile gathers the particles of the 3 x 3
-// surrounding bins whose disk can reach the tile, in ascending id order.
+// surrounding bins whose disk can reach the tile, in ascending id order, then (a lane per
+// tile row) the row masks and the row intervals of the first IVL_CAND candidates.
 __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCand *tiles, int ntiles) {
     __shared__ TileShared sh[WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -636,12 +644,36 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
         const int pid = sh[warp].id[lane];
         out->id[lane] = pid;
         out->p[lane] = P;
+        sh[warp].p[lane] = P;
         // the particle's entry for this tile: its place among the 3 x 3 tiles around its bin
         const int b = a.pbin[pid], pbx = b % a.nbx, pby = b / a.nbx;
         const int dx = wrap_rel(bx - pbx, a.nbx, a.bc_x == BC_PERIODIC);
         const int dy = wrap_rel(by - pby, a.nby, a.bc_y == BC_PERIODIC);
         if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) a.pslot[9 * pid + 3 * (dy + 1) + dx + 1] = t * TILE_CAND + lane;
     }
+    __syncwarp();
+    // tile row `lane`: which candidates can reach into it (dy_near^2 < r^2, the rounding of
+    // covers()), and the intervals of the first IVL_CAND from the per-row interval search
+    // settled with covers() and fully_covered() themselves
+    unsigned rm = 0u;
+    for (int s = 0; s < nc; ++s) {
+        const PRec P = sh[warp].p[s];
+        const float loy = __fsub_rn((float)(lane - P.cj), P.fy);
+        const float hiy = __fadd_rn(loy, 1.0f);
+        const float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
+        if (__fmul_rn(dy, dy) < __fmul_rn(P.r, P.r)) rm |= 1u << s;
+        if (s < IVL_CAND) {
+            int L, H, L2, H2;
+            row_reach(P.fx, loy, P.r, L, H);
+            row_full(P.fx, loy, P.r, L2, H2);
+            int lo = max(L + P.ci, 0), hi = min(H + P.ci, TILE - 1);
+            int lo2 = max(L2 + P.ci, 0), hi2 = min(H2 + P.ci, TILE - 1);
+            if (L > H || lo > hi) { lo = 64; hi = -64; }
+            if (L2 > H2 || lo2 > hi2) { lo2 = 64; hi2 = -64; }
+            out->ivl[s][lane] = make_char4((signed char)lo, (signed char)hi, (signed char)lo2, (signed char)hi2);
+        }
+    }
+    out->rowmask[lane] = rm;
 }
 
 // The map step of the coupling cycle (Sec. 2.4) for the partially covered cells: one
