@@ -14,13 +14,26 @@ struct NodeState {
     float n[9];   // non-equilibrium parts f_i - f_i^eq
 };
 
+// The eight moving directions as four pairs (q, -q), q = 1, 2, 5, 6: their equilibria share
+// the even part w (drho + rho (4.5 (c.u)^2 - 1.5 u^2)) and differ in the sign of the odd part
+// 3 w rho c.u, so a pair is computed with FP32x2 instructions (two lanes of arithmetic per
+// instruction) where the operations line up.
+__host__ __device__ constexpr int pair_q(int k) { return k < 2 ? k + 1 : k + 3; }
+
 __device__ __forceinline__ void node_state(const float (&d)[9], const LatticeArgs &a, const bool forced,
                                            const bool smag, NodeState &c) {
+    float2 P[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P[k] = make_float2(d[pair_q(k)], d[opp_of(pair_q(k))]);
     // ---- moments (Eqs. 3-4, Guo half-force shift)
-    c.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const float2 S = __fadd2_rn(__fadd2_rn(P[0], P[1]), __fadd2_rn(P[2], P[3]));
+    c.drho = d[0] + (S.x + S.y);
     c.rho = 1.0f + c.drho;
-    c.jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    c.jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    float D[4];   // d_q - d_-q
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D[k] = P[k].x - P[k].y;
+    c.jx = (D[0] + D[2]) - D[3];   // c_x: +1 for q = 1, 5, -1 for q = 6
+    c.jy = (D[1] + D[2]) + D[3];   // c_y: +1 for q = 2, 5, 6
     if (forced) {
         c.jx = fmaf(0.5f, a.Fx, c.jx);
         c.jy = fmaf(0.5f, a.Fy, c.jy);
@@ -30,18 +43,31 @@ __device__ __forceinline__ void node_state(const float (&d)[9], const LatticeArg
     c.uy = c.jy * inv;
     c.usq = c.ux * c.ux + c.uy * c.uy;
     // ---- non-equilibrium parts (Eq. 2)
+    const float m15 = -1.5f * c.usq;
+    c.n[0] = d[0] - w_of(0) * fmaf(c.rho, m15, c.drho);
+    float2 N[4];
+    const float2 rho2 = make_float2(c.rho, c.rho), drho2 = make_float2(c.drho, c.drho);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
+    for (int k = 0; k < 4; ++k) {
+        // n_{+-q} = d_{+-q} - w_q (drho + rho (4.5 (c.u)^2 - 1.5 u^2 +- 3 c.u)), each rounded once
+        const int q = pair_q(k);
         const float cu = cdot(q, c.ux, c.uy);
-        c.n[q] = d[q] - w_of(q) * (c.drho + c.rho * (cu * (3.0f + 4.5f * cu) - 1.5f * c.usq));
+        const float e = fmaf(4.5f * cu, cu, m15), o3 = 3.0f * cu;
+        const float2 X = __ffma2_rn(rho2, make_float2(e + o3, e - o3), drho2);
+        N[k] = __ffma2_rn(make_float2(-w_of(q), -w_of(q)), X, P[k]);
+        c.n[q] = N[k].x;
+        c.n[opp_of(q)] = N[k].y;
     }
     // ---- Smagorinsky effective relaxation time (Hou et al. 1996 closure)
     c.omega = a.omega0;
     c.te = a.tau;
     if (smag) {
-        const float pxx = (c.n[1] + c.n[3]) + (c.n[5] + c.n[6]) + (c.n[7] + c.n[8]);
-        const float pyy = (c.n[2] + c.n[4]) + (c.n[5] + c.n[6]) + (c.n[7] + c.n[8]);
-        const float pxy = (c.n[5] - c.n[6]) + (c.n[7] - c.n[8]);
+        const float2 E = __fadd2_rn(N[2], N[3]);                                // (n5 + n6, n7 + n8)
+        const float2 F = __fadd2_rn(N[2], make_float2(-N[3].x, -N[3].y));       // (n5 - n6, n7 - n8)
+        const float e = E.x + E.y;
+        const float pxx = (N[0].x + N[0].y) + e;
+        const float pyy = (N[1].x + N[1].y) + e;
+        const float pxy = F.x + F.y;
         const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
         const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;          // sqrt(Q)
         const float disc = fmaf(a.smag_coef * sq, inv, a.tau * a.tau);
@@ -64,18 +90,28 @@ template <typename S, bool IMB, bool FORCED>
 __device__ __forceinline__ void node_collide_store(const float (&d)[9], const NodeState &c,
                                                    const SolidMoments &sm, S *__restrict__ outp,
                                                    const LatticeArgs &a) {
-    float upd[9];
+    float upd0 = -c.omega * c.n[0];
+    float2 U[4];   // updates of the pairs (q, -q)
+    const float2 mo = make_float2(-c.omega, -c.omega);
+    if (IMB || FORCED) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) upd[q] = -c.omega * c.n[q];
+        for (int k = 0; k < 4; ++k) U[k] = __fmul2_rn(mo, make_float2(c.n[pair_q(k)], c.n[opp_of(pair_q(k))]));
+    }
     if (FORCED) {  // Guo forcing term
         const float sf = 1.0f - 0.5f * c.omega;
+        upd0 = fmaf(sf, w_of(0) * 3.0f * (-c.ux * a.Fx - c.uy * a.Fy), upd0);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float cxq = (float)cx_of(q), cyq = (float)cy_of(q);
-            const float cu = cdot(q, c.ux, c.uy);
-            const float S_q = w_of(q) * (3.0f * ((cxq - c.ux) * a.Fx + (cyq - c.uy) * a.Fy) +
-                                         9.0f * cu * cdot(q, a.Fx, a.Fy));
-            upd[q] = fmaf(sf, S_q, upd[q]);
+        for (int k = 0; k < 4; ++k) {
+            const int q = pair_q(k), o = opp_of(q);
+            float S2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int qq = h ? o : q;
+                const float cxq = (float)cx_of(qq), cyq = (float)cy_of(qq);
+                const float cu = cdot(qq, c.ux, c.uy);
+                S2[h] = w_of(qq) * (3.0f * ((cxq - c.ux) * a.Fx + (cyq - c.uy) * a.Fy) + 9.0f * cu * cdot(qq, a.Fx, a.Fy));
+            }
+            U[k] = __ffma2_rn(make_float2(sf, sf), make_float2(S2[0], S2[1]), U[k]);
         }
     }
     if (IMB) {
@@ -87,23 +123,29 @@ __device__ __forceinline__ void node_collide_store(const float (&d)[9], const No
         const float a2xx = sm.m2xx - B * c.ux * c.ux, a2yy = sm.m2yy - B * c.uy * c.uy;
         const float a2xy = sm.m2xy - B * c.ux * c.uy;
         const float tra2 = a2xx + a2yy;
-        upd[0] = fmaf(fl, upd[0], c.rho * w_of(0) * (-1.5f * tra2));
+        upd0 = fmaf(fl, upd0, c.rho * w_of(0) * (-1.5f * tra2));
+        const float2 fl2 = make_float2(fl, fl);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int q = k < 2 ? k + 1 : k + 3, o = opp_of(q);   // q = 1, 2, 5, 6
+            const int q = pair_q(k), o = opp_of(q);
             const float rw = c.rho * w_of(q);
             const float t1 = 3.0f * cdot(q, a1x, a1y);
             const float t2 = 4.5f * ccdot(q, a2xx, a2yy, a2xy) - 1.5f * tra2;
             const float bd = B * (c.n[o] - c.n[q]);
-            upd[q] = fmaf(fl, upd[q], bd) + rw * (t2 + t1);
-            upd[o] = fmaf(fl, upd[o], -bd) + rw * (t2 - t1);
+            U[k] = __ffma2_rn(fl2, U[k], make_float2(bd, -bd));
+            U[k] = __ffma2_rn(make_float2(rw, rw), make_float2(t2 + t1, t2 - t1), U[k]);
         }
     }
-    S *p = outp;
+    Store<S>::st(outp, d[0] + upd0);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        Store<S>::st(p, d[q] + upd[q]);
-        p += a.plane;
+    for (int k = 0; k < 4; ++k) {
+        const int q = pair_q(k), o = opp_of(q);
+        const float2 P = make_float2(d[q], d[o]);
+        // a fluid node in one rounding: d - omega n (+ the forcing term)
+        const float2 out = (IMB || FORCED) ? __fadd2_rn(P, U[k])
+                                           : __ffma2_rn(mo, make_float2(c.n[q], c.n[o]), P);
+        Store<S>::st(outp + (size_t)q * a.plane, out.x);
+        Store<S>::st(outp + (size_t)o * a.plane, out.y);
     }
 }
 
