@@ -355,7 +355,11 @@ template <typename S> struct Box {
     static constexpr int ACC_FLOATS = NACC * TILE_CAND * 3 * WARPS;
     // partials, the tile of each stage (index, column, row, unit), warps done per stage,
     // the producer's state (units issued, tile of the unit group, next tile, end reached)
-    static constexpr int EXTRA_BYTES = ACC_FLOATS * 4 + NST * 16 + (NST + 4 + 3) / 4 * 16;
+    // warps with more than two rows per unit keep their rows' coverage masks in shared memory
+    // ([warp][row][lane]) rather than in registers
+    static constexpr bool MASKS_IN_SMEM = RPW > 2;
+    static constexpr int MASK_WORDS = MASKS_IN_SMEM ? WARPS * RPW * 32 : 0;
+    static constexpr int EXTRA_BYTES = ACC_FLOATS * 4 + MASK_WORDS * 4 + NST * 16 + (NST + 4 + 3) / 4 * 16;
     static constexpr int SMEM_BYTES = NST * STAGE_BYTES + EXTRA_BYTES + NST * 8;
 };
 static_assert((Box<float>::WN * Box<float>::HROWS * 4) % 128 == 0 &&
@@ -393,7 +397,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
     float *acc = reinterpret_cast<float *>(extra);
-    int4 *stage_tile = reinterpret_cast<int4 *>(extra + G::ACC_FLOATS * 4);
+    unsigned *cm_smem = reinterpret_cast<unsigned *>(extra + G::ACC_FLOATS * 4);
+    int4 *stage_tile = reinterpret_cast<int4 *>(extra + G::ACC_FLOATS * 4 + G::MASK_WORDS * 4);
     int *done = reinterpret_cast<int *>(stage_tile + NST);
     int *prod = done + NST;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(extra + G::EXTRA_BYTES);
@@ -489,15 +494,17 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 }
                 if (!xin) cm = 0u;
             }
-            cmr[rr] = cm;
+            if (G::MASKS_IN_SMEM) cm_smem[(warp * RPW + rr) * 32 + lane] = cm;
+            else cmr[rr] = cm;
             const int s0 = cm ? __ffs(cm) - 1 : 0;
             e0r[rr] = !cm ? 0.0f
                           : s0 >= IVL_CAND ? cand_slot_eps(tc->p, tc->id, s0, lane, yy, a)
                                            : (a.eps_mode == EPS_EXACT && ((fm >> s0) & 1u))
                                                  ? 1.0f
                                                  : cand_table_eps(tc->p, tc->id, s0, lane, yy, a);
-            rowcr[rr] = __reduce_or_sync(FULL, cm);
-            uni |= rowcr[rr];
+            const unsigned rowc = __reduce_or_sync(FULL, cm);
+            if (!G::MASKS_IN_SMEM) rowcr[rr] = rowc;
+            uni |= rowc;
         }
         // register sums of the force terms of the first two candidates of these rows
         const int ka = uni ? __ffs(uni) - 1 : -1;
@@ -508,15 +515,24 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             const int yy = h * HROWS + warp + WARPS * rr;
             const int y = y0 + yy;
             if (y >= a.ny) continue;
-            unsigned cm = cmr[0], rowc = rowcr[0];
+            unsigned cm, rowc;
             float e0 = e0r[0];
 #pragma unroll
             for (int j = 1; j < RPW; ++j)
-                if (rr == j) {
-                    cm = cmr[j];
-                    rowc = rowcr[j];
-                    e0 = e0r[j];
-                }
+                if (rr == j) e0 = e0r[j];
+            if (G::MASKS_IN_SMEM) {
+                cm = cm_smem[(warp * RPW + rr) * 32 + lane];
+                rowc = __reduce_or_sync(FULL, cm);
+            } else {
+                cm = cmr[0];
+                rowc = rowcr[0];
+#pragma unroll
+                for (int j = 1; j < RPW; ++j)
+                    if (rr == j) {
+                        cm = cmr[j];
+                        rowc = rowcr[j];
+                    }
+            }
             float d[9];
             if (in) {
                 const int r = yy - h * HROWS;
