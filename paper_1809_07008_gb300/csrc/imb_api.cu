@@ -550,10 +550,7 @@ static int dem_cycle(imb_ctx *c, bool zero_forces) {
 }
 
 static int lattice_step(imb_ctx *c) {
-    if (c->np > 0 && !c->p.dem_on) {
-        CK(cudaMemsetAsync(c->F, 0, 16 * (size_t)c->np, c->stream), "zero forces");
-        CK(cudaMemsetAsync(c->T, 0, 8 * (size_t)c->np, c->stream), "zero torques");
-    }
+    // every particle's force and torque are written whole by the force gather below
     LatticeArgs a = lattice_args(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {

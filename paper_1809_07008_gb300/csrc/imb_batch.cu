@@ -48,28 +48,47 @@ struct RestNode {
     bool ok;              // |u|^2 below the Mach guard (false for NaN)
 };
 
+// The eight moving directions as four pairs (q, -q), q = 1, 2, 5, 6, whose terms differ only in
+// the sign of their odd parts: computed with FP32x2 instructions where the operations line up.
+__host__ __device__ constexpr int bpair_q(int k) { return k < 2 ? k + 1 : k + 3; }
+
 template <typename S>
 __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, const BatchDomain &D, S *__restrict__ outp) {
     RestNode r;
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    float2 P[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P[k] = make_float2(d[bpair_q(k)], d[opp_of(bpair_q(k))]);
+    const float2 Sm = __fadd2_rn(__fadd2_rn(P[0], P[1]), __fadd2_rn(P[2], P[3]));
+    const float drho = d[0] + (Sm.x + Sm.y);
     const float rho = 1.0f + drho;
-    const float jx = fmaf(0.5f, D.Fx, (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]));   // Eqs. 3-4
-    const float jy = fmaf(0.5f, D.Fy, (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]));
+    float Dq[4];   // d_q - d_-q
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Dq[k] = P[k].x - P[k].y;
+    const float jx = fmaf(0.5f, D.Fx, (Dq[0] + Dq[2]) - Dq[3]);   // Eqs. 3-4
+    const float jy = fmaf(0.5f, D.Fy, (Dq[1] + Dq[2]) + Dq[3]);
     const float inv = __fdividef(1.0f, rho);
     const float ux = jx * inv, uy = jy * inv;
     const float usq = ux * ux + uy * uy;
     const float t = fmaf(-1.5f * rho, usq, drho);
-    float n[9];
+    // non-equilibrium parts (Eq. 2): n_{+-q} = d_{+-q} - w_q (t + 4.5 rho (c.u)^2 +- 3 rho c.u)
+    const float n0 = d[0] - w_of(0) * t;
+    float2 N[4];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {   // non-equilibrium parts (Eq. 2)
+    for (int k = 0; k < 4; ++k) {
+        const int q = bpair_q(k);
         const float cu = cdot(q, ux, uy);
-        n[q] = d[q] - w_of(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+        const float rcu = rho * cu;
+        const float ev = fmaf(4.5f * rcu, cu, t), od = 3.0f * rcu;
+        N[k] = __ffma2_rn(make_float2(-w_of(q), -w_of(q)), make_float2(ev + od, ev - od), P[k]);
     }
     float omega = D.omega0, te = D.tau;
     if (D.smag_coef > 0.0f) {       // Smagorinsky closure, as in the single-lattice path
-        const float pxx = (n[1] + n[3]) + (n[5] + n[6]) + (n[7] + n[8]);
-        const float pyy = (n[2] + n[4]) + (n[5] + n[6]) + (n[7] + n[8]);
-        const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
+        const float2 Ep = __fadd2_rn(N[2], N[3]);                            // (n5 + n6, n7 + n8)
+        const float2 Fp = __fadd2_rn(N[2], make_float2(-N[3].x, -N[3].y));   // (n5 - n6, n7 - n8)
+        const float ee = Ep.x + Ep.y;
+        const float pxx = (N[0].x + N[0].y) + ee;
+        const float pyy = (N[1].x + N[1].y) + ee;
+        const float pxy = Fp.x + Fp.y;
         const float Q = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
         const float sq = Q > 0.0f ? Q * rsqrtf(Q) : 0.0f;
         const float disc = fmaf(D.smag_coef * sq, inv, D.tau * D.tau);
@@ -81,17 +100,22 @@ __device__ __forceinline__ RestNode rest_node(const float (&d)[9], float e, cons
     const float fl = 1.0f - B, flw = -fl * omega, fls = fl * (1.0f - 0.5f * omega), Bd = B * drho;
     const float g = -3.0f * (ux * D.Fx + uy * D.Fy);
     // d*_q = (1 - B) d_q - (1 - B) omega n_q + B n_{-q} + w_q [(1 - B)(1 - omega/2) S_q + B drho]
-    // with S_q / w_q = cF (3 + 9 cu) - 3 u.F (cF = c_q.F)
-    const float k0 = w_of(0) * fls, k1 = w_of(1) * fls, k5 = w_of(5) * fls;
-    const float b0 = w_of(0) * Bd, b1 = w_of(1) * Bd, b5 = w_of(5) * Bd;
+    // with S_q / w_q = cF (3 + 9 cu) - 3 u.F (cF = c_q.F); both halves of a pair: cu, cF -> -cu, -cF
+    Store<S>::st(outp, fmaf(fl, d[0], fmaf(flw, n0, fmaf(B, n0, fmaf(w_of(0) * fls, g, w_of(0) * Bd)))));
+    const float2 fl2 = make_float2(fl, fl), flw2 = make_float2(flw, flw), B2 = make_float2(B, B);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const float cu = cdot(q, ux, uy);
-        const float cF = cdot(q, D.Fx, D.Fy);
-        const float Sq = fmaf(cF, fmaf(9.0f, cu, 3.0f), g);
-        const float kq = q == 0 ? k0 : (q < 5 ? k1 : k5), bq = q == 0 ? b0 : (q < 5 ? b1 : b5);
-        const float v = fmaf(fl, d[q], fmaf(flw, n[q], fmaf(B, n[opp_of(q)], fmaf(kq, Sq, bq))));
-        Store<S>::st(outp + (size_t)q * D.plane, v);
+    for (int k = 0; k < 4; ++k) {
+        const int q = bpair_q(k), o = opp_of(q);
+        const float cu = cdot(q, ux, uy), cF = cdot(q, D.Fx, D.Fy);
+        const float kq = w_of(q) * fls, bq = w_of(q) * Bd;
+        const float2 Sq = __ffma2_rn(make_float2(cF, -cF), make_float2(fmaf(9.0f, cu, 3.0f), fmaf(-9.0f, cu, 3.0f)),
+                                     make_float2(g, g));
+        float2 v = __ffma2_rn(make_float2(kq, kq), Sq, make_float2(bq, bq));
+        v = __ffma2_rn(B2, make_float2(N[k].y, N[k].x), v);
+        v = __ffma2_rn(flw2, N[k], v);
+        v = __ffma2_rn(fl2, P[k], v);
+        Store<S>::st(outp + (size_t)q * D.plane, v.x);
+        Store<S>::st(outp + (size_t)o * D.plane, v.y);
     }
     r.B = B;
     r.jx = jx;

@@ -225,13 +225,27 @@ template <typename S>
 __device__ __forceinline__ int collide3_plain(const float (&d)[19], const Args3 &a, int x, int y, int z, size_t cell,
                                         const unsigned *__restrict__ map, const Sph3 *__restrict__ sph,
                                         S *__restrict__ fout, float (&fo)[6], bool &unstable) {
-    float drho = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+    // the 18 moving directions as nine pairs (q, q + 1) = (q, -q), q odd, computed with FP32x2
+    // instructions: their terms differ only in the sign of the odd parts
+    float2 P[9];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        drho += d[q];
-        if (cx3(q)) mx += cx3(q) * d[q];
-        if (cy3(q)) my += cy3(q) * d[q];
-        if (cz3(q)) mz += cz3(q) * d[q];
+    for (int k = 0; k < 9; ++k) P[k] = make_float2(d[2 * k + 1], d[2 * k + 2]);
+    float2 Sp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Sp[k] = P[k];
+#pragma unroll
+    for (int h = 1; h < 9; h <<= 1)
+#pragma unroll
+        for (int k = 0; k + h < 9; k += 2 * h) Sp[k] = __fadd2_rn(Sp[k], Sp[k + h]);
+    const float drho = d[0] + (Sp[0].x + Sp[0].y);
+    float mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {   // c_{-q} = -c_q: first moments from d_q - d_-q
+        const int q = 2 * k + 1;
+        const float Dk = P[k].x - P[k].y;
+        if (cx3(q)) mx += cx3(q) * Dk;
+        if (cy3(q)) my += cy3(q) * Dk;
+        if (cz3(q)) mz += cz3(q) * Dk;
     }
     const float rho = 1.0f + drho;
     const float jx = fmaf(0.5f, a.Fx, mx), jy = fmaf(0.5f, a.Fy, my), jz = fmaf(0.5f, a.Fz, mz);
@@ -240,11 +254,16 @@ __device__ __forceinline__ int collide3_plain(const float (&d)[19], const Args3 
     const float uu = ux * ux + uy * uy + uz * uz;
     if (!(uu < 0.09f)) unstable = true;   // Mach guard, also catches NaN
     const float t = fmaf(-1.5f * rho, uu, drho);
-    float n[19];
+    const float2 t2 = make_float2(t, t);
+    // non-equilibrium parts (Eq. 2), shifted by w: n_{+-q} = d_{+-q} - w_q (t +- rho c.u (3 +- 4.5 c.u))
+    const float n0 = d[0] - w3(0) * t;
+    float2 N[9];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {   // non-equilibrium parts (Eq. 2), shifted by w
-        const float cu = cdot3(q, ux, uy, uz);
-        n[q] = d[q] - w3(q) * fmaf(rho * cu, fmaf(4.5f, cu, 3.0f), t);
+    for (int k = 0; k < 9; ++k) {
+        const int q = 2 * k + 1;
+        const float cu = cdot3(q, ux, uy, uz), rcu = rho * cu;
+        const float2 X = __ffma2_rn(make_float2(rcu, -rcu), make_float2(fmaf(4.5f, cu, 3.0f), fmaf(-4.5f, cu, 3.0f)), t2);
+        N[k] = __ffma2_rn(make_float2(-w3(q), -w3(q)), X, P[k]);
     }
     const unsigned word = map[cell];
     int sid = -1;
@@ -254,36 +273,56 @@ __device__ __forceinline__ int collide3_plain(const float (&d)[19], const Args3 
         const float eps = (float)(word >> ID_BITS) * a.inv_nsub3;
         const float tm = a.tau - 0.5f;
         B = __fdividef(eps * tm, (1.0f - eps) + tm);
-        const Sph3 P = sph[sid];
-        rx = (float)min_image(x - P.ci, a.nx) + 0.5f - P.fx;
-        ry = (float)(a.wall_y ? y - P.cj : min_image(y - P.cj, a.ny)) + 0.5f - P.fy;
-        rz = (float)min_image(z - P.ck, a.nz) + 0.5f - P.fz;
-        usx = P.vx + (P.wy * rz - P.wz * ry);
-        usy = P.vy + (P.wz * rx - P.wx * rz);
-        usz = P.vz + (P.wx * ry - P.wy * rx);
+        const Sph3 Ps = sph[sid];
+        rx = (float)min_image(x - Ps.ci, a.nx) + 0.5f - Ps.fx;
+        ry = (float)(a.wall_y ? y - Ps.cj : min_image(y - Ps.cj, a.ny)) + 0.5f - Ps.fy;
+        rz = (float)min_image(z - Ps.ck, a.nz) + 0.5f - Ps.fz;
+        usx = Ps.vx + (Ps.wy * rz - Ps.wz * ry);
+        usy = Ps.vy + (Ps.wz * rx - Ps.wx * rz);
+        usz = Ps.vz + (Ps.wx * ry - Ps.wy * rx);
     }
     const float fl = 1.0f - B, sf = 1.0f - 0.5f * a.omega;
     const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
-    // BGK with Guo forcing (its source divided by 1 - 1/(2 tau)), weighted by 1 - B
-    auto fluid = [&](int q) {
-        const float cu = cdot3(q, ux, uy, uz);
-        const float cF = cdot3(q, a.Fx, a.Fy, a.Fz);
-        const float Sg = w3(q) * (3.0f * (cF - uF) + 9.0f * cu * cF);
-        return fmaf(-a.omega, n[q], sf * Sg);
+    // BGK with Guo forcing (its source divided by 1 - 1/(2 tau)), weighted by 1 - B:
+    // -omega n_q + sf w_q (3 (c_q.F - u.F) + 9 (c_q.u)(c_q.F)), for the pair (q, -q)
+    const float f0 = fmaf(-a.omega, n0, sf * (w3(0) * (-3.0f * uF)));
+    const float2 mo2 = make_float2(-a.omega, -a.omega), muF2 = make_float2(-uF, -uF);
+    auto fluid2 = [&](int k) {
+        const int q = 2 * k + 1;
+        const float cu = cdot3(q, ux, uy, uz), cF = cdot3(q, a.Fx, a.Fy, a.Fz);
+        const float e9 = 9.0f * cu * cF;
+        const float2 A = __fadd2_rn(make_float2(cF, -cF), muF2);
+        const float2 G = __ffma2_rn(make_float2(3.0f, 3.0f), A, make_float2(e9, e9));
+        const float sw = sf * w3(q);
+        return __ffma2_rn(mo2, N[k], __fmul2_rn(make_float2(sw, sw), G));
     };
     if (word) {   // Eq. 12 in shifted form: n_{-q} + (f^eq_q(u_s) - w_q) - d_q, weighted by B
         const float uss = usx * usx + usy * usy + usz * usz;
         const float ts = fmaf(-1.5f * rho, uss, drho);
+        const float2 ts2 = make_float2(ts, ts), B2 = make_float2(B, B), fl2 = make_float2(fl, fl);
+        Store<S>::st(fout + cell, d[0] + fmaf(B, n0 + w3(0) * ts - d[0], fl * f0));
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const float cs = cdot3(q, usx, usy, usz);
-            const float eqs = w3(q) * fmaf(rho * cs, fmaf(4.5f, cs, 3.0f), ts);
-            const float v = fmaf(B, n[opp3(q)] + eqs - d[q], fl * fluid(q));
-            Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + v);
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            const float cs = cdot3(q, usx, usy, usz), rcs = rho * cs;
+            const float2 Xs = __ffma2_rn(make_float2(rcs, -rcs), make_float2(fmaf(4.5f, cs, 3.0f), fmaf(-4.5f, cs, 3.0f)), ts2);
+            // n_{-q} + w_q Xs - d_q for q and -q
+            const float2 T = __fadd2_rn(__ffma2_rn(make_float2(w3(q), w3(q)), Xs, make_float2(N[k].y, N[k].x)),
+                                        make_float2(-P[k].x, -P[k].y));
+            const float2 v = __ffma2_rn(B2, T, __fmul2_rn(fl2, fluid2(k)));
+            const float2 o = __fadd2_rn(P[k], v);
+            Store<S>::st(fout + (size_t)q * a.plane + cell, o.x);
+            Store<S>::st(fout + (size_t)(q + 1) * a.plane + cell, o.y);
         }
     } else {      // no sphere: the fluid operator alone
+        Store<S>::st(fout + cell, d[0] + f0);
 #pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::st(fout + (size_t)q * a.plane + cell, d[q] + fluid(q));
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            const float2 o = __fadd2_rn(P[k], fluid2(k));
+            Store<S>::st(fout + (size_t)q * a.plane + cell, o.x);
+            Store<S>::st(fout + (size_t)(q + 1) * a.plane + cell, o.y);
+        }
     }
     if (word) {   // Eqs. 15-16: force on the sphere B (rho u - rho u_s - F), torque r x force
         fo[0] = B * (jx - rho * usx - a.Fx);
