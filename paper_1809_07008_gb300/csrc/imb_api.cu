@@ -28,6 +28,7 @@ struct imb_ctx {
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaStream_t side = nullptr;                  // solid-ratio tables beside the bins and tile lists
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_rows = nullptr;               // the particles' row intervals are written
     void *fbuf[2] = {nullptr, nullptr};
     int cur = 0;               // buffer holding the latest post-collision populations
     size_t plane = 0, elem = 4;
@@ -61,6 +62,8 @@ struct imb_ctx {
     double *tile_force = nullptr;   // per tile and candidate: partial force and torque sums
     float *eps_tab = nullptr;       // per particle: solid ratios of its partially covered cells
     size_t eps_tab_cap = 0;
+    char4 *pivl = nullptr;          // per particle and row: reached / fully covered cell intervals
+    size_t pivl_cap = 0;
     int tab_w = 0, tab_h = 0;
     CUtensorMap tmap[2][2];         // TMA descriptors [buffer][narrow, wide] of the populations
     // parameters derived on the host
@@ -160,6 +163,7 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.tile_ctr = c->tile_ctr;
     a.pbin = c->pbin;
     a.pslot = c->pslot;
+    a.pivl = c->pivl;
     return a;
 }
 
@@ -263,10 +267,12 @@ extern "C" void imb_destroy(imb_ctx *c) {
     dfree(c->tiles);
     dfree(c->tile_force);
     dfree(c->eps_tab);
+    dfree(c->pivl);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->side) cudaStreamSynchronize(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_rows) cudaEventDestroy(c->ev_rows);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -360,7 +366,8 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     c->stream = c->own_stream;
     if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming)) != cudaSuccess)
         return bail(e, "side stream");
     for (int b = 0; b < 2; ++b)
         if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess)
@@ -409,19 +416,23 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
                              0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
                              c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
        "particle table");
-    // the solid-ratio tables need only the particle records: they run on the side stream
-    // while the bins and the tile lists are built, and the stream waits for them at the end
+    // the rows' cell intervals and the solid-ratio tables need only the particle records: they
+    // run on the side stream while the bins are built; the tile lists wait for the intervals,
+    // the stream for the tables at the end
     CK(cudaEventRecord(c->ev_fork, c->stream), "fork");
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+    CK(launch_particle_rows(lattice_args(c), c->side), "row intervals");
+    CK(cudaEventRecord(c->ev_rows, c->side), "rows");
     CK(launch_particle_eps(lattice_args(c), c->side), "solid-ratio tables");
     CK(cudaEventRecord(c->ev_join, c->side), "join");
     CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->bin_bsum, c->counters, c->stream),
        "bin scan");
     CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
     CK(cudaMemsetAsync(c->pslot, 0xff, 9 * sizeof(int) * (size_t)c->np, c->stream), "clear tile slots");
+    CK(cudaStreamWaitEvent(c->stream, c->ev_rows, 0), "rows");
     CK(launch_tile_lists(lattice_args(c), c->tiles, c->stream), "tile lists");
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
-    c->launches += 6;   // table, scan (two passes), fill, tile lists, solid-ratio map
+    c->launches += 7;   // table, scan (two passes), fill, row intervals, tile lists, solid-ratio map
     return IMB_OK;
 }
 
@@ -495,6 +506,15 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
             cudaError_t e = dalloc(&c->eps_tab, need);
             if (e != cudaSuccess) return cuda_fail(c, e, "solid-ratio table");
             c->eps_tab_cap = need;
+        }
+        const size_t need_rows = (size_t)std::max(n, 1) * tw;
+        if (need_rows > c->pivl_cap) {
+            dfree(c->pivl);
+            c->pivl = nullptr;
+            c->pivl_cap = 0;
+            cudaError_t e = dalloc(&c->pivl, need_rows);
+            if (e != cudaSuccess) return cuda_fail(c, e, "row intervals");
+            c->pivl_cap = need_rows;
         }
         c->tab_h = th;
         c->tab_w = tw;

@@ -34,6 +34,8 @@ struct LatticeArgs {
     unsigned *err;
     unsigned *tile_ctr;        // [2] tiles handed out and blocks finished (zero between launches)
     const int *pbin;           // [np] bin of each particle
+    char4 *pivl;               // [np][tab_w] per particle row dk + tab_h: the cells (relative column) the disk
+                               // reaches into, [x, y], and covers whole, [z, w] (exact-area mode)
     int *pslot;                // [np][9] tile * TILE_CAND + slot of the particle in the candidate lists of the
                                // 3 x 3 tiles around its bin (row by row), -1 where it is not a candidate
 };
@@ -80,6 +82,9 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
 // a.F, a.T of every particle = its tiles' partial sums, in a fixed order
 cudaError_t launch_force_gather(const LatticeArgs &a, const double *tile_force, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
+// per particle and row, the reached and fully covered cell intervals (before the tile lists and
+// the solid-ratio tables, which read them)
+cudaError_t launch_particle_rows(const LatticeArgs &a, cudaStream_t s);
 cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s);
 int tma_box_width(int storage, int wide);
 int tma_box_rows(int storage);

@@ -635,9 +635,6 @@ __global__ void __launch_bounds__(256) k_force_gather(const LatticeArgs a, const
     a.T[p] = tz;
 }
 
-__device__ __forceinline__ void row_reach(float fx, float loy, float r, int &L, int &H);
-__device__ __forceinline__ void row_full(float fx, float loy, float r, int &L, int &H);
-
 // Per-tile candidate lists: one warp per tile gathers the particles of the 3 x 3
 // surrounding bins whose disk can reach the tile, in ascending id order, then (a lane per
 // tile row) the row masks and the row intervals of the first IVL_CAND candidates.
@@ -669,8 +666,8 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
     }
     __syncwarp();
     // tile row `lane`: which candidates can reach into it (dy_near^2 < r^2, the rounding of
-    // covers()), and the intervals of the first IVL_CAND from the per-row interval search
-    // settled with covers() and fully_covered() themselves
+    // covers()), and the intervals of the first IVL_CAND from k_particle_rows (the per-row
+    // interval search settled with covers() and fully_covered() themselves)
     unsigned rm = 0u;
     for (int s = 0; s < nc; ++s) {
         const PRec P = sh[warp].p[s];
@@ -679,9 +676,15 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
         const float dy = loy > 0.0f ? loy : (hiy < 0.0f ? hiy : 0.0f);
         if (__fmul_rn(dy, dy) < __fmul_rn(P.r, P.r)) rm |= 1u << s;
         if (s < IVL_CAND) {
-            int L, H, L2, H2;
-            row_reach(P.fx, loy, P.r, L, H);
-            row_full(P.fx, loy, P.r, L2, H2);
+            const int dk = lane - P.cj;   // the particle's row (the same loy as above)
+            int L = 1, H = 0, L2 = 1, H2 = 0;
+            if (dk >= -a.tab_h && dk <= a.tab_h) {
+                const char4 iv = a.pivl[(size_t)sh[warp].id[s] * a.tab_w + (dk + a.tab_h)];
+                L = iv.x;
+                H = iv.y;
+                L2 = iv.z;
+                H2 = iv.w;
+            }
             int lo = max(L + P.ci, 0), hi = min(H + P.ci, TILE - 1);
             int lo2 = max(L2 + P.ci, 0), hi2 = min(H2 + P.ci, TILE - 1);
             if (L > H || lo > hi) { lo = 64; hi = -64; }
@@ -745,9 +748,31 @@ __device__ __forceinline__ void row_full(float fx, float loy, float r, int &L, i
 // memory, and the lanes share the list's area evaluations evenly.
 constexpr int EPS_LIST = 256;
 
+// Reached and fully covered cell intervals of every row of a particle's bounding box, a warp per
+// particle and a lane per row (empty rows as [1, 0]).
+__global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_rows(const PRec *__restrict__ prec, int np,
+                                                                  char4 *pivl, int tw, int th) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * EPS_WARPS + warp;
+    if (p >= np) return;
+    const PRec P = prec[p];
+    const int span = (int)ceilf(P.r) + 1;
+    for (int dk0 = -th; dk0 <= th; dk0 += 32) {
+        const int dk = dk0 + lane;
+        if (dk > th) break;
+        int L = 1, H = 0, L2 = 1, H2 = 0;
+        if (dk >= -span && dk <= span) {
+            const float loy = __fsub_rn((float)dk, P.fy);
+            row_reach(P.fx, loy, P.r, L, H);
+            row_full(P.fx, loy, P.r, L2, H2);
+        }
+        pivl[(size_t)p * tw + (dk + th)] = make_char4((signed char)L, (signed char)H, (signed char)L2, (signed char)H2);
+    }
+}
+
 __global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_eps(const PRec *__restrict__ prec, int np,
                                                                  int eps_mode, int n_sub, float *tab, int tw,
-                                                                 int th, int stride) {
+                                                                 int th, int stride, const char4 *__restrict__ pivl) {
     __shared__ short2 s_lst[EPS_WARPS][EPS_LIST];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * EPS_WARPS + warp;
@@ -762,8 +787,13 @@ __global__ void __launch_bounds__(32 * EPS_WARPS) k_particle_eps(const PRec *__r
         const float loy = __fsub_rn((float)dk, P.fy);
         int L = 1, H = 0, L2 = 1, H2 = 0;
         if (dk <= span) {
-            row_reach(P.fx, loy, P.r, L, H);
-            if (exact) row_full(P.fx, loy, P.r, L2, H2);
+            const char4 iv = pivl[(size_t)p * tw + (dk + th)];
+            L = iv.x;
+            H = iv.y;
+            if (exact) {
+                L2 = iv.z;
+                H2 = iv.w;
+            }
         }
         // the row's tabulated cells: [L, H] minus the fully covered run [L2, H2]
         const bool split = L2 <= H2 && L2 >= L && H2 <= H;
@@ -949,7 +979,14 @@ cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_
 cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s) {
     if (a.np == 0) return cudaSuccess;
     k_particle_eps<<<(a.np + EPS_WARPS - 1) / EPS_WARPS, 32 * EPS_WARPS, 0, s>>>(
-        a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h, a.tab_stride);
+        a.prec, a.np, a.eps_mode, a.n_sub, a.eps_tab, a.tab_w, a.tab_h, a.tab_stride, a.pivl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particle_rows(const LatticeArgs &a, cudaStream_t s) {
+    if (a.np == 0) return cudaSuccess;
+    k_particle_rows<<<(a.np + EPS_WARPS - 1) / EPS_WARPS, 32 * EPS_WARPS, 0, s>>>(a.prec, a.np, a.pivl, a.tab_w,
+                                                                                  a.tab_h);
     return cudaGetLastError();
 }
 
