@@ -99,8 +99,10 @@ void imb_default_params(imb_params *p);
 
 /* Create a lattice (Sec. 2.1).  nx, ny >= 3; tau > 1/2 (Eq. 5: nu = (tau - 1/2)/3);
  * C_smag >= 0 is the Smagorinsky constant (0 = plain BGK).  p may be NULL (defaults).
- * Allocates two population buffers of 9 planes [q][ny][pitch] on the current device
- * and initialises them.  *out is set on success. */
+ * Allocates two population buffers of 9 planes on the current device and initialises
+ * them; each plane is a frame of ny + 2 rows (the ghost rows y = -1 and ny) around the
+ * lattice whose ghost cells carry the boundary rules for the pulls of the next step.
+ * *out is set on success. */
 int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, double C_smag,
                      const imb_params *p);
 

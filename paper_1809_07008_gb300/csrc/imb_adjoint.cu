@@ -52,6 +52,8 @@ __global__ void k_adjoint_inlet(float *__restrict__ lam, const float *__restrict
                                 double *g_uin) {
     const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), q = threadIdx.x & 31;
     if (y >= a.ny) return;   // whole warp
+    lam += a.origin;         // node (0, 0) of plane 0 in the frame
+    S1 += a.origin;
     const bool on = q < 9;
     const size_t row = (size_t)y * a.pitch;
     float *l = lam + (size_t)(on ? q : 0) * a.plane + row;
@@ -114,6 +116,9 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const float *__restrict__ 
                                                       float inv_T, double *g_tau) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     double gt = 0.0;
+    lam1 += a.origin;   // node (0, 0) of plane 0 in the frame
+    S0 += a.origin;
+    lam0 += a.origin;
     if (x < a.nx) {
         // adjoint of P(t) at (x, y): who pulled P_q(x, y); and f(t) at (x, y), pulled from
         // P(t-1) (shifted populations d = f - w).  Away from the edges no boundary rule applies.

@@ -31,7 +31,8 @@ struct imb_ctx {
     cudaEvent_t ev_rows = nullptr;               // the particles' row intervals are written
     void *fbuf[2] = {nullptr, nullptr};
     int cur = 0;               // buffer holding the latest post-collision populations
-    size_t plane = 0, elem = 4;
+    size_t plane = 0, origin = 0, elem = 4;
+    int ghost_x = 0;
     // particles
     int np = 0, cap = 0;
     double r_max = 0.0;
@@ -136,6 +137,8 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.bc_x = c->p.bc_x;
     a.bc_y = c->p.bc_y;
     a.plane = c->plane;
+    a.origin = c->origin;
+    a.ghost_x = c->ghost_x;
     a.tau = (float)c->tau;
     a.omega0 = (float)(1.0 / c->tau);
     a.smag_coef = (float)(18.0 * std::sqrt(2.0) * c->C_smag * c->C_smag);
@@ -294,7 +297,7 @@ static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map, int 
     const CUtensorMapDataType dt = c->p.storage == IMB_STORE_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->p.storage == IMB_STORE_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, 9};
+    cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny + 2, 9};   // the whole frame
     cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->elem, (cuuint64_t)c->plane * c->elem};
     cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(c->p.storage), 1};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -336,9 +339,13 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     c->C_smag = C_smag;
     c->p = p;
     cudaGetDevice(&c->device);
-    c->pitch = (nx + 31) / 32 * 32;
-    c->plane = (size_t)c->pitch * ny;
     c->elem = p.storage == IMB_STORE_FP32 ? 4 : 2;
+    // the frame: 128 bytes of ghost columns left of x = 0 (node rows start 128-byte aligned),
+    // the ghost column x = nx and padding up to a multiple of 32 elements, ghost rows -1 and ny
+    c->ghost_x = 128 / (int)c->elem;
+    c->pitch = (c->ghost_x + nx + 1 + 31) / 32 * 32;
+    c->plane = (size_t)c->pitch * (ny + 2);
+    c->origin = (size_t)c->pitch + c->ghost_x;
     c->nbx = (nx + TILE - 1) / TILE;
     c->nby = (ny + TILE - 1) / TILE;
     c->nbins = c->nbx * c->nby;
@@ -370,7 +377,8 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
         (e = cudaEventCreateWithFlags(&c->ev_rows, cudaEventDisableTiming)) != cudaSuccess)
         return bail(e, "side stream");
     for (int b = 0; b < 2; ++b)
-        if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess)
+        if ((e = cudaMalloc(&c->fbuf[b], 9 * c->plane * c->elem)) != cudaSuccess ||
+            (e = cudaMemsetAsync(c->fbuf[b], 0, 9 * c->plane * c->elem, c->stream)) != cudaSuccess)
             return bail(e, "population buffers");
     // bin arrays padded to a multiple of 32 entries (the scan moves 16-byte vectors)
     const int nbins_pad = (c->nbins + 31) / 32 * 32;
@@ -397,9 +405,10 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     LatticeArgs a = lattice_args(c);
     for (int b = 0; b < 2; ++b) {
         if ((e = launch_init_populations(c->fbuf[b], p.storage, a, (float)p.rho0, (float)p.ux0,
-                                         (float)p.uy0, c->stream)) != cudaSuccess)
+                                         (float)p.uy0, c->stream)) != cudaSuccess ||
+            (e = launch_fill_ghosts(c->fbuf[b], p.storage, a, c->stream)) != cudaSuccess)
             return bail(e, "init kernel");
-        c->launches++;
+        c->launches += 2;
     }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e, "init sync");
     *out = c;
@@ -587,11 +596,8 @@ static int lattice_step(imb_ctx *c) {
     CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur][0],
                              &c->tmap[c->cur][1], c->tiles, c->tile_force, c->stream),
        "stream-collide");
-    c->launches++;
-    if (c->np > 0) {
-        CK(launch_force_gather(a, c->tile_force, c->stream), "force gather");
-        c->launches++;
-    }
+    CK(launch_step_tail(c->fbuf[c->cur ^ 1], c->p.storage, a, c->tile_force, c->stream), "forces and ghosts");
+    c->launches += 2;
     if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");
     c->cur ^= 1;
     return IMB_OK;

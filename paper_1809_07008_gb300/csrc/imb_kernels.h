@@ -15,7 +15,12 @@ struct GridBarrier;
 // Everything the lattice kernels read about the lattice and the particles.
 struct LatticeArgs {
     int nx, ny, pitch, bc_x, bc_y;
-    size_t plane;
+    // population buffers: 9 planes of plane elements, each a frame of ny + 2 rows of pitch
+    // elements around the lattice (ghost rows y = -1 and ny, ghost_x columns left of x = 0 and
+    // at least one right of x = nx - 1); node (x, y) of plane q lies at
+    // origin + q plane + y pitch + x from the start of the buffer
+    size_t plane, origin;
+    int ghost_x;
     float tau, omega0;         // relaxation time and 1 / tau
     float smag_coef;           // 18 sqrt(2) C^2 (0 switches the Smagorinsky model off)
     float Fx, Fy;              // body force density (0, 0 = no forcing)
@@ -76,11 +81,15 @@ struct DemArgs {
 cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, float rho0, float ux0,
                                     float uy0, cudaStream_t s);
 // tile_force: [ntiles][TILE_CAND][3] FP64 partial force / torque sums of each tile's candidates
+// the ghost cells of the frame from the edge nodes' populations (after the populations were
+// written other than by the stream-collide kernel, which keeps them itself)
+cudaError_t launch_fill_ghosts(void *f, int storage, const LatticeArgs &a, cudaStream_t s);
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
                                   const TileCand *tiles, double *tile_force, cudaStream_t s);
-// a.F, a.T of every particle = its tiles' partial sums, in a fixed order
-cudaError_t launch_force_gather(const LatticeArgs &a, const double *tile_force, cudaStream_t s);
+// after a stream-collide launch that wrote f: a.F, a.T of every particle = its tiles' partial
+// sums, in a fixed order, and the ghost cells of f
+cudaError_t launch_step_tail(void *f, int storage, const LatticeArgs &a, const double *tile_force, cudaStream_t s);
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s);
 // per particle and row, the reached and fully covered cell intervals (before the tile lists and
 // the solid-ratio tables, which read them)

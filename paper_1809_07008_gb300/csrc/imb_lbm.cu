@@ -27,15 +27,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int BLOCK = 256;            // 8 warps; warp w handles rows w, w+8, w+16, w+24
 constexpr int WARPS = BLOCK / 32;
 
-template <typename S>
-__device__ __forceinline__ void pull_interior(const S *__restrict__ fin, const LatticeArgs &a, int x,
-                                              int y, float (&d)[9]) {
-    const S *base = fin + (size_t)y * a.pitch + x;
-#pragma unroll
-    for (int q = 0; q < 9; ++q)
-        d[q] = Store<S>::ld(base + (size_t)q * a.plane - (ptrdiff_t)cy_of(q) * a.pitch - cx_of(q));
-}
-
 // ------------------------------------------------------ tile prologue
 struct TileShared {
     PRec p[TILE_CAND];
@@ -372,16 +363,18 @@ static_assert(Box<float>::BLOCKS_PER_SM * (Box<float>::SMEM_BYTES + 1024) <= 228
                   Box<__half>::BLOCKS_PER_SM * (Box<__half>::SMEM_BYTES + 1024) <= 228 * 1024,
               "resident blocks per SM fit in shared memory");
 
-__device__ __forceinline__ bool tma_tile(int bx, int by, int nx, int ny) {
-    // every neighbour read of the tile lies inside the lattice: no boundary rule applies
-    return bx >= 1 && by >= 1 && (bx + 1) * TILE <= nx - 1 && (by + 1) * TILE <= ny - 1;
+__device__ __forceinline__ bool tma_tile(int bx, const LatticeArgs &a) {
+    // the frame's ghost cells give every pull of the tile, except at the inlet and outlet
+    // columns, whose nodes are rebuilt from the pulls of their neighbours
+    return a.bc_x != BC_INLET_OUTLET || (bx != 0 && bx != (a.nx - 1) / TILE);
 }
 
 // Persistent fused stream-collide.  Tiles are handed out dynamically (a counter in global
-// memory), so that blocks finish together whatever their mix of interior and boundary
-// tiles.  NST units are staged per block: for interior tiles nine TMA boxes (one per
-// population plane, rows shifted by -c_y) plus the tile's candidate block; boundary tiles
-// take the candidate block only and pull their populations with the boundary rules.  Each
+// memory), so that blocks finish together whatever their mix of tiles.  NST units are
+// staged per block: nine TMA boxes (one per population plane, rows shifted by -c_y, read
+// from the frame whose ghost cells carry the boundary rules) plus the tile's candidate
+// block; the tiles of the inlet and outlet columns take the candidate block only and pull
+// their populations with the boundary rules.  Each
 // warp takes its rows of a unit, collides every node and, where a disk reaches into the
 // row, the immersed nodes of the row with it.  There is no block-wide barrier: the last
 // warp to finish with a stage sums the unit's force partials over the warps (FP64, fixed
@@ -404,6 +397,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     uint64_t *mbar = reinterpret_cast<uint64_t *>(extra + G::EXTRA_BYTES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool smag = a.smag_coef > 0.0f;
+    fin += a.origin;    // node (0, 0) of plane 0
+    fout += a.origin;
 
     for (int i = threadIdx.x; i < G::ACC_FLOATS; i += BLOCK) acc[i] = 0.0f;
     if (threadIdx.x < NST) done[threadIdx.x] = 0;
@@ -437,11 +432,13 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         }
         const int bx = t % a.nbx, by = t / a.nbx;
         stage_tile[st] = make_int4(t, bx, by, h);
-        const bool in = tma_tile(bx, by, a.nx, a.ny);
+        const bool in = tma_tile(bx, a);
         mbar_arrive_expect_tx(&mbar[st], (uint32_t)sizeof(TileCand) + (in ? (uint32_t)G::POP_BYTES : 0u));
         bulk_load(stage_cand(st), &tiles[t], (uint32_t)sizeof(TileCand), &mbar[st]);
         if (in) {
-            const int x0 = bx * TILE, yb = by * TILE + h * HROWS;
+            // frame coordinates: column x + ghost_x, row y + 1 (ghost_x * sizeof(S) = 128 and
+            // HALO * sizeof(S) = 16, so every box starts 16-byte aligned)
+            const int x0 = bx * TILE + a.ghost_x, yb = by * TILE + h * HROWS + 1;
 #pragma unroll
             for (int q = 0; q < 9; ++q)
                 tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
@@ -463,7 +460,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         if (ti.x < 0) break;   // past the last tile (the same value in every warp)
         const int h = ti.w;
         const int x0 = ti.y * TILE, y0 = ti.z * TILE;
-        const bool in = tma_tile(ti.y, ti.z, a.nx, a.ny);
+        const bool in = tma_tile(ti.y, a);
         const TileCand *tc = stage_cand(st);
         const int nc = min(tc->n, TILE_CAND);
         const S *pop = stage_pop(st);
@@ -612,12 +609,10 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     }
 }
 
-// Force and torque of each particle: the sum of its partial sums over the tiles whose
+// Force and torque of particle p: the sum of its partial sums over the tiles whose
 // candidate lists hold it, in a fixed order (the 3 x 3 tiles around its bin, row by row), so
 // that the result does not depend on the order in which the tiles were worked.
-__global__ void __launch_bounds__(256) k_force_gather(const LatticeArgs a, const double *__restrict__ tile_force) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.np) return;
+__device__ __forceinline__ void force_gather(const LatticeArgs &a, const double *__restrict__ tile_force, int p) {
     int e[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) e[j] = a.pslot[9 * p + j];
@@ -837,7 +832,7 @@ __global__ void k_gather(const S *__restrict__ fin, const LatticeArgs a, double 
     const int y = blockIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     float d[9];
-    pull_cell(fin, a, x, y, d);
+    pull_cell(fin + a.origin, a, x, y, d);
     const size_t c = (size_t)y * a.nx + x, nn = (size_t)a.nx * a.ny;
     double r = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
@@ -896,16 +891,53 @@ __global__ void __launch_bounds__(BLOCK) k_cell_map(const LatticeArgs a, int *co
 }
 
 // ---------------------------------------------------------------- init
+// the lattice nodes (the rest of the frame is zero; launch_fill_ghosts follows)
 template <typename S>
 __global__ void k_init(S *f, const LatticeArgs a, float rho0, float ux0, float uy0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= a.pitch || y >= a.ny) return;
+    if (x >= a.nx || y >= a.ny) return;
     float d[9];
     equilibrium_shifted(rho0 - 1.0f, rho0, ux0, uy0, d);
+    f += a.origin;
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
-        Store<S>::st(f + (size_t)q * a.plane + (size_t)y * a.pitch + x, x < a.nx ? d[q] : 0.0f);
+    for (int q = 0; q < 9; ++q) Store<S>::st(f + (size_t)q * a.plane + (size_t)y * a.pitch + x, d[q]);
+}
+
+// the ghost cells of the frame from the stored populations of edge node i: rows 0 and
+// ny - 1, then columns 0 and nx - 1 of the rows between
+__host__ __device__ constexpr int edge_nodes(int nx, int ny) { return 2 * nx + 2 * (ny - 2); }
+
+template <typename S>
+__device__ __forceinline__ void fill_ghosts(S *f, const LatticeArgs &a, int i) {
+    int x, y;
+    if (i < 2 * a.nx) {
+        x = i % a.nx;
+        y = i < a.nx ? 0 : a.ny - 1;
+    } else {
+        const int j = i - 2 * a.nx;
+        x = j < a.ny - 2 ? 0 : a.nx - 1;
+        y = 1 + j % (a.ny - 2);
+    }
+    f += a.origin;
+    float v[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] = Store<S>::ld(f + (size_t)q * a.plane + (size_t)y * a.pitch + x);
+    ghost_store(f, a, x, y, v);
+}
+
+// What follows a stream-collide launch, in one launch: the first nbf blocks gather the
+// particles' forces, the rest fill the ghost cells of the buffer f the launch wrote.
+template <typename S>
+__global__ void __launch_bounds__(256) k_step_tail(const LatticeArgs a, const double *__restrict__ tile_force,
+                                                   S *f, int nbf) {
+    if ((int)blockIdx.x < nbf) {
+        const int p = blockIdx.x * blockDim.x + threadIdx.x;
+        if (p < a.np) force_gather(a, tile_force, p);
+    } else {
+        const int i = (blockIdx.x - nbf) * blockDim.x + threadIdx.x;
+        if (i < edge_nodes(a.nx, a.ny)) fill_ghosts(f, a, i);
+    }
 }
 
 // ------------------------------------------------------------ launchers
@@ -923,10 +955,28 @@ cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, 
                                     float uy0, cudaStream_t s) {
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        dim3 grid((a.pitch + 255) / 256, a.ny);
+        dim3 grid((a.nx + 255) / 256, a.ny);
         k_init<S><<<grid, 256, 0, s>>>((S *)f, a, rho0, ux0, uy0);
         return cudaGetLastError();
     });
+}
+
+static cudaError_t step_tail(void *f, int storage, const LatticeArgs &a, const double *tile_force, int nbf,
+                             cudaStream_t s) {
+    return by_storage(storage, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        const int nbg = (edge_nodes(a.nx, a.ny) + 255) / 256;
+        k_step_tail<S><<<nbf + nbg, 256, 0, s>>>(a, tile_force, (S *)f, nbf);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_fill_ghosts(void *f, int storage, const LatticeArgs &a, cudaStream_t s) {
+    return step_tail(f, storage, a, nullptr, 0, s);
+}
+
+cudaError_t launch_step_tail(void *f, int storage, const LatticeArgs &a, const double *tile_force, cudaStream_t s) {
+    return step_tail(f, storage, a, tile_force, (a.np + 255) / 256, s);
 }
 
 template <typename S, bool FORCED>
@@ -962,12 +1012,6 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
         }
         return cudaGetLastError();
     });
-}
-
-cudaError_t launch_force_gather(const LatticeArgs &a, const double *tile_force, cudaStream_t s) {
-    if (a.np == 0) return cudaSuccess;
-    k_force_gather<<<(a.np + 255) / 256, 256, 0, s>>>(a, tile_force);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_t s) {

@@ -51,9 +51,14 @@ def _run_pair(orc, imb, w, steps, storage="fp32"):
     return o, g
 
 
-@pytest.mark.parametrize("bc", ["channel", "periodic_forced_smag", "closed_box"])
+@pytest.mark.parametrize("bc", ["channel", "periodic_forced_smag", "closed_box", "walls_x_periodic_y"])
 def test_fluid_only_parity(orc, imb, bc):
-    if bc == "channel":
+    # the boundary rules on lattices that are not multiples of the tile (the corners of the
+    # ghost frame: bounce-back, periodic images and their precedence)
+    if bc == "walls_x_periodic_y":
+        w = W.Workload(name="wp", nx=50, ny=37, tau=0.7, bc_x=W.BC_WALL, bc_y=W.BC_PERIODIC,
+                       force=(1e-6, 3e-5), u0=(-0.01, 0.02))
+    elif bc == "channel":
         w = W.Workload(name="ch", nx=70, ny=45, tau=0.6, bc_x=W.BC_INLET_OUTLET, bc_y=W.BC_WALL,
                        u_in=(0.02, 0.0))
     elif bc == "periodic_forced_smag":
@@ -252,6 +257,19 @@ def test_moving_particles_coupled_parity(orc, imb):
     assert np.abs(xo - w.x).max() > 2.0
     assert np.abs(xo - xg).max() < 2e-5
     assert np.abs(vo - vg).max() < 1e-5 * np.abs(vo).max()
+
+
+def test_doubly_periodic_suspension_parity(orc, imb):
+    # moving disks in a box periodic in x and y whose sides are not multiples of the tile: the
+    # flow crosses the periodic images of the ghost frame, corners included, with gradients
+    w = W.c3sub(steps=0, nx=200, ny=150).with_(bc_y=W.BC_PERIODIC)
+    o, g = _run_pair(orc, imb, w, 300)
+    mask = _fluid_mask(o)
+    assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
+    Fo, To = o.forces()
+    Fg, Tg = g.forces()
+    errF, errT = _force_ok(Fg, Tg, Fo, To, w.r)
+    assert errF < 1e-4 and errT < 1e-4
 
 
 def test_collapse_stack_coupled_parity(orc, imb):
