@@ -460,6 +460,11 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
     }
     if (c->p.dem_on && 2.0 * rmax + c->p.skin > (double)TILE)
         return fail(c, IMB_E_INVALID_ARG, "DEM needs 2 r_max + skin <= 32 cells");
+    {   // the tile blocks address the solid-ratio tables with 32-bit offsets
+        const long long tw = 2 * ((long long)std::ceil(rmax) + 1) + 1;
+        if ((long long)n * tw * tw >= (1ll << 31))
+            return fail(c, IMB_E_INVALID_ARG, "n (2 ceil(r_max) + 3)^2 must stay below 2^31 (solid-ratio tables)");
+    }
     // a periodic axis must be long enough that a tile sees a single image of a disk
     if (n > 0 && ((c->p.bc_x == IMB_BC_PERIODIC && c->nx < 2.0 * (TILE + rmax + 2.0)) ||
                   (c->p.bc_y == IMB_BC_PERIODIC && c->ny < 2.0 * (TILE + rmax + 2.0))))

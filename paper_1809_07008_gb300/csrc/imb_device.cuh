@@ -73,7 +73,9 @@ struct __align__(16) PRec {
 constexpr int IVL_CAND = 4;     // candidates whose per-row cell intervals a tile block carries
 
 // Particles that can reach one 32 x 32 tile, ascending id (built by k_tile_lists,
-// bulk-copied into shared memory by the stream-collide kernel).  For each tile row, the
+// bulk-copied into shared memory by the stream-collide kernel), with the offset of each
+// one's solid-ratio table such that eps_tab[eoff + yy tab_w + xl] is the entry of tile node
+// (xl, yy) (32-bit: n tab_w^2 < 2^31 is checked when the particles are set).  For each tile row, the
 // candidates that can reach into it, and for the first IVL_CAND candidates the columns
 // (tile-relative) of the row's cells the disk reaches into, [x, y], and covers whole, [z, w]
 // (empty when the lower end exceeds the upper): the same decisions as covers() and
@@ -81,7 +83,7 @@ constexpr int IVL_CAND = 4;     // candidates whose per-row cell intervals a til
 struct __align__(16) TileCand {
     int n;
     int pad[3];
-    int id[TILE_CAND];
+    int eoff[TILE_CAND];
     PRec p[TILE_CAND];
     unsigned rowmask[TILE];
     char4 ivl[IVL_CAND][TILE];

@@ -174,15 +174,6 @@ __device__ void tile_candidates(const LatticeArgs &a, int bx, int by, TileShared
 }
 
 // ------------------------------------------------- fused stream-collide
-// Solid ratio of a node that candidate P is known to reach into (covers() true):
-// 1 when the cell is fully covered in exact-area mode, else the value k_particle_eps
-// stored for this particle and offset.
-__device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const float *__restrict__ tab, int tw,
-                                          int th, bool exact) {
-    if (exact && fully_covered(__fsub_rn((float)di, P.fx), __fsub_rn((float)dk, P.fy), P.r)) return 1.0f;
-    return __ldg(tab + (dk + th) * tw + (di + th));
-}
-
 // Immersed moving boundary on one row of a warp (Sec. 2.3).  Bit s of `cm` is set when
 // tile candidate s reaches into the lane's node, `rowc` is the union of cm over the warp
 // (non-zero: the caller tests it), e0 the solid ratio of the lane's first candidate
@@ -194,17 +185,20 @@ __device__ __forceinline__ float slot_eps(const PRec &P, int di, int dk, const f
 // added to the warp's column of the tile's partials acc_w[(3 s + c) * WARPS].
 // solid ratio of tile candidate s at node (xl, yy) from the particle's table (a cell the disk
 // covers in part, or any covered cell in the cell-decomposition mode)
-__device__ __forceinline__ float cand_table_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
-                                                int s, int xl, int yy, const LatticeArgs &a) {
-    const PRec &P = cand[s];
-    return __ldg(a.eps_tab + (size_t)cid[s] * a.tab_stride + (yy - P.cj + a.tab_h) * a.tab_w + (xl - P.ci + a.tab_h));
+__device__ __forceinline__ float cand_table_eps(const int *__restrict__ eoff, int s, int xl, int yy,
+                                                const LatticeArgs &a) {
+    return __ldg(a.eps_tab + (eoff[s] + yy * a.tab_w + xl));
 }
 
-__device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, const int *__restrict__ cid,
+// Solid ratio of a node that candidate s is known to reach into (covers() true): 1 when the
+// cell is fully covered in exact-area mode, else the value k_particle_eps stored for it.
+__device__ __forceinline__ float cand_slot_eps(const PRec *__restrict__ cand, const int *__restrict__ eoff,
                                                int s, int xl, int yy, const LatticeArgs &a) {
     const PRec &P = cand[s];
-    return slot_eps(P, xl - P.ci, yy - P.cj, a.eps_tab + (size_t)cid[s] * a.tab_stride, a.tab_w, a.tab_h,
-                    a.eps_mode == EPS_EXACT);
+    if (a.eps_mode == EPS_EXACT &&
+        fully_covered(__fsub_rn((float)(xl - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
+        return 1.0f;
+    return cand_table_eps(eoff, s, xl, yy, a);
 }
 
 // force and torque terms of one node and particle (Eq. 15 per cell: -Bp sum_i Omega^s_i c_i =
@@ -254,7 +248,7 @@ __device__ __forceinline__ void add_terms(const int s, float vx, float vy, float
 template <bool FORCED>
 __device__ __forceinline__ void row_imb(const NodeState &c, const int xl, const int yy, const unsigned cm,
                                         const unsigned rowc, const float e0, const PRec *__restrict__ cand,
-                                        const int *__restrict__ cid, const int ka, const int kb,
+                                        const int *__restrict__ eoff, const int ka, const int kb,
                                         float (&fa)[3], float (&fb)[3], float *__restrict__ acc_w,
                                         const LatticeArgs &a, SolidMoments &sm) {
     sm.B = sm.m1x = sm.m1y = sm.m2xx = sm.m2xy = sm.m2yy = 0.0f;
@@ -275,7 +269,7 @@ __device__ __forceinline__ void row_imb(const NodeState &c, const int xl, const 
     if (__popc(cm) > MAX_SLOTS) set_err(a.err, ERR_CELL_SLOTS);
     const int s0 = cm ? __ffs(cm) - 1 : 0;
     float esum = e0;   // summed in slot order
-    for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += cand_slot_eps(cand, cid, __ffs(m) - 1, xl, yy, a);
+    for (unsigned m = cm & (cm - 1u); m; m &= m - 1u) esum += cand_slot_eps(cand, eoff, __ffs(m) - 1, xl, yy, a);
     if (esum > 0.0f) {
         const float eps = fminf(esum, 1.0f);
         sm.B = __fdividef(eps * tm, (1.0f - eps) + tm);       // Eq. 14
@@ -286,7 +280,7 @@ __device__ __forceinline__ void row_imb(const NodeState &c, const int xl, const 
         float vx = 0.0f, vy = 0.0f, vt = 0.0f;
         if (((cm >> s) & 1u) && Bs > 0.0f) {
             const PRec &P = cand[s];
-            const float Bp = Bs * (s == s0 ? e0 : cand_slot_eps(cand, cid, s, xl, yy, a));
+            const float Bp = Bs * (s == s0 ? e0 : cand_slot_eps(cand, eoff, s, xl, yy, a));
             node_particle<FORCED>(c, P, xl - P.ci, yy - P.cj, Bp, a, sm, vx, vy, vt);
         }
         add_terms(s, vx, vy, vt, ka, kb, fa, fb, acc_w);
@@ -485,8 +479,11 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                         fm |= (unsigned)(lane >= iv.z && lane <= iv.w) << s;
                     } else {
                         const PRec &P = tc->p[s];
-                        if (covers(__fsub_rn((float)(lane - P.ci), P.fx), __fsub_rn((float)(yy - P.cj), P.fy), P.r))
+                        const float lox = __fsub_rn((float)(lane - P.ci), P.fx), loy = __fsub_rn((float)(yy - P.cj), P.fy);
+                        if (covers(lox, loy, P.r)) {
                             cm |= 1u << s;
+                            if (fully_covered(lox, loy, P.r)) fm |= 1u << s;
+                        }
                     }
                 }
                 if (!xin) cm = 0u;
@@ -495,10 +492,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
             else cmr[rr] = cm;
             const int s0 = cm ? __ffs(cm) - 1 : 0;
             e0r[rr] = !cm ? 0.0f
-                          : s0 >= IVL_CAND ? cand_slot_eps(tc->p, tc->id, s0, lane, yy, a)
-                                           : (a.eps_mode == EPS_EXACT && ((fm >> s0) & 1u))
-                                                 ? 1.0f
-                                                 : cand_table_eps(tc->p, tc->id, s0, lane, yy, a);
+                          : (a.eps_mode == EPS_EXACT && ((fm >> s0) & 1u)) ? 1.0f
+                                                                          : cand_table_eps(tc->eoff, s0, lane, yy, a);
             const unsigned rowc = __reduce_or_sync(FULL, cm);
             if (!G::MASKS_IN_SMEM) rowcr[rr] = rowc;
             uni |= rowc;
@@ -551,7 +546,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 }
             } else {
                 SolidMoments sm;
-                row_imb<FORCED>(c, lane, yy, cm, rowc, e0, tc->p, tc->id, ka, kb, fa, fb, acc_t + warp, a, sm);
+                row_imb<FORCED>(c, lane, yy, cm, rowc, e0, tc->p, tc->eoff, ka, kb, fa, fb, acc_t + warp, a, sm);
                 if (xin) node_collide_store<S, true, FORCED>(d, c, sm, fout + (size_t)y * a.pitch + x, a);
             }
         }
@@ -650,7 +645,8 @@ __global__ void __launch_bounds__(256) k_tile_lists(const LatticeArgs a, TileCan
         P.ci = TILE / 2 - wrap_rel(xc - P.ci, a.nx, a.bc_x == BC_PERIODIC);
         P.cj = TILE / 2 - wrap_rel(yc - P.cj, a.ny, a.bc_y == BC_PERIODIC);
         const int pid = sh[warp].id[lane];
-        out->id[lane] = pid;
+        // the solid-ratio table entry of tile node (xl, yy) is eps_tab[eoff + yy tab_w + xl]
+        out->eoff[lane] = pid * a.tab_stride + (a.tab_h - P.cj) * a.tab_w + (a.tab_h - P.ci);
         out->p[lane] = P;
         sh[warp].p[lane] = P;
         // the particle's entry for this tile: its place among the 3 x 3 tiles around its bin
