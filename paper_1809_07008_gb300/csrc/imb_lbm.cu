@@ -259,7 +259,7 @@ __device__ __forceinline__ void row_imb(const NodeState &c, const int xl, const 
         const int s = __ffs(rowc) - 1;
         const float eps = fminf(e0, 1.0f);
         sm.B = e0 > 0.0f ? __fdividef(eps * tm, (1.0f - eps) + tm) : 0.0f;   // Eq. 14
-        const float Bp = e0 > 0.0f ? __fdividef(sm.B, e0) * e0 : 0.0f;
+        const float Bp = sm.B;   // B_p = B eps_p / sum eps with a single particle
         const PRec &P = cand[s];
         float vx, vy, vt;
         node_particle<FORCED>(c, P, xl - P.ci, yy - P.cj, Bp, a, sm, vx, vy, vt);
@@ -336,7 +336,10 @@ template <typename S> struct Box {
     static constexpr int POP_BYTES = offset(9) * (int)sizeof(S);
     static constexpr int STAGE_BYTES = (POP_BYTES + (int)sizeof(TileCand) + 127) / 128 * 128;
     // force partials of the block's last NACC tiles: [tile slot][candidate][component][warp]
-    static constexpr int NACC = 3;
+    // a warp runs at most NST - 1 units ahead of the slowest, so at most two tiles are open at a
+    // time; a tile's partials are flushed before the copies of the unit that takes over its
+    // stage are issued, so the tile two ahead finds its slot cleared
+    static constexpr int NACC = 2;
     static constexpr int ACC_FLOATS = NACC * TILE_CAND * 3 * WARPS;
     // partials, the tile of each stage (index, column, row, unit), warps done per stage,
     // the producer's state (units issued, tile of the unit group, next tile, end reached)
@@ -558,9 +561,9 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 if (s >= 0) acc_t[(3 * s + j % 3) * WARPS + warp] += v;
             }
         }
-        // hand the stage back: the last warp to finish with it starts the copies of the unit
-        // NST ahead into it and, after the last unit of a tile, sums the tile's partials over
-        // the warps (FP64, fixed order) into the tile's force sums
+        // hand the stage back: the last warp to finish with it, after the last unit of a tile,
+        // sums the tile's partials over the warps (FP64, fixed order) into the tile's force
+        // sums, then starts the copies of the unit NST ahead into the stage
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -569,11 +572,6 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         }
         if (__shfl_sync(FULL, last, 0)) {
             __threadfence_block();
-            if (lane == 0) {
-                done[st] = 0;
-                fence_proxy_async_smem();
-                issue_next();
-            }
             if (h == UPT - 1) {
                 double *tf = tile_force + (size_t)ti.x * (TILE_CAND * 3);
                 for (int i = lane; i < nc * 3; i += 32) {
@@ -586,6 +584,12 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                     }
                     tf[i] = v;
                 }
+            }
+            __syncwarp();
+            if (lane == 0) {   // after the flush: the unit issued here may open the tile that reuses the slot
+                done[st] = 0;
+                fence_proxy_async_smem();
+                issue_next();
             }
             __syncwarp();
         }
