@@ -88,6 +88,12 @@ typedef struct imb_params {
                             from e_rest); E* = E / (2 (1 - nu^2)), G* = E / (4 (2 - nu)(1 + nu)),
                             walls of the same material; mu caps the tangential force           */
     double E_young, nu_poisson; /* Hertz-Mindlin material (E > 0, 0 <= nu < 1/2)               */
+    int work_units;      /* stream-collide work: 0 (default) chooses units of eight rows, one per
+                            thread block, when all of them fit on the GPU at once (lattices of
+                            up to about 114 tiles of 32 x 32), else tiles handed out to a
+                            persistent grid; 1 always the persistent tiles, 2 always the
+                            eight-row units.  Same results either way, to rounding of the
+                            force sums (each unit keeps its own partials)                      */
 } imb_params;
 
 typedef struct imb_ctx imb_ctx;

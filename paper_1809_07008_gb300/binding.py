@@ -93,7 +93,8 @@ class Params(C.Structure):
                 ("ct_ratio", C.c_double), ("mu", C.c_double), ("rho_s", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double), ("skin", C.c_double),
                 ("timeout_ms", C.c_int), ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double),
-                ("contact_model", C.c_int), ("E_young", C.c_double), ("nu_poisson", C.c_double)]
+                ("contact_model", C.c_int), ("E_young", C.c_double), ("nu_poisson", C.c_double),
+                ("work_units", C.c_int)]
 
 
 _lib = None

@@ -67,6 +67,7 @@ struct imb_ctx {
     size_t pivl_cap = 0;
     int tab_w = 0, tab_h = 0;
     CUtensorMap tmap[2][2];         // TMA descriptors [buffer][narrow, wide] of the populations
+    bool small = false;             // units of eight rows, one per block (all fit on the device at once)
     // parameters derived on the host
     double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
     double hm_kn0 = 0.0, hm_sn0 = 0.0, hm_kt0 = 0.0, hm_c0 = 0.0;   // Hertz-Mindlin constants
@@ -167,6 +168,7 @@ static LatticeArgs lattice_args(const imb_ctx *c) {
     a.pbin = c->pbin;
     a.pslot = c->pslot;
     a.pivl = c->pivl;
+    a.tf_units = c->small ? SMALL_UPT : 1;
     return a;
 }
 
@@ -299,7 +301,8 @@ static cudaError_t make_tensor_map(imb_ctx *c, void *buf, CUtensorMap *map, int 
                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny + 2, 9};   // the whole frame
     cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->elem, (cuuint64_t)c->plane * c->elem};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(c->p.storage), 1};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_width(c->p.storage, wide), (cuuint32_t)tma_box_rows(c->p.storage, c->small),
+                         1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(map, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -330,6 +333,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
          !(p.E_young > 0.0 && p.nu_poisson >= 0.0 && p.nu_poisson < 0.5)))
         return fail(nullptr, IMB_E_INVALID_ARG, "bad contact model or Hertz-Mindlin material");
     if (p.timeout_ms <= 0) p.timeout_ms = 60000;
+    if (p.work_units < 0 || p.work_units > 2) return fail(nullptr, IMB_E_INVALID_ARG, "work_units must be 0, 1 or 2");
     if ((long long)nx * ny > (1ll << 31) / 16) return fail(nullptr, IMB_E_INVALID_ARG, "lattice too large");
 
     imb_ctx *c = new imb_ctx();
@@ -349,6 +353,9 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     c->nbx = (nx + TILE - 1) / TILE;
     c->nby = (ny + TILE - 1) / TILE;
     c->nbins = c->nbx * c->nby;
+    // a lattice whose eight-row units all fit on the device at once takes one per block
+    c->small = p.work_units == 2 ||
+               (p.work_units == 0 && (long long)c->nbins * SMALL_UPT <= stream_collide_resident_blocks(p.storage));
     const double le = std::log(p.e_rest);
     c->zeta = -le / std::sqrt(M_PI * M_PI + le * le);
     {   // identical materials: E* = E / (2 (1 - nu^2)), G* = E / (4 (2 - nu)(1 + nu))
@@ -386,7 +393,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
         (e = dalloc(&c->bin_start, nbins_pad + 32)) != cudaSuccess || (e = dalloc(&c->counters, 8)) != cudaSuccess ||
         (e = dalloc(&c->barrier, 1)) != cudaSuccess || (e = dalloc(&c->err, 1)) != cudaSuccess ||
         (e = dalloc(&c->tile_ctr, 2)) != cudaSuccess || (e = dalloc(&c->tiles, c->nbins)) != cudaSuccess ||
-        (e = dalloc(&c->tile_force, (size_t)c->nbins * TILE_CAND * 3)) != cudaSuccess ||
+        (e = dalloc(&c->tile_force, (size_t)c->nbins * TILE_CAND * 3 * (c->small ? SMALL_UPT : 1))) != cudaSuccess ||
         (e = cudaMallocHost((void **)&c->h_err, sizeof(unsigned))) != cudaSuccess ||
         (e = dalloc(&c->bin_bsum, c->nbins / 1024 + 1)) != cudaSuccess)
         return bail(e, "bookkeeping buffers");
@@ -599,7 +606,7 @@ static int lattice_step(imb_ctx *c) {
         CK(cudaEventRecord(e0, c->stream), "event record");
     }
     CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur][0],
-                             &c->tmap[c->cur][1], c->tiles, c->tile_force, c->stream),
+                             &c->tmap[c->cur][1], c->tiles, c->tile_force, c->small, c->stream),
        "stream-collide");
     CK(launch_step_tail(c->fbuf[c->cur ^ 1], c->p.storage, a, c->tile_force, c->stream), "forces and ghosts");
     c->launches += 2;

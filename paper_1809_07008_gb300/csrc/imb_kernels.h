@@ -43,7 +43,11 @@ struct LatticeArgs {
                                // reaches into, [x, y], and covers whole, [z, w] (exact-area mode)
     int *pslot;                // [np][9] tile * TILE_CAND + slot of the particle in the candidate lists of the
                                // 3 x 3 tiles around its bin (row by row), -1 where it is not a candidate
+    int tf_units;              // force partials per tile: 1, or SMALL_UPT when each work unit keeps its own
 };
+
+// work units per tile of the small-lattice stream-collide (units of eight rows, one per block)
+constexpr int SMALL_UPT = 4;
 
 // DEM state and parameters (FP64).
 struct DemArgs {
@@ -84,9 +88,11 @@ cudaError_t launch_init_populations(void *f, int storage, const LatticeArgs &a, 
 // the ghost cells of the frame from the edge nodes' populations (after the populations were
 // written other than by the stream-collide kernel, which keeps them itself)
 cudaError_t launch_fill_ghosts(void *f, int storage, const LatticeArgs &a, cudaStream_t s);
+// small: one eight-row unit per block (a.tf_units == SMALL_UPT, tensor maps with boxes of
+// tma_box_rows(storage, true) rows)
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
-                                  const TileCand *tiles, double *tile_force, cudaStream_t s);
+                                  const TileCand *tiles, double *tile_force, bool small, cudaStream_t s);
 // after a stream-collide launch that wrote f: a.F, a.T of every particle = its tiles' partial
 // sums, in a fixed order, and the ghost cells of f
 cudaError_t launch_step_tail(void *f, int storage, const LatticeArgs &a, const double *tile_force, cudaStream_t s);
@@ -96,7 +102,9 @@ cudaError_t launch_tile_lists(const LatticeArgs &a, TileCand *tiles, cudaStream_
 cudaError_t launch_particle_rows(const LatticeArgs &a, cudaStream_t s);
 cudaError_t launch_particle_eps(const LatticeArgs &a, cudaStream_t s);
 int tma_box_width(int storage, int wide);
-int tma_box_rows(int storage);
+int tma_box_rows(int storage, bool small);
+// blocks of the stream-collide kernel resident on the current device at once
+int stream_collide_resident_blocks(int storage);
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s);
 cudaError_t launch_cell_map(const LatticeArgs &a, int *count, int *ids, float *eps, cudaStream_t s);

@@ -314,13 +314,15 @@ __device__ __forceinline__ float warp_sum6(const float (&fa)[3], const float (&f
 // per block, so that while the warps work on one, the others are loading.  TMA boxes: the
 // x start must be 16-byte aligned, so the six planes pulled from x - 1 or x + 1 (c_x = +-1)
 // take a box HALO cells wider than the tile (starting HALO cells left of the tile for
-// c_x = +1), the three with c_x = 0 exactly the tile width.
-template <typename S> struct Box {
-    static constexpr int HROWS = sizeof(S) == 4 ? 16 : 32;  // rows per work unit
+// c_x = +1), the three with c_x = 0 exactly the tile width.  SMALL: lattices whose units of
+// eight rows all fit on the device at once take one such unit per block (no tile counter,
+// one stage, the force partials of every unit kept apart).
+template <typename S, bool SMALL = false> struct Box {
+    static constexpr int HROWS = SMALL ? WARPS : sizeof(S) == 4 ? 16 : 32;   // rows per work unit
     static constexpr int UPT = TILE / HROWS;                 // work units per tile
     static constexpr int RPW = HROWS / WARPS;                // rows per warp per unit
     static constexpr int HALO = 16 / (int)sizeof(S);
-    static constexpr int NST = sizeof(S) == 4 ? 3 : 2;       // stages per block
+    static constexpr int NST = SMALL ? 1 : sizeof(S) == 4 ? 3 : 2;   // stages per block
     static constexpr int BLOCKS_PER_SM = 3;
     static constexpr int WN = TILE, WW = TILE + HALO;
     __host__ __device__ static constexpr int width(int q) { return cx_of(q) == 0 ? WN : WW; }
@@ -339,7 +341,7 @@ template <typename S> struct Box {
     // a warp runs at most NST - 1 units ahead of the slowest, so at most two tiles are open at a
     // time; a tile's partials are flushed before the copies of the unit that takes over its
     // stage are issued, so the tile two ahead finds its slot cleared
-    static constexpr int NACC = 2;
+    static constexpr int NACC = SMALL ? 1 : 2;
     static constexpr int ACC_FLOATS = NACC * TILE_CAND * 3 * WARPS;
     // partials, the tile of each stage (index, column, row, unit), warps done per stage,
     // the producer's state (units issued, tile of the unit group, next tile, end reached)
@@ -359,6 +361,10 @@ static_assert(Box<float>::EXTRA_BYTES % 8 == 0 && Box<__half>::EXTRA_BYTES % 8 =
 static_assert(Box<float>::BLOCKS_PER_SM * (Box<float>::SMEM_BYTES + 1024) <= 228 * 1024 &&
                   Box<__half>::BLOCKS_PER_SM * (Box<__half>::SMEM_BYTES + 1024) <= 228 * 1024,
               "resident blocks per SM fit in shared memory");
+static_assert((Box<float, true>::WW * Box<float, true>::HROWS * 4) % 128 == 0 &&
+                  (Box<__half, true>::WW * Box<__half, true>::HROWS * 2) % 128 == 0 &&
+                  Box<float, true>::UPT == Box<__half, true>::UPT && Box<float, true>::UPT == SMALL_UPT,
+              "small-lattice boxes stay 128-byte aligned; its units per tile");
 
 __device__ __forceinline__ bool tma_tile(int bx, const LatticeArgs &a) {
     // the frame's ghost cells give every pull of the tile, except at the inlet and outlet
@@ -377,12 +383,12 @@ __device__ __forceinline__ bool tma_tile(int bx, const LatticeArgs &a) {
 // warp to finish with a stage sums the unit's force partials over the warps (FP64, fixed
 // order) into the tile's partial sums, hands the stage back to the copy engine and starts
 // the next unit's copies, so warps run up to NST - 1 units apart.
-template <typename S, bool FORCED>
-__global__ void __launch_bounds__(BLOCK, Box<S>::BLOCKS_PER_SM)
+template <typename S, bool FORCED, bool SMALL>
+__global__ void __launch_bounds__(BLOCK, Box<S, SMALL>::BLOCKS_PER_SM)
 k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_constant__ CUtensorMap tmap_w,
                  const S *__restrict__ fin, S *__restrict__ fout, const LatticeArgs a,
                  const TileCand *__restrict__ tiles, const int ntiles, double *__restrict__ tile_force) {
-    using G = Box<S>;
+    using G = Box<S, SMALL>;
     constexpr int NST = G::NST, HROWS = G::HROWS, UPT = G::UPT, RPW = G::RPW;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *extra = smem + NST * G::STAGE_BYTES;
@@ -404,7 +410,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         fence_mbar_init();
         prod[0] = 0;
         prod[3] = 0;
-        prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // tiles are taken one ahead
+        if (!SMALL) prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // tiles are taken one ahead
     }
     __syncthreads();
 
@@ -417,10 +423,18 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     // marker, and nothing more is issued.
     auto issue_next = [&]() {
         if (prod[3]) return;
-        const int u = prod[0], st = u % NST, h = u % UPT;
+        const int u = prod[0], st = u % NST;
         prod[0] = u + 1;
-        if (h == 0) prod[1] = prod[2];
-        const int t = prod[1];
+        int t, h;
+        if (SMALL) {   // the block's one unit
+            const int unit = u == 0 ? (int)blockIdx.x : ntiles * UPT;
+            t = unit / UPT;
+            h = unit % UPT;
+        } else {
+            h = u % UPT;
+            if (h == 0) prod[1] = prod[2];
+            t = prod[1];
+        }
         if (t >= ntiles) {
             prod[3] = 1;
             stage_tile[st] = make_int4(-1, 0, 0, 0);
@@ -441,7 +455,7 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
                 tma_load_3d(stage_pop(st) + G::offset(q), cx_of(q) == 0 ? (const void *)&tmap_n : (const void *)&tmap_w,
                             cx_of(q) == 1 ? x0 - G::HALO : x0, yb - cy_of(q), q, &mbar[st]);
         }
-        if (h == 0) prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // after the copies are on their way
+        if (!SMALL && h == 0) prod[2] = (int)atomicAdd(&a.tile_ctr[0], 1u);   // after the copies are on their way
     };
     if (threadIdx.x == 0)
         for (int k = 0; k < NST; ++k) issue_next();
@@ -572,8 +586,8 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         }
         if (__shfl_sync(FULL, last, 0)) {
             __threadfence_block();
-            if (h == UPT - 1) {
-                double *tf = tile_force + (size_t)ti.x * (TILE_CAND * 3);
+            if (SMALL || h == UPT - 1) {   // small lattices: the partials of each unit apart
+                double *tf = tile_force + ((size_t)ti.x * (SMALL ? UPT : 1) + (SMALL ? h : 0)) * (TILE_CAND * 3);
                 for (int i = lane; i < nc * 3; i += 32) {
                     float *pa = acc_t + i * WARPS;
                     double v = 0.0;
@@ -618,11 +632,14 @@ __device__ __forceinline__ void force_gather(const LatticeArgs &a, const double 
     double fx = 0.0, fy = 0.0, tz = 0.0;
 #pragma unroll
     for (int j = 0; j < 9; ++j)
-        if (e[j] >= 0) {
-            const double *tf = tile_force + (size_t)e[j] * 3;
-            fx += tf[0];
-            fy += tf[1];
-            tz += tf[2];
+        if (e[j] >= 0) {   // entry tile * TILE_CAND + slot; tf_units partial sets per tile
+            const int t = e[j] / TILE_CAND, sl = e[j] % TILE_CAND;
+            for (int v = 0; v < a.tf_units; ++v) {
+                const double *tf = tile_force + (((size_t)t * a.tf_units + v) * TILE_CAND + sl) * 3;
+                fx += tf[0];
+                fy += tf[1];
+                tz += tf[2];
+            }
         }
     a.F[2 * p] = fx;
     a.F[2 * p + 1] = fy;
@@ -979,37 +996,55 @@ cudaError_t launch_step_tail(void *f, int storage, const LatticeArgs &a, const d
     return step_tail(f, storage, a, tile_force, (a.np + 255) / 256, s);
 }
 
-template <typename S, bool FORCED>
-static int stream_collide_grid(int ntiles) {
-    static int per_sm = -1, sms = 0;
+template <typename S, bool FORCED, bool SMALL>
+static int stream_collide_per_sm() {
+    static int per_sm = -1;   // one device per process
     if (per_sm < 0) {
-        cudaFuncSetAttribute(k_stream_collide<S, FORCED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Box<S>::SMEM_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<S, FORCED>, BLOCK,
-                                                      Box<S>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_stream_collide<S, FORCED, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Box<S, SMALL>::SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide<S, FORCED, SMALL>, BLOCK,
+                                                      Box<S, SMALL>::SMEM_BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm;
+}
+
+static int device_sms() {
+    static int sms = 0;
+    if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (per_sm < 1) per_sm = 1;
     }
-    return std::min(ntiles, per_sm * sms);
+    return sms;
+}
+
+int stream_collide_resident_blocks(int storage) {
+    const int per_sm = storage == 0 ? stream_collide_per_sm<float, false, false>()
+                                    : stream_collide_per_sm<__half, false, false>();
+    return per_sm * device_sms();
 }
 
 cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, const LatticeArgs &a,
                                   const CUtensorMap *tmap_narrow, const CUtensorMap *tmap_wide,
-                                  const TileCand *tiles, double *tile_force, cudaStream_t s) {
+                                  const TileCand *tiles, double *tile_force, bool small, cudaStream_t s) {
     const int ntiles = a.nbx * a.nby;
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        if (a.Fx != 0.0f || a.Fy != 0.0f) {
-            const int grid = stream_collide_grid<S, true>(ntiles);
-            k_stream_collide<S, true><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(
+        auto go = [&](auto forced, auto sm) {
+            constexpr bool F = decltype(forced)::value, SM = decltype(sm)::value;
+            // small lattices: one unit per block; else a persistent grid over the tiles
+            const int grid = SM ? ntiles * Box<S, true>::UPT
+                                : std::min(ntiles, stream_collide_per_sm<S, F, false>() * device_sms());
+            if (SM) stream_collide_per_sm<S, F, true>();   // sets the shared-memory attribute
+            k_stream_collide<S, F, SM><<<grid, BLOCK, Box<S, SM>::SMEM_BYTES, s>>>(
                 *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
-        } else {
-            const int grid = stream_collide_grid<S, false>(ntiles);
-            k_stream_collide<S, false><<<grid, BLOCK, Box<S>::SMEM_BYTES, s>>>(
-                *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
-        }
+        };
+        const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
+        if (forced && small) go(std::true_type{}, std::true_type{});
+        else if (forced) go(std::true_type{}, std::false_type{});
+        else if (small) go(std::false_type{}, std::true_type{});
+        else go(std::false_type{}, std::false_type{});
         return cudaGetLastError();
     });
 }
@@ -1038,7 +1073,10 @@ int tma_box_width(int storage, int wide) {
     if (storage == 0) return wide ? Box<float>::WW : Box<float>::WN;
     return wide ? Box<__half>::WW : Box<__half>::WN;
 }
-int tma_box_rows(int storage) { return storage == 0 ? Box<float>::HROWS : Box<__half>::HROWS; }
+int tma_box_rows(int storage, bool small) {
+    if (small) return Box<float, true>::HROWS;
+    return storage == 0 ? Box<float>::HROWS : Box<__half>::HROWS;
+}
 
 cudaError_t launch_gather(const void *fin, int storage, const LatticeArgs &a, double *f_out,
                           double *rho, double *ux, double *uy, cudaStream_t s) {

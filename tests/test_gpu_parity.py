@@ -43,16 +43,21 @@ def _force_ok(Fg, Tg, Fo, To, r, tol=1e-4):
     return errF, errT
 
 
-def _run_pair(orc, imb, w, steps, storage="fp32"):
+def _run_pair(orc, imb, w, steps, storage="fp32", **kw):
     o = orc.Sim(w)
-    g = imb.Lattice.from_workload(w, storage=storage)
+    g = imb.Lattice.from_workload(w, storage=storage, **kw)
     o.step(steps)
     g.step(steps)
     return o, g
 
 
+# work units: 1 = tiles handed out to a persistent grid, 2 = eight-row units, one per block
+UNITS = [1, 2]
+
+
+@pytest.mark.parametrize("units", UNITS)
 @pytest.mark.parametrize("bc", ["channel", "periodic_forced_smag", "closed_box", "walls_x_periodic_y"])
-def test_fluid_only_parity(orc, imb, bc):
+def test_fluid_only_parity(orc, imb, bc, units):
     # the boundary rules on lattices that are not multiples of the tile (the corners of the
     # ghost frame: bounce-back, periodic images and their precedence)
     if bc == "walls_x_periodic_y":
@@ -67,7 +72,7 @@ def test_fluid_only_parity(orc, imb, bc):
     else:
         w = W.Workload(name="box", nx=64, ny=33, tau=0.8, bc_x=W.BC_WALL, bc_y=W.BC_WALL,
                        u0=(0.03, -0.02))
-    o, g = _run_pair(orc, imb, w, 300)
+    o, g = _run_pair(orc, imb, w, 300, work_units=units)
     fo, fg = o.f(), g.populations()
     assert np.abs(fg - fo).max() < 1e-6
     mask = np.ones(o.shape, bool)
@@ -82,10 +87,11 @@ def test_initial_state_and_readback(orc, imb):
     assert np.abs(g.populations() - o.f()).max() < 2e-7
 
 
-def test_channel_disk_c1_parity(orc, imb):
+@pytest.mark.parametrize("units", UNITS)
+def test_channel_disk_c1_parity(orc, imb, units):
     # 200 x 100 channel, fixed disk d = 20 at the centre, u_in = 0.01, tau = 0.6 (2000 steps)
     w = W.c1(steps=2000)
-    o, g = _run_pair(orc, imb, w, w.steps)
+    o, g = _run_pair(orc, imb, w, w.steps, work_units=units)
     mask = _fluid_mask(o)
     assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
     Fo, To = o.forces()
@@ -240,11 +246,12 @@ def test_dem_gas_quiet_and_touching_islands_bit_exact(orc, imb, bc_x):
     assert touched >= 10
 
 
-def test_moving_particles_coupled_parity(orc, imb):
+@pytest.mark.parametrize("units", UNITS)
+def test_moving_particles_coupled_parity(orc, imb, units):
     # c3 at the same density on 256 x 192: DEM + IMB + Smagorinsky, tau = 0.51, 1000 coupling
     # cycles (the horizon the FP32 bars are stated for)
     w = W.c3sub(steps=0, nx=256, ny=192)
-    o, g = _run_pair(orc, imb, w, 1000)
+    o, g = _run_pair(orc, imb, w, 1000, work_units=units)
     mask = _fluid_mask(o)
     assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
     Fo, To = o.forces()
@@ -259,11 +266,12 @@ def test_moving_particles_coupled_parity(orc, imb):
     assert np.abs(vo - vg).max() < 1e-5 * np.abs(vo).max()
 
 
-def test_doubly_periodic_suspension_parity(orc, imb):
+@pytest.mark.parametrize("units", UNITS)
+def test_doubly_periodic_suspension_parity(orc, imb, units):
     # moving disks in a box periodic in x and y whose sides are not multiples of the tile: the
     # flow crosses the periodic images of the ghost frame, corners included, with gradients
     w = W.c3sub(steps=0, nx=200, ny=150).with_(bc_y=W.BC_PERIODIC)
-    o, g = _run_pair(orc, imb, w, 300)
+    o, g = _run_pair(orc, imb, w, 300, work_units=units)
     mask = _fluid_mask(o)
     assert _u_rel_l2(g.macro(), o.macro(), mask) < 1e-5
     Fo, To = o.forces()
@@ -348,6 +356,8 @@ def test_invalid_arguments(imb):
     with pytest.raises(imb.ImbError) as e:
         imb.Lattice(2, 10, 0.6)
     assert e.value.code == -1
+    with pytest.raises(imb.ImbError):
+        imb.Lattice(64, 64, 0.6, work_units=3)
     with pytest.raises(imb.ImbError):
         imb.Lattice(10, 10, 0.5)
     lat = imb.Lattice(64, 64, 0.6)
