@@ -15,6 +15,7 @@
 // the particles that can reach the tile sit in the 3 x 3 surrounding bins.
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "imb_device.cuh"
 #include "imb_kernels.h"
@@ -402,6 +403,9 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
     const bool smag = a.smag_coef > 0.0f;
     fin += a.origin;    // node (0, 0) of plane 0
     fout += a.origin;
+    // on small lattices launched as a programmatic dependent of the previous kernel in the
+    // stream: nothing that kernel writes or reads is touched before it has completed
+    cudaGridDependencySynchronize();
 
     for (int i = threadIdx.x; i < G::ACC_FLOATS; i += BLOCK) acc[i] = 0.0f;
     if (threadIdx.x < NST) done[threadIdx.x] = 0;
@@ -609,6 +613,9 @@ k_stream_collide(const __grid_constant__ CUtensorMap tmap_n, const __grid_consta
         }
     }
     if (__any_sync(FULL, unstable) && lane == 0) set_err(a.err, ERR_UNSTABLE);
+    // the kernel that follows may be scheduled now (it waits for this one's completion before
+    // it reads; scheduled earlier, its blocks held resources the persistent grid works with)
+    cudaTriggerProgrammaticLaunchCompletion();
     __syncthreads();
     if (threadIdx.x == 0) {
         // after a failed wait: let every copy that was started land before the block leaves
@@ -948,6 +955,8 @@ __device__ __forceinline__ void fill_ghosts(S *f, const LatticeArgs &a, int i) {
 template <typename S>
 __global__ void __launch_bounds__(256) k_step_tail(const LatticeArgs a, const double *__restrict__ tile_force,
                                                    S *f, int nbf) {
+    cudaGridDependencySynchronize();   // on small lattices a programmatic dependent of the stream-collide launch
+    cudaTriggerProgrammaticLaunchCompletion();
     if ((int)blockIdx.x < nbf) {
         const int p = blockIdx.x * blockDim.x + threadIdx.x;
         if (p < a.np) force_gather(a, tile_force, p);
@@ -958,6 +967,26 @@ __global__ void __launch_bounds__(256) k_step_tail(const LatticeArgs a, const do
 }
 
 // ------------------------------------------------------------ launchers
+// A launch that, with `early`, may begin while the previous kernel in the stream finishes
+// (programmatic dependent launch): the kernel waits for that kernel's completion itself,
+// before it touches memory (cudaGridDependencySynchronize), so only the launch latency
+// overlaps.  Taken on small lattices, where the launch latency is a good part of a step.
+template <typename... P, typename... A>
+static cudaError_t launch_dependent(void (*kernel)(P...), int grid, int block, int smem, cudaStream_t s,
+                                    bool early, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 template <typename F>
 static cudaError_t by_storage(int storage, F &&fn) {
     switch (storage) {
@@ -983,8 +1012,8 @@ static cudaError_t step_tail(void *f, int storage, const LatticeArgs &a, const d
     return by_storage(storage, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         const int nbg = (edge_nodes(a.nx, a.ny) + 255) / 256;
-        k_step_tail<S><<<nbf + nbg, 256, 0, s>>>(a, tile_force, (S *)f, nbf);
-        return cudaGetLastError();
+        return launch_dependent(k_step_tail<S>, nbf + nbg, 256, 0, s, a.tf_units == SMALL_UPT, a, tile_force, (S *)f,
+                                nbf);
     });
 }
 
@@ -1037,15 +1066,14 @@ cudaError_t launch_stream_collide(const void *fin, void *fout, int storage, cons
             const int grid = SM ? ntiles * Box<S, true>::UPT
                                 : std::min(ntiles, stream_collide_per_sm<S, F, false>() * device_sms());
             if (SM) stream_collide_per_sm<S, F, true>();   // sets the shared-memory attribute
-            k_stream_collide<S, F, SM><<<grid, BLOCK, Box<S, SM>::SMEM_BYTES, s>>>(
-                *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
+            return launch_dependent(k_stream_collide<S, F, SM>, grid, BLOCK, Box<S, SM>::SMEM_BYTES, s, SM,
+                                    *tmap_narrow, *tmap_wide, (const S *)fin, (S *)fout, a, tiles, ntiles, tile_force);
         };
         const bool forced = a.Fx != 0.0f || a.Fy != 0.0f;
-        if (forced && small) go(std::true_type{}, std::true_type{});
-        else if (forced) go(std::true_type{}, std::false_type{});
-        else if (small) go(std::false_type{}, std::true_type{});
-        else go(std::false_type{}, std::false_type{});
-        return cudaGetLastError();
+        if (forced && small) return go(std::true_type{}, std::true_type{});
+        if (forced) return go(std::true_type{}, std::false_type{});
+        if (small) return go(std::false_type{}, std::true_type{});
+        return go(std::false_type{}, std::false_type{});
     });
 }
 
