@@ -991,26 +991,6 @@ __global__ void __launch_bounds__(256) k_step_tail(const LatticeArgs a, const do
 }
 
 // ------------------------------------------------------------ launchers
-// A launch that, with `early`, may begin while the previous kernel in the stream finishes
-// (programmatic dependent launch): the kernel waits for that kernel's completion itself,
-// before it touches memory (cudaGridDependencySynchronize), so only the launch latency
-// overlaps.  Taken on small lattices, where the launch latency is a good part of a step.
-template <typename... P, typename... A>
-static cudaError_t launch_dependent(void (*kernel)(P...), int grid, int block, int smem, cudaStream_t s,
-                                    bool early, A &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = early ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
 template <typename F>
 static cudaError_t by_storage(int storage, F &&fn) {
     switch (storage) {

@@ -43,6 +43,7 @@ __global__ void k_particle_table(const double *__restrict__ x, const double *__r
                                  int bc_y, double skin_half, int nbx, int nby, int *bin_count, int *pbin,
                                  PRec *prec, const double *__restrict__ v, const double *__restrict__ w,
                                  double *F, double *T, unsigned *err) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const double px = x[2 * p], py = x[2 * p + 1];
@@ -106,6 +107,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum, int &total
 
 __global__ void __launch_bounds__(256) k_bin_scan_local(int *count, int *start, int nbins, int *bsum,
                                                         int *dem_counters) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     __shared__ int wsum[8];
     const int b0 = blockIdx.x * SCAN_BINS + threadIdx.x * 4;
     int4 v = make_int4(0, 0, 0, 0);
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(256) k_bin_scan_local(int *count, int *start, 
 }
 
 __global__ void __launch_bounds__(256) k_bin_scan_add(int *fill, int *start, int nbins, const int *bsum) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     __shared__ int s_off;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {   // totals of the blocks before this one
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(256) k_bin_scan_add(int *fill, int *start, int
 
 __global__ void k_bin_fill(const int *__restrict__ pbin, int np, int *fill, const int *__restrict__ start,
                            int *ids) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const int b = pbin[p];
@@ -349,6 +353,7 @@ constexpr int NB_WARPS = 4;
 constexpr int NB_HITS = 64;   // hits a warp can hold before the overflow is reported
 
 __global__ void __launch_bounds__(32 * NB_WARPS) k_dem_neighbours(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     __shared__ int s_hit[NB_WARPS][NB_HITS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = blockIdx.x * NB_WARPS + warp;
@@ -457,6 +462,7 @@ __global__ void __launch_bounds__(32 * NB_WARPS) k_dem_neighbours(const DemArgs 
 }
 
 __global__ void k_dem_free(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int nfree = d.counters[0];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nfree; c += gridDim.x * blockDim.x) {
         const int p = d.free_ids[c];
@@ -603,6 +609,7 @@ __device__ __forceinline__ int uf_find(int *parent, int x) {
 }
 
 __global__ void k_uf_link(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int ncpl = d.counters[1];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
@@ -629,6 +636,7 @@ __global__ void k_uf_link(const DemArgs d) {
 }
 
 __global__ void k_uf_label(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int ncpl = d.counters[1];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
@@ -645,6 +653,7 @@ constexpr int ISL_PAIRS = 96;          // pair-parallel up to this many candidat
 
 // Roots reserve a contiguous range of the member list for their island.
 __global__ void k_island_alloc(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int ncpl = d.counters[1];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
@@ -653,6 +662,7 @@ __global__ void k_island_alloc(const DemArgs d) {
 }
 
 __global__ void k_island_fill(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     const int ncpl = d.counters[1];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += gridDim.x * blockDim.x) {
         const int p = d.coupled_ids[c];
@@ -678,6 +688,7 @@ __global__ void k_island_fill(const DemArgs d) {
 constexpr int SMALL_PER_WARP = 32 / ISL_SMALL;
 
 __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
     __shared__ int s_id[ISL_WARPS][32];
     __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
@@ -749,6 +760,7 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemA
 // sequential evaluation -- adds the walls and integrates.
 
 __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
     __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
     __shared__ double s_f[ISL_WARPS][3][ISL_PAIRS];     // fx, fy, Ft per pair
     __shared__ int s_id[ISL_WARPS][32];
@@ -895,37 +907,33 @@ cudaError_t launch_particle_table(const double *x, const double *r, const double
                                   const double *w, double *F, double *T, unsigned *err,
                                   cudaStream_t s) {
     if (np == 0) return cudaSuccess;
-    k_particle_table<<<blocks_for(np, 128), 128, 0, s>>>(x, r, x_start, np, nx, ny, bc_x, bc_y,
-                                                         skin_half, nbx, nby, bin_count, pbin, prec,
-                                                         v, w, F, T, err);
-    return cudaGetLastError();
+    return launch_dependent(k_particle_table, blocks_for(np, 128), 128, 0, s, true, x, r, x_start, np, nx, ny, bc_x,
+                            bc_y, skin_half, nbx, nby, bin_count, pbin, prec, v, w, F, T, err);
 }
 
 cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int nbins, int *bsum,
                             int *dem_counters, cudaStream_t s) {
     const int nb = (nbins + SCAN_BINS - 1) / SCAN_BINS;
-    k_bin_scan_local<<<nb, 256, 0, s>>>(bin_count, bin_start, nbins, bsum, dem_counters);
-    k_bin_scan_add<<<nb, 256, 0, s>>>(bin_fill, bin_start, nbins, bsum);
-    return cudaGetLastError();
+    cudaError_t e = launch_dependent(k_bin_scan_local, nb, 256, 0, s, true, bin_count, bin_start, nbins, bsum,
+                                     dem_counters);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(k_bin_scan_add, nb, 256, 0, s, true, bin_fill, bin_start, nbins, (const int *)bsum);
 }
 
 cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *bin_start,
                             int *bin_ids, cudaStream_t s) {
     if (np == 0) return cudaSuccess;
-    k_bin_fill<<<blocks_for(np, 128), 128, 0, s>>>(pbin, np, bin_fill, bin_start, bin_ids);
-    return cudaGetLastError();
+    return launch_dependent(k_bin_fill, blocks_for(np, 128), 128, 0, s, true, pbin, np, bin_fill, bin_start, bin_ids);
 }
 
 cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
-    k_dem_neighbours<<<blocks_for(d.np, NB_WARPS), 32 * NB_WARPS, 0, s>>>(d);
-    return cudaGetLastError();
+    return launch_dependent(k_dem_neighbours, blocks_for(d.np, NB_WARPS), 32 * NB_WARPS, 0, s, true, d);
 }
 
 cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
-    k_dem_free<<<blocks_for(d.np, 64), 64, 0, s>>>(d);
-    return cudaGetLastError();
+    return launch_dependent(k_dem_free, blocks_for(d.np, 64), 64, 0, s, true, d);
 }
 
 static int g_coupled_blocks = 0;
@@ -950,20 +958,20 @@ cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s) {
 cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
     const int g = blocks_for(d.np, 128);
-    k_uf_link<<<g, 128, 0, s>>>(d);
-    k_uf_label<<<g, 128, 0, s>>>(d);
-    k_island_alloc<<<g, 128, 0, s>>>(d);
-    k_island_fill<<<g, 128, 0, s>>>(d);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    for (auto k : {k_uf_link, k_uf_label, k_island_alloc, k_island_fill})
+        if (e == cudaSuccess) e = launch_dependent(k, g, 128, 0, s, true, d);
+    return e;
 }
 
 cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
     // enough warps for every island at once: at most np/2 islands of two or more particles,
     // at most np/5 of five or more
-    k_dem_small_islands<<<blocks_for(blocks_for(d.np / 2 + 1, SMALL_PER_WARP), ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
-    k_dem_islands<<<blocks_for(d.np / 5 + 1, ISL_WARPS), 32 * ISL_WARPS, 0, s>>>(d);
-    return cudaGetLastError();
+    cudaError_t e = launch_dependent(k_dem_small_islands, blocks_for(blocks_for(d.np / 2 + 1, SMALL_PER_WARP), ISL_WARPS),
+                                     32 * ISL_WARPS, 0, s, true, d);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(k_dem_islands, blocks_for(d.np / 5 + 1, ISL_WARPS), 32 * ISL_WARPS, 0, s, true, d);
 }
 
 cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
