@@ -423,7 +423,8 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
 }
 
 // rebuild bins and the lattice particle records for the current positions
-static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
+// (bins_only: the particle records and bins, for a DEM cycle that rebuilds the rest after it)
+static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces, bool bins_only = false) {
     if (c->np == 0) {
         CK(cudaMemsetAsync(c->tiles, 0, sizeof(TileCand) * c->nbins, c->stream), "clear tile lists");
         return IMB_OK;
@@ -432,6 +433,13 @@ static int rebuild_table(imb_ctx *c, const double *x_start, bool zero_forces) {
                              0.5 * c->p.skin, c->nbx, c->nby, c->bin_count, c->pbin, c->prec, c->v,
                              c->w, zero_forces ? c->F : nullptr, c->T, c->err, c->stream),
        "particle table");
+    if (bins_only) {
+        CK(launch_bin_scan(c->bin_count, c->bin_fill, c->bin_start, c->nbins, c->bin_bsum, c->counters, c->stream),
+           "bin scan");
+        CK(launch_bin_fill(c->pbin, c->np, c->bin_fill, c->bin_start, c->bin_ids, c->stream), "bin fill");
+        c->launches += 4;   // table, scan (two passes), fill
+        return IMB_OK;
+    }
     // the rows' cell intervals and the solid-ratio tables need only the particle records: they
     // run on the side stream while the bins are built; the tile lists wait for the intervals,
     // the stream for the tables at the end
@@ -574,7 +582,9 @@ extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, 
     CK(cudaMemcpyAsync(c->x, x, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy x");
     CK(cudaMemcpyAsync(c->v, v, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy v");
     CK(cudaMemcpyAsync(c->w, omega, 8 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy omega");
-    return rebuild_table(c, nullptr, false);
+    // with the DEM on, the next coupling cycle starts from the bins and rebuilds the map after
+    // moving the particles, so the tile lists and solid-ratio tables would go unused
+    return rebuild_table(c, nullptr, false, c->p.dem_on != 0);
 }
 
 // ------------------------------------------------------------- stepping
