@@ -284,8 +284,9 @@ class Lattice:
         n_p = self.np
         xi = vi = wi = None
         if kin_in is not None:
-            xi, vi, wi = kin_in
-            xi, vi, wi = _d(_f64(xi, 2 * n_p)), _d(_f64(vi, 2 * n_p)), _d(_f64(wi, n_p))
+            # converted copies (if any) stay referenced until the call returns
+            kin = (_f64(kin_in[0], 2 * n_p), _f64(kin_in[1], 2 * n_p), _f64(kin_in[2], n_p))
+            xi, vi, wi = (_d(a) for a in kin)
         outs = []
         for a, k in ((F, 2), (T, 1), (x, 2), (v, 2), (w, 1)):
             if a is not None and (a.size != k * n_p or a.dtype != np.float64 or not a.flags.c_contiguous):

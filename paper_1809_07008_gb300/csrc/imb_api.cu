@@ -572,6 +572,19 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
     return IMB_OK;
 }
 
+// The device address of a pinned host array the device can address (page-locked and mapped,
+// as cudaHostAlloc / cudaHostRegister give under unified addressing), else NULL.
+template <typename T>
+static T *device_view(T *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error an unknown pointer leaves
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? static_cast<T *>(at.devicePointer) : nullptr;
+}
+
 extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, const double *omega) {
     if (!c) return IMB_E_INVALID_ARG;
     if (c->np == 0) return IMB_OK;
@@ -579,9 +592,15 @@ extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, 
     for (int i = 0; i < c->np; ++i)
         if (!(x[2 * i] >= 0.0 && x[2 * i] < c->nx && x[2 * i + 1] >= 0.0 && x[2 * i + 1] < c->ny))
             return fail(c, IMB_E_INVALID_ARG, "particle centre outside [0,nx) x [0,ny)");
-    CK(cudaMemcpyAsync(c->x, x, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy x");
-    CK(cudaMemcpyAsync(c->v, v, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy v");
-    CK(cudaMemcpyAsync(c->w, omega, 8 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy omega");
+    const double *dx = device_view(x), *dv = device_view(v), *dw = device_view(omega);
+    if (dx && dv && dw) {   // one launch reads the three arrays from host memory
+        CK(launch_kinematics_in(dx, dv, dw, c->x, c->v, c->w, c->np, c->stream), "upload kinematics");
+        c->launches++;
+    } else {
+        CK(cudaMemcpyAsync(c->x, x, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy x");
+        CK(cudaMemcpyAsync(c->v, v, 16 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy v");
+        CK(cudaMemcpyAsync(c->w, omega, 8 * (size_t)c->np, cudaMemcpyHostToDevice, c->stream), "copy omega");
+    }
     // with the DEM on, the next coupling cycle starts from the bins and rebuilds the map after
     // moving the particles, so the tile lists and solid-ratio tables would go unused
     return rebuild_table(c, nullptr, false, c->p.dem_on != 0);
@@ -691,7 +710,17 @@ extern "C" int imb_step_io(imb_ctx *c, int n, const double *x_in, const double *
     if (in && (rc = imb_set_kinematics(c, x_in, v_in, omega_in))) return rc;
     if ((rc = queue_steps(c, n))) return rc;
     const size_t np = (size_t)c->np;
-    if (np) {
+    double *outs[5] = {F_out, T_out, x_out, v_out, omega_out}, *dev[5];
+    bool mapped = true;
+    for (int k = 0; k < 5; ++k) {
+        dev[k] = device_view(outs[k]);
+        if (outs[k] && !dev[k]) mapped = false;
+    }
+    if (np && mapped) {   // one launch writes every output into host memory
+        CK(launch_state_out(c->F, c->T, c->x, c->v, c->w, dev[0], dev[1], dev[2], dev[3], dev[4], c->np, c->stream),
+           "read back");
+        c->launches++;
+    } else if (np) {
         if (F_out) CK(cudaMemcpyAsync(F_out, c->F, 16 * np, cudaMemcpyDeviceToHost, c->stream), "copy F");
         if (T_out) CK(cudaMemcpyAsync(T_out, c->T, 8 * np, cudaMemcpyDeviceToHost, c->stream), "copy T");
         if (x_out) CK(cudaMemcpyAsync(x_out, c->x, 16 * np, cudaMemcpyDeviceToHost, c->stream), "copy x");

@@ -154,6 +154,11 @@ cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s);
 cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s);
+// device-addressable pinned host arrays (see device_view in the API) <-> the particle arrays
+cudaError_t launch_kinematics_in(const double *hx, const double *hv, const double *hw, double *x, double *v, double *w,
+                                 int np, cudaStream_t s);
+cudaError_t launch_state_out(const double *F, const double *T, const double *x, const double *v, const double *w,
+                             double *hF, double *hT, double *hx, double *hv, double *hw, int np, cudaStream_t s);
 cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
                             int bc_y, const int *bin_start, const int *bin_ids, const int *pbin,
                             int nbx, int nby, int reach, int *pair_cnt, int *pairs, int max_per,

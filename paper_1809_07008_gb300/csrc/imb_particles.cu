@@ -974,6 +974,55 @@ cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s) {
     return launch_dependent(k_dem_islands, blocks_for(d.np / 5 + 1, ISL_WARPS), 32 * ISL_WARPS, 0, s, true, d);
 }
 
+// Host round trips through pinned host memory that the device can address (NVLink-C2C or PCIe
+// mapped pages): one launch moves the particles' kinematics in, one the forces and state out,
+// instead of a DMA copy per array.
+__global__ void k_kinematics_in(const double *__restrict__ hx, const double *__restrict__ hv,
+                                const double *__restrict__ hw, double *x, double *v, double *w, int np) {
+    cudaGridDependencySynchronize();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    x[2 * p] = hx[2 * p];
+    x[2 * p + 1] = hx[2 * p + 1];
+    v[2 * p] = hv[2 * p];
+    v[2 * p + 1] = hv[2 * p + 1];
+    w[p] = hw[p];
+}
+
+__global__ void k_state_out(const double *__restrict__ F, const double *__restrict__ T, const double *__restrict__ x,
+                            const double *__restrict__ v, const double *__restrict__ w, double *hF, double *hT,
+                            double *hx, double *hv, double *hw, int np) {
+    cudaGridDependencySynchronize();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    if (hF) {
+        hF[2 * p] = F[2 * p];
+        hF[2 * p + 1] = F[2 * p + 1];
+    }
+    if (hT) hT[p] = T[p];
+    if (hx) {
+        hx[2 * p] = x[2 * p];
+        hx[2 * p + 1] = x[2 * p + 1];
+    }
+    if (hv) {
+        hv[2 * p] = v[2 * p];
+        hv[2 * p + 1] = v[2 * p + 1];
+    }
+    if (hw) hw[p] = w[p];
+}
+
+cudaError_t launch_kinematics_in(const double *hx, const double *hv, const double *hw, double *x, double *v, double *w,
+                                 int np, cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    return launch_dependent(k_kinematics_in, blocks_for(np, 128), 128, 0, s, true, hx, hv, hw, x, v, w, np);
+}
+
+cudaError_t launch_state_out(const double *F, const double *T, const double *x, const double *v, const double *w,
+                             double *hF, double *hT, double *hx, double *hv, double *hw, int np, cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    return launch_dependent(k_state_out, blocks_for(np, 128), 128, 0, s, true, F, T, x, v, w, hF, hT, hx, hv, hw, np);
+}
+
 cudaError_t launch_contacts(const double *x, const double *r, int np, int nx, int ny, int bc_x,
                             int bc_y, const int *bin_start, const int *bin_ids, const int *pbin,
                             int nbx, int nby, int reach, int *pair_cnt, int *pairs, int max_per,

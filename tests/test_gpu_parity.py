@@ -434,8 +434,11 @@ def test_drag_gradient_refuses_moving_walls(imb):
     g.close()
 
 
-def test_step_io_equals_separate_calls(imb):
-    # imb_step_io (upload, cycles, read-back, one wait) gives what the separate calls give
+@pytest.mark.parametrize("pinned", [False, True])
+def test_step_io_equals_separate_calls(imb, pinned):
+    # imb_step_io (upload, cycles, read-back, one wait) gives what the separate calls give, to the
+    # bit (the forces are summed in a fixed order); pinned host arrays take the one-launch upload
+    # and read-back through host memory, pageable ones the copies
     w = W.c3sub(steps=0, nx=128, ny=96)
     a = imb.Lattice.from_workload(w)
     b = imb.Lattice.from_workload(w)
@@ -443,18 +446,25 @@ def test_step_io_equals_separate_calls(imb):
     b.step(3)
     x, v, om = a.particles()
     x = x + 0.01
-    F, T = np.zeros((w.n_particles, 2)), np.zeros(w.n_particles)
-    xo, vo, wo = np.zeros((w.n_particles, 2)), np.zeros((w.n_particles, 2)), np.zeros(w.n_particles)
-    a.step_io(2, (x, v, om), F, T, xo, vo, wo)
+    n = w.n_particles
+
+    def buf(arr):
+        if not pinned:
+            return np.ascontiguousarray(arr)
+        import torch
+        return torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
+
+    xi, vi, wi = buf(x), buf(v), buf(om)
+    F, T = buf(np.zeros((n, 2))), buf(np.zeros(n))
+    xo, vo, wo = buf(np.zeros((n, 2))), buf(np.zeros((n, 2))), buf(np.zeros(n))
+    a.step_io(2, (xi, vi, wi), F, T, xo, vo, wo)
     b.set_kinematics(x, v, om)
     b.step(2)
     Fb, Tb = b.forces()
     xb, vb, wb = b.particles()
-    # the forces are sums of FP32 cell terms in no fixed order (1e-6 level), so the two lattices may differ in
-    # the last bits of what the DEM makes of them
-    assert np.abs(xo - xb).max() < 1e-8 and np.abs(vo - vb).max() < 1e-8 and np.abs(wo - wb).max() < 1e-8
-    assert np.abs(F - Fb).max() <= 1e-5 * np.abs(Fb).max() and np.abs(T - Tb).max() <= 1e-5 * np.abs(Tb).max()
-    assert np.abs(a.populations() - b.populations()).max() < 1e-6
+    assert np.array_equal(xo, xb) and np.array_equal(vo, vb) and np.array_equal(wo, wb)
+    assert np.array_equal(F, Fb) and np.array_equal(T, Tb)
+    assert np.array_equal(a.populations(), b.populations())
     a.step_io(1)                       # no arrays: just the cycles and the wait
     with pytest.raises(ValueError):
         a.step_io(1, None, np.zeros(3))
