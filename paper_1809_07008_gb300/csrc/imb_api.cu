@@ -572,6 +572,18 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
     return IMB_OK;
 }
 
+// Every centre (x[2i], x[2i+1]) inside [0, nx) x [0, ny), NaN failing: a branch-free pass (the
+// check sits between two host-coupled steps, before the next step's first launch)
+static bool centres_inside(const double *x, int n, int nx, int ny) {
+    const double X = (double)nx, Y = (double)ny;
+    int ok = 1;
+    for (int i = 0; i < n; ++i) {
+        const double a = x[2 * i], b = x[2 * i + 1];
+        ok &= (int)(a >= 0.0) & (int)(a < X) & (int)(b >= 0.0) & (int)(b < Y);
+    }
+    return ok != 0;
+}
+
 // The device address of a pinned host array the device can address (page-locked and mapped,
 // as cudaHostAlloc / cudaHostRegister give under unified addressing), else NULL.
 template <typename T>
@@ -589,9 +601,8 @@ extern "C" int imb_set_kinematics(imb_ctx *c, const double *x, const double *v, 
     if (!c) return IMB_E_INVALID_ARG;
     if (c->np == 0) return IMB_OK;
     if (!x || !v || !omega) return fail(c, IMB_E_INVALID_ARG, "bad kinematics arrays");
-    for (int i = 0; i < c->np; ++i)
-        if (!(x[2 * i] >= 0.0 && x[2 * i] < c->nx && x[2 * i + 1] >= 0.0 && x[2 * i + 1] < c->ny))
-            return fail(c, IMB_E_INVALID_ARG, "particle centre outside [0,nx) x [0,ny)");
+    if (!centres_inside(x, c->np, c->nx, c->ny))
+        return fail(c, IMB_E_INVALID_ARG, "particle centre outside [0,nx) x [0,ny)");
     const double *dx = device_view(x), *dv = device_view(v), *dw = device_view(omega);
     if (dx && dv && dw) {   // one launch reads the three arrays from host memory
         CK(launch_kinematics_in(dx, dv, dw, c->x, c->v, c->w, c->np, c->stream), "upload kinematics");

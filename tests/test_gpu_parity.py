@@ -468,6 +468,16 @@ def test_step_io_equals_separate_calls(imb, pinned):
     a.step_io(1)                       # no arrays: just the cycles and the wait
     with pytest.raises(ValueError):
         a.step_io(1, None, np.zeros(3))
+    # centres outside the lattice, or NaN, are refused before anything is uploaded
+    xs, _, _ = a.particles()
+    for bad in ((0, 0, w.nx + 0.5), (1, 1, -1e-9), (2, 0, float("nan"))):
+        xb = xs.copy()
+        xb[bad[0], bad[1]] = bad[2]
+        with pytest.raises(imb.ImbError):
+            a.set_kinematics(xb, v, om)
+        with pytest.raises(imb.ImbError):
+            a.step_io(1, (xb, v, om), F, T)
+    assert np.array_equal(a.particles()[0], xs)
     a.close()
     b.close()
 
