@@ -133,7 +133,9 @@ int imb_step(imb_ctx *ctx, int n);
  * then n coupling cycles run, then the force F_out[2n] and torque T_out[n] of the last
  * cycle and the particle state x_out[2n], v_out[2n], omega_out[n] are read back (each
  * output may be NULL).  Everything is queued on the context stream and the call waits
- * once; for pinned host arrays the copies are asynchronous.  Errors as imb_step and
+ * once; for pinned host arrays the copies are asynchronous, and when every array given is
+ * pinned memory the device can address (cudaHostAlloc'd or mapped), one kernel reads the
+ * inputs and one writes the outputs through host memory instead.  Errors as imb_step and
  * imb_set_kinematics.  After IMB_E_TIMEOUT the copies into the output arrays may still be
  * queued: the caller must keep those arrays alive and unused until imb_sync returns
  * IMB_OK or the context is destroyed. */
