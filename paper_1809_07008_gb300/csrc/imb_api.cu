@@ -701,6 +701,7 @@ extern "C" int imb_sync(imb_ctx *c) {
     if (bits & ERR_BARRIER) return fail(c, IMB_E_TIMEOUT, "DEM grid barrier timed out");
     if (bits & ERR_TMA) return fail(c, IMB_E_TIMEOUT, "wait on a stream-collide tile copy timed out");
     if (bits & ERR_SKIN) return fail(c, IMB_E_SKIN, "a particle moved more than skin/2 in one step");
+    if (bits & ERR_LIST) return fail(c, IMB_E_STATE, "a per-cycle DEM particle list overflowed");
     return fail(c, IMB_E_CUDA, "unknown device error flag");
 }
 

@@ -54,6 +54,7 @@ enum : unsigned {
     ERR_SKIN = 16u,          // a particle moved more than skin/2 in one coupling cycle
     ERR_BARRIER = 32u,       // a bounded grid barrier gave up
     ERR_TMA = 64u,           // a bounded wait on a TMA / bulk copy gave up
+    ERR_LIST = 128u,         // a per-cycle particle list met its capacity (its count not reset)
 };
 
 constexpr int TILE = 32;        // stream-collide tile edge == bin edge (cells)

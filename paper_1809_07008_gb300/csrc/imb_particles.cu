@@ -349,6 +349,14 @@ __device__ __forceinline__ bool pair_apart(const DemArgs &d, double px, double p
 // r_p + r_q + skin), the hits are ranked by id (the list is in ascending id order), and
 // each kept pair carries its tangential spring and damping constant over from the
 // previous list.
+// append particle p to a per-cycle list of capacity np (the counts are reset by the bin scan
+// of every rebuild); a full list is reported, not overrun
+__device__ __forceinline__ void list_append(int *list, int *count, int np, int p, unsigned *err) {
+    const int k = atomicAdd(count, 1);
+    if (k < np) list[k] = p;
+    else set_err(err, ERR_LIST);
+}
+
 constexpr int NB_WARPS = 4;
 constexpr int NB_HITS = 64;   // hits a warp can hold before the overflow is reported
 
@@ -456,8 +464,8 @@ __global__ void __launch_bounds__(32 * NB_WARPS) k_dem_neighbours(const DemArgs 
             d.exc[2 * p + 1] = f.ey;
             d.loud[p] = !free_of_edges(d, f, px, py, rp);
         }
-        if (n == 0) d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
-        else d.coupled_ids[atomicAdd(&d.counters[1], 1)] = p;
+        if (n == 0) list_append(d.free_ids, &d.counters[0], d.np, p, d.err);
+        else list_append(d.coupled_ids, &d.counters[1], d.np, p, d.err);
     }
 }
 
@@ -668,7 +676,7 @@ __global__ void k_island_fill(const DemArgs d) {
         const int p = d.coupled_ids[c];
         const int r = d.label[p];
         if (!d.iloud[r]) {   // nothing in the island can touch within the cycle: free particles
-            d.free_ids[atomicAdd(&d.counters[0], 1)] = p;
+            list_append(d.free_ids, &d.counters[0], d.np, p, d.err);
             continue;
         }
         const int size = d.isz[r];
