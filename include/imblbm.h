@@ -94,6 +94,13 @@ typedef struct imb_params {
                             persistent grid; 1 always the persistent tiles, 2 always the
                             eight-row units.  Same results either way, to rounding of the
                             force sums (each unit keeps its own partials)                      */
+    int plain_launches;  /* 0 (default): a coupling cycle with the DEM is captured as a CUDA graph
+                            on its first run (one per buffer pair, re-captured after
+                            imb_set_particles) and replayed with one graph launch; 1: its kernels
+                            are launched one by one.  Results identical to the bit; launch
+                            counts and kernel timing the same either way.  A capture that fails
+                            (e.g. on a stream the caller is itself capturing) falls back to
+                            launches for the rest of the context's life                        */
 } imb_params;
 
 typedef struct imb_ctx imb_ctx;

@@ -94,7 +94,7 @@ class Params(C.Structure):
                 ("gx", C.c_double), ("gy", C.c_double), ("skin", C.c_double),
                 ("timeout_ms", C.c_int), ("wall_u_bot", C.c_double), ("wall_u_top", C.c_double),
                 ("contact_model", C.c_int), ("E_young", C.c_double), ("nu_poisson", C.c_double),
-                ("work_units", C.c_int)]
+                ("work_units", C.c_int), ("plain_launches", C.c_int)]
 
 
 _lib = None

@@ -20,6 +20,20 @@
 
 using namespace imb;
 
+// A run of steps captured as a CUDA graph: the instantiated graph, the graph itself (its
+// event-record nodes, which time the steps, are re-pointed through it), the launches it holds
+// and the buffer indices it leaves.
+struct StepGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> ev;
+    long long launches = 0;
+    int cur_after = 0, nbr_after = 0;
+};
+
+// lattice steps without the DEM per graph (even, so the populations come back to their buffer)
+constexpr int GRAPH_STEPS = 8;
+
 struct imb_ctx {
     int nx = 0, ny = 0, pitch = 0;
     double tau = 0.0, C_smag = 0.0;
@@ -68,6 +82,12 @@ struct imb_ctx {
     int tab_w = 0, tab_h = 0;
     CUtensorMap tmap[2][2];         // TMA descriptors [buffer][narrow, wide] of the populations
     bool small = false;             // units of eight rows, one per block (all fit on the device at once)
+    // steps captured as CUDA graphs (see graph_steps): [0, 8) one coupling cycle with the DEM,
+    // by (kernel timing, population buffer, neighbour-list buffer); [8, 12) GRAPH_STEPS lattice
+    // steps without it, by (kernel timing, population buffer); off for good after a failed capture
+    StepGraph graphs[12];
+    bool use_graphs = true;
+    bool capturing = false;   // inside graph_steps' capture: timing events become graph nodes
     // parameters derived on the host
     double zeta = 0.0, gx_eff = 0.0, gy_eff = 0.0;
     double hm_kn0 = 0.0, hm_sn0 = 0.0, hm_kt0 = 0.0, hm_c0 = 0.0;   // Hertz-Mindlin constants
@@ -239,7 +259,16 @@ static DemArgs dem_args(imb_ctx *c) {
     return d;
 }
 
+static void drop_step_graphs(imb_ctx *c) {
+    for (StepGraph &sg : c->graphs) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        if (sg.graph) cudaGraphDestroy(sg.graph);
+        sg = StepGraph();
+    }
+}
+
 static void free_particles(imb_ctx *c) {
+    drop_step_graphs(c);   // they hold the particle arrays' addresses
     double **dp[] = {&c->x, &c->v, &c->w, &c->r, &c->m, &c->I, &c->F, &c->T,
                      &c->x1, &c->v1, &c->w1, &c->xs, &c->nbr_xi[0], &c->nbr_xi[1], &c->wall_xi,
                      &c->nbr_cn[0], &c->nbr_cn[1], &c->exc};
@@ -334,6 +363,8 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
         return fail(nullptr, IMB_E_INVALID_ARG, "bad contact model or Hertz-Mindlin material");
     if (p.timeout_ms <= 0) p.timeout_ms = 60000;
     if (p.work_units < 0 || p.work_units > 2) return fail(nullptr, IMB_E_INVALID_ARG, "work_units must be 0, 1 or 2");
+    if (p.plain_launches != 0 && p.plain_launches != 1)
+        return fail(nullptr, IMB_E_INVALID_ARG, "plain_launches must be 0 or 1");
     if ((long long)nx * ny > (1ll << 31) / 16) return fail(nullptr, IMB_E_INVALID_ARG, "lattice too large");
 
     imb_ctx *c = new imb_ctx();
@@ -354,6 +385,7 @@ extern "C" int imb_init_lattice(imb_ctx **out, int nx, int ny, double tau, doubl
     c->nby = (ny + TILE - 1) / TILE;
     c->nbins = c->nbx * c->nby;
     // a lattice whose eight-row units all fit on the device at once takes one per block
+    c->use_graphs = p.plain_launches == 0;
     c->small = p.work_units == 2 ||
                (p.work_units == 0 && (long long)c->nbins * SMALL_UPT <= stream_collide_resident_blocks(p.storage));
     const double le = std::log(p.e_rest);
@@ -486,6 +518,7 @@ extern "C" int imb_set_particles(imb_ctx *c, int n, const double *x, const doubl
         return fail(c, IMB_E_INVALID_ARG, "periodic extent must be at least 2 (32 + r_max + 2) cells");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(c->stream), "sync");
+    drop_step_graphs(c);   // captured with the old count and table shape
     if (n > c->cap) {
         free_particles(c);
         cudaError_t e = cudaSuccess;
@@ -622,10 +655,9 @@ static int dem_cycle(imb_ctx *c, bool zero_forces) {
     DemArgs d = dem_args(c);
     CK(launch_dem_neighbours(d, c->stream), "dem neighbours");
     CK(launch_dem_islands_setup(d, c->stream), "dem islands");
-    CK(launch_dem_free(d, c->stream), "dem free");
-    CK(launch_dem_islands(d, c->stream), "dem islands");
+    CK(launch_dem_local(d, c->stream), "dem free particles and islands");
     CK(launch_dem_coupled(d, dem_coupled_blocks(), c->stream), "dem coupled");
-    c->launches += 9;   // neighbours, link, label, alloc, fill, free, small + medium islands, coupled
+    c->launches += 7;   // neighbours, link, label, alloc, fill, free particles and islands, coupled
     c->nbr_cur ^= 1;
     return rebuild_table(c, c->xs, zero_forces);
 }
@@ -643,15 +675,101 @@ static int lattice_step(imb_ctx *c) {
         e0 = c->events[c->ev_used];
         e1 = c->events[c->ev_used + 1];
         c->ev_used += 2;
-        CK(cudaEventRecord(e0, c->stream), "event record");
+        // (an event-record node of its own when the steps are captured)
+        CK(cudaEventRecordWithFlags(e0, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault),
+           "event record");
     }
     CK(launch_stream_collide(c->fbuf[c->cur], c->fbuf[c->cur ^ 1], c->p.storage, a, &c->tmap[c->cur][0],
                              &c->tmap[c->cur][1], c->tiles, c->tile_force, c->small, c->stream),
        "stream-collide");
     CK(launch_step_tail(c->fbuf[c->cur ^ 1], c->p.storage, a, c->tile_force, c->stream), "forces and ghosts");
     c->launches += 2;
-    if (c->timing) CK(cudaEventRecord(e1, c->stream), "event record");
+    if (c->timing)
+        CK(cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault),
+           "event record");
     c->cur ^= 1;
+    return IMB_OK;
+}
+
+// Steps from a CUDA graph: `dem` one coupling cycle with the DEM (DEM, particle map,
+// stream-collide, tail, ~25 kernels), else GRAPH_STEPS lattice steps.  Captured on first use for
+// the current buffers, then replayed with one launch, so that the kernels reach the GPU without a
+// host launch each.  With kernel timing on, the events that bracket each stream-collide and its
+// tail are event-record nodes, pointed at the context's next events before every replay.  A
+// capture that fails (a stream the caller is capturing, a call the capture refuses) turns graphs
+// off and the steps run as launches.
+static int graph_steps(imb_ctx *c, bool dem, bool &done) {
+    done = false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!c->use_graphs || cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return IMB_OK;
+    const int steps = dem ? 1 : GRAPH_STEPS, nev = c->timing ? 2 * steps : 0;
+    StepGraph &sg = c->graphs[dem ? 4 * (int)c->timing + 2 * c->cur + c->nbr_cur : 8 + 2 * (int)c->timing + c->cur];
+    while (c->events.size() < c->ev_used + nev) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "cudaEventCreate");
+        c->events.push_back(e);
+    }
+    if (!sg.exec) {
+        const int cur0 = c->cur, nbr0 = c->nbr_cur;
+        const long long l0 = c->launches;
+        const size_t ev0 = c->ev_used;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->use_graphs = false;
+            return IMB_OK;
+        }
+        c->capturing = true;
+        int rc = dem ? dem_cycle(c, true) : IMB_OK;
+        for (int t = 0; t < steps && !rc; ++t) rc = lattice_step(c);
+        c->capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        sg.cur_after = c->cur;
+        sg.nbr_after = c->nbr_cur;
+        sg.launches = c->launches - l0;
+        c->cur = cur0;   // the capture ran nothing
+        c->nbr_cur = nbr0;
+        c->launches = l0;
+        c->ev_used = ev0;
+        bool ok = !rc && e == cudaSuccess && g;
+        sg.ev.assign(nev, nullptr);
+        if (ok && nev) {   // the nodes that record the events, in the order the steps record them
+            size_t nn = 0;
+            ok = cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess;
+            std::vector<cudaGraphNode_t> nodes(nn);
+            ok = ok && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess;
+            for (size_t i = 0; ok && i < nn; ++i) {
+                cudaGraphNodeType t;
+                cudaEvent_t ev = nullptr;
+                if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) ok = false;
+                else if (t == cudaGraphNodeTypeEventRecord && cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) == cudaSuccess)
+                    for (int h = 0; h < nev; ++h)
+                        if (ev == c->events[ev0 + h]) sg.ev[h] = nodes[i];
+            }
+            for (int h = 0; h < nev; ++h) ok = ok && sg.ev[h];
+        }
+        cudaGraphExec_t x = nullptr;
+        ok = ok && cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+        if (!ok) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            c->msg.clear();
+            sg = StepGraph();
+            c->use_graphs = false;
+            return IMB_OK;
+        }
+        sg.graph = g;   // kept: the event nodes are the graph's
+        sg.exec = x;
+    }
+    for (int h = 0; h < nev; ++h)
+        CK(cudaGraphExecEventRecordNodeSetEvent(sg.exec, sg.ev[h], c->events[c->ev_used + h]), "timing events");
+    c->ev_used += nev;
+    CK(cudaGraphLaunch(sg.exec, c->stream), "step graph");
+    c->launches += sg.launches;
+    c->cur = sg.cur_after;
+    c->nbr_cur = sg.nbr_after;
+    done = true;
     return IMB_OK;
 }
 
@@ -659,13 +777,25 @@ static int queue_steps(imb_ctx *c, int n) {
     if (!c) return IMB_E_INVALID_ARG;
     if (n < 0) return fail(c, IMB_E_INVALID_ARG, "n must be >= 0");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    for (int t = 0; t < n; ++t) {
-        if (c->p.dem_on && c->np > 0) {
+    const bool dem = c->p.dem_on && c->np > 0;
+    for (int t = 0; t < n;) {
+        // (timed lattice steps stay launches: the events between steps cost more in a graph)
+        if (dem || (n - t >= GRAPH_STEPS && !c->timing)) {
+            bool done = false;
+            int rc = graph_steps(c, dem, done);
+            if (rc) return rc;
+            if (done) {
+                t += dem ? 1 : GRAPH_STEPS;
+                continue;
+            }
+        }
+        if (dem) {
             int rc = dem_cycle(c, true);
             if (rc) return rc;
         }
         int rc = lattice_step(c);
         if (rc) return rc;
+        ++t;
     }
     return IMB_OK;
 }

@@ -150,10 +150,10 @@ cudaError_t launch_bin_scan(int *bin_count, int *bin_fill, int *bin_start, int n
 cudaError_t launch_bin_fill(const int *pbin, int np, int *bin_fill, const int *bin_start,
                             int *bin_ids, cudaStream_t s);
 cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s);
-cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s);
 cudaError_t launch_dem_coupled(const DemArgs &d, int nblocks, cudaStream_t s);
 cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s);
-cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s);
+// free particles and islands of up to 32 particles, one launch
+cudaError_t launch_dem_local(const DemArgs &d, cudaStream_t s);
 // device-addressable pinned host arrays (see device_view in the API) <-> the particle arrays
 cudaError_t launch_kinematics_in(const double *hx, const double *hv, const double *hw, double *x, double *v, double *w,
                                  int np, cudaStream_t s);

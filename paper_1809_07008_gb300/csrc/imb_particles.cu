@@ -8,7 +8,9 @@
 //   k_dem_neighbours  sorted neighbour candidates within r_a + r_b + skin, carrying
 //                     the tangential spring of each pair over, and the split of the
 //                     particles into free (no candidate) and coupled ones;
-//   k_dem_free        the N_sub sub-cycles (Eq. 17) of a free particle in registers;
+//   k_dem_local       the N_sub sub-cycles (Eq. 17) of the free particles (in registers)
+//                     and of the islands of up to 32 particles (a warp each, or eight
+//                     islands of up to four to a warp, in shared memory), in one launch;
 //   k_dem_coupled     the N_sub sub-cycles of the coupled particles, one bounded grid
 //                     barrier per sub-cycle (cooperative launch);
 //   k_contacts        pairs in contact (Eq. 7) for readback.
@@ -244,10 +246,12 @@ __device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const 
     return true;
 }
 
-// Walls on the domain edges of non-periodic axes, an immovable partner (m* = m).
-__device__ __forceinline__ void wall_contacts(const DemArgs &d, int p, double px, double py, double vx,
+// Walls on the domain edges of non-periodic axes, an immovable partner (m* = m).  Returns
+// whether any wall touches.
+__device__ __forceinline__ bool wall_contacts(const DemArgs &d, int p, double px, double py, double vx,
                                               double vy, double w, double rp, double mp, double *xiw,
                                               double &Fcx, double &Fcy, double &Tc) {
+    bool touched = false;
 #pragma unroll
     for (int wl = 0; wl < 4; ++wl) {
         const bool active = wl < 2 ? d.bc_x == BC_WALL : d.bc_y == BC_WALL;
@@ -266,6 +270,22 @@ __device__ __forceinline__ void wall_contacts(const DemArgs &d, int p, double px
         Fcx += fx;
         Fcy += fy;
         Tc += rp * Ft;
+        touched = true;
+    }
+    return touched;
+}
+
+// The drift of the leapfrog update (Eq. 11), wrapped on periodic axes.
+__device__ __forceinline__ void drift(const DemArgs &d, double &px, double &py, double vx, double vy) {
+    px = px + vx * d.dt;
+    py = py + vy * d.dt;
+    if (d.bc_x == BC_PERIODIC) {
+        if (px >= d.nx) px -= d.nx;
+        else if (px < 0.0) px += d.nx;
+    }
+    if (d.bc_y == BC_PERIODIC) {
+        if (py >= d.ny) py -= d.ny;
+        else if (py < 0.0) py += d.ny;
     }
 }
 
@@ -278,16 +298,29 @@ __device__ __forceinline__ void integrate(const DemArgs &d, int p, double Fcx, d
     vx = vx + ax * d.dt;
     vy = vy + ay * d.dt;
     w = w + al * d.dt;
-    px = px + vx * d.dt;
-    py = py + vy * d.dt;
-    if (d.bc_x == BC_PERIODIC) {
-        if (px >= d.nx) px -= d.nx;
-        else if (px < 0.0) px += d.nx;
-    }
-    if (d.bc_y == BC_PERIODIC) {
-        if (py >= d.ny) py -= d.ny;
-        else if (py < 0.0) py += d.ny;
-    }
+    drift(d, px, py, vx, vy);
+}
+
+// The velocity increments a dt of a sub-cycle without contacts: integrate()'s operations on
+// zero contact sums (0 + F), evaluated once per coupling cycle since F, T, m, I are fixed.
+struct Kick {
+    double dvx, dvy, dw;
+};
+
+__device__ __forceinline__ Kick free_kick(const DemArgs &d, int p) {
+    const double ax = (0.0 + d.F[2 * p]) / d.m[p] + d.gx_eff;
+    const double ay = (0.0 + d.F[2 * p + 1]) / d.m[p] + d.gy_eff;
+    const double al = (0.0 + d.T[p]) / d.I[p];
+    return {ax * d.dt, ay * d.dt, al * d.dt};
+}
+
+// integrate() when nothing touched in the sub-cycle, to the bit.
+__device__ __forceinline__ void coast(const DemArgs &d, const Kick &k, double &px, double &py, double &vx,
+                                      double &vy, double &w) {
+    vx = vx + k.dvx;
+    vy = vy + k.dvy;
+    w = w + k.dw;
+    drift(d, px, py, vx, vy);
 }
 
 // Motion of particle p over one coupling cycle when it touches nothing: the accelerations
@@ -469,10 +502,10 @@ __global__ void __launch_bounds__(32 * NB_WARPS) k_dem_neighbours(const DemArgs 
     }
 }
 
-__global__ void k_dem_free(const DemArgs d) {
-    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
+// Free particles, one per thread: blocks blk of nblk.
+__device__ __forceinline__ void dem_free(const DemArgs &d, const int blk, const int nblk) {
     const int nfree = d.counters[0];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nfree; c += gridDim.x * blockDim.x) {
+    for (int c = blk * blockDim.x + threadIdx.x; c < nfree; c += nblk * blockDim.x) {
         const int p = d.free_ids[c];
         double px = d.x[2 * p], py = d.x[2 * p + 1], vx = d.v[2 * p], vy = d.v[2 * p + 1], w = d.w[p];
         const double rp = d.r[p], mp = d.m[p];
@@ -482,7 +515,7 @@ __global__ void k_dem_free(const DemArgs d) {
         // candidate partners of a quiet island stay out of reach: their springs are released
         for (int j = 0, nn = d.nbr_cnt[p]; j < nn; ++j) d.nbr_xi[p * MAX_NBR + j] = 0.0;
         const FreeMotion f = free_motion(d, p, vx, vy);
-        const double dvx0 = f.ax * d.dt, dvy0 = f.ay * d.dt, dw0 = f.al * d.dt;   // as integrate() rounds them
+        const Kick kick = free_kick(d, p);
         if (free_of_edges(d, f, px, py, rp)) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
@@ -502,19 +535,7 @@ __global__ void k_dem_free(const DemArgs d) {
                     // a released wall spring (wall_contacts would zero it)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) xiw[k] = 0.0;
-                    vx = vx + dvx0;
-                    vy = vy + dvy0;
-                    w = w + dw0;
-                    px = px + vx * d.dt;
-                    py = py + vy * d.dt;
-                    if (d.bc_x == BC_PERIODIC) {
-                        if (px >= d.nx) px -= d.nx;
-                        else if (px < 0.0) px += d.nx;
-                    }
-                    if (d.bc_y == BC_PERIODIC) {
-                        if (py >= d.ny) py -= d.ny;
-                        else if (py < 0.0) py += d.ny;
-                    }
+                    coast(d, kick, px, py, vx, vy, w);
                 }
             }
         }
@@ -532,10 +553,11 @@ __global__ void k_dem_free(const DemArgs d) {
 // ascending id order, then the walls, then the leapfrog update.  nb(j, q, ...) yields
 // the state of the j-th candidate q at the start of the sub-cycle.
 template <typename NB>
-__device__ __forceinline__ void particle_substep(const DemArgs &d, const int p, double &px, double &py,
-                                                 double &vx, double &vy, double &w, NB &&nb) {
+__device__ __forceinline__ void particle_substep(const DemArgs &d, const int p, const Kick &kick, double &px,
+                                                 double &py, double &vx, double &vy, double &w, NB &&nb) {
     const double rp = d.r[p], mp = d.m[p];
     double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+    bool touched = false;
     const int n = d.nbr_cnt[p];
     for (int j = 0; j < n; ++j) {
         double qx, qy, qvx, qvy, qw;
@@ -545,9 +567,11 @@ __device__ __forceinline__ void particle_substep(const DemArgs &d, const int p, 
         Fcx += fx;
         Fcy += fy;
         Tc += rp * Ft;
+        touched = true;
     }
-    wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
-    integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+    touched |= wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
+    if (touched) integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+    else coast(d, kick, px, py, vx, vy, w);
 }
 
 // Particles of islands larger than a warp: all blocks step them together, one bounded
@@ -557,6 +581,8 @@ __global__ void k_dem_coupled(const DemArgs d) {
     const int nb_active = min((int)gridDim.x, (ncpl + (int)blockDim.x - 1) / (int)blockDim.x);
     if (ncpl == 0 || (int)blockIdx.x >= nb_active) return;
     const int stride = nb_active * blockDim.x;
+    const int c0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const Kick k0 = c0 < ncpl ? free_kick(d, d.big_ids[c0]) : Kick{0.0, 0.0, 0.0};   // usually its only particle
     for (int s = 0; s < d.N_sub; ++s) {
         const double *xc = (s & 1) ? d.x1 : d.x;
         const double *vc = (s & 1) ? d.v1 : d.v;
@@ -564,11 +590,11 @@ __global__ void k_dem_coupled(const DemArgs d) {
         double *xn = (s & 1) ? d.x : d.x1;
         double *vn = (s & 1) ? d.v : d.v1;
         double *wn = (s & 1) ? d.w : d.w1;
-        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncpl; c += stride) {
+        for (int c = c0; c < ncpl; c += stride) {
             const int p = d.big_ids[c];
             double px = __ldcg(&xc[2 * p]), py = __ldcg(&xc[2 * p + 1]);
             double vx = __ldcg(&vc[2 * p]), vy = __ldcg(&vc[2 * p + 1]), w = __ldcg(&wc[p]);
-            particle_substep(d, p, px, py, vx, vy, w,
+            particle_substep(d, p, c == c0 ? k0 : free_kick(d, p), px, py, vx, vy, w,
                              [&](int, int q, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
                                  qx = __ldcg(&xc[2 * q]);
                                  qy = __ldcg(&xc[2 * q + 1]);
@@ -695,16 +721,22 @@ __global__ void k_island_fill(const DemArgs d) {
 // all N_sub sub-cycles with the state in shared memory, the whole warp in lockstep.
 constexpr int SMALL_PER_WARP = 32 / ISL_SMALL;
 
-__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemArgs d) {
-    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
-    __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
-    __shared__ int s_id[ISL_WARPS][32];
-    __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
+struct SmallIslandSmem {
+    double st[ISL_WARPS][2][5][32];   // x, y, vx, vy, w
+    int id[ISL_WARPS][32];
+    unsigned char nl[ISL_WARPS][32][MAX_NBR];
+};
+
+// Small islands: block blk of the role (SMALL_PER_WARP islands per warp).
+__device__ __forceinline__ void dem_small_islands(const DemArgs &d, const int blk, SmallIslandSmem &sm) {
+    auto &s_st = sm.st;
+    auto &s_id = sm.id;
+    auto &s_nl = sm.nl;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / ISL_SMALL, k = lane % ISL_SMALL, g0 = grp * ISL_SMALL;
     const int nisl = d.counters[2];
-    const int i = (blockIdx.x * ISL_WARPS + warp) * SMALL_PER_WARP + grp;
-    if ((blockIdx.x * ISL_WARPS + warp) * SMALL_PER_WARP >= nisl) return;   // whole warp idle
+    const int i = (blk * ISL_WARPS + warp) * SMALL_PER_WARP + grp;
+    if ((blk * ISL_WARPS + warp) * SMALL_PER_WARP >= nisl) return;   // whole warp idle
     int p = -1, n = 0;
     if (i < nisl) {
         const int r = d.roots[i];
@@ -728,13 +760,14 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemA
         s_st[warp][0][3][lane] = d.v[2 * p + 1];
         s_st[warp][0][4][lane] = d.w[p];
     }
+    const Kick kick = act ? free_kick(d, p) : Kick{0.0, 0.0, 0.0};
     __syncwarp();
     for (int s = 0; s < d.N_sub; ++s) {
         const int cur = s & 1;
         const double(*st)[32] = s_st[warp][cur];
         if (act) {
             double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], w = st[4][lane];
-            particle_substep(d, p, px, py, vx, vy, w,
+            particle_substep(d, p, kick, px, py, vx, vy, w,
                              [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
                                  const int l = s_nl[warp][lane][j];
                                  qx = st[0][l];
@@ -767,16 +800,26 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_small_islands(const DemA
 // slot j on particle i), then lane i sums its pairs in slot order -- the order of a
 // sequential evaluation -- adds the walls and integrates.
 
-__global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d) {
-    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
-    __shared__ double s_st[ISL_WARPS][2][5][32];        // x, y, vx, vy, w
-    __shared__ double s_f[ISL_WARPS][3][ISL_PAIRS];     // fx, fy, Ft per pair
-    __shared__ int s_id[ISL_WARPS][32];
-    __shared__ unsigned char s_nl[ISL_WARPS][32][MAX_NBR];
-    __shared__ unsigned char s_pi[ISL_WARPS][ISL_PAIRS], s_pj[ISL_WARPS][ISL_PAIRS], s_on[ISL_WARPS][ISL_PAIRS];
+struct IslandSmem {
+    double st[ISL_WARPS][2][5][32];     // x, y, vx, vy, w
+    double f[ISL_WARPS][3][ISL_PAIRS];  // fx, fy, Ft per pair
+    int id[ISL_WARPS][32];
+    unsigned char nl[ISL_WARPS][32][MAX_NBR];
+    unsigned char pi[ISL_WARPS][ISL_PAIRS], pj[ISL_WARPS][ISL_PAIRS], on[ISL_WARPS][ISL_PAIRS];
+};
+
+// Islands of five to 32 particles, one per warp: block blk of nblk.
+__device__ __forceinline__ void dem_islands(const DemArgs &d, const int blk, const int nblk, IslandSmem &sm) {
+    auto &s_st = sm.st;
+    auto &s_f = sm.f;
+    auto &s_id = sm.id;
+    auto &s_nl = sm.nl;
+    auto &s_pi = sm.pi;
+    auto &s_pj = sm.pj;
+    auto &s_on = sm.on;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nisl = d.counters[5];
-    for (int i = blockIdx.x * ISL_WARPS + warp; i < nisl; i += gridDim.x * ISL_WARPS) {
+    for (int i = blk * ISL_WARPS + warp; i < nisl; i += nblk * ISL_WARPS) {
         const int r = d.roots[d.np - 1 - i];
         const int b = d.istart[r], n = d.isz[r];
         const bool act = lane < n;
@@ -811,6 +854,7 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d)
             s_st[warp][0][3][lane] = d.v[2 * p + 1];
             s_st[warp][0][4][lane] = d.w[p];
         }
+        const Kick kick = act ? free_kick(d, p) : Kick{0.0, 0.0, 0.0};
         __syncwarp();
         for (int s = 0; s < d.N_sub; ++s) {
             const int cur = s & 1;
@@ -833,16 +877,19 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d)
                 if (pairwise) {
                     const double rp = d.r[p], mp = d.m[p];
                     double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+                    bool touched = false;
                     for (int j = 0; j < nn; ++j) {
                         if (!s_on[warp][off + j]) continue;
                         Fcx += s_f[warp][0][off + j];
                         Fcy += s_f[warp][1][off + j];
                         Tc += rp * s_f[warp][2][off + j];
+                        touched = true;
                     }
-                    wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
-                    integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+                    touched |= wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
+                    if (touched) integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
+                    else coast(d, kick, px, py, vx, vy, w);
                 } else {
-                    particle_substep(d, p, px, py, vx, vy, w,
+                    particle_substep(d, p, kick, px, py, vx, vy, w,
                                      [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
                                          const int l = s_nl[warp][lane][j];
                                          qx = st[0][l];
@@ -870,6 +917,27 @@ __global__ void __launch_bounds__(32 * ISL_WARPS) k_dem_islands(const DemArgs d)
         }
         __syncwarp();
     }
+}
+
+// The particles of one coupling cycle that need no grid barrier -- free particles, islands
+// of up to four, islands of five to 32 -- in one launch: the roles take consecutive block
+// ranges in that order and run side by side (the three sets of particles are disjoint), so
+// an island's chain of N_sub sub-cycles, bound by the latency of its FP64 instructions,
+// overlaps the free particles' FP64 throughput and the other islands' chains.
+constexpr int LOCAL_THREADS = 32 * ISL_WARPS;
+
+union DemLocalSmem {
+    SmallIslandSmem small;
+    IslandSmem medium;
+};
+
+__global__ void __launch_bounds__(LOCAL_THREADS) k_dem_local(const DemArgs d, int nb_islands, int nb_small) {
+    cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
+    __shared__ DemLocalSmem sm;
+    const int b = blockIdx.x, nb_free = (int)gridDim.x - nb_islands - nb_small;
+    if (b < nb_free) dem_free(d, b, nb_free);
+    else if (b < nb_free + nb_small) dem_small_islands(d, b - nb_free, sm.small);
+    else dem_islands(d, b - nb_free - nb_small, nb_islands, sm.medium);
 }
 
 __global__ void k_contacts(const double *__restrict__ x, const double *__restrict__ r, int np, int nx,
@@ -939,10 +1007,6 @@ cudaError_t launch_dem_neighbours(const DemArgs &d, cudaStream_t s) {
     return launch_dependent(k_dem_neighbours, blocks_for(d.np, NB_WARPS), 32 * NB_WARPS, 0, s, true, d);
 }
 
-cudaError_t launch_dem_free(const DemArgs &d, cudaStream_t s) {
-    if (d.np == 0) return cudaSuccess;
-    return launch_dependent(k_dem_free, blocks_for(d.np, 64), 64, 0, s, true, d);
-}
 
 static int g_coupled_blocks = 0;
 
@@ -972,14 +1036,15 @@ cudaError_t launch_dem_islands_setup(const DemArgs &d, cudaStream_t s) {
     return e;
 }
 
-cudaError_t launch_dem_islands(const DemArgs &d, cudaStream_t s) {
+cudaError_t launch_dem_local(const DemArgs &d, cudaStream_t s) {
     if (d.np == 0) return cudaSuccess;
-    // enough warps for every island at once: at most np/2 islands of two or more particles,
-    // at most np/5 of five or more
-    cudaError_t e = launch_dependent(k_dem_small_islands, blocks_for(blocks_for(d.np / 2 + 1, SMALL_PER_WARP), ISL_WARPS),
-                                     32 * ISL_WARPS, 0, s, true, d);
-    if (e != cudaSuccess) return e;
-    return launch_dependent(k_dem_islands, blocks_for(d.np / 5 + 1, ISL_WARPS), 32 * ISL_WARPS, 0, s, true, d);
+    // enough warps for every island at once: at most np/5 islands of five or more, at most
+    // np/2 of two or more
+    const int nb_islands = blocks_for(d.np / 5 + 1, ISL_WARPS);
+    const int nb_small = blocks_for(blocks_for(d.np / 2 + 1, SMALL_PER_WARP), ISL_WARPS);
+    const int nb_free = blocks_for(d.np, LOCAL_THREADS);
+    return launch_dependent(k_dem_local, nb_islands + nb_small + nb_free, LOCAL_THREADS, 0, s, true, d, nb_islands,
+                            nb_small);
 }
 
 // Host round trips through pinned host memory that the device can address (NVLink-C2C or PCIe

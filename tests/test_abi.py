@@ -49,7 +49,7 @@ def test_default_params_match_header(lib):
     p = binding.default_params()
     assert (p.bc_x, p.bc_y, p.storage, p.eps_mode, p.n_sub) == (0, 1, 0, 0, 5)
     assert (p.N_sub, p.kn, p.kt, p.e_rest, p.mu, p.rho_s, p.skin) == (100, 1e5, 5e4, 0.5, 0.5, 2.65, 1.0)
-    assert p.rho0 == 1.0 and p.timeout_ms == 60000 and p.work_units == 0
+    assert p.rho0 == 1.0 and p.timeout_ms == 60000 and p.work_units == 0 and p.plain_launches == 0
 
 
 def test_params_struct_layout_matches_header(lib):

@@ -359,6 +359,8 @@ def test_invalid_arguments(imb):
     with pytest.raises(imb.ImbError):
         imb.Lattice(64, 64, 0.6, work_units=3)
     with pytest.raises(imb.ImbError):
+        imb.Lattice(64, 64, 0.6, plain_launches=2)
+    with pytest.raises(imb.ImbError):
         imb.Lattice(10, 10, 0.5)
     lat = imb.Lattice(64, 64, 0.6)
     with pytest.raises(imb.ImbError):
@@ -480,6 +482,68 @@ def test_step_io_equals_separate_calls(imb, pinned):
     assert np.array_equal(a.particles()[0], xs)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("units", UNITS)
+def test_cycle_graph_equals_launches(imb, units):
+    # a coupling cycle with the DEM replays a captured CUDA graph (timed, with its event nodes
+    # re-pointed every replay, or untimed) unless plain_launches asks for kernel launches: all
+    # three give the same state to the bit and count the same launches and timed cycles, and a
+    # new particle set between cycles (another count, another table shape) is taken up
+    w = W.c3sub(steps=0, nx=160, ny=96)
+    g = imb.Lattice.from_workload(w, work_units=units)
+    gt = imb.Lattice.from_workload(w, work_units=units)
+    p = imb.Lattice.from_workload(w, work_units=units, plain_launches=1)
+    lats = (g, gt, p)
+    gt.enable_kernel_timing(True)
+    p.enable_kernel_timing(True)
+    n0 = [lat.launch_count() for lat in lats]
+    for lat in lats:
+        lat.step(5)
+    assert len({lat.launch_count() - n for lat, n in zip(lats, n0)}) == 1
+    (mt, kt), (mp, kp) = gt.kernel_time(), p.kernel_time()
+    assert kt == kp == 5 and mt > 0 and mp > 0
+    x, v, om = g.particles()
+    keep = slice(0, max(1, w.n_particles // 2))
+    r = np.asarray(w.r)[keep] * 0.9
+    for lat in lats:
+        lat.set_particles(x[keep], v[keep], om[keep], r)
+        lat.step(4)
+    for o in (gt, p):
+        for a, b in zip(g.particles() + g.forces(), o.particles() + o.forces()):
+            assert np.array_equal(a, b)
+        assert np.array_equal(g.populations(), o.populations())
+        assert np.array_equal(g.contacts(), o.contacts())
+    assert gt.kernel_time()[1] == p.kernel_time()[1] == 4
+    for lat in lats:
+        lat.close()
+
+
+@pytest.mark.parametrize("units", UNITS)
+def test_lattice_step_graphs_equal_launches(imb, units):
+    # without the DEM, untimed runs of eight lattice steps replay a captured graph and the rest
+    # are launched: the channel with its fixed disk, 21 steps in calls of 3, 13 and 5 (a call
+    # shorter than eight, one with a replay and a remainder), equals plain launches, timed or
+    # not, to the bit
+    w = W.c1(steps=0)
+    g = imb.Lattice.from_workload(w, work_units=units)
+    gt = imb.Lattice.from_workload(w, work_units=units)
+    p = imb.Lattice.from_workload(w, work_units=units, plain_launches=1)
+    lats = (g, gt, p)
+    gt.enable_kernel_timing(True)
+    p.enable_kernel_timing(True)
+    n0 = [lat.launch_count() for lat in lats]
+    for k in (3, 13, 5):
+        for lat in lats:
+            lat.step(k)
+    assert len({lat.launch_count() - n for lat, n in zip(lats, n0)}) == 1
+    assert gt.kernel_time()[1] == p.kernel_time()[1] == 21
+    for o in (gt, p):
+        assert np.array_equal(g.populations(), o.populations())
+        for a, b in zip(g.forces(), o.forces()):
+            assert np.array_equal(a, b)
+    for lat in lats:
+        lat.close()
 
 
 def test_lid_driven_cavity_parity(orc, imb):
