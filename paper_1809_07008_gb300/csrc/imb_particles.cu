@@ -214,16 +214,15 @@ __device__ __forceinline__ void contact_law(const DemArgs &d, double nxv, double
                    xi, fx, fy, Ft);
 }
 
-// Force of candidate slot j on particle p (seen from p), the pair's damping constant
-// cached in the neighbour list.  Returns false (and releases the spring) without overlap.
-__device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const int j, const double px,
-                                           const double py, const double w, const double qx, const double qy,
-                                           const double qvx, const double qvy, const double qw,
-                                           const double vx, const double vy, double &fx, double &fy,
-                                           double &Ft) {
+// Force on particle p of its candidate q in slot j (seen from p), with the pair's tangential
+// spring xi; the pair's damping constant is cached in the neighbour list.  Returns false (and
+// releases the spring) without overlap.
+__device__ __forceinline__ bool pair_force_xi(const DemArgs &d, const int p, const int j, const int q, double &xi,
+                                              const double px, const double py, const double w, const double qx,
+                                              const double qy, const double qvx, const double qvy, const double qw,
+                                              const double vx, const double vy, double &fx, double &fy,
+                                              double &Ft) {
     const bool perx = d.bc_x == BC_PERIODIC, pery = d.bc_y == BC_PERIODIC;
-    const int q = d.nbr_id[p * MAX_NBR + j];
-    double &xi = d.nbr_xi[p * MAX_NBR + j];
     const double rp = d.r[p];
     const double dx = min_image(qx - px, perx, d.nx);
     const double dy = min_image(qy - py, pery, d.ny);
@@ -244,6 +243,16 @@ __device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const 
     contact_law_cn(d, nxv, nyv, R - dist, qvx - vx, qvy - vy, rot, d.nbr_cn[p * MAX_NBR + j], Rstar, mstar, xi,
                    fx, fy, Ft);
     return true;
+}
+
+// The same for candidate slot j, its spring in the neighbour list.
+__device__ __forceinline__ bool pair_force(const DemArgs &d, const int p, const int j, const double px,
+                                           const double py, const double w, const double qx, const double qy,
+                                           const double qvx, const double qvy, const double qw,
+                                           const double vx, const double vy, double &fx, double &fy,
+                                           double &Ft) {
+    return pair_force_xi(d, p, j, d.nbr_id[p * MAX_NBR + j], d.nbr_xi[p * MAX_NBR + j], px, py, w, qx, qy, qvx,
+                         qvy, qw, vx, vy, fx, fy, Ft);
 }
 
 // Walls on the domain edges of non-periodic axes, an immovable partner (m* = m).  Returns
@@ -683,7 +692,7 @@ __global__ void k_uf_label(const DemArgs d) {
 
 constexpr int ISL_SMALL = 4;           // islands up to this size share a warp, 8 to a warp
 constexpr int ISL_WARPS = 4;
-constexpr int ISL_PAIRS = 96;          // pair-parallel up to this many candidate pairs
+constexpr int ISL_PAIRS = 96;          // pairs evaluated a lane each, beyond that particle by particle
 
 // Roots reserve a contiguous range of the member list for their island.
 __global__ void k_island_alloc(const DemArgs d) {
@@ -717,23 +726,173 @@ __global__ void k_island_fill(const DemArgs d) {
     }
 }
 
-// Islands of at most ISL_SMALL particles, eight per warp in lane groups of ISL_SMALL:
-// all N_sub sub-cycles with the state in shared memory, the whole warp in lockstep.
+// The islands a warp steps together: lane l holds particle id[l] (or -1), its candidates are
+// members of its own island, and all N_sub sub-cycles run with the state in shared memory
+// (double-buffered).  A sub-cycle is one round of pair forces, each candidate pair once with a
+// lane of its own, then one round of particle updates, lane l summing its pairs in slot order
+// -- the order of a sequential evaluation -- and adding the walls.  A pair's force on its
+// second particle is the negated force on its first, to the bit: every operation of Eqs. 7-9
+// is odd or even under the exchange of the two particles (n -> -n, t -> -t, the relative
+// velocity -> its negative, sums and products of the two radii and masses unchanged) and IEEE
+// rounding to nearest is symmetric, so the two tangential springs stay equal as well.  Every
+// FP64 instruction costs a warp the same whatever its active lanes, so a sub-cycle's cost is
+// the instructions of its two rounds.
 constexpr int SMALL_PER_WARP = 32 / ISL_SMALL;
 
-struct SmallIslandSmem {
-    double st[ISL_WARPS][2][5][32];   // x, y, vx, vy, w
-    int id[ISL_WARPS][32];
-    unsigned char nl[ISL_WARPS][32][MAX_NBR];
+struct WarpIslands {
+    double st[2][5][32];                 // x, y, vx, vy, w
+    double f[3][ISL_PAIRS];              // fx, fy, Ft on the pair's first particle
+    double xi[ISL_PAIRS];                // the pair's tangential spring
+    int id[32];
+    unsigned char nn[32];                // candidates of lane l
+    unsigned char nl[32][MAX_NBR];       // lane of candidate j
+    unsigned char slot[32][MAX_NBR];     // pair of candidate j, bit 7 set on the pair's second particle
+    unsigned char pi[ISL_PAIRS], pj[ISL_PAIRS], pr[ISL_PAIRS], on[ISL_PAIRS];
 };
 
-// Small islands: block blk of the role (SMALL_PER_WARP islands per warp).
-__device__ __forceinline__ void dem_small_islands(const DemArgs &d, const int blk, SmallIslandSmem &sm) {
-    auto &s_st = sm.st;
-    auto &s_id = sm.id;
-    auto &s_nl = sm.nl;
+// p: this lane's particle or -1; [g0, g0 + gn): the lanes of its island.
+__device__ __forceinline__ void warp_islands(const DemArgs &d, WarpIslands &w, const int p, const int g0,
+                                             const int gn) {
+    const int lane = threadIdx.x & 31;
+    const bool act = p >= 0;
+    const int nn = act ? d.nbr_cnt[p] : 0;
+    w.id[lane] = p;
+    w.nn[lane] = (unsigned char)nn;
+    __syncwarp();
+    int own = 0;   // pairs this lane leads: its candidates on higher lanes
+    if (act) {
+        for (int j = 0; j < nn; ++j) {
+            const int q = d.nbr_id[p * MAX_NBR + j];
+            int l = g0;
+            while (l < g0 + gn - 1 && w.id[l] != q) ++l;   // q is in the same island
+            w.nl[lane][j] = (unsigned char)l;
+            w.slot[lane][j] = 255;   // set below by the pair's leading lane
+            own += l > lane;
+        }
+        w.st[0][0][lane] = d.x[2 * p];
+        w.st[0][1][lane] = d.x[2 * p + 1];
+        w.st[0][2][lane] = d.v[2 * p];
+        w.st[0][3][lane] = d.v[2 * p + 1];
+        w.st[0][4][lane] = d.w[p];
+    }
+    int off = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += t;
+    }
+    const int npairs = __shfl_sync(0xffffffffu, off, 31);
+    off -= own;
+    __syncwarp();
+    if (act && npairs <= ISL_PAIRS) {
+        int k = off;
+        for (int j = 0; j < nn; ++j) {
+            const int l = w.nl[lane][j];
+            if (l <= lane) continue;
+            int jr = 0;
+            while (jr < w.nn[l] && w.nl[l][jr] != lane) ++jr;
+            w.pi[k] = (unsigned char)lane;
+            w.pj[k] = (unsigned char)j;
+            w.pr[k] = (unsigned char)(jr < w.nn[l] ? jr : 0);
+            w.slot[lane][j] = (unsigned char)k;
+            if (jr < w.nn[l]) w.slot[l][jr] = (unsigned char)(k | 128);
+            w.xi[k] = d.nbr_xi[p * MAX_NBR + j];   // equal to the partner's spring of the pair
+            ++k;
+        }
+    }
+    __syncwarp();
+    // pairs evaluated a lane each only when every candidate slot of the warp names a pair (the
+    // candidate lists are symmetric and stay within the island), else particle by particle
+    bool ok = npairs <= ISL_PAIRS;
+    for (int j = 0; ok && j < nn; ++j) ok = (w.slot[lane][j] & 127) < npairs && w.nl[lane][j] != lane;
+    const bool pairwise = __all_sync(0xffffffffu, ok);
+    const Kick kick = act ? free_kick(d, p) : Kick{0.0, 0.0, 0.0};
+    const double rp = act ? d.r[p] : 0.0, mp = act ? d.m[p] : 0.0;
+    double xiw[4];   // wall springs, in registers on the pair-parallel path
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xiw[q] = act ? d.wall_xi[4 * p + q] : 0.0;
+    __syncwarp();
+    for (int s = 0; s < d.N_sub; ++s) {
+        const int cur = s & 1;
+        const double(*st)[32] = w.st[cur];
+        if (pairwise) {
+            for (int k = lane; k < npairs; k += 32) {
+                const int i = w.pi[k], j = w.pj[k], l = w.nl[i][j];
+                double xi = w.xi[k];
+                double fx = 0.0, fy = 0.0, Ft = 0.0;
+                w.on[k] = pair_force_xi(d, w.id[i], j, w.id[l], xi, st[0][i], st[1][i], st[4][i], st[0][l],
+                                        st[1][l], st[2][l], st[3][l], st[4][l], st[2][i], st[3][i], fx, fy, Ft);
+                w.xi[k] = xi;
+                w.f[0][k] = fx;
+                w.f[1][k] = fy;
+                w.f[2][k] = Ft;
+            }
+            __syncwarp();
+        }
+        if (act) {
+            double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], om = st[4][lane];
+            if (pairwise) {
+                double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
+                bool touched = false;
+                for (int j = 0; j < nn; ++j) {
+                    const int e = w.slot[lane][j], k = e & 127;
+                    if (!w.on[k]) continue;
+                    if (e & 128) {
+                        Fcx += -w.f[0][k];
+                        Fcy += -w.f[1][k];
+                    } else {
+                        Fcx += w.f[0][k];
+                        Fcy += w.f[1][k];
+                    }
+                    Tc += rp * w.f[2][k];
+                    touched = true;
+                }
+                touched |= wall_contacts(d, p, px, py, vx, vy, om, rp, mp, xiw, Fcx, Fcy, Tc);
+                if (touched) integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, om);
+                else coast(d, kick, px, py, vx, vy, om);
+            } else {
+                particle_substep(d, p, kick, px, py, vx, vy, om,
+                                 [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
+                                     const int l = w.nl[lane][j];
+                                     qx = st[0][l];
+                                     qy = st[1][l];
+                                     qvx = st[2][l];
+                                     qvy = st[3][l];
+                                     qw = st[4][l];
+                                 });
+            }
+            w.st[cur ^ 1][0][lane] = px;
+            w.st[cur ^ 1][1][lane] = py;
+            w.st[cur ^ 1][2][lane] = vx;
+            w.st[cur ^ 1][3][lane] = vy;
+            w.st[cur ^ 1][4][lane] = om;
+        }
+        __syncwarp();
+    }
+    if (act) {
+        const int fin = d.N_sub & 1;
+        d.x[2 * p] = w.st[fin][0][lane];
+        d.x[2 * p + 1] = w.st[fin][1][lane];
+        d.v[2 * p] = w.st[fin][2][lane];
+        d.v[2 * p + 1] = w.st[fin][3][lane];
+        d.w[p] = w.st[fin][4][lane];
+        if (pairwise) {   // the springs back into both particles' lists
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d.wall_xi[4 * p + q] = xiw[q];
+            for (int j = 0; j < nn; ++j) {
+                const int e = w.slot[lane][j];
+                d.nbr_xi[p * MAX_NBR + j] = w.xi[e & 127];
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Islands of up to ISL_SMALL particles, SMALL_PER_WARP to a warp in lane groups of
+// ISL_SMALL: block blk of the role.
+__device__ __forceinline__ void dem_small_islands(const DemArgs &d, const int blk, WarpIslands (&sm)[ISL_WARPS]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / ISL_SMALL, k = lane % ISL_SMALL, g0 = grp * ISL_SMALL;
+    const int grp = lane / ISL_SMALL, k = lane % ISL_SMALL;
     const int nisl = d.counters[2];
     const int i = (blk * ISL_WARPS + warp) * SMALL_PER_WARP + grp;
     if ((blk * ISL_WARPS + warp) * SMALL_PER_WARP >= nisl) return;   // whole warp idle
@@ -743,179 +902,18 @@ __device__ __forceinline__ void dem_small_islands(const DemArgs &d, const int bl
         n = d.isz[r];
         if (k < n) p = d.members[d.istart[r] + k];
     }
-    const bool act = p >= 0;
-    s_id[warp][lane] = p;
-    __syncwarp();
-    if (act) {
-        const int nn = d.nbr_cnt[p];
-        for (int j = 0; j < nn; ++j) {
-            const int q = d.nbr_id[p * MAX_NBR + j];
-            int l = g0;
-            while (l < g0 + n - 1 && s_id[warp][l] != q) ++l;   // q is in the same island
-            s_nl[warp][lane][j] = (unsigned char)l;
-        }
-        s_st[warp][0][0][lane] = d.x[2 * p];
-        s_st[warp][0][1][lane] = d.x[2 * p + 1];
-        s_st[warp][0][2][lane] = d.v[2 * p];
-        s_st[warp][0][3][lane] = d.v[2 * p + 1];
-        s_st[warp][0][4][lane] = d.w[p];
-    }
-    const Kick kick = act ? free_kick(d, p) : Kick{0.0, 0.0, 0.0};
-    __syncwarp();
-    for (int s = 0; s < d.N_sub; ++s) {
-        const int cur = s & 1;
-        const double(*st)[32] = s_st[warp][cur];
-        if (act) {
-            double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], w = st[4][lane];
-            particle_substep(d, p, kick, px, py, vx, vy, w,
-                             [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
-                                 const int l = s_nl[warp][lane][j];
-                                 qx = st[0][l];
-                                 qy = st[1][l];
-                                 qvx = st[2][l];
-                                 qvy = st[3][l];
-                                 qw = st[4][l];
-                             });
-            s_st[warp][cur ^ 1][0][lane] = px;
-            s_st[warp][cur ^ 1][1][lane] = py;
-            s_st[warp][cur ^ 1][2][lane] = vx;
-            s_st[warp][cur ^ 1][3][lane] = vy;
-            s_st[warp][cur ^ 1][4][lane] = w;
-        }
-        __syncwarp();
-    }
-    if (act) {
-        const int fin = d.N_sub & 1;
-        d.x[2 * p] = s_st[warp][fin][0][lane];
-        d.x[2 * p + 1] = s_st[warp][fin][1][lane];
-        d.v[2 * p] = s_st[warp][fin][2][lane];
-        d.v[2 * p + 1] = s_st[warp][fin][3][lane];
-        d.w[p] = s_st[warp][fin][4][lane];
-    }
+    warp_islands(d, sm[warp], p, grp * ISL_SMALL, n);
 }
 
-// One warp per island of at most 32 particles: all N_sub sub-cycles with the island
-// state in shared memory (double-buffered), lanes synchronised by __syncwarp.  Each
-// sub-cycle first evaluates the island's candidate pairs one per lane (the force of
-// slot j on particle i), then lane i sums its pairs in slot order -- the order of a
-// sequential evaluation -- adds the walls and integrates.
-
-struct IslandSmem {
-    double st[ISL_WARPS][2][5][32];     // x, y, vx, vy, w
-    double f[ISL_WARPS][3][ISL_PAIRS];  // fx, fy, Ft per pair
-    int id[ISL_WARPS][32];
-    unsigned char nl[ISL_WARPS][32][MAX_NBR];
-    unsigned char pi[ISL_WARPS][ISL_PAIRS], pj[ISL_WARPS][ISL_PAIRS], on[ISL_WARPS][ISL_PAIRS];
-};
-
 // Islands of five to 32 particles, one per warp: block blk of nblk.
-__device__ __forceinline__ void dem_islands(const DemArgs &d, const int blk, const int nblk, IslandSmem &sm) {
-    auto &s_st = sm.st;
-    auto &s_f = sm.f;
-    auto &s_id = sm.id;
-    auto &s_nl = sm.nl;
-    auto &s_pi = sm.pi;
-    auto &s_pj = sm.pj;
-    auto &s_on = sm.on;
+__device__ __forceinline__ void dem_islands(const DemArgs &d, const int blk, const int nblk,
+                                            WarpIslands (&sm)[ISL_WARPS]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nisl = d.counters[5];
     for (int i = blk * ISL_WARPS + warp; i < nisl; i += nblk * ISL_WARPS) {
         const int r = d.roots[d.np - 1 - i];
-        const int b = d.istart[r], n = d.isz[r];
-        const bool act = lane < n;
-        const int p = act ? d.members[b + lane] : -1;
-        const int nn = act ? d.nbr_cnt[p] : 0;
-        s_id[warp][lane] = p;
-        // pairs of lane i occupy [off, off + nn)
-        int off = nn;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, off, o);
-            if (lane >= o) off += t;
-        }
-        const int npairs = __shfl_sync(0xffffffffu, off, 31);
-        off -= nn;
-        const bool pairwise = npairs <= ISL_PAIRS;
-        __syncwarp();
-        if (act) {
-            for (int j = 0; j < nn; ++j) {
-                const int q = d.nbr_id[p * MAX_NBR + j];
-                int l = 0;
-                while (l < n - 1 && s_id[warp][l] != q) ++l;   // q is in the same island
-                s_nl[warp][lane][j] = (unsigned char)l;
-                if (pairwise) {
-                    s_pi[warp][off + j] = (unsigned char)lane;
-                    s_pj[warp][off + j] = (unsigned char)j;
-                }
-            }
-            s_st[warp][0][0][lane] = d.x[2 * p];
-            s_st[warp][0][1][lane] = d.x[2 * p + 1];
-            s_st[warp][0][2][lane] = d.v[2 * p];
-            s_st[warp][0][3][lane] = d.v[2 * p + 1];
-            s_st[warp][0][4][lane] = d.w[p];
-        }
-        const Kick kick = act ? free_kick(d, p) : Kick{0.0, 0.0, 0.0};
-        __syncwarp();
-        for (int s = 0; s < d.N_sub; ++s) {
-            const int cur = s & 1;
-            const double(*st)[32] = s_st[warp][cur];
-            if (pairwise) {
-                for (int k = lane; k < npairs; k += 32) {
-                    const int li = s_pi[warp][k], j = s_pj[warp][k];
-                    const int l = s_nl[warp][li][j];
-                    double fx = 0.0, fy = 0.0, Ft = 0.0;
-                    s_on[warp][k] = pair_force(d, s_id[warp][li], j, st[0][li], st[1][li], st[4][li], st[0][l],
-                                               st[1][l], st[2][l], st[3][l], st[4][l], st[2][li], st[3][li], fx, fy, Ft);
-                    s_f[warp][0][k] = fx;
-                    s_f[warp][1][k] = fy;
-                    s_f[warp][2][k] = Ft;
-                }
-                __syncwarp();
-            }
-            if (act) {
-                double px = st[0][lane], py = st[1][lane], vx = st[2][lane], vy = st[3][lane], w = st[4][lane];
-                if (pairwise) {
-                    const double rp = d.r[p], mp = d.m[p];
-                    double Fcx = 0.0, Fcy = 0.0, Tc = 0.0;
-                    bool touched = false;
-                    for (int j = 0; j < nn; ++j) {
-                        if (!s_on[warp][off + j]) continue;
-                        Fcx += s_f[warp][0][off + j];
-                        Fcy += s_f[warp][1][off + j];
-                        Tc += rp * s_f[warp][2][off + j];
-                        touched = true;
-                    }
-                    touched |= wall_contacts(d, p, px, py, vx, vy, w, rp, mp, &d.wall_xi[4 * p], Fcx, Fcy, Tc);
-                    if (touched) integrate(d, p, Fcx, Fcy, Tc, px, py, vx, vy, w);
-                    else coast(d, kick, px, py, vx, vy, w);
-                } else {
-                    particle_substep(d, p, kick, px, py, vx, vy, w,
-                                     [&](int j, int, double &qx, double &qy, double &qvx, double &qvy, double &qw) {
-                                         const int l = s_nl[warp][lane][j];
-                                         qx = st[0][l];
-                                         qy = st[1][l];
-                                         qvx = st[2][l];
-                                         qvy = st[3][l];
-                                         qw = st[4][l];
-                                     });
-                }
-                s_st[warp][cur ^ 1][0][lane] = px;
-                s_st[warp][cur ^ 1][1][lane] = py;
-                s_st[warp][cur ^ 1][2][lane] = vx;
-                s_st[warp][cur ^ 1][3][lane] = vy;
-                s_st[warp][cur ^ 1][4][lane] = w;
-            }
-            __syncwarp();
-        }
-        if (act) {
-            const int fin = d.N_sub & 1;
-            d.x[2 * p] = s_st[warp][fin][0][lane];
-            d.x[2 * p + 1] = s_st[warp][fin][1][lane];
-            d.v[2 * p] = s_st[warp][fin][2][lane];
-            d.v[2 * p + 1] = s_st[warp][fin][3][lane];
-            d.w[p] = s_st[warp][fin][4][lane];
-        }
-        __syncwarp();
+        const int n = d.isz[r];
+        warp_islands(d, sm[warp], lane < n ? d.members[d.istart[r] + lane] : -1, 0, n);
     }
 }
 
@@ -926,18 +924,13 @@ __device__ __forceinline__ void dem_islands(const DemArgs &d, const int blk, con
 // overlaps the free particles' FP64 throughput and the other islands' chains.
 constexpr int LOCAL_THREADS = 32 * ISL_WARPS;
 
-union DemLocalSmem {
-    SmallIslandSmem small;
-    IslandSmem medium;
-};
-
 __global__ void __launch_bounds__(LOCAL_THREADS) k_dem_local(const DemArgs d, int nb_islands, int nb_small) {
     cudaGridDependencySynchronize();   // launched as a dependent of the kernel before it
-    __shared__ DemLocalSmem sm;
+    __shared__ WarpIslands sm[ISL_WARPS];
     const int b = blockIdx.x, nb_free = (int)gridDim.x - nb_islands - nb_small;
     if (b < nb_free) dem_free(d, b, nb_free);
-    else if (b < nb_free + nb_small) dem_small_islands(d, b - nb_free, sm.small);
-    else dem_islands(d, b - nb_free - nb_small, nb_islands, sm.medium);
+    else if (b < nb_free + nb_small) dem_small_islands(d, b - nb_free, sm);
+    else dem_islands(d, b - nb_free - nb_small, nb_islands, sm);
 }
 
 __global__ void k_contacts(const double *__restrict__ x, const double *__restrict__ r, int np, int nx,
