@@ -94,13 +94,14 @@ typedef struct imb_params {
                             persistent grid; 1 always the persistent tiles, 2 always the
                             eight-row units.  Same results either way, to rounding of the
                             force sums (each unit keeps its own partials)                      */
-    int plain_launches;  /* 0 (default): a coupling cycle with the DEM is captured as a CUDA graph
-                            on its first run (one per buffer pair, re-captured after
-                            imb_set_particles) and replayed with one graph launch; 1: its kernels
-                            are launched one by one.  Results identical to the bit; launch
-                            counts and kernel timing the same either way.  A capture that fails
-                            (e.g. on a stream the caller is itself capturing) falls back to
-                            launches for the rest of the context's life                        */
+    int plain_launches;  /* 0 (default): imb_step / imb_step_async / imb_step_io capture a
+                            coupling cycle with the DEM -- and, with kernel timing off, a run
+                            of eight lattice steps without it -- as a CUDA graph the first time
+                            it runs from a given pair of buffers (again after
+                            imb_set_particles) and replay it with one graph launch; 1: every
+                            kernel is launched by itself.  Results identical to the bit; launch
+                            counts and kernel timing the same either way.  If a capture
+                            fails, the context launches its kernels one by one from then on    */
 } imb_params;
 
 typedef struct imb_ctx imb_ctx;
@@ -304,9 +305,9 @@ long long imb_launch_count(imb_ctx *ctx);
 double imb_bytes_per_cell(imb_ctx *ctx);
 
 /* Particle-to-bin map into caller-owned device buffers, allocating nothing.  The
- * paper has no counterpart: this serves callers that cannot call cudaMalloc (code
- * running under CUDA graph capture, hosts whose device memory belongs to their own
- * pool, real-time loops that must not touch the allocator).
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc (hosts
+ * whose device memory belongs to their own pool, real-time loops that must not touch
+ * the allocator).
  * d_x: DEVICE pointer to 2n doubles (x, y of each centre, inside [0,nx) x [0,ny));
  * d_bin_start: DEVICE pointer to nbins + 1 ints, nbins = ceil(nx/32) * ceil(ny/32);
  * d_bin_ids: DEVICE pointer to n ints, the particle ids grouped by bin (bin = by * nbx

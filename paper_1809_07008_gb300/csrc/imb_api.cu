@@ -696,8 +696,8 @@ static int lattice_step(imb_ctx *c) {
 // the current buffers, then replayed with one launch, so that the kernels reach the GPU without a
 // host launch each.  With kernel timing on, the events that bracket each stream-collide and its
 // tail are event-record nodes, pointed at the context's next events before every replay.  A
-// capture that fails (a stream the caller is capturing, a call the capture refuses) turns graphs
-// off and the steps run as launches.
+// stream that is already capturing is left alone, and a capture that fails turns graphs off:
+// the steps then run as launches.
 static int graph_steps(imb_ctx *c, bool dem, bool &done) {
     done = false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

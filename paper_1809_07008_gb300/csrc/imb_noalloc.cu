@@ -1,8 +1,7 @@
 // imb_noalloc.cu -- particle-to-bin map that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured, hosts that hand every byte of device memory to their own pool, or
-// real-time loops that must not touch the allocator.  imb_bin_particles_noalloc
+// Some callers cannot call cudaMalloc: hosts that hand every byte of device memory
+// to their own pool, or real-time loops that must not touch the allocator.  imb_bin_particles_noalloc
 // gives them the binning step of the particle map with inputs and outputs in their
 // own device buffers; its scratch (per-bin counts and fill cursors) lives in the
 // fixed array below, which every GPU that loads the library holds until exit.

@@ -1,8 +1,8 @@
 """The allocation-free binning entry point (imb_bin_particles_noalloc) against the
 context's own binning (imb_get_bins), through the C ABI, on consecutive calls.
 
-It exists for callers that cannot call cudaMalloc (graph capture, hosts that own all
-device memory, real-time loops): the test allocates the caller's buffers with PyTorch,
+It exists for callers that cannot call cudaMalloc (hosts that own all device memory,
+real-time loops): the test allocates the caller's buffers with PyTorch,
 the entry point itself allocates nothing and keeps its scratch in a fixed device array
 shared by all calls.  Bins are integer bookkeeping, so the outputs must be identical.
 """
