@@ -99,6 +99,7 @@ class Params(C.Structure):
 
 _lib = None
 _dp = C.POINTER(C.c_double)
+_F64 = np.dtype(np.float64)
 _fp = C.POINTER(C.c_float)
 _ip = C.POINTER(C.c_int)
 _vp = C.c_void_p
@@ -126,7 +127,8 @@ def load(build_if_missing: bool = True):
     for name in ("imb_step", "imb_step_async", "imb_dem_step"):
         getattr(L, name).argtypes = [_vp, C.c_int]
     L.imb_sync.argtypes = [_vp]
-    L.imb_step_io.argtypes = [_vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    # plain addresses: the per-cycle call takes them from Lattice._io_addr
+    L.imb_step_io.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.imb_get_populations.argtypes = [_vp, _dp]
     L.imb_get_macro.argtypes = [_vp, _dp, _dp, _dp]
     L.imb_get_forces.argtypes = [_vp, _dp, _dp]
@@ -222,6 +224,7 @@ class Lattice:
             raise ImbError(rc, L.imb_last_error(None).decode())
         self.h = h
         self.np = 0
+        self._addr_table = {}
         self._L = L
 
     @classmethod
@@ -255,6 +258,7 @@ class Lattice:
         if getattr(self, "h", None):
             self._L.imb_destroy(self.h)
             self.h = None
+        self._addr_table = {}
 
     def __del__(self):
         try:
@@ -278,21 +282,49 @@ class Lattice:
     def step(self, n=1):
         self._check(self._L.imb_step(self.h, int(n)))
 
+    def _io_addr(self, a):
+        """Address of the data of array ``a``, looked up once per array object: the host waits
+        on this call every coupling cycle, and numpy's own lookup costs about a microsecond an
+        array.  Holding ``a`` in the table keeps its id and its buffer (which numpy cannot
+        reallocate while another reference exists) tied to the stored address."""
+        e = self._addr_table.get(id(a))
+        if e is not None and e[0] is a:
+            return e[1]
+        if len(self._addr_table) >= 32:
+            self._addr_table.clear()
+        p = a.ctypes.data
+        self._addr_table[id(a)] = (a, p)
+        return p
+
     def step_io(self, n=1, kin_in=None, F=None, T=None, x=None, v=None, w=None):
         """imb_step_io: optional upload of (x, v, omega), n cycles, read-back into the given
         host arrays (any may be None), one wait."""
         n_p = self.np
         xi = vi = wi = None
+        keep = None
         if kin_in is not None:
-            # converted copies (if any) stay referenced until the call returns
-            kin = (_f64(kin_in[0], 2 * n_p), _f64(kin_in[1], 2 * n_p), _f64(kin_in[2], n_p))
-            xi, vi, wi = (_d(a) for a in kin)
+            kin = []
+            for a, k in zip(kin_in, (2, 2, 1)):
+                if type(a) is np.ndarray and a.dtype == _F64 and a.size == k * n_p and a.flags.c_contiguous:
+                    kin.append(self._io_addr(a))
+                else:   # a converted copy, referenced until the call returns
+                    a = _f64(a, k * n_p)
+                    keep = (keep or ()) + (a,)
+                    kin.append(a.ctypes.data)
+            if len(kin) != 3:
+                raise ValueError("kin_in must hold x, v and omega")
+            xi, vi, wi = kin
         outs = []
         for a, k in ((F, 2), (T, 1), (x, 2), (v, 2), (w, 1)):
-            if a is not None and (a.size != k * n_p or a.dtype != np.float64 or not a.flags.c_contiguous):
+            if a is None:
+                outs.append(None)
+                continue
+            if type(a) is not np.ndarray or a.size != k * n_p or a.dtype != _F64 or not a.flags.c_contiguous:
                 raise ValueError(f"outputs must be contiguous float64 arrays of {k} x {n_p} values")
-            outs.append(None if a is None else _d(a))
-        self._check(self._L.imb_step_io(self.h, int(n), xi, vi, wi, *outs))
+            outs.append(self._io_addr(a))
+        rc = self._L.imb_step_io(self.h, int(n), xi, vi, wi, *outs)
+        del keep
+        self._check(rc)
 
     def step_async(self, n=1):
         self._check(self._L.imb_step_async(self.h, int(n)))

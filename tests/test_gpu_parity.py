@@ -467,7 +467,24 @@ def test_step_io_equals_separate_calls(imb, pinned):
     assert np.array_equal(xo, xb) and np.array_equal(vo, vb) and np.array_equal(wo, wb)
     assert np.array_equal(F, Fb) and np.array_equal(T, Tb)
     assert np.array_equal(a.populations(), b.populations())
+    # again with the same arrays (the binding looks each array object's address up once), then
+    # with fresh arrays, one input Fortran-ordered (converted to a contiguous copy for the call)
+    for fresh in (False, True):
+        kin = (xo.copy(), vo.copy(), wo.copy())
+        if fresh:
+            F, T, xo, vo, wo = (buf(np.zeros_like(o)) for o in (F, T, xo, vo, wo))
+            ins = (buf(kin[0]), np.asfortranarray(kin[1]), buf(kin[2]))
+        else:
+            ins = (xo, vo, wo)
+        a.step_io(1, ins, F, T, xo, vo, wo)
+        b.set_kinematics(*kin)
+        b.step(1)
+        Fb, Tb = b.forces()
+        xb, vb, wb = b.particles()
+        assert np.array_equal(xo, xb) and np.array_equal(vo, vb) and np.array_equal(wo, wb)
+        assert np.array_equal(F, Fb) and np.array_equal(T, Tb)
     a.step_io(1)                       # no arrays: just the cycles and the wait
+    b.step(1)
     with pytest.raises(ValueError):
         a.step_io(1, None, np.zeros(3))
     # centres outside the lattice, or NaN, are refused before anything is uploaded
