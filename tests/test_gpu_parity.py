@@ -246,6 +246,59 @@ def test_dem_gas_quiet_and_touching_islands_bit_exact(orc, imb, bc_x):
     assert touched >= 10
 
 
+def _edge_velocities(rng, n):
+    """Velocity components on the hard cases of the free particles' repeated velocity sums:
+    zero, values a few ulps from powers of two (the sums cross into the next binade within a
+    cycle), tiny values that change sign, and magnitudes from 1e-9 to 0.1."""
+    out = np.empty(n)
+    for k in range(n):
+        kind = k % 5
+        if kind == 0:
+            out[k] = 0.0
+        elif kind in (1, 2):
+            p = 2.0 ** -int(rng.integers(4, 30))
+            ulps = int(rng.integers(1, 6)) * (1 if kind == 1 else -1)
+            out[k] = np.nextafter(p, np.inf if ulps > 0 else 0.0)
+            for _ in range(abs(ulps) - 1):
+                out[k] = np.nextafter(out[k], np.inf if ulps > 0 else 0.0)
+            out[k] *= rng.choice([-1.0, 1.0])
+        elif kind == 3:
+            out[k] = rng.uniform(-1e-9, 1e-9)
+        else:
+            out[k] = rng.choice([-1.0, 1.0]) * 10.0 ** rng.uniform(-9, -1)
+    return rng.permutation(out)
+
+
+def test_free_particles_bit_exact_across_binades(orc, imb):
+    # disks far apart in a periodic box (no contacts, no walls): every sub-cycle is a free
+    # update (the register-only path, or the sub-cycle loop near the periodic edges);
+    # velocities and accelerations chosen so that the sums cross powers of two, pass through
+    # zero and fall below the ulp, compared with the oracle's sequential FP64 updates bit for bit
+    n = 120
+    rng = np.random.default_rng(21)
+    x, r = W.random_sequential_addition(480, 360, n, lambda g: 4.0 + g.uniform_range(-0.5, 0.5), 21, gap=12.0,
+                                        periodic_x=True, wall_gap=2.0)
+    v = np.stack([_edge_velocities(rng, n), _edge_velocities(rng, n)], axis=1)
+    om = _edge_velocities(rng, n)
+    w = W.Workload(name="free_gas", nx=480, ny=360, tau=0.6, bc_x=W.BC_PERIODIC, bc_y=W.BC_PERIODIC, dem_on=1,
+                   N_sub=100, gravity=(0.0, 0.0), x=x, v=v, omega=om, r=r)
+    m = w.rho_s * np.pi * r ** 2
+    F = (rng.choice([-1.0, 1.0], (n, 2)) * 10.0 ** rng.uniform(-9, -3, (n, 2))) * m[:, None] * 10.0
+    F[::7] = 0.0
+    T = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-9, -3, n) * m * r ** 2 * 5.0
+    o = orc.Sim(w)
+    g = imb.Lattice.from_workload(w)
+    o.set_forces(F, T)
+    g.set_forces(F, T)
+    for cycle in range(12):
+        o.dem_substeps(w.N_sub)
+        g.dem_step(1)
+        assert len(o.contacts()) == 0
+        for a, b in zip(o.particles(), g.particles()):
+            assert np.array_equal(a, b), cycle
+    g.close()
+
+
 @pytest.mark.parametrize("units", UNITS)
 def test_moving_particles_coupled_parity(orc, imb, units):
     # c3 at the same density on 256 x 192: DEM + IMB + Smagorinsky, tau = 0.51, 1000 coupling
