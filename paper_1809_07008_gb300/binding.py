@@ -303,23 +303,23 @@ class Lattice:
         xi = vi = wi = None
         keep = None
         if kin_in is not None:
+            if len(kin_in) != 3:
+                raise ValueError("kin_in must hold x, v and omega")
             kin = []
             for a, k in zip(kin_in, (2, 2, 1)):
-                if type(a) is np.ndarray and a.dtype == _F64 and a.size == k * n_p and a.flags.c_contiguous:
+                if isinstance(a, np.ndarray) and a.dtype == _F64 and a.size == k * n_p and a.flags.c_contiguous:
                     kin.append(self._io_addr(a))
                 else:   # a converted copy, referenced until the call returns
                     a = _f64(a, k * n_p)
                     keep = (keep or ()) + (a,)
                     kin.append(a.ctypes.data)
-            if len(kin) != 3:
-                raise ValueError("kin_in must hold x, v and omega")
             xi, vi, wi = kin
         outs = []
         for a, k in ((F, 2), (T, 1), (x, 2), (v, 2), (w, 1)):
             if a is None:
                 outs.append(None)
                 continue
-            if type(a) is not np.ndarray or a.size != k * n_p or a.dtype != _F64 or not a.flags.c_contiguous:
+            if not isinstance(a, np.ndarray) or a.size != k * n_p or a.dtype != _F64 or not a.flags.c_contiguous:
                 raise ValueError(f"outputs must be contiguous float64 arrays of {k} x {n_p} values")
             outs.append(self._io_addr(a))
         rc = self._L.imb_step_io(self.h, int(n), xi, vi, wi, *outs)

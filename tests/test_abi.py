@@ -120,3 +120,72 @@ def test_host_validation_refuses_before_any_device_call(lib):
     # solid-ratio launch would need 20 000 x 4095^2 / 128 > 2^31 - 1 blocks
     n = 20000
     assert batch(4096, 4096, 0.6, np.full((n, 2), 2048.0), np.full(n, 2046.0)) == BAD
+
+
+def test_step_io_marshalling_passes_each_arrays_own_address():
+    # the per-cycle call's marshalling, with the library call replaced by a recorder: every
+    # pointer argument is the data address of the array given for it (looked up once per array
+    # object, so an array freed and another allocated in its place, possibly under the same id,
+    # gets its own address), non-contiguous or non-float64 inputs go as converted copies that
+    # hold the same values, and malformed outputs are refused before the call
+    import numpy as np
+    from paper_1809_07008_gb300 import binding
+
+    calls = []
+
+    class Recorder:
+        def imb_step_io(self, h, n, *ptrs):
+            # the arrays behind the addresses, read while the call is in progress
+            calls.append((n, ptrs))
+            return 0
+
+    class Host:
+        np = 5
+        h = None
+        _L = Recorder()
+        _io_addr = binding.Lattice._io_addr
+
+        def __init__(self):
+            self._addr_table = {}
+
+        def _check(self, rc):
+            assert rc == 0
+
+    lat = Host()
+    n = Host.np
+
+    def arrays():
+        return (np.arange(2 * n, dtype=np.float64).reshape(n, 2), np.ones((n, 2)), np.zeros(n),
+                np.zeros((n, 2)), np.zeros(n))
+
+    for rnd in range(3):
+        x, v, w, F, T = arrays()
+        binding.Lattice.step_io(lat, 2, (x, v, w), F, T, x, v, w)
+        got = calls[-1][1]
+        want = [a.ctypes.data for a in (x, v, w, F, T, x, v, w)]
+        assert calls[-1][0] == 2 and list(got) == want, rnd
+        del x, v, w, F, T   # the next round's arrays may reuse these ids and addresses
+
+    x, v, w, F, T = arrays()
+    vf = np.asfortranarray(np.stack([np.arange(n, dtype=np.float64), -np.arange(n, dtype=np.float64)], axis=1))
+    seen = {}
+
+    class Reader(Recorder):
+        def imb_step_io(self, h, n_, *ptrs):
+            # the converted velocity copy, read back from its address during the call
+            buf = (ctypes.c_double * (2 * n)).from_address(ptrs[1])
+            seen["v"] = np.frombuffer(buf, dtype=np.float64).copy()
+            return 0
+
+    lat._L = Reader()
+    binding.Lattice.step_io(lat, 1, (x, vf, w.astype(np.float32)), F, T)
+    assert np.array_equal(seen["v"], np.ascontiguousarray(vf).reshape(-1))
+    lat._L = Recorder()
+    binding.Lattice.step_io(lat, 1)
+    assert calls[-1][1] == (None,) * 8
+    for bad in (np.zeros((n, 2), dtype=np.float32), np.zeros((n, 3)), np.zeros((2, n)).T, [0.0] * (2 * n)):
+        with pytest.raises(ValueError):
+            binding.Lattice.step_io(lat, 1, None, bad)
+    for kin in ((x, v), (x, v, w, w)):
+        with pytest.raises(ValueError):
+            binding.Lattice.step_io(lat, 1, kin)
