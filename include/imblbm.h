@@ -286,22 +286,31 @@ int imb_get_contacts(imb_ctx *ctx, int max_pairs, int *pairs, int *n_pairs);
  * within each bin), nbins = ceil(nx/32) * ceil(ny/32), bin = by * nbx + bx. */
 int imb_get_bins(imb_ctx *ctx, int *bin_start, int *bin_ids);
 
-/* Use an external cudaStream_t (e.g. PyTorch's current stream); NULL restores the
- * context's own stream.  The caller keeps ownership of the stream. */
+/* Queue the context's work on an external cudaStream_t of the context's device (e.g.
+ * PyTorch's current stream) from the next call on; NULL restores the context's own stream.
+ * The caller keeps ownership of the stream and must keep it alive while the context uses it;
+ * work already queued stays where it was queued.  IMB_E_INVALID_ARG for a NULL ctx. */
 int imb_set_stream(imb_ctx *ctx, void *stream);
+/* The stream the context queues its work on (NULL for a NULL ctx). */
 void *imb_get_stream(imb_ctx *ctx);
 
-/* Timing of the fused stream-collide kernel: when enabled, every launch is
- * bracketed by CUDA events on the context stream; imb_kernel_time returns the
- * summed milliseconds and launch count since the last reset (waits first). */
+/* Timing of the fused stream-collide: with on != 0, every lattice step from now on records a
+ * CUDA event on the context stream before its stream-collide launch and one after the launch
+ * of the force gather and ghost cells that completes it (event-record nodes inside the
+ * captured cycles).  Either value of on discards the timings not yet read.  IMB_E_INVALID_ARG
+ * for a NULL ctx. */
 int imb_enable_kernel_timing(imb_ctx *ctx, int on);
+/* Waits (bounded) for the context stream, then returns in *ms the summed milliseconds of the
+ * timed steps since the last read or enable call and in *launches their number, and restarts
+ * the count.  IMB_E_INVALID_ARG for NULL arguments, IMB_E_TIMEOUT or IMB_E_CUDA as imb_sync. */
 int imb_kernel_time(imb_ctx *ctx, double *ms, long long *launches);
 
-/* Number of kernels this context has launched (all kinds). */
+/* Number of kernels this context has launched (all kinds; the kernels of a captured cycle
+ * count once per replay).  0 for a NULL ctx. */
 long long imb_launch_count(imb_ctx *ctx);
 
 /* Algorithmic bytes of one stream-collide cell update for this lattice's storage
- * (9 loads + 9 stores of one population). */
+ * (9 loads + 9 stores of one population: 72 in FP32, 36 in FP16/BF16); 0 for a NULL ctx. */
 double imb_bytes_per_cell(imb_ctx *ctx);
 
 /* Particle-to-bin map into caller-owned device buffers, allocating nothing.  The
