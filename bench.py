@@ -490,8 +490,12 @@ def run_reference(args):
         return
     w = make_workload(args.workload, args.nx, args.ny, args.particles, args.csmag)
     mlups, cpu = time_oracle(target_s=max(5.0, min(60.0, 0.05 * (args.steps + args.warmup))))
+    # time of one coupling cycle of the whole workload at the sample's throughput
+    ms_step = w.cells / (mlups * 1e6) * 1e3 if mlups > 0 else None
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 1) if ms_step else None,
+            "ms_per_step_basis": "cells of the workload / the sample's MLUPS",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "sample": oracle_sample_workload().name},
